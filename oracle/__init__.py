@@ -1,0 +1,231 @@
+"""Plain FP64 CPU oracle for randomized block Gram-Schmidt (RBGS).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA library never links or calls it, and the two share no code:
+the C source here is compiled on its own with gcc.
+
+What each function follows (Balabanov & Grigori, arXiv 2111.14641):
+
+* ``theta_*`` / ``srht_samples`` / ``philox``: the sketching matrices of
+  Sec. 2.3 (Rademacher, SRHT with zero padding) plus the Gaussian N(0, 1/k)
+  sketch, drawn from a Philox4x32-10 counter generator whose bit-level
+  layout is a project convention (the paper asks only for a seeded
+  generator).  Each side implements that convention separately.
+* ``rbgs``: Alg. 2 with steps 4-5 from Alg. 4, 5 or 6 and step-2 solvers
+  from Sec. 3.1 and its supplement (Householder, Richardson, CG).
+* ``rcholqr``: the closed form that RBGS reaches in exact arithmetic
+  (R = R factor of Theta W with a positive diagonal, Q = W R^{-1}).
+* ``householder_qr``: textbook Householder QR with a positive diagonal.
+
+Every array is float64, column-major (Fortran order).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "rbgs_oracle.c"
+_BUILD = _HERE / "_build"
+_LIB = _BUILD / "liborbgs.so"
+
+THETA = {"gauss": 0, "rademacher": 1, "srht": 2, "identity": 3}
+LS = {"householder": 0, "richardson": 1, "cg": 2}
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (plain C99, -ffp-contract=off so the x86 and
+    Arm builds round identically)."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
+        cmd = ["gcc", "-O2", "-std=gnu99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-pthread", "-o", str(tmp), str(_SRC), "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(str(_LIB))
+        i64, u64, dp = ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
+        lib.or_philox4x32_10.argtypes = [dp, dp, dp]
+        lib.or_theta_dense.argtypes = [ctypes.c_int, i64, i64, u64, dp]
+        lib.or_theta_dense.restype = ctypes.c_int
+        lib.or_theta_apply.argtypes = [ctypes.c_int, i64, i64, u64, dp, i64, i64, dp, i64]
+        lib.or_theta_apply.restype = ctypes.c_int
+        lib.or_srht_samples.argtypes = [u64, i64, i64, dp]
+        lib.or_srht_samples.restype = ctypes.c_int
+        lib.or_srht_sign.argtypes = [u64, i64]
+        lib.or_srht_sign.restype = ctypes.c_double
+        lib.or_srht_padded.argtypes = [i64]
+        lib.or_srht_padded.restype = i64
+        lib.or_fwht.argtypes = [dp, i64]
+        lib.or_householder_qr.argtypes = [i64, i64, dp, i64, dp]
+        lib.or_qr_r.argtypes = [i64, i64, dp, i64, dp, i64]
+        lib.or_qr_r.restype = ctypes.c_int
+        lib.or_qr_full.argtypes = [i64, i64, dp, i64, dp, i64, dp, i64]
+        lib.or_qr_full.restype = ctypes.c_int
+        lib.or_rbgs.argtypes = [dp, i64, i64, i64, i64, ctypes.c_int, i64, u64, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int, dp, i64, dp, i64, dp, dp, dp]
+        lib.or_rbgs.restype = ctypes.c_int
+        lib.or_rcholqr.argtypes = [dp, i64, i64, i64, ctypes.c_int, i64, u64, dp, i64, dp, i64]
+        lib.or_rcholqr.restype = ctypes.c_int
+        lib.or_ls_solve.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, dp, i64, dp, i64, i64, dp, i64]
+        lib.or_ls_solve.restype = ctypes.c_int
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        lib.or_get_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    """Worker threads for the tall loops (rows of step 3, columns of Theta X)."""
+    _load().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().or_get_threads())
+
+
+def philox(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block: four uint32 counter words, two key words."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def srht_padded(n: int) -> int:
+    return int(_load().or_srht_padded(int(n)))
+
+
+def srht_samples(seed: int, n: int, k: int) -> np.ndarray:
+    """Sorted sampled rows s_0 < ... < s_{k-1} of the n' x n' Hadamard matrix."""
+    out = np.zeros(k, dtype=np.int64)
+    if _load().or_srht_samples(int(seed), srht_padded(n), int(k), _ptr(out)):
+        raise ValueError("k exceeds the padded dimension")
+    return out
+
+
+def srht_signs(seed: int, n: int) -> np.ndarray:
+    lib = _load()
+    return np.array([lib.or_srht_sign(int(seed), j) for j in range(int(n))])
+
+
+def theta_dense(kind: str, k: int, n: int, seed: int) -> np.ndarray:
+    """Theta (k x n) from the entry definitions, for small cases."""
+    T = np.zeros((k, n), dtype=np.float64, order="F")
+    if _load().or_theta_dense(THETA[kind], int(k), int(n), int(seed), _ptr(T)):
+        raise ValueError("bad sketch arguments")
+    return T
+
+
+def theta_apply(kind: str, k: int, seed: int, X) -> np.ndarray:
+    """Theta X for X (n x c); SRHT goes through the Hadamard transform."""
+    X = _f64(X)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1, order="F")
+    n, c = X.shape
+    Y = np.zeros((k, c), dtype=np.float64, order="F")
+    if _load().or_theta_apply(THETA[kind], int(k), int(n), int(seed), _ptr(X), max(n, 1), int(c), _ptr(Y), max(k, 1)):
+        raise ValueError("bad sketch arguments")
+    return Y
+
+
+def fwht(x) -> np.ndarray:
+    """Sylvester-ordered Walsh-Hadamard transform (unnormalised) of a vector of length 2^q."""
+    y = np.ascontiguousarray(np.asarray(x, dtype=np.float64).copy())
+    _load().or_fwht(_ptr(y), y.size)
+    return y
+
+
+def householder_qr(A):
+    """Thin Householder QR with a positive diagonal: returns (Q, R)."""
+    A = _f64(A)
+    m, n = A.shape
+    Q = np.zeros((m, n), order="F")
+    R = np.zeros((n, n), order="F")
+    rc = _load().or_qr_full(m, n, _ptr(A), m, _ptr(Q), m, _ptr(R), n)
+    return Q, R, rc
+
+
+def rbgs(W, mp: int, kind: str, k: int, seed: int, variant: int = 5, ls: str = "householder",
+         ls_iters: int = 5, reorth: bool = False):
+    """Alg. 2.  Returns dict(Q, R, S, P, delta, delta_tilde, passes2, rc)."""
+    W = _f64(W)
+    n, m = W.shape
+    Q = np.zeros((n, m), order="F")
+    R = np.zeros((m, m), order="F")
+    S = np.zeros((k, m), order="F")
+    P = np.zeros((k, m), order="F")
+    st = np.zeros(3)
+    rc = _load().or_rbgs(_ptr(W), n, m, n, int(mp), THETA[kind], int(k), int(seed), int(variant), LS[ls],
+                         int(ls_iters), int(bool(reorth)), _ptr(Q), n, _ptr(R), m, _ptr(S), _ptr(P), _ptr(st))
+    if rc == -1:
+        raise ValueError("bad RBGS arguments")
+    return dict(Q=Q, R=R, S=S, P=P, delta=st[0], delta_tilde=st[1], passes2=int(st[2]), rc=rc)
+
+
+def ls_solve(S, P, method: str = "householder", iters: int = 5) -> np.ndarray:
+    """Step-2 solution X = argmin ||S X - P||_F by the chosen method."""
+    S = _f64(S)
+    P = _f64(P)
+    k, c = S.shape
+    mp = P.shape[1]
+    X = np.zeros((c, mp), order="F")
+    rc = _load().or_ls_solve(LS[method], int(iters), k, c, _ptr(S), k, _ptr(P), k, mp, _ptr(X), c)
+    if rc:
+        raise np.linalg.LinAlgError("singular least-squares matrix")
+    return X
+
+
+def rcholqr(W, kind: str, k: int, seed: int):
+    """Closed form: R = R(Theta W), Q = W R^{-1}.  Returns (Q, R, rc)."""
+    W = _f64(W)
+    n, m = W.shape
+    Q = np.zeros((n, m), order="F")
+    R = np.zeros((m, m), order="F")
+    rc = _load().or_rcholqr(_ptr(W), n, m, n, THETA[kind], int(k), int(seed), _ptr(Q), n, _ptr(R), m)
+    if rc == -1:
+        raise ValueError("bad arguments")
+    return Q, R, rc
+
+
+# ---- quality measures, computed in FP64 with the oracle's own Theta ----------
+
+def sketched_orthogonality(Q, kind: str, k: int, seed: int):
+    """(||I - (Theta Q)^T (Theta Q)||_F, same in the 2-norm)."""
+    S = theta_apply(kind, k, seed, Q)
+    E = np.eye(S.shape[1]) - S.T @ S
+    return float(np.linalg.norm(E, "fro")), float(np.linalg.norm(E, 2))
+
+
+def factorization_error(W, Q, R) -> float:
+    """||W - Q R||_F / ||W||_F."""
+    W = np.asarray(W, dtype=np.float64)
+    return float(np.linalg.norm(W - np.asarray(Q, np.float64) @ np.asarray(R, np.float64)) / np.linalg.norm(W))
+
+
+def cond(Q) -> float:
+    s = np.linalg.svd(np.asarray(Q, dtype=np.float64), compute_uv=False)
+    return float(s[0] / s[-1])

@@ -1,0 +1,71 @@
+"""Seeded synthetic inputs shared by the tests, the oracle runs and bench.py.
+
+This module holds none of the method's arithmetic: it only draws matrices with
+prescribed structure.  Recipes:
+
+* ``svd_matrix``: W = U diag(sigma) V^T with U (n x m) and V (m x m) the
+  orthonormal factors of seeded N(0,1) matrices and sigma log-spaced from 1
+  down to 1/cond (the test matrices of the QR workloads).
+* ``ex1_matrix``: the parametric test matrix of the paper's first experiment,
+  W_ij = sin(10(mu_j + x_i)) / (cos(100(mu_j - x_i)) + 1.1) on equispaced grids
+  x_i = i/(n-1), mu_j = j/(m-1) (0-based), numerically rank-deficient.
+* ``gaussian``: seeded N(0,1) blocks.
+
+CPU draws use numpy's PCG64; device draws (large sizes) use torch's generator
+on the given device, so the two do not produce the same numbers: a test that
+needs both sides on the same input copies one array to the other side.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def sigmas(m: int, cond: float) -> np.ndarray:
+    """m singular values log-spaced from 1 down to 1/cond."""
+    if m == 1:
+        return np.ones(1)
+    return np.logspace(0.0, -np.log10(cond), m)
+
+
+def svd_matrix(n: int, m: int, cond: float, seed: int, dtype=np.float64) -> np.ndarray:
+    """W = U diag(sigma) V^T (n x m, Fortran order) built on the CPU in FP64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    G = rng.standard_normal((n, m))
+    U, _ = np.linalg.qr(G)
+    H = rng.standard_normal((m, m))
+    V, _ = np.linalg.qr(H)
+    W = (U * sigmas(m, cond)) @ V.T
+    return np.asfortranarray(W.astype(dtype))
+
+
+def svd_matrix_torch(n: int, m: int, cond: float, seed: int, device="cuda", dtype=None):
+    """Same recipe drawn with torch on ``device`` (for sizes too large for the
+    host).  Returns a column-major (n x m) tensor: shape (n, m), strides (1, n)."""
+    import torch
+
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    G = torch.randn((m, n), generator=g, device=device, dtype=torch.float64).t()  # column-major n x m
+    U, _ = torch.linalg.qr(G)
+    del G
+    H = torch.randn((m, m), generator=g, device=device, dtype=torch.float64)
+    V, _ = torch.linalg.qr(H)
+    s = torch.as_tensor(sigmas(m, cond), device=device, dtype=torch.float64)
+    Wt = (V * s) @ U.t()  # (m x n) row-major == W column-major
+    del U
+    out = Wt.to(dtype).contiguous()
+    del Wt
+    return out.t()
+
+
+def ex1_matrix(n: int, m: int, dtype=np.float64) -> np.ndarray:
+    x = np.linspace(0.0, 1.0, n)[:, None]
+    mu = np.linspace(0.0, 1.0, m)[None, :]
+    W = np.sin(10.0 * (mu + x)) / (np.cos(100.0 * (mu - x)) + 1.1)
+    return np.asfortranarray(W.astype(dtype))
+
+
+def gaussian(n: int, m: int, seed: int, dtype=np.float64) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.asfortranarray(rng.standard_normal((n, m)).astype(dtype))
