@@ -1,0 +1,144 @@
+/*
+ * rbgs.h -- C ABI of librbgs: randomized block Gram-Schmidt (RBGS) on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Balabanov & Grigori, "Randomized block Gram-Schmidt process for the
+ * solution of linear systems and eigenvalue problems", arXiv 2111.14641.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are column-major with an explicit leading dimension (ld >= rows).
+ *  - Pointers named W, Q, X, Y, R, ... are DEVICE pointers on the current CUDA
+ *    device unless the comment says "host".  The caller owns them; the library
+ *    never frees or keeps them beyond the call.
+ *  - Element type: double when prec == RBGS_P_FP64, otherwise float (W, Q, X).
+ *    R and the sketches Y returned to the caller are always double.
+ *  - Work is enqueued on opts->stream (a cudaStream_t; NULL = legacy default).
+ *    With opts->sync != 0 (the default) the call waits for its work and reports
+ *    device-side failures (breakdown) in its return code.
+ *  - Errors are reported only through the return code; nothing aborts, traps
+ *    or prints.  Internal workspace is allocated by the library (cudaMalloc),
+ *    cached per device and released by rbgs_release_workspace().
+ *  - Entry points are not re-entrant for concurrent calls on different host
+ *    threads (they share the cached workspace).
+ */
+#ifndef RBGS_H
+#define RBGS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RBGS_API __attribute__((visibility("default")))
+#else
+#define RBGS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RBGS_OK = 0,
+  RBGS_EINVAL = 1,         /* an argument is out of range (sizes, ld, null pointer)          */
+  RBGS_ENOMEM = 2,         /* device workspace allocation failed                            */
+  RBGS_ECUDA = 3,          /* a CUDA runtime call or a kernel launch failed                  */
+  RBGS_EBREAKDOWN = 4,     /* R_ii got a non-positive or non-finite pivot (rank breakdown)   */
+  RBGS_ENOTCERTIFIED = 5,  /* Delta or Delta~ > 0.1, Thm. 4.1 cannot certify (on request)    */
+  RBGS_ETIMEOUT = 6,       /* a bounded device-side wait expired                            */
+  RBGS_ENOCONV = 7,        /* an iterative solver stopped before its tolerance               */
+  RBGS_ENODEV = 8          /* no usable sm_103 device                                        */
+} rbgs_status;
+
+/* Sketching matrices Theta (k x n).  Sec. 2.3 uses Rademacher and SRHT; the
+ * Gaussian N(0, 1/k) matrix is the classical oblivious embedding.  Theta is
+ * never stored: its entries are regenerated from a Philox4x32-10 counter
+ * generator keyed by `seed` (layout in the library's DESIGN notes; the CPU
+ * oracle implements the same definition independently).                   */
+typedef enum { RBGS_SK_GAUSS = 0, RBGS_SK_RADEMACHER = 1, RBGS_SK_SRHT = 2 } rbgs_sketch;
+
+/* Arithmetic of the tall (n-row) operations: the projection of step 3 fused
+ * with R_ii^{-1}, and the sketches.
+ *  FP64    double storage, double arithmetic everywhere.
+ *  FP32    float storage of W and Q; SIMT FP32 tall product; sketch-space
+ *          products in FP32, small m_p x m_p factorizations in FP64.
+ *  TF32X3  as FP32, but the tall product runs on the tcgen05 tensor cores
+ *          with split operands (a = a_hi + a_lo in TF32, three products),
+ *          accurate to about 2^-22 relative per product.                  */
+typedef enum { RBGS_P_FP64 = 0, RBGS_P_FP32 = 1, RBGS_P_TF32X3 = 2 } rbgs_prec;
+
+typedef struct {
+  int32_t prec;        /* rbgs_prec                                                      */
+  int32_t ls_iters;    /* step 2: Richardson iterations X <- X + S^T (P - S X) (>= 1)   */
+  int32_t reorth;      /* 0: Alg. 2 as written (one projection per block);
+                          1: second projection pass on every block i > 1;
+                          2: second pass only where ||S_{1:i-1}^T S_i||_F > reorth_tol */
+  int32_t certify;     /* 1: compute Delta and Delta~ (step 6) into stats             */
+  double reorth_tol;   /* threshold for reorth == 2                                      */
+  void* stream;        /* cudaStream_t                                                   */
+  int32_t sync;        /* 1: wait and report device-side status; 0: enqueue only        */
+  int32_t reserved[3];
+} rbgs_opts;
+
+typedef struct {
+  double delta;        /* ||I - S^T S||_F, S = Theta Q (step 6 of Alg. 2)              */
+  double delta_tilde;  /* ||P - S R||_F / ||P||_F, P = Theta W                          */
+  int32_t passes2;     /* blocks that took the second projection pass                   */
+  int32_t certified;   /* delta <= 0.1 && delta_tilde <= 0.1 (Thm. 4.1 hypothesis)      */
+} rbgs_stats;
+
+/* Fill *opts with the defaults: FP64, 2 Richardson iterations, reorth 0,
+ * certify 0, reorth_tol 1e-8, default stream, sync 1.                     */
+RBGS_API void rbgs_opts_default(rbgs_opts* opts);
+
+/* RBGS QR factorization, Alg. 2 with steps 4-5 by Alg. 5 (RCholeskyQR with the
+ * sketch of Q'_i obtained as P_i - S_{1:i-1} R_{1:i-1,i}, one reduction per
+ * block) and step 2 by Richardson iterations (supplement to Sec. 3.1).
+ *
+ *  W    device, n x m, ld ldw >= n, float or double per opts->prec (read only)
+ *  n    rows, 1 <= n < 2^31
+ *  m    columns, m = mb * p
+ *  mb   block size m_p, 1 <= mb <= 64, mb divides m
+ *  sketch, k, seed   Theta (k x n); m <= k; k <= n (Gaussian, Rademacher) or
+ *       k <= n' = 2^ceil(log2 n) (SRHT)
+ *  Q    device, n x m, ld ldq >= n, same type as W; receives the
+ *       sketch-orthonormal factor ((Theta Q)^T (Theta Q) = I up to rounding)
+ *  R    device, m x m double, ld ldr >= m; receives the upper-triangular
+ *       factor with positive diagonal (strictly lower part set to zero)
+ *  opts may be NULL (defaults); stats may be NULL (host pointer).
+ * W and Q must not overlap.  Returns RBGS_OK, RBGS_EINVAL, RBGS_ENOMEM,
+ * RBGS_ECUDA or RBGS_EBREAKDOWN (the last only with opts->sync).          */
+RBGS_API rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch, int64_t k,
+                    uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts* opts,
+                    rbgs_stats* stats);
+
+/* Y = Theta X (Sec. 2.3), the sketch of steps 1 and 5 of Alg. 2.
+ *  X device n x ncols (ldx), double if prec == RBGS_P_FP64 else float.
+ *  Y device k x ncols (ldy), double.  FP64 sums in double; other precisions
+ *  sum in float.  stream: cudaStream_t.  Synchronous only if sync != 0.    */
+RBGS_API rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,
+                              int64_t ldx, int64_t ncols, double* Y, int64_t ldy, void* stream, int32_t sync);
+
+/* Tall update of step 3 fused with the triangular solve of Alg. 5:
+ *   Qout = [Qprev | X] * G,   Qprev n x c (ldq), X n x mb (ldx),
+ *   G (c + mb) x mb double (ldg), Qout n x mb (ldo), mb <= 64.
+ * With G = [-R_{1:i-1,i}; I] R_ii^{-1} this is Q_i = (W_i - Q_{1:i-1}R_{1:i-1,i}) R_ii^{-1}.
+ * Qout may alias X exactly (same pointer and ld); it must not overlap Qprev.
+ * Types per prec as for rbgs_qr (G is rounded/split inside).             */
+RBGS_API rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_t mb, const void* Qprev, int64_t ldq,
+                             const void* X, int64_t ldx, const double* G, int64_t ldg, void* Qout, int64_t ldo,
+                             void* stream, int32_t sync);
+
+/* Philox4x32-10 blocks on the device: out[4i..4i+3] = philox(ctr[4i..4i+3],
+ * key = (seed_lo, seed_hi)) for i < count (device pointers).              */
+RBGS_API rbgs_status rbgs_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t count, void* stream, int32_t sync);
+
+/* Release the cached device workspace of the current device.             */
+RBGS_API rbgs_status rbgs_release_workspace(void);
+
+/* Library version string (static storage).                               */
+RBGS_API const char* rbgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBGS_H */

@@ -1,0 +1,11 @@
+"""librbgs: randomized block Gram-Schmidt (Balabanov & Grigori, arXiv 2111.14641)
+on one NVIDIA GB300 (sm_103a).
+
+The computation lives in the C-ABI library ``librbgs.so`` (hand-written CUDA
+kernels, include/rbgs.h); this package is its Python binding.
+"""
+from .rbgs import (PREC, SKETCH, QRStats, RbgsError, colmajor, load, philox, rbgs_qr, release_workspace,
+                   sketch_apply, tall_update, version)
+
+__all__ = ["PREC", "SKETCH", "QRStats", "RbgsError", "colmajor", "load", "philox", "rbgs_qr", "release_workspace",
+           "sketch_apply", "tall_update", "version"]

@@ -1,0 +1,81 @@
+// Common device helpers for librbgs (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rbgs.h"
+
+namespace rbgs {
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 32x32->64-bit products on counter words 0 and 2, the high halves xor-ed
+// with words 1 and 3 and the key; key bumped by the Weyl increments between
+// rounds.
+__host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+#ifdef __CUDA_ARCH__
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#else
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
+  return make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+}
+
+// Stream purposes carried in counter word 2.
+enum : uint32_t { kPurposeGauss = 0, kPurposeRademacher = 1, kPurposeSrhtSign = 2, kPurposeSrhtSample = 3 };
+
+// Gaussian pair for column j, row pair rp of Theta (Box-Muller on 53-bit
+// uniforms in (0,1)); z0 serves row 2 rp, z1 row 2 rp + 1.
+__device__ __forceinline__ void gauss_pair(uint2 key, int64_t j, uint32_t rp, double& z0, double& z1) {
+  const uint4 x = philox10(make_uint4((uint32_t)j, rp, kPurposeGauss, (uint32_t)(j >> 32)), key);
+  const double u1 = ((double)(x.x >> 5) * 67108864.0 + (double)(x.y >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+  const double u2 = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+  const double rad = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+// 128 Rademacher sign bits for column j, rows [128 g, 128 g + 128).
+__device__ __forceinline__ uint4 rademacher_bits(uint2 key, int64_t j, uint32_t g) {
+  return philox10(make_uint4((uint32_t)j, g, kPurposeRademacher, (uint32_t)(j >> 32)), key);
+}
+
+// 128 SRHT diagonal sign bits for padded rows [128 g, 128 g + 128).
+__device__ __forceinline__ uint4 srht_sign_bits(uint2 key, uint32_t g) {
+  return philox10(make_uint4(g, 0u, kPurposeSrhtSign, 0u), key);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int w) {
+  return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+
+}  // namespace rbgs
+
+#define RBGS_CUDA_TRY(expr)                  \
+  do {                                       \
+    cudaError_t _e = (expr);                 \
+    if (_e != cudaSuccess) return RBGS_ECUDA; \
+  } while (0)
+
+#define RBGS_LAUNCH_CHECK()                          \
+  do {                                               \
+    if (cudaGetLastError() != cudaSuccess) return RBGS_ECUDA; \
+  } while (0)

@@ -1,0 +1,114 @@
+// Internal interfaces between the librbgs translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/rbgs.h"
+
+namespace rbgs {
+
+// ---------------------------------------------------------------- sketches --
+// SRHT plan: sampled Hadamard rows split as i = i_hi * B + i_lo with the tile
+// length B = min(n', kSrhtTile); L = sorted distinct i_lo values.
+constexpr int kSrhtTile = 16384;
+
+struct SrhtPlan {
+  uint64_t seed = 0;
+  int64_t n = 0, np = 0, k = 0;
+  int B = 0, T = 0, L = 0;   // tile length, number of tiles, distinct low indices
+  int* d_lvals = nullptr;    // [L]  distinct low indices (sorted)
+  int* d_rhi = nullptr;      // [k]  i_hi of sample r
+  int* d_rl = nullptr;       // [k]  position of i_lo(sample r) in lvals
+  std::vector<int64_t> samples;
+};
+
+// Host: k distinct sorted rows of the n' x n' Hadamard matrix (Floyd's
+// algorithm on the Philox stream of purpose 3).
+int srht_samples_host(uint64_t seed, int64_t np, int64_t k, int64_t* out);
+
+// Cached per (device, seed, n, k).
+rbgs_status srht_plan_get(uint64_t seed, int64_t n, int64_t k, const SrhtPlan** plan);
+void srht_plans_release();
+
+// Scratch (bytes) needed by sketch_apply for `ncols` columns.
+size_t sketch_scratch_bytes(rbgs_sketch kind, int64_t k, int64_t n, int64_t ncols, bool fp64);
+
+// Y (k x ncols, ldy) = Theta X (n x ncols, ldx).  TX = float|double input,
+// TY = float|double output; the arithmetic is double iff TX is double.
+template <class TX, class TY>
+rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed, const TX* X, int64_t ldx,
+                           int64_t ncols, TY* Y, int64_t ldy, void* scratch, size_t scratch_bytes,
+                           cudaStream_t st, const int* active = nullptr);
+
+// --------------------------------------------------------------- tall ops ---
+// Qout (n x mb) = [A1 (n x c) | A2 (n x mb)] * G ((c+mb) x mb, ldg).  Qout may
+// alias A2 exactly.  mb <= 64.
+template <class T>
+rbgs_status tall_update_simt(int64_t n, int64_t c, int64_t mb, const T* A1, int64_t lda1, const T* A2, int64_t lda2,
+                             const T* G, int64_t ldg, T* Qout, int64_t ldo, const int* active, cudaStream_t st);
+
+// tcgen05 3xTF32 version; Ghi/Glo are the TF32 split of G stored K-major in a
+// padded layout (see tall_tc.cu).  Returns RBGS_EINVAL for shapes it does not
+// take (the caller then uses the SIMT kernel).
+rbgs_status tall_update_tc(int64_t n, int64_t c, int64_t mb, const float* A1, int64_t lda1, const float* A2,
+                           int64_t lda2, const float* Gsplit, float* Qout, int64_t ldo, const int* active,
+                           cudaStream_t st);
+size_t tc_gsplit_floats(int64_t K);  // floats needed for the split G of K rows
+// Build the split operand of the tensor-core kernel from the FP64 G.
+rbgs_status tc_split_g(int64_t K, int64_t mb, const double* G, int64_t ldg, float* Gsplit, const int* active,
+                       cudaStream_t st);
+
+// ------------------------------------------------------------ sketch space --
+// out (M x N, ldo) = alpha * op(A) * B + beta * out, op(A) = A (TRANS=0, A M x K)
+// or A^T (TRANS=1, A K x M); B K x N; N <= 64.  TA/TB input, TO output type,
+// accumulation in TACC.  Uses `part` scratch of ksplit * M * N TACC.
+template <class TA, class TO, class TACC>
+rbgs_status small_gemm(int trans, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t lda,
+                       const TA* B, int64_t ldb, double beta, TO* out, int64_t ldo, TACC* part, int64_t part_elems,
+                       const int* active, cudaStream_t st);
+
+// Cholesky G = R^T R (upper R, positive diagonal) of an mb x mb FP64 matrix and
+// R^{-1}; sets *flag |= 1 on a non-positive or non-finite pivot.
+rbgs_status chol_inv(int mb, const double* G, double* R, double* Rinv, int* flag, const int* active, cudaStream_t st);
+
+// A (k x mb, lda) <- A * U (U upper mb x mb FP64, ldu = mb).
+template <class TS>
+rbgs_status trmm_right_upper(int64_t k, int mb, TS* A, int64_t lda, const double* U, const int* active,
+                             cudaStream_t st);
+
+// C (mb x mb) = A * B for upper-triangular FP64 mb x mb matrices (ld mb).
+rbgs_status tri_mul(int mb, const double* A, const double* B, double* C, const int* active, cudaStream_t st);
+
+// Coefficient matrix of the fused projection + triangular solve and the R
+// column block:  G = [-Rc * Rii^{-1} ; Rii^{-1}]  ((c+mb) x mb, ldg), written
+// as TG; when `R` is non-null also R[0:c, col] = Rc, R[c:c+mb, col] = Rii.
+template <class TS, class TG>
+rbgs_status assemble_g(int64_t c, int mb, const TS* Rc, int64_t ldrc, const double* Rii, const double* Riinv,
+                       TG* G, int64_t ldg, double* R, int64_t ldr, const int* active, cudaStream_t st);
+
+// Second-pass update of the R column block:
+//   R[0:c, col] += R2c * Rii_old ;  R[c:c+mb, col] = R2ii * Rii_old
+// with Rii_old read from R[c:c+mb, col] (upper part).
+template <class TS>
+rbgs_status reorth_update_r(int64_t c, int mb, const TS* R2c, int64_t ldr2, const double* R2ii, double* Rcol,
+                            int64_t ldr, double* tmp, const int* active, cudaStream_t st);
+
+// Adaptive second pass: flag = (||X||_F > tol) with X c x mb; counts passes.
+template <class TS>
+rbgs_status reorth_decide(int64_t c, int mb, const TS* X, int64_t ldx, double tol, int mode, int* active,
+                          int* count, cudaStream_t st);
+
+// Elementwise C = A - B (k x mb) in TS.
+template <class TS>
+rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,
+                    const int* active, cudaStream_t st);
+
+// Frobenius norms for step 6.
+rbgs_status fro_identity_defect(int64_t m, const double* G, int64_t ldg, double* out, cudaStream_t st);
+rbgs_status fro_norm_diff(int64_t rows, int64_t cols, const double* A, int64_t lda, const double* B, int64_t ldb,
+                          double* out_diff, double* out_a, cudaStream_t st);
+
+}  // namespace rbgs

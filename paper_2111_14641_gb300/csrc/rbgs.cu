@@ -1,0 +1,472 @@
+// Host orchestrator of Alg. 2 and the C-ABI entry points of librbgs.
+//
+// Per block i (c = (i-1) m_p columns done), all on one stream, no host sync:
+//   step 2   R_{1:i-1,i} by Richardson iterations on S_{1:i-1}, P_i (sketch space)
+//   Alg. 5   S'_i = P_i - S_{1:i-1} R_{1:i-1,i};  R_ii = R factor of S'_i
+//            (Cholesky QR twice, FP64 factorizations)
+//   step 3+  Q_i = [Q_{1:i-1} | W_i] G_i  with  G_i = [-R_{1:i-1,i}; I] R_ii^{-1}
+//            (one tall pass: projection and triangular solve fused)
+//   step 5/1 S_i = Theta Q_i and P_{i+1} = Theta W_{i+1}
+//   option   a second projection pass of Q_i against Q_{1:i-1} (reorth)
+//   step 6   Delta, Delta~ on request.
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace rbgs {
+namespace {
+
+// ------------------------------------------------------------ workspace ---
+struct DevWs {
+  int dev = -1;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_ws_mu;
+std::vector<DevWs> g_ws;
+
+rbgs_status workspace(size_t bytes, void** out) {
+  int dev = 0;
+  RBGS_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  for (auto& w : g_ws) {
+    if (w.dev != dev) continue;
+    if (w.bytes >= bytes) {
+      *out = w.ptr;
+      return RBGS_OK;
+    }
+    cudaDeviceSynchronize();
+    cudaFree(w.ptr);
+    w.ptr = nullptr;
+    w.bytes = 0;
+    if (cudaMalloc(&w.ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return RBGS_ENOMEM;
+    }
+    w.bytes = bytes;
+    *out = w.ptr;
+    return RBGS_OK;
+  }
+  DevWs w;
+  w.dev = dev;
+  if (cudaMalloc(&w.ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  w.bytes = bytes;
+  g_ws.push_back(w);
+  *out = w.ptr;
+  return RBGS_OK;
+}
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = (T*)(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+template <class T>
+__global__ void convert_kernel(int64_t rows, int64_t cols, const T* __restrict__ A, int64_t lda,
+                               double* __restrict__ B, int64_t ldb) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const int64_t i = idx % rows, j = idx / rows;
+  B[i + j * ldb] = (double)A[i + j * lda];
+}
+
+__global__ void cast_d2f_kernel(int64_t rows, int64_t cols, const double* __restrict__ A, int64_t lda,
+                                float* __restrict__ B, int64_t ldb) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const int64_t i = idx % rows, j = idx / rows;
+  B[i + j * ldb] = (float)A[i + j * lda];
+}
+
+__global__ void philox_kernel(uint2 key, const uint32_t* __restrict__ ctr, uint32_t* __restrict__ out,
+                              int64_t count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 r = philox10(c, key);
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+constexpr int64_t kPartElems = 1 << 22;  // partial-sum scratch of the sketch-space GEMMs (doubles)
+
+bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + bbytes && pb < pa + abytes;
+}
+
+// Cholesky QR twice of Sp (k x mb, in place):  R = R2 R1, Rinv = R1^{-1} R2^{-1}.
+template <class TS>
+rbgs_status cholqr2(int64_t k, int mb, TS* Sp, double* gram, double* R1, double* R1inv, double* R2, double* R2inv,
+                    double* R, double* Rinv, double* part, int* flag, const int* active, cudaStream_t st) {
+  rbgs_status s;
+  s = small_gemm<TS, double, double>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
+  if (s) return s;
+  if ((s = chol_inv(mb, gram, R1, R1inv, flag, active, st))) return s;
+  if ((s = trmm_right_upper<TS>(k, mb, Sp, k, R1inv, active, st))) return s;
+  s = small_gemm<TS, double, double>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
+  if (s) return s;
+  if ((s = chol_inv(mb, gram, R2, R2inv, flag, active, st))) return s;
+  if ((s = tri_mul(mb, R2, R1, R, active, st))) return s;
+  if ((s = tri_mul(mb, R1inv, R2inv, Rinv, active, st))) return s;
+  return RBGS_OK;
+}
+
+// Step 2 by l Richardson iterations from X = 0:  X <- X + S^T (P - S X).
+// X is c x mb (ldx); Res is k x mb scratch.
+template <class TS>
+rbgs_status richardson(int64_t k, int64_t c, int mb, const TS* S, const TS* Pi, TS* X, int64_t ldx, TS* Res, int l,
+                       TS* partf, const int* active, cudaStream_t st) {
+  rbgs_status s;
+  s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Pi, k, 0.0, X, ldx, partf, kPartElems, active, st);
+  if (s) return s;
+  for (int it = 1; it < l; ++it) {
+    RBGS_CUDA_TRY(cudaMemcpyAsync(Res, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
+    s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X, ldx, 1.0, Res, k, partf, kPartElems, active, st);
+    if (s) return s;
+    s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Res, k, 1.0, X, ldx, partf, kPartElems, active, st);
+    if (s) return s;
+  }
+  return RBGS_OK;
+}
+
+// T: storage of W and Q; TS: storage/arithmetic of the sketch space.
+template <class T, class TS>
+rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_sketch sketch, int64_t k,
+                    uint64_t seed, T* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts& o, rbgs_stats* stats,
+                    bool tensor) {
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int64_t p = m / mb;
+  const int l = o.ls_iters < 1 ? 1 : o.ls_iters;
+  const bool fp64 = sizeof(T) == 8;
+  const size_t sk_bytes = sketch_scratch_bytes(sketch, k, n, mb, fp64) + 256;
+  const bool cert = o.certify != 0 && stats != nullptr;
+
+  // ---- carve the workspace
+  size_t need = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    void* base = nullptr;
+    if (pass == 1) {
+      rbgs_status s = workspace(need, &base);
+      if (s) return s;
+    }
+    Carver cv(pass == 0 ? nullptr : base);
+    TS* S = cv.take<TS>((size_t)k * m);
+    TS* P = cv.take<TS>((size_t)k * m);
+    TS* X = cv.take<TS>((size_t)m * mb);
+    TS* X2 = cv.take<TS>((size_t)m * mb);
+    TS* Res = cv.take<TS>((size_t)k * mb);
+    TS* Sp = cv.take<TS>((size_t)k * mb);
+    double* sm[12];
+    for (auto& q : sm) q = cv.take<double>(64 * 64);
+    T* Gmat = cv.take<T>((size_t)m * mb);
+    double* Gd = tensor ? cv.take<double>((size_t)m * mb) : nullptr;
+    float* Gsplit = tensor ? cv.take<float>(tc_gsplit_floats(m)) : nullptr;
+    double* part = cv.take<double>(kPartElems);
+    TS* partf = cv.take<TS>(kPartElems);
+    void* skscr = cv.take<char>(sk_bytes);
+    int* flags = cv.take<int>(64);
+    double* cert_buf = cert ? cv.take<double>((size_t)k * m * 3 + (size_t)m * 64 + 8) : nullptr;
+    if (pass == 0) {
+      need = cv.off + 256;
+      continue;
+    }
+    double *gram = sm[0], *R1 = sm[1], *R1inv = sm[2], *R2 = sm[3], *R2inv = sm[4], *Rii = sm[5], *Riinv = sm[6],
+           *R2ii = sm[7], *R2iinv = sm[8], *tmp = sm[9];
+    int* brk = flags;          // breakdown
+    int* active = flags + 1;   // second pass on/off for this block
+    int* npass2 = flags + 2;   // number of second passes
+    RBGS_CUDA_TRY(cudaMemsetAsync(flags, 0, 64 * sizeof(int), st));
+    RBGS_CUDA_TRY(cudaMemset2DAsync(R, ldr * sizeof(double), 0, m * sizeof(double), m, st));
+
+    rbgs_status s;
+    auto tall = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act) -> rbgs_status {
+      if (tensor) {
+        rbgs_status e = tc_split_g(c + mb, mb, Gd, c + mb, Gsplit, act, st);
+        if (e) return e;
+        return tall_update_tc(n, c, mb, (const float*)Q, ldq, (const float*)X2src, ldx2, Gsplit, (float*)out, ldq,
+                              act, st);
+      }
+      return tall_update_simt<T>(n, c, mb, Q, ldq, X2src, ldx2, Gmat, c + mb, out, ldq, act, st);
+    };
+    auto make_g = [&](int64_t c, const TS* Rc, const double* Rd, const double* Rdinv, double* Rcol,
+                      const int* act) -> rbgs_status {
+      if (tensor) return assemble_g<TS, double>(c, mb, Rc, m, Rd, Rdinv, Gd, c + mb, Rcol, ldr, act, st);
+      return assemble_g<TS, T>(c, mb, Rc, m, Rd, Rdinv, Gmat, c + mb, Rcol, ldr, act, st);
+    };
+
+    // step 1 of the first block
+    if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, W, ldw, mb, P, k, skscr, sk_bytes, st))) return s;
+    for (int64_t blk = 0; blk < p; ++blk) {
+      const int64_t c = blk * mb;
+      const T* Wi = W + c * ldw;
+      T* Qi = Q + c * ldq;
+      TS* Pi = P + c * k;
+      TS* Si = S + c * k;
+      double* Rcol = R + c * ldr;
+      // step 2 and the implicit sketch of Alg. 5
+      if (c > 0) {
+        if ((s = richardson<TS>(k, c, mb, S, Pi, X, m, Res, l, partf, nullptr, st))) return s;
+        RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
+        s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X, m, 1.0, Sp, k, partf, kPartElems, nullptr, st);
+        if (s) return s;
+      } else {
+        RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
+      }
+      if ((s = cholqr2<TS>(k, mb, Sp, gram, R1, R1inv, R2, R2inv, Rii, Riinv, part, brk, nullptr, st))) return s;
+      if ((s = make_g(c, X, Rii, Riinv, Rcol, nullptr))) return s;
+      // step 3 fused with the triangular solve
+      if ((s = tall(c, Wi, ldw, Qi, nullptr))) return s;
+      // step 5, and step 1 of the next block
+      if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st))) return s;
+      if (blk + 1 < p) {
+        s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi + mb * ldw, ldw, mb, Pi + mb * k, k, skscr, sk_bytes, st);
+        if (s) return s;
+      }
+      // optional second projection pass
+      if (o.reorth && c > 0) {
+        s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Si, k, 0.0, X2, m, partf, kPartElems, nullptr, st);
+        if (s) return s;
+        if ((s = reorth_decide<TS>(c, mb, X2, m, o.reorth_tol, o.reorth, active, npass2, st))) return s;
+        for (int it = 1; it < l; ++it) {
+          RBGS_CUDA_TRY(cudaMemcpyAsync(Res, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
+          s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Res, k, partf, kPartElems, active, st);
+          if (s) return s;
+          s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Res, k, 1.0, X2, m, partf, kPartElems, active, st);
+          if (s) return s;
+        }
+        RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
+        s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Sp, k, partf, kPartElems, active, st);
+        if (s) return s;
+        if ((s = cholqr2<TS>(k, mb, Sp, gram, R1, R1inv, R2, R2inv, R2ii, R2iinv, part, brk, active, st))) return s;
+        if ((s = make_g(c, X2, R2ii, R2iinv, nullptr, active))) return s;
+        if ((s = tall(c, Qi, ldq, Qi, active))) return s;
+        if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st, active))) return s;
+        if ((s = reorth_update_r<TS>(c, mb, X2, m, R2ii, Rcol, ldr, tmp, active, st))) return s;
+      }
+    }
+    RBGS_LAUNCH_CHECK();
+
+    // step 6 (optional): Delta = ||I - S^T S||_F, Delta~ = ||P - S R||_F / ||P||_F
+    double* dres = (double*)(flags + 16);
+    if (cert) {
+      double* Sd = cert_buf;
+      double* Pd = Sd + (size_t)k * m;
+      double* SR = Pd + (size_t)k * m;
+      double* Gt = SR + (size_t)k * m;
+      const int64_t tot = k * m;
+      convert_kernel<TS><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k, m, S, k, Sd, k);
+      convert_kernel<TS><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k, m, P, k, Pd, k);
+      RBGS_LAUNCH_CHECK();
+      // Gram S^T S in column tiles of 64; accumulate ||I - G||_F^2 tile by tile on the host side
+      double acc_d = 0.0;
+      for (int64_t j0 = 0; j0 < m; j0 += 64) {
+        const int64_t nc = std::min<int64_t>(64, m - j0);
+        s = small_gemm<double, double, double>(1, m, nc, k, 1.0, Sd, k, Sd + j0 * k, k, 0.0, Gt, m, part, kPartElems,
+                                               nullptr, st);
+        if (s) return s;
+        // ||I - G||_F^2 over this column tile, summed on the host
+        std::vector<double> hG((size_t)m * nc);
+        RBGS_CUDA_TRY(cudaMemcpyAsync(hG.data(), Gt, sizeof(double) * m * nc, cudaMemcpyDeviceToHost, st));
+        RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t jj = 0; jj < nc; ++jj)
+          for (int64_t i = 0; i < m; ++i) {
+            const double d = (i == j0 + jj ? 1.0 : 0.0) - hG[i + jj * m];
+            acc_d += d * d;
+          }
+      }
+      for (int64_t j0 = 0; j0 < m; j0 += 64) {
+        const int64_t nc = std::min<int64_t>(64, m - j0);
+        s = small_gemm<double, double, double>(0, k, nc, m, 1.0, Sd, k, R + j0 * ldr, ldr, 0.0, SR + j0 * k, k,
+                                               part, kPartElems, nullptr, st);
+        if (s) return s;
+      }
+      if ((s = fro_norm_diff(k, m, Pd, k, SR, k, dres, dres + 1, st))) return s;
+      double hv[2];
+      RBGS_CUDA_TRY(cudaMemcpyAsync(hv, dres, sizeof(hv), cudaMemcpyDeviceToHost, st));
+      RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+      stats->delta = std::sqrt(acc_d);
+      stats->delta_tilde = hv[1] > 0 ? hv[0] / hv[1] : 0.0;
+      stats->certified = (stats->delta <= 0.1 && stats->delta_tilde <= 0.1) ? 1 : 0;
+    }
+    if (o.sync || stats) {
+      int hf[4] = {0, 0, 0, 0};
+      RBGS_CUDA_TRY(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+      RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+      if (stats) {
+        stats->passes2 = hf[2];
+        if (!cert) {
+          stats->delta = -1.0;
+          stats->delta_tilde = -1.0;
+          stats->certified = 0;
+        }
+      }
+      if (hf[0]) return RBGS_EBREAKDOWN;
+    }
+  }
+  return RBGS_OK;
+}
+
+}  // namespace
+}  // namespace rbgs
+
+using namespace rbgs;
+
+extern "C" {
+
+void rbgs_opts_default(rbgs_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->prec = RBGS_P_FP64;
+  o->ls_iters = 2;
+  o->reorth = 0;
+  o->certify = 0;
+  o->reorth_tol = 1e-8;
+  o->stream = nullptr;
+  o->sync = 1;
+}
+
+const char* rbgs_version(void) { return "librbgs 0.1 (sm_103a)"; }
+
+rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch, int64_t k,
+                    uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts* opts,
+                    rbgs_stats* stats) {
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  if (!W || !Q || !R) return RBGS_EINVAL;
+  if (n < 1 || n >= ((int64_t)1 << 31) || m < 1 || mb < 1 || mb > 64 || m % mb != 0) return RBGS_EINVAL;
+  if (ldw < n || ldq < n || ldr < m || k < m) return RBGS_EINVAL;
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_TF32X3 || o.reorth < 0 || o.reorth > 2) return RBGS_EINVAL;
+  if (sketch == RBGS_SK_SRHT) {
+    int64_t np = 1;
+    while (np < n) np <<= 1;
+    if (k > np) return RBGS_EINVAL;
+  } else if (sketch == RBGS_SK_GAUSS || sketch == RBGS_SK_RADEMACHER) {
+    if (k > n) return RBGS_EINVAL;
+  } else {
+    return RBGS_EINVAL;
+  }
+  const size_t es = o.prec == RBGS_P_FP64 ? 8 : 4;
+  if (ranges_overlap(W, es * (size_t)(ldw * (m - 1) + n), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
+  if (ranges_overlap(R, 8 * (size_t)(ldr * (m - 1) + m), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
+  if (o.prec == RBGS_P_FP64)
+    return qr_impl<double, double>((const double*)W, n, m, ldw, (int)mb, sketch, k, seed, (double*)Q, ldq, R, ldr, o,
+                                   stats, false);
+  if (o.prec == RBGS_P_TF32X3) {
+    // tensor-core path: TMA needs 16-byte aligned bases and leading dimensions
+    if (((uintptr_t)W & 15) || ((uintptr_t)Q & 15) || (ldw % 4) || (ldq % 4)) return RBGS_EINVAL;
+    return qr_impl<float, float>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o,
+                                 stats, true);
+  }
+  return qr_impl<float, float>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o, stats,
+                               false);
+}
+
+rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,
+                              int64_t ldx, int64_t ncols, double* Y, int64_t ldy, void* stream, int32_t sync) {
+  if (!X || !Y || n < 1 || k < 1 || ncols < 0 || ldx < n || ldy < k) return RBGS_EINVAL;
+  if (prec < RBGS_P_FP64 || prec > RBGS_P_TF32X3) return RBGS_EINVAL;
+  if (sketch == RBGS_SK_SRHT) {
+    int64_t np = 1;
+    while (np < n) np <<= 1;
+    if (k > np) return RBGS_EINVAL;
+  } else if (sketch != RBGS_SK_GAUSS && sketch != RBGS_SK_RADEMACHER) {
+    return RBGS_EINVAL;
+  }
+  const bool fp64 = prec == RBGS_P_FP64;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sketch_scratch_bytes(sketch, k, n, ncols, fp64) + 256;
+  void* scr = nullptr;
+  rbgs_status s = workspace(bytes, &scr);
+  if (s) return s;
+  if (fp64) s = sketch_apply_t<double, double>(sketch, k, n, seed, (const double*)X, ldx, ncols, Y, ldy, scr, bytes, st);
+  else s = sketch_apply_t<float, double>(sketch, k, n, seed, (const float*)X, ldx, ncols, Y, ldy, scr, bytes, st);
+  if (s) return s;
+  if (sync) RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  return RBGS_OK;
+}
+
+rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_t mb, const void* Qprev, int64_t ldq,
+                             const void* X, int64_t ldx, const double* G, int64_t ldg, void* Qout, int64_t ldo,
+                             void* stream, int32_t sync) {
+  if (!X || !G || !Qout || (c > 0 && !Qprev)) return RBGS_EINVAL;
+  if (n < 1 || c < 0 || mb < 1 || mb > 64 || ldx < n || ldo < n || (c > 0 && ldq < n) || ldg < c + mb)
+    return RBGS_EINVAL;
+  if (prec < RBGS_P_FP64 || prec > RBGS_P_TF32X3) return RBGS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t K = c + mb;
+  rbgs_status s;
+  if (prec == RBGS_P_FP64) {
+    s = tall_update_simt<double>(n, c, mb, (const double*)Qprev, ldq, (const double*)X, ldx, G, ldg, (double*)Qout,
+                                 ldo, nullptr, st);
+  } else if (prec == RBGS_P_FP32) {
+    void* scr = nullptr;
+    if ((s = workspace(sizeof(float) * K * mb + 256, &scr))) return s;
+    float* Gf = (float*)scr;
+    const int64_t tot = K * mb;
+    cast_d2f_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(K, mb, G, ldg, Gf, K);
+    RBGS_LAUNCH_CHECK();
+    s = tall_update_simt<float>(n, c, mb, (const float*)Qprev, ldq, (const float*)X, ldx, Gf, K, (float*)Qout, ldo,
+                                nullptr, st);
+  } else {
+    if (((uintptr_t)X & 15) || ((uintptr_t)Qout & 15) || (c > 0 && ((uintptr_t)Qprev & 15)) || (ldx % 4) ||
+        (ldo % 4) || (c > 0 && (ldq % 4)))
+      return RBGS_EINVAL;
+    void* scr = nullptr;
+    if ((s = workspace(sizeof(float) * tc_gsplit_floats(K) + 256, &scr))) return s;
+    float* Gs = (float*)scr;
+    if ((s = tc_split_g(K, mb, G, ldg, Gs, nullptr, st))) return s;
+    s = tall_update_tc(n, c, mb, (const float*)Qprev, ldq, (const float*)X, ldx, Gs, (float*)Qout, ldo, nullptr, st);
+  }
+  if (s) return s;
+  if (sync) RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  return RBGS_OK;
+}
+
+rbgs_status rbgs_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t count, void* stream,
+                        int32_t sync) {
+  if (!ctr || !out || count < 0) return RBGS_EINVAL;
+  if (count == 0) return RBGS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  philox_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(seed_key(seed), ctr, out, count);
+  RBGS_LAUNCH_CHECK();
+  if (sync) RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  return RBGS_OK;
+}
+
+rbgs_status rbgs_release_workspace(void) {
+  int dev = 0;
+  RBGS_CUDA_TRY(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    for (auto& w : g_ws)
+      if (w.dev == dev && w.ptr) {
+        cudaDeviceSynchronize();
+        cudaFree(w.ptr);
+        w.ptr = nullptr;
+        w.bytes = 0;
+      }
+  }
+  srht_plans_release();
+  return RBGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,415 @@
+// Sketching kernels: Y = Theta X without materialising Theta (Sec. 2.3).
+//
+// SRHT, Theta = k^{-1/2} Samp H D with zero padding to n' = 2^ceil(log2 n):
+// with the tile length B | n', H_{n'} = H_{n'/B} (x) H_B, so a sampled row
+// i = i_hi B + i_lo of H D x is  sum_t (-1)^{popcount(i_hi & t)} [H_B (D x)_t]_{i_lo}.
+// Stage 1 (one CTA per tile t and column): load B entries of the column,
+// apply D, transform in shared memory with radix-32 register butterflies,
+// keep the entries at the distinct sampled low indices.  Stage 2: for each
+// sampled row, the signed sum over tiles.  Both stages are deterministic.
+//
+// Gaussian / Rademacher: a CTA owns 64 rows of Theta and a slice of the n
+// rows of X, regenerates its Theta tile from Philox in shared memory and
+// accumulates Theta_tile * X_tile; slice partials are summed in fixed order.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <unordered_set>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace rbgs {
+
+// ------------------------------------------------------------------ SRHT ---
+
+int srht_samples_host(uint64_t seed, int64_t np, int64_t k, int64_t* out) {
+  if (k < 0 || k > np) return -1;
+  std::unordered_set<int64_t> chosen;
+  chosen.reserve((size_t)k * 2 + 1);
+  const uint2 key = seed_key(seed);
+  for (int64_t t = 0; t < k; ++t) {
+    const int64_t J = np - k + t;
+    const uint4 x = philox10(make_uint4((uint32_t)t, 0u, kPurposeSrhtSample, 0u), key);
+    const uint64_t r64 = ((uint64_t)x.y << 32) | (uint64_t)x.x;
+    const int64_t v = (int64_t)(r64 % (uint64_t)(J + 1));
+    const int64_t pick = chosen.count(v) ? J : v;
+    chosen.insert(pick);
+    out[t] = pick;
+  }
+  std::sort(out, out + k);
+  return 0;
+}
+
+namespace {
+struct PlanCache {
+  std::mutex mu;
+  std::vector<std::pair<int, SrhtPlan*>> plans;  // (device, plan)
+};
+PlanCache& plan_cache() {
+  static PlanCache c;
+  return c;
+}
+}  // namespace
+
+rbgs_status srht_plan_get(uint64_t seed, int64_t n, int64_t k, const SrhtPlan** out) {
+  int dev = 0;
+  RBGS_CUDA_TRY(cudaGetDevice(&dev));
+  PlanCache& pc = plan_cache();
+  std::lock_guard<std::mutex> lock(pc.mu);
+  for (auto& e : pc.plans)
+    if (e.first == dev && e.second->seed == seed && e.second->n == n && e.second->k == k) {
+      *out = e.second;
+      return RBGS_OK;
+    }
+  SrhtPlan* p = new SrhtPlan();
+  p->seed = seed;
+  p->n = n;
+  p->k = k;
+  int64_t np = 1;
+  while (np < n) np <<= 1;
+  p->np = np;
+  p->B = (int)std::min<int64_t>(np, kSrhtTile);
+  p->T = (int)(np / p->B);
+  p->samples.resize((size_t)k);
+  if (srht_samples_host(seed, np, k, p->samples.data())) {
+    delete p;
+    return RBGS_EINVAL;
+  }
+  std::vector<int> lo((size_t)k), rhi((size_t)k), rl((size_t)k);
+  for (int64_t r = 0; r < k; ++r) {
+    lo[r] = (int)(p->samples[r] % p->B);
+    rhi[r] = (int)(p->samples[r] / p->B);
+  }
+  std::vector<int> lv(lo);
+  std::sort(lv.begin(), lv.end());
+  lv.erase(std::unique(lv.begin(), lv.end()), lv.end());
+  for (int64_t r = 0; r < k; ++r) rl[r] = (int)(std::lower_bound(lv.begin(), lv.end(), lo[r]) - lv.begin());
+  p->L = (int)lv.size();
+  cudaError_t e1 = cudaMalloc(&p->d_lvals, sizeof(int) * std::max<size_t>(1, lv.size()));
+  cudaError_t e2 = cudaMalloc(&p->d_rhi, sizeof(int) * std::max<int64_t>(1, k));
+  cudaError_t e3 = cudaMalloc(&p->d_rl, sizeof(int) * std::max<int64_t>(1, k));
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    cudaFree(p->d_lvals);
+    cudaFree(p->d_rhi);
+    cudaFree(p->d_rl);
+    delete p;
+    return RBGS_ENOMEM;
+  }
+  if (cudaMemcpy(p->d_lvals, lv.data(), sizeof(int) * lv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->d_rhi, rhi.data(), sizeof(int) * k, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->d_rl, rl.data(), sizeof(int) * k, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(p->d_lvals);
+    cudaFree(p->d_rhi);
+    cudaFree(p->d_rl);
+    delete p;
+    return RBGS_ECUDA;
+  }
+  pc.plans.push_back({dev, p});
+  *out = p;
+  return RBGS_OK;
+}
+
+void srht_plans_release() {
+  PlanCache& pc = plan_cache();
+  std::lock_guard<std::mutex> lock(pc.mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<std::pair<int, SrhtPlan*>> keep;
+  for (auto& e : pc.plans) {
+    if (e.first == dev) {
+      cudaFree(e.second->d_lvals);
+      cudaFree(e.second->d_rhi);
+      cudaFree(e.second->d_rl);
+      delete e.second;
+    } else {
+      keep.push_back(e);
+    }
+  }
+  pc.plans.swap(keep);
+}
+
+namespace {
+
+constexpr int kSrhtThreads = 512;
+
+__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 31); }
+
+template <class TC, int R>
+__device__ __forceinline__ void fwht_stage(TC* buf, int B, int lo) {
+  constexpr int G = 1 << R;
+  const int ngroups = B >> R;
+  const int lomask = (1 << lo) - 1;
+  for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const int base = ((g >> lo) << (lo + R)) | (g & lomask);
+    TC v[G];
+#pragma unroll
+    for (int e = 0; e < G; ++e) v[e] = buf[swz(base + (e << lo))];
+#pragma unroll
+    for (int h = 1; h < G; h <<= 1) {
+#pragma unroll
+      for (int e = 0; e < G; ++e) {
+        if ((e & h) == 0) {
+          const TC a = v[e], b = v[e + h];
+          v[e] = a + b;
+          v[e + h] = a - b;
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < G; ++e) buf[swz(base + (e << lo))] = v[e];
+  }
+}
+
+// Stage 1: grid (T, ncols).  z[(col * T + t) * L + l] = [H_B (D x)_t]_{lvals[l]}.
+template <class TX, class TC>
+__global__ void __launch_bounds__(kSrhtThreads) srht_stage1(const TX* __restrict__ X, int64_t ldx, int64_t n, int B,
+                                                            int logB, int T, uint2 key,
+                                                            const int* __restrict__ lvals, int L,
+                                                            TC* __restrict__ z, const int* active) {
+  if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* buf = reinterpret_cast<TC*>(smem_raw);
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(buf + B);
+  const int t = blockIdx.x;
+  const int col = blockIdx.y;
+  const int64_t row0 = (int64_t)t * B;
+  const int nwords = (B + 31) >> 5;
+  for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+    const int64_t e0 = row0 + 32 * (int64_t)w;
+    const uint4 bits = srht_sign_bits(key, (uint32_t)(e0 >> 7));
+    sgn[w] = word_of(bits, (int)((e0 >> 5) & 3));
+  }
+  __syncthreads();
+  const TX* xc = X + (int64_t)col * ldx;
+  for (int j = threadIdx.x; j < B; j += blockDim.x) {
+    const int64_t gr = row0 + j;
+    TC v = gr < n ? (TC)xc[gr] : (TC)0;
+    if ((sgn[j >> 5] >> (j & 31)) & 1u) v = -v;
+    buf[swz(j)] = v;
+  }
+  for (int lo = 0; lo < logB; lo += 5) {
+    __syncthreads();
+    const int r = min(5, logB - lo);
+    switch (r) {
+      case 5: fwht_stage<TC, 5>(buf, B, lo); break;
+      case 4: fwht_stage<TC, 4>(buf, B, lo); break;
+      case 3: fwht_stage<TC, 3>(buf, B, lo); break;
+      case 2: fwht_stage<TC, 2>(buf, B, lo); break;
+      default: fwht_stage<TC, 1>(buf, B, lo); break;
+    }
+  }
+  __syncthreads();
+  TC* zo = z + ((int64_t)col * T + t) * L;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) zo[l] = buf[swz(lvals[l])];
+}
+
+// Stage 2: Y[r, col] = scale * sum_t (-1)^{popcount(rhi[r] & t)} z[col, t, rl[r]].
+template <class TC, class TY>
+__global__ void srht_stage2(const TC* __restrict__ z, int T, int L, const int* __restrict__ rhi,
+                            const int* __restrict__ rl, int64_t k, int64_t ncols, TC scale, TY* __restrict__ Y,
+                            int64_t ldy, const int* active) {
+  if (active && *active == 0) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * ncols) return;
+  const int64_t r = idx % k;
+  const int64_t col = idx / k;
+  const TC* zc = z + (int64_t)col * T * L + rl[r];
+  const int hi = rhi[r];
+  TC acc = 0;
+  for (int t = 0; t < T; ++t) {
+    const TC v = zc[(int64_t)t * L];
+    acc += (__popc(hi & t) & 1) ? -v : v;
+  }
+  Y[r + col * ldy] = (TY)(acc * scale);
+}
+
+// ------------------------------------------------------- Gaussian/Rademacher
+
+constexpr int kDenseRows = 64;   // Theta rows per CTA
+constexpr int kDenseJ = 32;      // X rows per step
+constexpr int kDenseCols = 64;   // max columns per launch
+constexpr int kDenseThreads = 256;
+
+template <int KIND, class TX, class TC>
+__global__ void __launch_bounds__(kDenseThreads) dense_sketch_part(const TX* __restrict__ X, int64_t ldx, int64_t n,
+                                                                   int ncols, int64_t k, uint2 key, double scale,
+                                                                   int64_t rows_per_split, TC* __restrict__ part,
+                                                                   const int* active) {
+  if (active && *active == 0) return;
+  __shared__ TC th[kDenseRows][kDenseJ + 1];
+  __shared__ TC xs[kDenseJ][kDenseCols + 1];
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * kDenseRows;
+  const int split = blockIdx.y;
+  const int64_t j0 = (int64_t)split * rows_per_split;
+  const int64_t j1 = min(n, j0 + rows_per_split);
+  const int tr = tid & 15, tc = tid >> 4;
+  TC acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[i][q] = 0;
+
+  for (int64_t jj0 = j0; jj0 < j1; jj0 += kDenseJ) {
+    if (KIND == RBGS_SK_GAUSS) {
+      // 32 row pairs x 32 columns of Theta, 4 Box-Muller pairs per thread
+      for (int p = tid; p < (kDenseRows / 2) * kDenseJ; p += kDenseThreads) {
+        const int rpl = p & 31, jl = p >> 5;
+        const int64_t j = jj0 + jl;
+        const int64_t rr = r0 + 2 * rpl;
+        double z0 = 0.0, z1 = 0.0;
+        if (j < j1 && rr < k) gauss_pair(key, j, (uint32_t)(rr >> 1), z0, z1);
+        th[2 * rpl][jl] = (TC)(z0 * scale);
+        th[2 * rpl + 1][jl] = (TC)(z1 * scale);
+      }
+    } else {
+      if (tid < kDenseJ) {
+        const int64_t j = jj0 + tid;
+        uint4 bits = make_uint4(0, 0, 0, 0);
+        if (j < j1) bits = rademacher_bits(key, j, (uint32_t)(r0 >> 7));
+        const int off = (int)(r0 & 127);  // 0 or 64
+        for (int rl = 0; rl < kDenseRows; ++rl) {
+          const int rb = off + rl;
+          const uint32_t b = (word_of(bits, rb >> 5) >> (rb & 31)) & 1u;
+          th[rl][tid] = (j < j1) ? (TC)(b ? -scale : scale) : (TC)0;
+        }
+      }
+    }
+    for (int e = tid; e < kDenseJ * kDenseCols; e += kDenseThreads) {
+      const int jl = e % kDenseJ, c = e / kDenseJ;
+      const int64_t j = jj0 + jl;
+      xs[jl][c] = (c < ncols && j < j1) ? (TC)X[j + (int64_t)c * ldx] : (TC)0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jl = 0; jl < kDenseJ; ++jl) {
+      TC a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = th[tr + 16 * i][jl];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = xs[jl][tc + 16 * q];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] += a[i] * b[q];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t r = r0 + tr + 16 * i;
+      const int c = tc + 16 * q;
+      if (r < k && c < ncols) part[((int64_t)split * ncols + c) * k + r] = acc[i][q];
+    }
+}
+
+template <class TC, class TY>
+__global__ void dense_sketch_reduce(const TC* __restrict__ part, int nsplit, int64_t k, int ncols,
+                                    TY* __restrict__ Y, int64_t ldy, const int* active) {
+  if (active && *active == 0) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * ncols) return;
+  const int64_t r = idx % k;
+  const int64_t c = idx / k;
+  TC s = 0;
+  for (int p = 0; p < nsplit; ++p) s += part[((int64_t)p * ncols + c) * k + r];
+  Y[r + c * ldy] = (TY)s;
+}
+
+int dense_nsplit(int64_t k, int64_t n) {
+  const int64_t rblocks = (k + kDenseRows - 1) / kDenseRows;
+  int64_t target = std::max<int64_t>(1, 2 * 152 / std::max<int64_t>(1, rblocks));
+  const int64_t maxsplit = std::max<int64_t>(1, (n + 255) / 256);
+  return (int)std::min<int64_t>(target, maxsplit);
+}
+
+}  // namespace
+
+size_t sketch_scratch_bytes(rbgs_sketch kind, int64_t k, int64_t n, int64_t ncols, bool fp64) {
+  const size_t es = fp64 ? 8 : 4;
+  if (kind == RBGS_SK_SRHT) {
+    int64_t np = 1;
+    while (np < n) np <<= 1;
+    const int64_t B = std::min<int64_t>(np, kSrhtTile);
+    const int64_t T = np / B;
+    const int64_t L = std::min<int64_t>(B, k);
+    return es * (size_t)(ncols * T * L);
+  }
+  const int64_t c = std::min<int64_t>(ncols, kDenseCols);
+  return es * (size_t)(dense_nsplit(k, n) * c * k);
+}
+
+template <class TX, class TY>
+rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed, const TX* X, int64_t ldx,
+                           int64_t ncols, TY* Y, int64_t ldy, void* scratch, size_t scratch_bytes, cudaStream_t st,
+                           const int* active) {
+  using TC = TX;  // arithmetic follows the input precision
+  if (ncols == 0 || k == 0) return RBGS_OK;
+  const uint2 key = seed_key(seed);
+  const double dscale = 1.0 / std::sqrt((double)k);
+  const TC scale = (TC)dscale;
+  if (kind == RBGS_SK_SRHT) {
+    const SrhtPlan* plan = nullptr;
+    rbgs_status s = srht_plan_get(seed, n, k, &plan);
+    if (s != RBGS_OK) return s;
+    const size_t need = sizeof(TC) * (size_t)(ncols * plan->T) * (size_t)plan->L;
+    if (scratch_bytes < need) return RBGS_EINVAL;
+    TC* z = reinterpret_cast<TC*>(scratch);
+    int logB = 0;
+    while ((1 << logB) < plan->B) ++logB;
+    const size_t smem = sizeof(TC) * (size_t)plan->B + sizeof(uint32_t) * (size_t)((plan->B + 31) / 32);
+    RBGS_CUDA_TRY(cudaFuncSetAttribute(srht_stage1<TX, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(TC) * kSrhtTile + 4 * kSrhtTile / 32)));
+    for (int64_t c0 = 0; c0 < ncols; c0 += 65535) {
+      const int64_t nc = std::min<int64_t>(65535, ncols - c0);
+      dim3 grid((unsigned)plan->T, (unsigned)nc);
+      srht_stage1<TX, TC><<<grid, kSrhtThreads, smem, st>>>(X + c0 * ldx, ldx, n, plan->B, logB, plan->T, key,
+                                                           plan->d_lvals, plan->L, z + c0 * plan->T * plan->L,
+                                                           active);
+      RBGS_LAUNCH_CHECK();
+    }
+    const int64_t tot = k * ncols;
+    srht_stage2<TC, TY><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(z, plan->T, plan->L, plan->d_rhi,
+                                                                      plan->d_rl, k, ncols, scale, Y, ldy, active);
+    RBGS_LAUNCH_CHECK();
+    return RBGS_OK;
+  }
+  if (kind != RBGS_SK_GAUSS && kind != RBGS_SK_RADEMACHER) return RBGS_EINVAL;
+  const int nsplit = dense_nsplit(k, n);
+  const int64_t rows_per_split = ((n + nsplit - 1) / nsplit + kDenseJ - 1) / kDenseJ * kDenseJ;
+  TC* part = reinterpret_cast<TC*>(scratch);
+  for (int64_t c0 = 0; c0 < ncols; c0 += kDenseCols) {
+    const int nc = (int)std::min<int64_t>(kDenseCols, ncols - c0);
+    const size_t need = sizeof(TC) * (size_t)nsplit * nc * (size_t)k;
+    if (scratch_bytes < need) return RBGS_EINVAL;
+    dim3 grid((unsigned)((k + kDenseRows - 1) / kDenseRows), (unsigned)nsplit);
+    if (kind == RBGS_SK_GAUSS)
+      dense_sketch_part<RBGS_SK_GAUSS, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
+                                                                              dscale, rows_per_split, part, active);
+    else
+      dense_sketch_part<RBGS_SK_RADEMACHER, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
+                                                                                   dscale, rows_per_split, part, active);
+    RBGS_LAUNCH_CHECK();
+    const int64_t tot = k * nc;
+    dense_sketch_reduce<TC, TY><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nsplit, k, nc, Y + c0 * ldy, ldy,
+                                                                                       active);
+    RBGS_LAUNCH_CHECK();
+  }
+  return RBGS_OK;
+}
+
+template rbgs_status sketch_apply_t<double, double>(rbgs_sketch, int64_t, int64_t, uint64_t, const double*, int64_t,
+                                                    int64_t, double*, int64_t, void*, size_t, cudaStream_t,
+                                                    const int*);
+template rbgs_status sketch_apply_t<float, double>(rbgs_sketch, int64_t, int64_t, uint64_t, const float*, int64_t,
+                                                   int64_t, double*, int64_t, void*, size_t, cudaStream_t,
+                                                    const int*);
+template rbgs_status sketch_apply_t<float, float>(rbgs_sketch, int64_t, int64_t, uint64_t, const float*, int64_t,
+                                                  int64_t, float*, int64_t, void*, size_t, cudaStream_t,
+                                                  const int*);
+
+}  // namespace rbgs

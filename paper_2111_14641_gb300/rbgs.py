@@ -1,0 +1,197 @@
+"""Thin Python binding of librbgs (ctypes).  Argument marshalling only: every
+step of the computation runs in the CUDA library; there is no fallback.
+
+Tensors are torch CUDA tensors in column-major layout: shape (rows, cols) with
+stride (1, ld), ld >= rows (``colmajor(t)`` converts).  Work is enqueued on the
+current torch CUDA stream unless ``stream`` is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import re
+from dataclasses import dataclass
+from pathlib import Path
+
+import torch
+
+from . import build as _build
+
+_HDR = Path(__file__).resolve().parent.parent / "include" / "rbgs.h"
+
+SKETCH = {"gauss": 0, "rademacher": 1, "srht": 2}
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2}
+STATUS = {0: "RBGS_OK", 1: "RBGS_EINVAL", 2: "RBGS_ENOMEM", 3: "RBGS_ECUDA", 4: "RBGS_EBREAKDOWN",
+          5: "RBGS_ENOTCERTIFIED", 6: "RBGS_ETIMEOUT", 7: "RBGS_ENOCONV", 8: "RBGS_ENODEV"}
+
+
+class RbgsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("ls_iters", ctypes.c_int32), ("reorth", ctypes.c_int32),
+                ("certify", ctypes.c_int32), ("reorth_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("sync", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("delta_tilde", ctypes.c_double), ("passes2", ctypes.c_int32),
+                ("certified", ctypes.c_int32)]
+
+
+@dataclass
+class QRStats:
+    delta: float
+    delta_tilde: float
+    passes2: int
+    certified: bool
+
+
+_lib = None
+
+
+def lib_path() -> Path:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load librbgs.so; raises if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not path.exists():
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"librbgs.so not built ({path}); run paper_2111_14641_gb300.build.build()")
+    lib = ctypes.CDLL(str(path))
+    i64, u64, vp, i32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int32
+    lib.rbgs_opts_default.argtypes = [ctypes.POINTER(Opts)]
+    lib.rbgs_qr.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
+                            ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
+    lib.rbgs_sketch_apply.argtypes = [ctypes.c_int, i64, i64, u64, i32, vp, i64, i64, vp, i64, vp, i32]
+    lib.rbgs_tall_update.argtypes = [i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i32]
+    lib.rbgs_philox.argtypes = [u64, vp, vp, i64, vp, i32]
+    lib.rbgs_release_workspace.argtypes = []
+    lib.rbgs_version.restype = ctypes.c_char_p
+    for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_philox", "rbgs_release_workspace"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions that include/rbgs.h declares."""
+    txt = _HDR.read_text()
+    return sorted(set(re.findall(r"^\s*(?:RBGS_API\s+)?(?:rbgs_status|void|const char\*)\s+(rbgs_\w+)\s*\(", txt, re.M)))
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Column-major copy (shape kept, stride (1, rows))."""
+    return t.t().contiguous().t()
+
+
+def _ld(t: torch.Tensor, name: str) -> int:
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if t.shape[1] > 1 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride (1, ld)); use colmajor()")
+    if t.shape[1] <= 1:
+        return max(t.shape[0], 1) if t.stride(0) == 1 else t.stride(0)
+    return t.stride(1)
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise RbgsError(code, where)
+
+
+def _prec_of(t: torch.Tensor, prec: str | None) -> str:
+    if prec is None:
+        return "fp64" if t.dtype == torch.float64 else "tf32x3"
+    want = torch.float64 if prec == "fp64" else torch.float32
+    if t.dtype != want:
+        raise ValueError(f"precision {prec} needs {want}, got {t.dtype}")
+    return prec
+
+
+def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
+            prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
+            certify: bool = False, Q: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None,
+            sync: bool = True):
+    """RBGS QR of W (n x m, column-major).  Returns (Q, R, QRStats | None)."""
+    lib = load()
+    prec = _prec_of(W, prec)
+    n, m = W.shape
+    k = 2 * m if k is None else k
+    if Q is None:
+        Q = torch.empty((m, n), dtype=W.dtype, device=W.device).t()
+    if R is None:
+        R = torch.empty((m, m), dtype=torch.float64, device=W.device).t()
+    o = Opts()
+    lib.rbgs_opts_default(ctypes.byref(o))
+    o.prec, o.ls_iters, o.reorth, o.certify = PREC[prec], ls_iters, reorth, int(certify)
+    o.reorth_tol, o.stream, o.sync = reorth_tol, _stream_ptr(stream), int(sync)
+    st = Stats()
+    code = lib.rbgs_qr(W.data_ptr(), n, m, _ld(W, "W"), mb, SKETCH[sketch], k, seed, Q.data_ptr(), _ld(Q, "Q"),
+                       R.data_ptr(), _ld(R, "R"), ctypes.byref(o), ctypes.byref(st) if sync else None)
+    _check(code, "rbgs_qr")
+    stats = QRStats(st.delta, st.delta_tilde, st.passes2, bool(st.certified)) if sync else None
+    return Q, R, stats
+
+
+def sketch_apply(X: torch.Tensor, sketch: str, k: int, seed: int, prec: str | None = None, stream=None,
+                 sync: bool = True) -> torch.Tensor:
+    """Y = Theta X (k x ncols, float64)."""
+    lib = load()
+    prec = _prec_of(X, prec)
+    n, c = X.shape
+    Y = torch.empty((c, k), dtype=torch.float64, device=X.device).t()
+    code = lib.rbgs_sketch_apply(SKETCH[sketch], k, n, seed, PREC[prec], X.data_ptr(), _ld(X, "X"), c, Y.data_ptr(),
+                                 k, _stream_ptr(stream), int(sync))
+    _check(code, "rbgs_sketch_apply")
+    return Y
+
+
+def tall_update(Qprev: torch.Tensor | None, X: torch.Tensor, G: torch.Tensor, prec: str | None = None,
+                out: torch.Tensor | None = None, stream=None, sync: bool = True) -> torch.Tensor:
+    """Qout = [Qprev | X] G."""
+    lib = load()
+    prec = _prec_of(X, prec)
+    n, mb = X.shape
+    c = 0 if Qprev is None else Qprev.shape[1]
+    if out is None:
+        out = torch.empty((mb, n), dtype=X.dtype, device=X.device).t()
+    Gc = colmajor(G.to(torch.float64))
+    code = lib.rbgs_tall_update(PREC[prec], n, c, mb, 0 if Qprev is None else Qprev.data_ptr(),
+                                n if Qprev is None else _ld(Qprev, "Qprev"), X.data_ptr(), _ld(X, "X"),
+                                Gc.data_ptr(), _ld(Gc, "G"), out.data_ptr(), _ld(out, "out"), _stream_ptr(stream),
+                                int(sync))
+    _check(code, "rbgs_tall_update")
+    return out
+
+
+def philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
+    """Philox4x32-10 blocks for counters ctr (count x 4, int32/uint32 bits, CUDA)."""
+    lib = load()
+    c = ctr.contiguous()
+    out = torch.empty_like(c)
+    code = lib.rbgs_philox(seed, c.data_ptr(), out.data_ptr(), c.shape[0], _stream_ptr(stream), 1)
+    _check(code, "rbgs_philox")
+    return out
+
+
+def release_workspace():
+    _check(load().rbgs_release_workspace(), "rbgs_release_workspace")
+
+
+def version() -> str:
+    return load().rbgs_version().decode()

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every symbol include/rbgs.h declares.
+No compute call here: this file runs without a GPU."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2111_14641_gb300 import build as b
+
+    path = b.build()
+    return ctypes.CDLL(str(path))
+
+
+def _declared():
+    txt = (ROOT / "include" / "rbgs.h").read_text()
+    return sorted(set(re.findall(r"^RBGS_API\s+(?:rbgs_status|void|const char\*)\s+(rbgs_\w+)\s*\(", txt, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_philox", "rbgs_opts_default",
+                 "rbgs_release_workspace", "rbgs_version"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_matches_header():
+    from paper_2111_14641_gb300 import rbgs
+
+    assert rbgs.header_functions() == _declared()
+
+
+def test_opts_default_and_version(lib):
+    from paper_2111_14641_gb300.rbgs import Opts
+
+    o = Opts()
+    lib.rbgs_opts_default(ctypes.byref(o))
+    assert (o.prec, o.ls_iters, o.reorth, o.certify, o.sync) == (0, 2, 0, 0, 1)
+    assert o.reorth_tol == 1e-8
+    lib.rbgs_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.rbgs_version()
+
+
+def test_argument_checks_need_no_device(lib):
+    """Invalid sizes are rejected before any CUDA call (RBGS_EINVAL == 1)."""
+    i64 = ctypes.c_int64
+    lib.rbgs_qr.argtypes = [ctypes.c_void_p, i64, i64, i64, i64, ctypes.c_int, i64, ctypes.c_uint64,
+                            ctypes.c_void_p, i64, ctypes.c_void_p, i64, ctypes.c_void_p, ctypes.c_void_p]
+    fake = ctypes.c_void_p(0x1000)
+    other = ctypes.c_void_p(0x10000000)
+    rr = ctypes.c_void_p(0x20000000)
+    # m not a multiple of mb
+    assert lib.rbgs_qr(fake, 100, 10, 100, 4, 0, 20, 0, other, 100, rr, 10, None, None) == 1
+    # k < m
+    assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 4, 0, other, 100, rr, 8, None, None) == 1
+    # k > n for a dense sketch
+    assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 101, 0, other, 100, rr, 8, None, None) == 1
+    # ld too small
+    assert lib.rbgs_qr(fake, 100, 8, 99, 4, 0, 16, 0, other, 100, rr, 8, None, None) == 1
+    # null pointer
+    assert lib.rbgs_qr(None, 100, 8, 100, 4, 0, 16, 0, other, 100, rr, 8, None, None) == 1
+    # block size above 64
+    assert lib.rbgs_qr(fake, 1000, 128, 1000, 128, 0, 256, 0, other, 1000, rr, 128, None, None) == 1
+    # W and Q overlap
+    assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 16, 0, fake, 100, rr, 8, None, None) == 1

@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Paper references: Balabanov & Grigori, arXiv 2111.14641."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2111_14641_gb300 as rb
+    from paper_2111_14641_gb300 import build
+
+    build.build()
+    rb.load()
+    return rb
+
+
+def dev(A, dtype=torch.float64):
+    """numpy (n x m) -> column-major CUDA tensor."""
+    A = np.asarray(A)
+    return torch.from_numpy(np.ascontiguousarray(A.T)).to("cuda", dtype).t()
+
+
+def host(T):
+    return T.detach().double().cpu().numpy()
+
+
+# ------------------------------------------------------------------ Philox --
+
+def test_philox_bits_match_oracle(rb):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(257, 4), dtype=np.uint64).astype(np.uint32)
+    seed = (7 << 35) + 12345
+    out = rb.philox(torch.from_numpy(ctr.view(np.int32)).cuda(), seed).cpu().numpy().view(np.uint32)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(ctr.shape[0]):
+        np.testing.assert_array_equal(out[i], oracle.philox(ctr[i], key))
+
+
+# ---------------------------------------------------------------- sketches --
+
+SKETCH_CASES = [
+    ("gauss", 1, 1, 1), ("gauss", 100, 3, 40), ("gauss", 1000, 65, 130), ("gauss", 5000, 5, 64),
+    ("rademacher", 100, 3, 40), ("rademacher", 3001, 9, 200), ("rademacher", 777, 64, 129),
+    ("srht", 1, 2, 1), ("srht", 100, 3, 40), ("srht", 1000, 65, 130), ("srht", 16384, 4, 300),
+    ("srht", 16385, 3, 300), ("srht", 70000, 2, 500), ("srht", 4096, 1, 4096),
+]
+
+
+@pytest.mark.parametrize("kind,n,c,k", SKETCH_CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sketch_matches_oracle(rb, kind, n, c, k, prec):
+    """Y = Theta X (Sec. 2.3) against the oracle's Theta X."""
+    seed = 1234 + n
+    X = synth.gaussian(n, c, seed=n + c)
+    if prec == "fp32":
+        X = X.astype(np.float32).astype(np.float64)
+    Y = host(rb.sketch_apply(dev(X, torch.float64 if prec == "fp64" else torch.float32), kind, k, seed, prec=prec))
+    Yr = oracle.theta_apply(kind, k, seed, X)
+    scale = np.linalg.norm(X, axis=0)[None, :] + 1e-300
+    err = np.abs(Y - Yr) / scale
+    tol = 1e-13 if prec == "fp64" else 3e-6
+    assert err.max() <= tol, f"max rel err {err.max():.3e}"
+
+
+# --------------------------------------------------------------- tall ops ---
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,c,mb", [(1, 0, 1), (129, 5, 3), (1000, 64, 16), (4097, 200, 50), (300, 0, 64)])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_tall_update_matches_numpy(rb, prec, n, c, mb, inplace):
+    """Qout = [Qprev | X] G, the fused step 3 + triangular solve of Alg. 5."""
+    rng = np.random.default_rng(n + c + mb)
+    Qp = rng.standard_normal((n, c))
+    X = rng.standard_normal((n, mb))
+    G = rng.standard_normal((c + mb, mb))
+    td = torch.float64 if prec == "fp64" else torch.float32
+    if prec == "fp32":
+        Qp = Qp.astype(np.float32).astype(np.float64)
+        X = X.astype(np.float32).astype(np.float64)
+    Qd = dev(Qp, td) if c > 0 else None
+    Xd = dev(X, td)
+    out = Xd if inplace else None
+    res = host(rb.tall_update(Qd, Xd, torch.from_numpy(G), prec=prec, out=out))
+    ref = np.hstack([Qp, X]) @ G
+    scale = np.abs(np.hstack([Qp, X])).sum(axis=1, keepdims=True) * np.abs(G).max() + 1e-300
+    tol = 1e-15 * (c + mb) if prec == "fp64" else 2e-7 * (c + mb)
+    assert (np.abs(res - ref) / scale).max() <= tol
+
+
+# ------------------------------------------------------------------ RBGS ----
+
+def _check_qr_against_oracle(rb, W, mb, kind, k, seed, l, reorth, cond, prec="fp64"):
+    td = torch.float64 if prec == "fp64" else torch.float32
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    Qd, Rd, st = rb.rbgs_qr(dev(W, td), mb, kind, k, seed, prec=prec, ls_iters=l, reorth=int(reorth), certify=True)
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, seed, variant=5, ls="richardson", ls_iters=l, reorth=reorth)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    fact = oracle.factorization_error(W, Q, R)
+    ortho = oracle.sketched_orthogonality(Q, kind, k, seed)[0]
+    return Q, R, ref, fact, ortho, st
+
+
+QR_CASES = [
+    # n, m, mb, kind, k
+    (3000, 32, 8, "gauss", 160),
+    (777, 12, 3, "rademacher", 60),
+    (5000, 64, 64, "gauss", 128),
+    (4096, 16, 1, "srht", 64),
+    (3000, 40, 10, "srht", 200),
+    (20000, 48, 16, "srht", 300),
+    (1000, 6, 2, "gauss", 6),
+]
+
+
+@pytest.mark.parametrize("n,m,mb,kind,k", QR_CASES)
+@pytest.mark.parametrize("reorth", [False, True])
+def test_rbgs_fp64_matches_oracle(rb, n, m, mb, kind, k, reorth):
+    cond = 1e4
+    W = synth.svd_matrix(n, m, cond, n + m)
+    Q, R, ref, fact, ortho, st = _check_qr_against_oracle(rb, W, mb, kind, k, 99, 3, reorth, cond)
+    tol = 1e-13 * cond
+    assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+    assert np.abs(Q - ref["Q"]).max() <= tol * np.abs(ref["Q"]).max()
+    assert fact < 1e-14
+    assert abs(st.delta - ref["delta"]) <= 1e-10 + 1e-3 * ref["delta"]
+    assert st.passes2 == (m // mb - 1 if reorth else 0)
+
+
+def test_c1_config_fp64(rb):
+    """n = 1e4, m = 100, m_p = 10, Gaussian k = 200, cond(W) = 1e8:
+    ||W - QR||/||W|| <= 1e-13 and sketched orthogonality <= 1e-12 with the
+    second pass; the single pass (Alg. 2 as written) loses ~u cond(W)."""
+    n, m, mb, k = 10_000, 100, 10, 200
+    W = synth.svd_matrix(n, m, 1e8, 7)
+    Q, R, ref, fact, ortho, st = _check_qr_against_oracle(rb, W, mb, "gauss", k, 1, 3, True, 1e8)
+    assert fact <= 1e-13
+    assert ortho <= 1e-12
+    assert np.linalg.norm(R - ref["R"]) <= 1e-7 * np.linalg.norm(ref["R"])
+    Q1, R1, ref1, fact1, ortho1, _ = _check_qr_against_oracle(rb, W, mb, "gauss", k, 1, 3, False, 1e8)
+    assert fact1 <= 1e-13
+    assert 1e-12 < ortho1 < 1e-5
+    assert abs(ortho1 - ref1["delta"]) <= 0.5 * ref1["delta"]
+
+
+@pytest.mark.parametrize("kind", ["gauss", "srht"])
+def test_rbgs_fp32_path(rb, kind):
+    """FP32 storage, SIMT FP32 tall product: errors at u_fp32 * cond level."""
+    n, m, mb, k = 6000, 48, 8, 240
+    cond = 1e3
+    W = synth.svd_matrix(n, m, cond, 3)
+    Q, R, ref, fact, ortho, st = _check_qr_against_oracle(rb, W, mb, kind, k, 5, 3, True, cond, prec="fp32")
+    assert fact < 1e-6
+    assert ortho < 1e-4
+    assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
+
+
+def test_breakdown_reported(rb):
+    """A zero block makes R_ii singular: the call reports RBGS_EBREAKDOWN
+    through its return code (no device fault)."""
+    W = synth.gaussian(500, 8, 1)
+    W[:, 4:] = 0.0
+    with pytest.raises(rb.RbgsError) as e:
+        rb.rbgs_qr(dev(W), 4, "gauss", 32, 0, prec="fp64")
+    assert e.value.code == 4
+
+
+def test_invalid_arguments(rb):
+    W = dev(synth.gaussian(100, 8, 1))
+    with pytest.raises(rb.RbgsError):
+        rb.rbgs_qr(W, 3, "gauss", 16, 0, prec="fp64")     # m % mb != 0
+    with pytest.raises(rb.RbgsError):
+        rb.rbgs_qr(W, 4, "gauss", 101, 0, prec="fp64")    # k > n
+    with pytest.raises(rb.RbgsError):
+        rb.rbgs_qr(W, 4, "srht", 129, 0, prec="fp64")     # k > n'
