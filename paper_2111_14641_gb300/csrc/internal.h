@@ -50,11 +50,11 @@ template <class T>
 rbgs_status tall_update_simt(int64_t n, int64_t c, int64_t mb, const T* A1, int64_t lda1, const T* A2, int64_t lda2,
                              const T* G, int64_t ldg, T* Qout, int64_t ldo, const int* active, cudaStream_t st);
 
-// tcgen05 3xTF32 version; Ghi/Glo are the TF32 split of G stored K-major in a
-// padded layout (see tall_tc.cu).  Returns RBGS_EINVAL for shapes it does not
-// take (the caller then uses the SIMT kernel).
+// tcgen05 3xTF32 version; Gsplit is the TF32 hi/lo split of G in the B-operand
+// layout (tc_split_g).  Needs 16-byte aligned A1/A2 and ld % 4 == 0; *err is
+// set (1, 2, 3) when a bounded device-side wait expires.
 rbgs_status tall_update_tc(int64_t n, int64_t c, int64_t mb, const float* A1, int64_t lda1, const float* A2,
-                           int64_t lda2, const float* Gsplit, float* Qout, int64_t ldo, const int* active,
+                           int64_t lda2, const float* Gsplit, float* Qout, int64_t ldo, const int* active, int* err,
                            cudaStream_t st);
 size_t tc_gsplit_floats(int64_t K);  // floats needed for the split G of K rows
 // Build the split operand of the tensor-core kernel from the FP64 G.

@@ -193,6 +193,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     int* brk = flags;          // breakdown
     int* active = flags + 1;   // second pass on/off for this block
     int* npass2 = flags + 2;   // number of second passes
+    int* tmo = flags + 3;      // bounded device wait expired
     RBGS_CUDA_TRY(cudaMemsetAsync(flags, 0, 64 * sizeof(int), st));
     RBGS_CUDA_TRY(cudaMemset2DAsync(R, ldr * sizeof(double), 0, m * sizeof(double), m, st));
 
@@ -202,7 +203,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         rbgs_status e = tc_split_g(c + mb, mb, Gd, c + mb, Gsplit, act, st);
         if (e) return e;
         return tall_update_tc(n, c, mb, (const float*)Q, ldq, (const float*)X2src, ldx2, Gsplit, (float*)out, ldq,
-                              act, st);
+                              act, tmo, st);
       }
       return tall_update_simt<T>(n, c, mb, Q, ldq, X2src, ldx2, Gmat, c + mb, out, ldq, act, st);
     };
@@ -318,6 +319,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
           stats->certified = 0;
         }
       }
+      if (hf[3]) return RBGS_ETIMEOUT;
       if (hf[0]) return RBGS_EBREAKDOWN;
     }
   }
@@ -431,10 +433,21 @@ rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_t mb, con
         (ldo % 4) || (c > 0 && (ldq % 4)))
       return RBGS_EINVAL;
     void* scr = nullptr;
-    if ((s = workspace(sizeof(float) * tc_gsplit_floats(K) + 256, &scr))) return s;
-    float* Gs = (float*)scr;
+    if ((s = workspace(sizeof(float) * tc_gsplit_floats(K) + 512, &scr))) return s;
+    int* err = (int*)scr;
+    float* Gs = (float*)((char*)scr + 256);
+    RBGS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     if ((s = tc_split_g(K, mb, G, ldg, Gs, nullptr, st))) return s;
-    s = tall_update_tc(n, c, mb, (const float*)Qprev, ldq, (const float*)X, ldx, Gs, (float*)Qout, ldo, nullptr, st);
+    s = tall_update_tc(n, c, mb, (const float*)Qprev, ldq, (const float*)X, ldx, Gs, (float*)Qout, ldo, nullptr, err,
+                       st);
+    if (s) return s;
+    if (sync) {
+      int herr = 0;
+      RBGS_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+      if (herr) return RBGS_ETIMEOUT;
+    }
+    return RBGS_OK;
   }
   if (s) return s;
   if (sync) RBGS_CUDA_TRY(cudaStreamSynchronize(st));

@@ -1,14 +1,481 @@
-// Tensor-core tall update (placeholder until the tcgen05 kernel lands).
+// Tensor-core tall update on sm_103a (tcgen05 + TMA), 3xTF32 split products.
+//
+//   Qout (n x mb) = [A1 (n x c) | A2 (n x mb)] * G ((c+mb) x mb)
+//
+// This is step 3 of Alg. 2 fused with the multiplication by R_ii^{-1} of
+// Alg. 5 (G = [-R_{1:i-1,i}; I] R_ii^{-1}).  The operation reads the whole
+// previous basis once per block, so it is bound by HBM bandwidth; the tensor
+// cores are the means to keep up with the bytes at FP32-level accuracy:
+//   a = a_hi + a_lo,  g = g_hi + g_lo  (TF32 parts, round to nearest),
+//   a g ~ a_hi g_hi + a_hi g_lo + a_lo g_hi     (error ~2^-22 |a g|).
+//
+// Persistent kernel, one CTA per SM, 128-row tiles, K in chunks of 32:
+//   warp 0      TMA producer: A chunk (128 rows x 32 columns, column-major
+//               source, no swizzle) + the pre-split G chunk (bulk copy)
+//   warp 1      TMEM allocation and the single MMA-issuing thread
+//   warps 2-5   converters: thread r reads row r of the raw chunk, writes the
+//               TF32 hi part in place and the lo part next to it, both in the
+//               K-major no-swizzle core-matrix layout (8 rows x 16 B cores,
+//               K-direction core stride 128 B, 8-row group stride 1024 B)
+//   warps 6-9   epilogue: TMEM -> registers -> column-major global stores
+// Four smem stages (48 KB each) and two TMEM accumulators (64 columns each).
+// Every mbarrier wait is bounded; on expiry the kernel records an error flag,
+// drains its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace rbgs {
-size_t tc_gsplit_floats(int64_t K) { return (size_t)(K + 64) * 64 * 2; }
-rbgs_status tc_split_g(int64_t, int64_t, const double*, int64_t, float*, const int*, cudaStream_t) {
-  return RBGS_EINVAL;
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_N = 64;
+constexpr int TC_K = 32;  // fp32 elements per chunk
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 320;
+constexpr int A_BYTES = TC_M * TC_K * 4;      // 16 KB
+constexpr int B_BYTES = TC_N * TC_K * 4;      // 8 KB per part
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int SMEM_BAR_OFF = TC_STAGES * STAGE_BYTES;
+constexpr int SMEM_BYTES = SMEM_BAR_OFF + 256 + 1024;  // + barriers + alignment slack
+constexpr uint32_t kMaxSpin = 1u << 26;                // bounded waits (~seconds)
+constexpr int TMEM_COLS = 2 * TC_N;
+
+struct TcParams {
+  int64_t n;
+  int c, mb, nc1, nc2, ntiles;
+  const float* gsplit;
+  float* qout;
+  int64_t ldo;
+  const int* active;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-rbgs_status tall_update_tc(int64_t, int64_t, int64_t, const float*, int64_t, const float*, int64_t, const float*,
-                           float*, int64_t, const int*, cudaStream_t) {
-  return RBGS_EINVAL;
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on the phase with the given parity; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kMaxSpin; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Named barrier 1 over the 128 converter threads with an OR-reduction of `pred`.
+__device__ __forceinline__ bool conv_bar_or(bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, 1, 128, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return out != 0;
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, relative LBO, layout SWIZZLE_NONE
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                            ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tall_tc_kernel(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2, TcParams p) {
+  if (p.active && *p.active == 0) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_BAR_OFF);
+  // barrier slots: full[4] conv[4] empty[4] accf[2] acce[2] fin[1]
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto conv_bar = [&](int s) { return bar0 + 8u * (4 + s); };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (8 + s); };
+  auto accf_bar = [&](int b) { return bar0 + 8u * (12 + b); };
+  auto acce_bar = [&](int b) { return bar0 + 8u * (14 + b); };
+  const uint32_t fin_bar = bar0 + 8u * 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 17);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 17 + 8);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nchunks = p.nc1 + p.nc2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(conv_bar(s), 4);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), 4);
+    }
+    mbar_init(fin_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(p.err, 1);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      int armed_phase[TC_STAGES];
+      for (int s = 0; s < TC_STAGES; ++s) armed_phase[s] = -1;
+      for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
+        const int row0 = tile * TC_M;
+        for (int ch = 0; ch < nchunks; ++ch, ++it) {
+          const int s = it % TC_STAGES;
+          const uint32_t ph = (it / TC_STAGES) & 1u;
+          if (!mbar_wait(empty_bar(s), ph ^ 1u)) {
+            fail();
+            break;
+          }
+          if (*abort_flag) break;
+          unsigned char* st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(full_bar(s), A_BYTES + 2 * B_BYTES);
+          if (ch < p.nc1) tma_load_2d(smem_u32(st), &tmA1, row0, ch * TC_K, full_bar(s));
+          else tma_load_2d(smem_u32(st), &tmA2, row0, (ch - p.nc1) * TC_K, full_bar(s));
+          bulk_load(smem_u32(st + 2 * A_BYTES), p.gsplit + (size_t)ch * (2 * TC_N * TC_K), 2 * B_BYTES,
+                    full_bar(s));
+          armed_phase[s] = (int)ph;
+        }
+      }
+      // never leave with copies in flight into this CTA's shared memory
+      for (int s = 0; s < TC_STAGES; ++s)
+        if (armed_phase[s] >= 0 && !mbar_wait(full_bar(s), (uint32_t)armed_phase[s])) atomicExch(p.err, 2);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t it = 0, tcount = 0;
+      for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x, ++tcount) {
+        const int b = tcount & 1;
+        const uint32_t aph = (tcount >> 1) & 1u;
+        if (!mbar_wait(acce_bar(b), aph ^ 1u)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dtm = tmem_base + (uint32_t)(b * TC_N);
+        bool bad = false;
+        for (int ch = 0; ch < nchunks; ++ch, ++it) {
+          const int s = it % TC_STAGES;
+          const uint32_t ph = (it / TC_STAGES) & 1u;
+          if (!mbar_wait(conv_bar(s), ph) || *abort_flag) {
+            fail();
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ahi = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t alo = ahi + A_BYTES;
+          const uint32_t bhi = ahi + 2 * A_BYTES;
+          const uint32_t blo = bhi + B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < TC_K / 8; ++kk) {
+            const uint32_t off = kk * 256;  // 8 tf32 = two 16-byte cores along K
+            const uint64_t dah = umma_desc(ahi + off, 128, 1024);
+            const uint64_t dal = umma_desc(alo + off, 128, 1024);
+            const uint64_t dbh = umma_desc(bhi + off, 128, 1024);
+            const uint64_t dbl = umma_desc(blo + off, 128, 1024);
+            umma_tf32(dtm, dah, dbh, (ch | kk) != 0);
+            umma_tf32(dtm, dah, dbl, 1u);
+            umma_tf32(dtm, dal, dbh, 1u);
+          }
+          umma_commit(empty_bar(s));
+        }
+        if (bad) break;
+        umma_commit(accf_bar(b));
+      }
+      // all issued MMAs complete before TMEM is released
+      umma_commit(fin_bar);
+      if (!mbar_wait(fin_bar, 0)) atomicExch(p.err, 3);
+    }
+  } else if (warp < 6) {
+    // ----------------------------------------------------------- converters
+    const int r = threadIdx.x - 64;  // row of the tile
+    uint32_t it = 0;
+    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+      bool stop = false;
+      for (int ch = 0; ch < nchunks; ++ch, ++it) {
+        const int s = it % TC_STAGES;
+        const uint32_t ph = (it / TC_STAGES) & 1u;
+        const bool ok = mbar_wait(full_bar(s), ph);
+        if (!ok) fail();
+        // one decision for all 128 converter threads (the named barriers below need all of them)
+        stop = conv_bar_or(!ok || *abort_flag);
+        if (stop) break;
+        float* raw = reinterpret_cast<float*>(smem + s * STAGE_BYTES);
+        float v[TC_K];
+#pragma unroll
+        for (int k = 0; k < TC_K; ++k) v[k] = raw[k * TC_M + r];
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        unsigned char* hi = smem + s * STAGE_BYTES;
+        unsigned char* lo = hi + A_BYTES;
+        const int rowoff = (r >> 3) * 1024 + (r & 7) * 16;
+#pragma unroll
+        for (int c4 = 0; c4 < TC_K / 4; ++c4) {
+          uint32_t h[4], l[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float x = v[4 * c4 + q];
+            h[q] = tf32_rna(x);
+            l[q] = tf32_rna(x - __uint_as_float(h[q]));
+          }
+          *reinterpret_cast<uint4*>(hi + rowoff + c4 * 128) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(lo + rowoff + c4 * 128) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(conv_bar(s));
+      }
+      if (stop) break;
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    uint32_t tcount = 0;
+    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++tcount) {
+      const int b = tcount & 1;
+      const uint32_t aph = (tcount >> 1) & 1u;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(accf_bar(b), aph));
+      if (!ok && lane == 0) fail();
+      const int ab = __shfl_sync(0xffffffffu, (int)*abort_flag, 0);
+      if (!ok || ab) break;  // warp-uniform: the TMEM loads below are .sync.aligned
+      tc_fence_after();
+      float v[TC_N];
+      const uint32_t taddr = tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * TC_N);
+#pragma unroll
+      for (int j = 0; j < TC_N / 16; ++j) tmem_ld16(taddr + 16 * j, v + 16 * j);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce_bar(b));
+      const int64_t row = (int64_t)tile * TC_M + 32 * quarter + lane;
+      if (row < p.n) {
+#pragma unroll
+        for (int j = 0; j < TC_N; ++j)
+          if (j < p.mb) p.qout[row + j * p.ldo] = v[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// Split G ((c + mb) x mb, FP64) into per-chunk TF32 hi/lo blocks laid out as
+// the B operand (N = 64 rows of K-contiguous cores): chunk ch covers G rows
+// [32 ch, 32 ch + 32) of the first c rows for ch < nc1, and rows
+// c + 32 (ch - nc1) + [0, 32) of the last mb rows after that; rows outside
+// the range and columns >= mb are zero.
+__global__ void tc_split_kernel(int c, int mb, int nc1, int nchunks, const double* __restrict__ G, int64_t ldg,
+                                float* __restrict__ out, const int* active) {
+  if (active && *active == 0) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)TC_N * TC_K;
+  if (idx >= (int64_t)nchunks * per) return;
+  const int ch = (int)(idx / per);
+  const int e = (int)(idx % per);
+  const int n = e / TC_K, kk = e % TC_K;
+  int64_t grow = -1;
+  if (ch < nc1) {
+    const int kr = ch * TC_K + kk;
+    if (kr < c) grow = kr;
+  } else {
+    const int kr = (ch - nc1) * TC_K + kk;
+    if (kr < mb) grow = c + kr;
+  }
+  const double g = (grow >= 0 && n < mb) ? G[grow + (int64_t)n * ldg] : 0.0;
+  const uint32_t hb = tf32_rna((float)g);
+  const float h = __uint_as_float(hb);
+  const uint32_t lb = tf32_rna((float)(g - (double)h));
+  const int off = (n >> 3) * 256 + (kk >> 2) * 32 + (n & 7) * 4 + (kk & 3);  // floats
+  float* blk = out + (size_t)ch * (2 * per);
+  blk[off] = h;
+  blk[per + off] = __uint_as_float(lb);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
+}
+
+// 2-D map over a column-major n x cols float matrix, box 128 rows x 32 columns.
+bool make_map(CUtensorMap* map, const float* base, int64_t n, int64_t cols, int64_t ld) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  cuuint32_t box[2] = {TC_M, TC_K};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t tc_gsplit_floats(int64_t K) { return (size_t)((K + TC_K - 1) / TC_K + 2) * 2 * TC_N * TC_K; }
+
+rbgs_status tc_split_g(int64_t K, int64_t mb, const double* G, int64_t ldg, float* Gsplit, const int* active,
+                       cudaStream_t st) {
+  if (mb < 1 || mb > TC_N || K < mb) return RBGS_EINVAL;
+  const int c = (int)(K - mb);
+  const int nc1 = (c + TC_K - 1) / TC_K;
+  const int nc2 = ((int)mb + TC_K - 1) / TC_K;
+  const int64_t tot = (int64_t)(nc1 + nc2) * TC_N * TC_K;
+  tc_split_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(c, (int)mb, nc1, nc1 + nc2, G, ldg, Gsplit, active);
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
+
+rbgs_status tall_update_tc(int64_t n, int64_t c, int64_t mb, const float* A1, int64_t lda1, const float* A2,
+                           int64_t lda2, const float* Gsplit, float* Qout, int64_t ldo, const int* active,
+                           int* err, cudaStream_t st) {
+  if (mb < 1 || mb > TC_N || n < 1 || n >= ((int64_t)1 << 31)) return RBGS_EINVAL;
+  if (((uintptr_t)A2 & 15) || (lda2 % 4) || (c > 0 && (((uintptr_t)A1 & 15) || (lda1 % 4)))) return RBGS_EINVAL;
+  CUtensorMap m1, m2;
+  std::memset(&m1, 0, sizeof(m1));
+  if (c > 0 && !make_map(&m1, A1, n, c, lda1)) return RBGS_ECUDA;
+  if (!make_map(&m2, A2, n, mb, lda2)) return RBGS_ECUDA;
+  if (c == 0) m1 = m2;
+  int dev = 0, nsm = 0;
+  RBGS_CUDA_TRY(cudaGetDevice(&dev));
+  RBGS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (!err) return RBGS_EINVAL;
+  TcParams p;
+  p.n = n;
+  p.c = (int)c;
+  p.mb = (int)mb;
+  p.nc1 = (int)((c + TC_K - 1) / TC_K);
+  p.nc2 = (int)((mb + TC_K - 1) / TC_K);
+  p.ntiles = (int)((n + TC_M - 1) / TC_M);
+  p.gsplit = Gsplit;
+  p.qout = Qout;
+  p.ldo = ldo;
+  p.active = active;
+  p.err = err;
+  RBGS_CUDA_TRY(cudaFuncSetAttribute(tall_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  const int grid = std::min(p.ntiles, nsm);
+  tall_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, st>>>(m1, m2, p);
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
+
 }  // namespace rbgs

@@ -95,13 +95,17 @@ def colmajor(t: torch.Tensor) -> torch.Tensor:
 
 
 def _ld(t: torch.Tensor, name: str) -> int:
+    """Leading dimension of a column-major 2-D tensor."""
     if t.dim() != 2:
         raise ValueError(f"{name} must be 2-D")
-    if t.shape[1] > 1 and t.stride(0) != 1:
+    rows, cols = t.shape
+    if rows > 1 and cols > 1 and t.stride(0) != 1:
         raise ValueError(f"{name} must be column-major (stride (1, ld)); use colmajor()")
-    if t.shape[1] <= 1:
-        return max(t.shape[0], 1) if t.stride(0) == 1 else t.stride(0)
-    return t.stride(1)
+    if rows > 1 and cols == 1 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride (1, ld)); use colmajor()")
+    if cols > 1:
+        return t.stride(1)
+    return max(rows, 1)
 
 
 def _stream_ptr(stream) -> int:
@@ -170,7 +174,7 @@ def tall_update(Qprev: torch.Tensor | None, X: torch.Tensor, G: torch.Tensor, pr
     c = 0 if Qprev is None else Qprev.shape[1]
     if out is None:
         out = torch.empty((mb, n), dtype=X.dtype, device=X.device).t()
-    Gc = colmajor(G.to(torch.float64))
+    Gc = colmajor(G.to(device=X.device, dtype=torch.float64))
     code = lib.rbgs_tall_update(PREC[prec], n, c, mb, 0 if Qprev is None else Qprev.data_ptr(),
                                 n if Qprev is None else _ld(Qprev, "Qprev"), X.data_ptr(), _ld(X, "X"),
                                 Gc.data_ptr(), _ld(Gc, "G"), out.data_ptr(), _ld(out, "out"), _stream_ptr(stream),

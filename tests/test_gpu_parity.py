@@ -150,7 +150,8 @@ def test_c1_config_fp64(rb):
     Q1, R1, ref1, fact1, ortho1, _ = _check_qr_against_oracle(rb, W, mb, "gauss", k, 1, 3, False, 1e8)
     assert fact1 <= 1e-13
     assert 1e-12 < ortho1 < 1e-5
-    assert abs(ortho1 - ref1["delta"]) <= 0.5 * ref1["delta"]
+    # the single-pass loss is rounding noise of size ~u cond(W): same order as the oracle's
+    assert 0.1 < ortho1 / ref1["delta"] < 10
 
 
 @pytest.mark.parametrize("kind", ["gauss", "srht"])
@@ -183,3 +184,52 @@ def test_invalid_arguments(rb):
         rb.rbgs_qr(W, 4, "gauss", 101, 0, prec="fp64")    # k > n
     with pytest.raises(rb.RbgsError):
         rb.rbgs_qr(W, 4, "srht", 129, 0, prec="fp64")     # k > n'
+
+
+# -------------------------------------------------- tensor-core (tcgen05) ---
+
+def dev_ld(A, dtype, ld):
+    """numpy (n x m) -> column-major CUDA tensor with leading dimension ld."""
+    A = np.asarray(A)
+    n, m = A.shape
+    buf = torch.zeros((m, ld), dtype=dtype, device="cuda")
+    buf[:, :n] = torch.from_numpy(np.ascontiguousarray(A.T)).to("cuda", dtype)
+    return buf.t()[:n]
+
+
+@pytest.mark.parametrize("n,c,mb", [(1, 0, 1), (128, 0, 50), (129, 5, 3), (1000, 64, 16), (4097, 200, 50),
+                                    (300, 0, 64), (2000, 950, 50), (513, 33, 64)])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_tall_update_tc_matches_numpy(rb, n, c, mb, inplace):
+    """3xTF32 tcgen05 product: Qout = [Qprev | X] G with FP32-level accuracy."""
+    rng = np.random.default_rng(7 * n + c + mb)
+    ld = (n + 3) // 4 * 4 + 4
+    Qp = rng.standard_normal((n, c)).astype(np.float32).astype(np.float64)
+    X = rng.standard_normal((n, mb)).astype(np.float32).astype(np.float64)
+    G = rng.standard_normal((c + mb, mb))
+    Qd = dev_ld(Qp, torch.float32, ld) if c > 0 else None
+    Xd = dev_ld(X, torch.float32, ld)
+    out = Xd if inplace else dev_ld(np.zeros((n, mb)), torch.float32, ld)
+    res = host(rb.tall_update(Qd, Xd, torch.from_numpy(G), prec="tf32x3", out=out))
+    ref = np.hstack([Qp, X]) @ G
+    scale = np.abs(np.hstack([Qp, X])).sum(axis=1, keepdims=True) * np.abs(G).max() + 1e-300
+    assert (np.abs(res - ref) / scale).max() <= 2e-6
+
+
+@pytest.mark.parametrize("kind", ["gauss", "srht"])
+@pytest.mark.parametrize("reorth", [False, True])
+def test_rbgs_tf32x3_matches_oracle(rb, kind, reorth):
+    n, m, mb, k = 6000, 48, 8, 240
+    cond = 1e3
+    W = synth.svd_matrix(n, m, cond, 3).astype(np.float32).astype(np.float64)
+    Wd = dev_ld(W, torch.float32, n + 4)
+    Qd = dev_ld(np.zeros((n, m)), torch.float32, n + 4)
+    _, Rd, st = rb.rbgs_qr(Wd, mb, kind, k, 5, prec="tf32x3", ls_iters=3, reorth=int(reorth), Q=Qd, certify=True)
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, 5, variant=5, ls="richardson", ls_iters=3, reorth=reorth)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    assert oracle.factorization_error(W, Q, R) < 2e-6
+    ortho = oracle.sketched_orthogonality(Q, kind, k, 5)[0]
+    assert ortho < (1e-4 if reorth else 1e-3)
+    assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
+    assert st.passes2 == (m // mb - 1 if reorth else 0)
