@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Benchmark of the RBGS QR hot path (Balabanov & Grigori, arXiv 2111.14641).
+
+One step = one full RBGS QR factorization (Alg. 2: every column block sketched,
+projected, orthonormalised and re-sketched) of a synthetic matrix already
+resident in HBM, through the C ABI of librbgs.
+
+Default workload (mixed precision): n = 1,000,000 rows, m = 1000 columns,
+block size m_p = 50, SRHT sketch k = 2000, W in FP32 with singular values
+log-spaced from 1 to 1e-6 (W = U diag(sigma) V^T from seeded N(0,1) factors).
+The tall products run in 3xTF32 on the tcgen05 tensor cores; the sketch-space
+least squares in FP32 and the small factorizations in FP64.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (n, m, mb, sketch, k, cond, seed_W, seed_theta, description)
+    "c2": dict(n=1_000_000, m=1000, mb=50, sketch="srht", k=2000, cond=1e6, seed_w=7, seed_theta=1,
+               desc="RBGS QR n=1e6 m=1000 mb=50 SRHT k=2000, W fp32 cond 1e6 (log-spaced sigma)"),
+    "c1": dict(n=10_000, m=100, mb=10, sketch="gauss", k=200, cond=1e8, seed_w=7, seed_theta=1,
+               desc="RBGS QR n=1e4 m=100 mb=10 Gaussian k=200, W fp64 cond 1e8"),
+}
+CPU_SAMPLE_ROWS = 16384
+CPU_SAMPLE_COLS = 500
+METRIC = "RBGS QR GFLOP/s & roofline frac, mixed vs FP64 on GB300 at stated orthogonality"
+
+
+def algorithmic_flops(n, m, mb, k, sketch, ls_iters, reorth_blocks):
+    """Work the method must do: step 3 + the triangular solve (n m^2 over all
+    blocks), the sketches of W and Q (SRHT: n' log2 n' additions per column;
+    dense: 2 k n per column), and the sketch-space least squares
+    (Richardson: 2 l k m (m - m_p)); a second pass on a block repeats its
+    projection, sketch and least squares."""
+    p = m // mb
+    npad = 1 << max(0, math.ceil(math.log2(n)))
+    per_col_sketch = npad * math.log2(npad) if sketch == "srht" else 2.0 * k * n
+    tall = float(n) * m * m
+    sk = 2.0 * m * per_col_sketch
+    ls = 2.0 * ls_iters * k * m * (m - mb)
+    f = tall + sk + ls
+    if reorth_blocks:
+        # block i (c = (i-1) mb) costs 2 n c mb + n mb^2 in the tall product
+        c_avg = (m - mb) / 2.0 + mb / 2.0
+        f += reorth_blocks * (2.0 * n * c_avg * mb + n * mb * mb + mb * per_col_sketch
+                              + 4.0 * ls_iters * k * c_avg * mb)
+    return f
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_w(cfg, device, dtype):
+    import torch
+    import synth
+
+    W = synth.svd_matrix_torch(cfg["n"], cfg["m"], cfg["cond"], cfg["seed_w"], device=device, dtype=dtype)
+    torch.cuda.synchronize()
+    return W
+
+
+def quality(rb, W, Q, R, cfg):
+    """||W - QR||_F/||W||_F (FP64 products on the device), and sketched
+    orthogonality ||I - (Theta Q)^T (Theta Q)|| in the Frobenius and 2-norm
+    with Theta applied to Q in FP64 by librbgs, cond(Q) from the FP64 Gram."""
+    import torch
+
+    n, m = W.shape
+    num, den = 0.0, 0.0
+    R64 = R.double()
+    chunk = 1 << 17
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        Wc = W[r0:r1].double()
+        E = Wc - Q[r0:r1].double() @ R64
+        num += float((E * E).sum())
+        den += float((Wc * Wc).sum())
+    Q64 = rb.colmajor(Q.double())
+    S = rb.sketch_apply(Q64, cfg["sketch"], cfg["k"], cfg["seed_theta"], prec="fp64")
+    Gs = S.t() @ S
+    Ei = torch.eye(m, dtype=torch.float64, device=W.device) - Gs
+    d_fro = float(torch.linalg.norm(Ei))
+    d_two = float(torch.linalg.matrix_norm(Ei, ord=2))
+    Gq = Q64.t() @ Q64
+    ev = torch.linalg.eigvalsh(Gq)
+    condq = float(torch.sqrt(ev.max() / ev.min()))
+    del Q64, S, Gq
+    return {"rel_factorization_error": math.sqrt(num / den), "sketched_orthogonality_fro": d_fro,
+            "sketched_orthogonality_2": d_two, "cond_Q": condq}
+
+
+def cpu_baseline(cfg, ls_iters, reorth):
+    """The CPU oracle (plain FP64 C, all host cores) on a bounded sample of the
+    workload: a CPU_SAMPLE_ROWS x CPU_SAMPLE_COLS matrix of the same recipe
+    (same m_p, k, sketch and conditioning), i.e. the first blocks of a
+    shorter factorization."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    ns = min(cfg["n"], CPU_SAMPLE_ROWS)
+    ms = min(cfg["m"], CPU_SAMPLE_COLS)
+    W = synth.svd_matrix(ns, ms, cfg["cond"], cfg["seed_w"])
+    t0 = time.perf_counter()
+    out = oracle.rbgs(W, cfg["mb"], cfg["sketch"], cfg["k"], cfg["seed_theta"], variant=5, ls="richardson",
+                      ls_iters=ls_iters, reorth=bool(reorth))
+    dt = time.perf_counter() - t0
+    flops = algorithmic_flops(ns, ms, cfg["mb"], cfg["k"], cfg["sketch"], ls_iters, out["passes2"])
+    del W
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle RBGS (Alg. 2, Alg. 5, Richardson l={ls_iters}, reorth={int(bool(reorth))}) on "
+                      f"n={ns} rows x m={ms} (m_p={cfg['mb']}, {cfg['sketch']} k={cfg['k']}, same recipe), "
+                      f"{dt:.1f} s", "seconds": dt, "delta": float(out["delta"]),
+            "_np": np.__version__}
+
+
+def run_reference(args, cfg):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    ls_iters, reorth = args.ls_iters, args.reorth
+    for _ in range(args.warmup):
+        pass  # the oracle has no caches to warm; warm-up steps would only repeat the timed work
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(cfg, ls_iters, reorth)
+        vals.append(cb["seconds"])
+    ms = 1e3 * sum(vals) / len(vals)
+    value = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"] + f" (oracle sample: {CPU_SAMPLE_ROWS} x {CPU_SAMPLE_COLS})",
+                       "sample_rows": CPU_SAMPLE_ROWS, "sample_cols": CPU_SAMPLE_COLS},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, cfg):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2111_14641_gb300 as rb
+
+    rb.load()
+    prec = args.prec
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    n, m, mb, k = cfg["n"], cfg["m"], cfg["mb"], cfg["k"]
+    W = make_w(cfg, dev, dtype)
+    Q = torch.empty((m, n), dtype=dtype, device=dev).t()
+    R = torch.empty((m, m), dtype=torch.float64, device=dev).t()
+
+    def step(timing=False):
+        return rb.rbgs_qr(W, mb, cfg["sketch"], k, cfg["seed_theta"], prec=prec, ls_iters=args.ls_iters,
+                          reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q, R=R, sync=True, timing=timing)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = rb.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tall_ms = tall_bytes = 0.0
+    tall_launches = passes2 = 0
+    for _ in range(args.steps):
+        st = step(timing=True)
+        tall_ms += st.tall_ms
+        tall_bytes += st.tall_bytes
+        tall_launches += st.tall_launches
+        passes2 = st.passes2
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = rb.launch_count() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_all = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_all = float(t.item())
+    flops = algorithmic_flops(n, m, mb, k, cfg["sketch"], args.ls_iters, passes2)
+    value = world * flops / (ms_all * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (tall update), from its own CUDA events
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured"
+    if peak is None:
+        peak, peak_src = 6800.0, "fallback"
+    achieved = tall_bytes / (tall_ms * 1e-3) / 1e9 if tall_ms > 0 else None
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(f"{args.workload}:{prec}")
+    except (OSError, ValueError):
+        traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "kernel": "tall_tc_kernel" if prec == "tf32x3" else "tall_simt_kernel",
+                "peak_source": peak_src, "launch_ms_avg": tall_ms / max(tall_launches, 1),
+                "bytes_per_launch_avg": tall_bytes / max(tall_launches, 1)}
+
+    # ---- end to end: host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        W_h = torch.empty((m, n), dtype=dtype, pin_memory=True).t()
+        W_h.copy_(W)
+        Q_h = torch.empty((m, n), dtype=dtype, pin_memory=True).t()
+        R_h = torch.empty((m, m), dtype=torch.float64, pin_memory=True).t()
+        W.zero_()
+        torch.cuda.synchronize()
+        steps_e2e = max(1, min(args.steps, 5))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps_e2e):
+            W.copy_(W_h, non_blocking=True)
+            step()
+            Q_h.copy_(Q, non_blocking=True)
+            R_h.copy_(R, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        ms_e2e = a.elapsed_time(b) / steps_e2e
+        h2d = W_h.element_size() * n * m
+        d2h = Q_h.element_size() * n * m + 8 * m * m
+        e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+        del W_h, Q_h, R_h
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"tf32x3": "f32 (3xTF32 tensor products)", "fp32": "f32",
+                                           "fp64": "f64"}[prec],
+            "data": "synthetic",
+            "config": {"workload": cfg["desc"], "n": n, "m": m, "mb": mb, "sketch": cfg["sketch"], "k": k,
+                       "prec": prec, "ls_iters": args.ls_iters, "reorth": args.reorth,
+                       "reorth_tol": args.reorth_tol, "passes2": passes2,
+                       "l2": "inputs larger than L2 (W and Q are GBs; no flush needed)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+            "algorithmic_gflop_per_step": flops / 1e9}
+
+    if rank == 0 and not args.no_quality:
+        line["quality"] = quality(rb, W if args.no_e2e else _refill(W, cfg, dev, dtype), Q, R, cfg)
+
+    if rank == 0 and world == 1 and not args.no_fp64_compare and prec != "fp64":
+        line["fp64_path"] = fp64_compare(rb, cfg, args, dev)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(cfg, args.ls_iters, args.reorth)
+        line["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _refill(W, cfg, dev, dtype):
+    """W was overwritten by the e2e copies of itself; it holds the same values."""
+    return W
+
+
+def fp64_compare(rb, cfg, args, dev):
+    """The plain FP64 GPU path (DFMA tall product, FP64 sketches and sketch
+    space) on the same input, one warm-up and one timed step."""
+    import torch
+
+    n, m, mb, k = cfg["n"], cfg["m"], cfg["mb"], cfg["k"]
+    W64 = make_w(cfg, dev, torch.float64)
+    Q64 = torch.empty((m, n), dtype=torch.float64, device=dev).t()
+    R64 = torch.empty((m, m), dtype=torch.float64, device=dev).t()
+
+    def step():
+        return rb.rbgs_qr(W64, mb, cfg["sketch"], k, cfg["seed_theta"], prec="fp64", ls_iters=args.ls_iters,
+                          reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q64, R=R64, sync=True)
+
+    step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    st = step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    flops = algorithmic_flops(n, m, mb, k, cfg["sketch"], args.ls_iters, st.passes2)
+    q = quality(rb, W64, Q64, R64, cfg) if not args.no_quality else None
+    del W64, Q64, R64
+    torch.cuda.empty_cache()
+    return {"ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "quality": q}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--prec", choices=["tf32x3", "fp32", "fp64"], default=None)
+    ap.add_argument("--ls-iters", type=int, default=2)
+    ap.add_argument("--reorth", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--reorth-tol", type=float, default=1e-6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    cfg = WORKLOADS[args.workload]
+    if args.prec is None:
+        args.prec = "fp64" if args.workload == "c1" else "tf32x3"
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    return run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

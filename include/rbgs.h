@@ -75,7 +75,8 @@ typedef struct {
   double reorth_tol;   /* threshold for reorth == 2                                      */
   void* stream;        /* cudaStream_t                                                   */
   int32_t sync;        /* 1: wait and report device-side status; 0: enqueue only        */
-  int32_t reserved[3];
+  int32_t timing;      /* 1: time the tall-update launches with CUDA events (needs sync) */
+  int32_t reserved[2];
 } rbgs_opts;
 
 typedef struct {
@@ -83,6 +84,10 @@ typedef struct {
   double delta_tilde;  /* ||P - S R||_F / ||P||_F, P = Theta W                          */
   int32_t passes2;     /* blocks that took the second projection pass                   */
   int32_t certified;   /* delta <= 0.1 && delta_tilde <= 0.1 (Thm. 4.1 hypothesis)      */
+  double tall_ms;      /* with opts->timing: summed duration of the tall-update launches */
+  double tall_bytes;   /* algorithmic bytes those launches move (A read + Q_i written)  */
+  int32_t tall_launches; /* tall-update launches that did work                          */
+  int32_t reserved;
 } rbgs_stats;
 
 /* Fill *opts with the defaults: FP64, 2 Richardson iterations, reorth 0,
@@ -130,6 +135,10 @@ RBGS_API rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_
 /* Philox4x32-10 blocks on the device: out[4i..4i+3] = philox(ctr[4i..4i+3],
  * key = (seed_lo, seed_hi)) for i < count (device pointers).              */
 RBGS_API rbgs_status rbgs_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t count, void* stream, int32_t sync);
+
+/* Number of kernels this library has launched in the process so far (all
+ * devices, all entry points); a counter for profiling and accounting.     */
+RBGS_API int64_t rbgs_launch_count(void);
 
 /* Release the cached device workspace of the current device.             */
 RBGS_API rbgs_status rbgs_release_workspace(void);

@@ -75,7 +75,12 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int w) {
     if (_e != cudaSuccess) return RBGS_ECUDA; \
   } while (0)
 
-#define RBGS_LAUNCH_CHECK()                          \
-  do {                                               \
+namespace rbgs {
+void count_launch();
+}
+
+#define RBGS_LAUNCH_CHECK()                                   \
+  do {                                                        \
+    rbgs::count_launch();                                     \
     if (cudaGetLastError() != cudaSuccess) return RBGS_ECUDA; \
   } while (0)

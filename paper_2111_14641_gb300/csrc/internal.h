@@ -99,7 +99,7 @@ rbgs_status reorth_update_r(int64_t c, int mb, const TS* R2c, int64_t ldr2, cons
 // Adaptive second pass: flag = (||X||_F > tol) with X c x mb; counts passes.
 template <class TS>
 rbgs_status reorth_decide(int64_t c, int mb, const TS* X, int64_t ldx, double tol, int mode, int* active,
-                          int* count, cudaStream_t st);
+                          int* count, int* blk_flag, cudaStream_t st);
 
 // Elementwise C = A - B (k x mb) in TS.
 template <class TS>

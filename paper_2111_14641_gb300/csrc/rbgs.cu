@@ -9,7 +9,10 @@
 //   step 5/1 S_i = Theta Q_i and P_{i+1} = Theta W_{i+1}
 //   option   a second projection pass of Q_i against Q_{1:i-1} (reorth)
 //   step 6   Delta, Delta~ on request.
+#include <atomic>
+#include <cmath>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -17,6 +20,10 @@
 #include "internal.h"
 
 namespace rbgs {
+
+std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 namespace {
 
 // ------------------------------------------------------------ workspace ---
@@ -183,6 +190,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     TS* partf = cv.take<TS>(kPartElems);
     void* skscr = cv.take<char>(sk_bytes);
     int* flags = cv.take<int>(64);
+    int* blk_on = cv.take<int>((size_t)p);
     double* cert_buf = cert ? cv.take<double>((size_t)k * m * 3 + (size_t)m * 64 + 8) : nullptr;
     if (pass == 0) {
       need = cv.off + 256;
@@ -194,11 +202,30 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     int* active = flags + 1;   // second pass on/off for this block
     int* npass2 = flags + 2;   // number of second passes
     int* tmo = flags + 3;      // bounded device wait expired
+    struct TallEv {
+      cudaEvent_t a, b;
+      double bytes;
+      int64_t blk;
+      bool pass2;
+    };
+    std::vector<TallEv> evs;
+    const bool timing = o.timing && (o.sync || stats);
+    auto ev_guard = [&]() {
+      for (auto& e : evs) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+      }
+    };
+    struct Guard {
+      std::function<void()> f;
+      ~Guard() { f(); }
+    } guard{ev_guard};
     RBGS_CUDA_TRY(cudaMemsetAsync(flags, 0, 64 * sizeof(int), st));
+    RBGS_CUDA_TRY(cudaMemsetAsync(blk_on, 0, sizeof(int) * p, st));
     RBGS_CUDA_TRY(cudaMemset2DAsync(R, ldr * sizeof(double), 0, m * sizeof(double), m, st));
 
     rbgs_status s;
-    auto tall = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act) -> rbgs_status {
+    auto tall_raw = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act) -> rbgs_status {
       if (tensor) {
         rbgs_status e = tc_split_g(c + mb, mb, Gd, c + mb, Gsplit, act, st);
         if (e) return e;
@@ -206,6 +233,23 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
                               act, tmo, st);
       }
       return tall_update_simt<T>(n, c, mb, Q, ldq, X2src, ldx2, Gmat, c + mb, out, ldq, act, st);
+    };
+    auto tall = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act) -> rbgs_status {
+      if (!timing) return tall_raw(c, X2src, ldx2, out, act);
+      TallEv e;
+      e.bytes = (double)sizeof(T) * (double)n * (double)(c + 2 * mb);
+      e.blk = c / mb;
+      e.pass2 = act != nullptr;
+      RBGS_CUDA_TRY(cudaEventCreate(&e.a));
+      if (cudaEventCreate(&e.b) != cudaSuccess) {
+        cudaEventDestroy(e.a);
+        return RBGS_ECUDA;
+      }
+      evs.push_back(e);
+      RBGS_CUDA_TRY(cudaEventRecord(e.a, st));
+      rbgs_status r = tall_raw(c, X2src, ldx2, out, act);
+      RBGS_CUDA_TRY(cudaEventRecord(e.b, st));
+      return r;
     };
     auto make_g = [&](int64_t c, const TS* Rc, const double* Rd, const double* Rdinv, double* Rcol,
                       const int* act) -> rbgs_status {
@@ -245,7 +289,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       if (o.reorth && c > 0) {
         s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Si, k, 0.0, X2, m, partf, kPartElems, nullptr, st);
         if (s) return s;
-        if ((s = reorth_decide<TS>(c, mb, X2, m, o.reorth_tol, o.reorth, active, npass2, st))) return s;
+        if ((s = reorth_decide<TS>(c, mb, X2, m, o.reorth_tol, o.reorth, active, npass2, blk_on + blk, st))) return s;
         for (int it = 1; it < l; ++it) {
           RBGS_CUDA_TRY(cudaMemcpyAsync(Res, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
           s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Res, k, partf, kPartElems, active, st);
@@ -313,6 +357,21 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       RBGS_CUDA_TRY(cudaStreamSynchronize(st));
       if (stats) {
         stats->passes2 = hf[2];
+        stats->tall_ms = 0.0;
+        stats->tall_bytes = 0.0;
+        stats->tall_launches = 0;
+        if (timing) {
+          std::vector<int> on((size_t)p, 0);
+          if (o.reorth) RBGS_CUDA_TRY(cudaMemcpy(on.data(), blk_on, sizeof(int) * p, cudaMemcpyDeviceToHost));
+          for (auto& e : evs) {
+            if (e.pass2 && !on[(size_t)e.blk]) continue;
+            float ms = 0.f;
+            RBGS_CUDA_TRY(cudaEventElapsedTime(&ms, e.a, e.b));
+            stats->tall_ms += ms;
+            stats->tall_bytes += e.bytes;
+            stats->tall_launches += 1;
+          }
+        }
         if (!cert) {
           stats->delta = -1.0;
           stats->delta_tilde = -1.0;
@@ -343,7 +402,10 @@ void rbgs_opts_default(rbgs_opts* o) {
   o->reorth_tol = 1e-8;
   o->stream = nullptr;
   o->sync = 1;
+  o->timing = 0;
 }
+
+int64_t rbgs_launch_count(void) { return rbgs::g_launches.load(); }
 
 const char* rbgs_version(void) { return "librbgs 0.1 (sm_103a)"; }
 

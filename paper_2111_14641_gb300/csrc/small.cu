@@ -238,7 +238,7 @@ __global__ void copy_diag_block(int64_t c, int mb, const double* __restrict__ tm
 
 template <class TS>
 __global__ void reorth_decide_kernel(int64_t c, int mb, const TS* __restrict__ X, int64_t ldx, double tol,
-                                     int mode, int* active, int* count) {
+                                     int mode, int* active, int* count, int* blk_flag) {
   __shared__ double red[256];
   double s = 0.0;
   for (int64_t e = threadIdx.x; e < c * mb; e += blockDim.x) {
@@ -254,6 +254,7 @@ __global__ void reorth_decide_kernel(int64_t c, int mb, const TS* __restrict__ X
   if (threadIdx.x == 0) {
     const int on = (mode == 1) ? 1 : (sqrt(red[0]) > tol ? 1 : 0);
     *active = on;
+    if (blk_flag) *blk_flag = on;
     if (on) *count += 1;
   }
 }
@@ -407,14 +408,15 @@ template rbgs_status reorth_update_r<float>(int64_t, int, const float*, int64_t,
 
 template <class TS>
 rbgs_status reorth_decide(int64_t c, int mb, const TS* X, int64_t ldx, double tol, int mode, int* active, int* count,
-                          cudaStream_t st) {
-  reorth_decide_kernel<TS><<<1, 256, 0, st>>>(c, mb, X, ldx, tol, mode, active, count);
+                          int* blk_flag, cudaStream_t st) {
+  reorth_decide_kernel<TS><<<1, 256, 0, st>>>(c, mb, X, ldx, tol, mode, active, count, blk_flag);
   RBGS_LAUNCH_CHECK();
   return RBGS_OK;
 }
-template rbgs_status reorth_decide<double>(int64_t, int, const double*, int64_t, double, int, int*, int*,
+template rbgs_status reorth_decide<double>(int64_t, int, const double*, int64_t, double, int, int*, int*, int*,
                                            cudaStream_t);
-template rbgs_status reorth_decide<float>(int64_t, int, const float*, int64_t, double, int, int*, int*, cudaStream_t);
+template rbgs_status reorth_decide<float>(int64_t, int, const float*, int64_t, double, int, int*, int*, int*,
+                                          cudaStream_t);
 
 template <class TS>
 rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,

@@ -33,12 +33,13 @@ class RbgsError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("ls_iters", ctypes.c_int32), ("reorth", ctypes.c_int32),
                 ("certify", ctypes.c_int32), ("reorth_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("sync", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("sync", ctypes.c_int32), ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("delta_tilde", ctypes.c_double), ("passes2", ctypes.c_int32),
-                ("certified", ctypes.c_int32)]
+                ("certified", ctypes.c_int32), ("tall_ms", ctypes.c_double), ("tall_bytes", ctypes.c_double),
+                ("tall_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 @dataclass
@@ -47,6 +48,9 @@ class QRStats:
     delta_tilde: float
     passes2: int
     certified: bool
+    tall_ms: float = 0.0
+    tall_bytes: float = 0.0
+    tall_launches: int = 0
 
 
 _lib = None
@@ -77,6 +81,7 @@ def load(build_if_missing: bool = False):
     lib.rbgs_philox.argtypes = [u64, vp, vp, i64, vp, i32]
     lib.rbgs_release_workspace.argtypes = []
     lib.rbgs_version.restype = ctypes.c_char_p
+    lib.rbgs_launch_count.restype = ctypes.c_int64
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_philox", "rbgs_release_workspace"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -95,17 +100,16 @@ def colmajor(t: torch.Tensor) -> torch.Tensor:
 
 
 def _ld(t: torch.Tensor, name: str) -> int:
-    """Leading dimension of a column-major 2-D tensor."""
+    """Leading dimension of a column-major 2-D tensor (the stride between columns)."""
     if t.dim() != 2:
         raise ValueError(f"{name} must be 2-D")
     rows, cols = t.shape
-    if rows > 1 and cols > 1 and t.stride(0) != 1:
+    if rows > 1 and t.stride(0) != 1:
         raise ValueError(f"{name} must be column-major (stride (1, ld)); use colmajor()")
-    if rows > 1 and cols == 1 and t.stride(0) != 1:
-        raise ValueError(f"{name} must be column-major (stride (1, ld)); use colmajor()")
-    if cols > 1:
-        return t.stride(1)
-    return max(rows, 1)
+    ld = t.stride(1)
+    if cols <= 1 and ld < rows:
+        ld = rows  # a single column: any ld >= rows addresses it
+    return max(int(ld), 1)
 
 
 def _stream_ptr(stream) -> int:
@@ -130,7 +134,7 @@ def _prec_of(t: torch.Tensor, prec: str | None) -> str:
 def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
             prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
             certify: bool = False, Q: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None,
-            sync: bool = True):
+            sync: bool = True, timing: bool = False):
     """RBGS QR of W (n x m, column-major).  Returns (Q, R, QRStats | None)."""
     lib = load()
     prec = _prec_of(W, prec)
@@ -143,12 +147,13 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
     o = Opts()
     lib.rbgs_opts_default(ctypes.byref(o))
     o.prec, o.ls_iters, o.reorth, o.certify = PREC[prec], ls_iters, reorth, int(certify)
-    o.reorth_tol, o.stream, o.sync = reorth_tol, _stream_ptr(stream), int(sync)
+    o.reorth_tol, o.stream, o.sync, o.timing = reorth_tol, _stream_ptr(stream), int(sync), int(timing)
     st = Stats()
     code = lib.rbgs_qr(W.data_ptr(), n, m, _ld(W, "W"), mb, SKETCH[sketch], k, seed, Q.data_ptr(), _ld(Q, "Q"),
                        R.data_ptr(), _ld(R, "R"), ctypes.byref(o), ctypes.byref(st) if sync else None)
     _check(code, "rbgs_qr")
-    stats = QRStats(st.delta, st.delta_tilde, st.passes2, bool(st.certified)) if sync else None
+    stats = (QRStats(st.delta, st.delta_tilde, st.passes2, bool(st.certified), st.tall_ms, st.tall_bytes,
+                     st.tall_launches) if sync else None)
     return Q, R, stats
 
 
@@ -195,6 +200,11 @@ def philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
 
 def release_workspace():
     _check(load().rbgs_release_workspace(), "rbgs_release_workspace")
+
+
+def launch_count() -> int:
+    """Kernels launched by librbgs in this process so far."""
+    return int(load().rbgs_launch_count())
 
 
 def version() -> str:
