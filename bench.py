@@ -241,7 +241,7 @@ def run_ours(args, cfg):
 
     def step(timing=False):
         return rb.rbgs_qr(W, mb, cfg["sketch"], k, cfg["seed_theta"], prec=prec, ls_iters=args.ls_iters,
-                          reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q, R=R, sync=True, timing=timing)
+                          reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q, R=R, sync=True, timing=timing)[2]
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -374,7 +374,7 @@ def fp64_compare(rb, cfg, args, dev):
 
     def step():
         return rb.rbgs_qr(W64, mb, cfg["sketch"], k, cfg["seed_theta"], prec="fp64", ls_iters=args.ls_iters,
-                          reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q64, R=R64, sync=True)
+                          reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q64, R=R64, sync=True)[2]
 
     step()
     torch.cuda.synchronize()

@@ -70,30 +70,33 @@ rbgs_status small_gemm(int trans, int64_t M, int64_t N, int64_t K, double alpha,
                        const TA* B, int64_t ldb, double beta, TO* out, int64_t ldo, TACC* part, int64_t part_elems,
                        const int* active, cudaStream_t st);
 
-// Cholesky G = R^T R (upper R, positive diagonal) of an mb x mb FP64 matrix and
-// R^{-1}; sets *flag |= 1 on a non-positive or non-finite pivot.
-rbgs_status chol_inv(int mb, const double* G, double* R, double* Rinv, int* flag, const int* active, cudaStream_t st);
+// Cholesky G (+ shift * trace(G) I) = R^T R (upper R, positive diagonal) of an
+// mb x mb matrix and R^{-1}, in the arithmetic of T; sets *flag |= 1 on a
+// non-positive or non-finite pivot.
+template <class T>
+rbgs_status chol_inv(int mb, const T* G, T* R, T* Rinv, double shift, int* flag, const int* active, cudaStream_t st);
 
-// A (k x mb, lda) <- A * U (U upper mb x mb FP64, ldu = mb).
+// Out (k x mb, ldo) = A (k x mb, lda) * U (U upper mb x mb, ld mb).
 template <class TS>
-rbgs_status trmm_right_upper(int64_t k, int mb, TS* A, int64_t lda, const double* U, const int* active,
-                             cudaStream_t st);
+rbgs_status trmm_right_upper(int64_t k, int mb, const TS* A, int64_t lda, const TS* U, TS* Out, int64_t ldo,
+                             const int* active, cudaStream_t st);
 
-// C (mb x mb) = A * B for upper-triangular FP64 mb x mb matrices (ld mb).
-rbgs_status tri_mul(int mb, const double* A, const double* B, double* C, const int* active, cudaStream_t st);
+// C (mb x mb) = A * B for upper-triangular mb x mb matrices (ld mb).
+template <class T>
+rbgs_status tri_mul(int mb, const T* A, const T* B, T* C, const int* active, cudaStream_t st);
 
 // Coefficient matrix of the fused projection + triangular solve and the R
 // column block:  G = [-Rc * Rii^{-1} ; Rii^{-1}]  ((c+mb) x mb, ldg), written
 // as TG; when `R` is non-null also R[0:c, col] = Rc, R[c:c+mb, col] = Rii.
 template <class TS, class TG>
-rbgs_status assemble_g(int64_t c, int mb, const TS* Rc, int64_t ldrc, const double* Rii, const double* Riinv,
+rbgs_status assemble_g(int64_t c, int mb, const TS* Rc, int64_t ldrc, const TS* Rii, const TS* Riinv,
                        TG* G, int64_t ldg, double* R, int64_t ldr, const int* active, cudaStream_t st);
 
 // Second-pass update of the R column block:
 //   R[0:c, col] += R2c * Rii_old ;  R[c:c+mb, col] = R2ii * Rii_old
 // with Rii_old read from R[c:c+mb, col] (upper part).
 template <class TS>
-rbgs_status reorth_update_r(int64_t c, int mb, const TS* R2c, int64_t ldr2, const double* R2ii, double* Rcol,
+rbgs_status reorth_update_r(int64_t c, int mb, const TS* R2c, int64_t ldr2, const TS* R2ii, double* Rcol,
                             int64_t ldr, double* tmp, const int* active, cudaStream_t st);
 
 // Adaptive second pass: flag = (||X||_F > tol) with X c x mb; counts passes.

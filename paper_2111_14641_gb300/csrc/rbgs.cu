@@ -119,20 +119,26 @@ bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) 
   return pa < pb + bbytes && pb < pa + abytes;
 }
 
-// Cholesky QR twice of Sp (k x mb, in place):  R = R2 R1, Rinv = R1^{-1} R2^{-1}.
+// Cholesky QR twice of Sp (k x mb):  R = R2 R1, Rinv = R1^{-1} R2^{-1}, all in
+// the sketch-space arithmetic TS.  The first round of the FP32 path factors the
+// Gram matrix with a small diagonal shift so that it cannot break down on a
+// nearly rank-deficient block; the second round removes the shift's effect.
+// Sp2 is a k x mb scratch for Sp R1^{-1}.
 template <class TS>
-rbgs_status cholqr2(int64_t k, int mb, TS* Sp, double* gram, double* R1, double* R1inv, double* R2, double* R2inv,
-                    double* R, double* Rinv, double* part, int* flag, const int* active, cudaStream_t st) {
+rbgs_status cholqr2(int64_t k, int mb, const TS* Sp, TS* Sp2, TS** sm, TS* part, int* flag, const int* active,
+                    cudaStream_t st, TS* R, TS* Rinv) {
+  TS *gram = sm[0], *R1 = sm[1], *R1inv = sm[2], *R2 = sm[3], *R2inv = sm[4];
+  const double shift = sizeof(TS) == 4 ? 1e-6 : 0.0;
   rbgs_status s;
-  s = small_gemm<TS, double, double>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
+  s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
   if (s) return s;
-  if ((s = chol_inv(mb, gram, R1, R1inv, flag, active, st))) return s;
-  if ((s = trmm_right_upper<TS>(k, mb, Sp, k, R1inv, active, st))) return s;
-  s = small_gemm<TS, double, double>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
+  if ((s = chol_inv<TS>(mb, gram, R1, R1inv, shift, flag, active, st))) return s;
+  if ((s = trmm_right_upper<TS>(k, mb, Sp, k, R1inv, Sp2, k, active, st))) return s;
+  s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp2, k, Sp2, k, 0.0, gram, mb, part, kPartElems, active, st);
   if (s) return s;
-  if ((s = chol_inv(mb, gram, R2, R2inv, flag, active, st))) return s;
-  if ((s = tri_mul(mb, R2, R1, R, active, st))) return s;
-  if ((s = tri_mul(mb, R1inv, R2inv, Rinv, active, st))) return s;
+  if ((s = chol_inv<TS>(mb, gram, R2, R2inv, 0.0, flag, active, st))) return s;
+  if ((s = tri_mul<TS>(mb, R2, R1, R, active, st))) return s;
+  if ((s = tri_mul<TS>(mb, R1inv, R2inv, Rinv, active, st))) return s;
   return RBGS_OK;
 }
 
@@ -181,8 +187,9 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     TS* X2 = cv.take<TS>((size_t)m * mb);
     TS* Res = cv.take<TS>((size_t)k * mb);
     TS* Sp = cv.take<TS>((size_t)k * mb);
-    double* sm[12];
-    for (auto& q : sm) q = cv.take<double>(64 * 64);
+    TS* sm[12];
+    for (auto& q : sm) q = cv.take<TS>(64 * 64);
+    double* tmp = cv.take<double>(64 * 64);
     T* Gmat = cv.take<T>((size_t)m * mb);
     double* Gd = tensor ? cv.take<double>((size_t)m * mb) : nullptr;
     float* Gsplit = tensor ? cv.take<float>(tc_gsplit_floats(m)) : nullptr;
@@ -196,8 +203,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       need = cv.off + 256;
       continue;
     }
-    double *gram = sm[0], *R1 = sm[1], *R1inv = sm[2], *R2 = sm[3], *R2inv = sm[4], *Rii = sm[5], *Riinv = sm[6],
-           *R2ii = sm[7], *R2iinv = sm[8], *tmp = sm[9];
+    TS *Rii = sm[5], *Riinv = sm[6], *R2ii = sm[7], *R2iinv = sm[8];
     int* brk = flags;          // breakdown
     int* active = flags + 1;   // second pass on/off for this block
     int* npass2 = flags + 2;   // number of second passes
@@ -251,7 +257,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       RBGS_CUDA_TRY(cudaEventRecord(e.b, st));
       return r;
     };
-    auto make_g = [&](int64_t c, const TS* Rc, const double* Rd, const double* Rdinv, double* Rcol,
+    auto make_g = [&](int64_t c, const TS* Rc, const TS* Rd, const TS* Rdinv, double* Rcol,
                       const int* act) -> rbgs_status {
       if (tensor) return assemble_g<TS, double>(c, mb, Rc, m, Rd, Rdinv, Gd, c + mb, Rcol, ldr, act, st);
       return assemble_g<TS, T>(c, mb, Rc, m, Rd, Rdinv, Gmat, c + mb, Rcol, ldr, act, st);
@@ -275,7 +281,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       } else {
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
       }
-      if ((s = cholqr2<TS>(k, mb, Sp, gram, R1, R1inv, R2, R2inv, Rii, Riinv, part, brk, nullptr, st))) return s;
+      if ((s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, nullptr, st, Rii, Riinv))) return s;
       if ((s = make_g(c, X, Rii, Riinv, Rcol, nullptr))) return s;
       // step 3 fused with the triangular solve
       if ((s = tall(c, Wi, ldw, Qi, nullptr))) return s;
@@ -300,7 +306,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
         s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Sp, k, partf, kPartElems, active, st);
         if (s) return s;
-        if ((s = cholqr2<TS>(k, mb, Sp, gram, R1, R1inv, R2, R2inv, R2ii, R2iinv, part, brk, active, st))) return s;
+        if ((s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, active, st, R2ii, R2iinv))) return s;
         if ((s = make_g(c, X2, R2ii, R2iinv, nullptr, active))) return s;
         if ((s = tall(c, Qi, ldq, Qi, active))) return s;
         if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st, active))) return s;

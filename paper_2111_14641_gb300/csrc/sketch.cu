@@ -163,7 +163,10 @@ __device__ __forceinline__ void fwht_stage(TC* buf, int B, int lo) {
 }
 
 // Stage 1: grid (T, ncols).  z[(col * T + t) * L + l] = [H_B (D x)_t]_{lvals[l]}.
-template <class TX, class TC>
+// Thread t holds the E = B / 512 entries j = t + 512 e: their loads are all in
+// flight together, the transform over the top log2(E) index bits runs in
+// registers, the remaining 9 bits in two shared-memory stages.
+template <class TX, class TC, int E>
 __global__ void __launch_bounds__(kSrhtThreads) srht_stage1(const TX* __restrict__ X, int64_t ldx, int64_t n, int B,
                                                             int logB, int T, uint2 key,
                                                             const int* __restrict__ lvals, int L,
@@ -174,24 +177,49 @@ __global__ void __launch_bounds__(kSrhtThreads) srht_stage1(const TX* __restrict
   uint32_t* sgn = reinterpret_cast<uint32_t*>(buf + B);
   const int t = blockIdx.x;
   const int col = blockIdx.y;
+  const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)t * B;
+  const TX* xc = X + (int64_t)col * ldx;
+  TC v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = tid + kSrhtThreads * e;
+    const int64_t gr = row0 + j;
+    v[e] = (j < B && gr < n) ? (TC)__ldg(xc + gr) : (TC)0;
+  }
   const int nwords = (B + 31) >> 5;
-  for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+  for (int w = tid; w < nwords; w += blockDim.x) {
     const int64_t e0 = row0 + 32 * (int64_t)w;
     const uint4 bits = srht_sign_bits(key, (uint32_t)(e0 >> 7));
     sgn[w] = word_of(bits, (int)((e0 >> 5) & 3));
   }
   __syncthreads();
-  const TX* xc = X + (int64_t)col * ldx;
-  for (int j = threadIdx.x; j < B; j += blockDim.x) {
-    const int64_t gr = row0 + j;
-    TC v = gr < n ? (TC)xc[gr] : (TC)0;
-    if ((sgn[j >> 5] >> (j & 31)) & 1u) v = -v;
-    buf[swz(j)] = v;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = tid + kSrhtThreads * e;
+    if (j < B && ((sgn[j >> 5] >> (j & 31)) & 1u)) v[e] = -v[e];
   }
-  for (int lo = 0; lo < logB; lo += 5) {
+  // index bits 9 .. logB-1 live in e
+#pragma unroll
+  for (int h = 1; h < E; h <<= 1) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((e & h) == 0) {
+        const TC a = v[e], b = v[e + h];
+        v[e] = a + b;
+        v[e + h] = a - b;
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = tid + kSrhtThreads * e;
+    if (j < B) buf[swz(j)] = v[e];
+  }
+  const int lowbits = logB < 9 ? logB : 9;
+  for (int lo = 0; lo < lowbits; lo += 5) {
     __syncthreads();
-    const int r = min(5, logB - lo);
+    const int r = min(5, lowbits - lo);
     switch (r) {
       case 5: fwht_stage<TC, 5>(buf, B, lo); break;
       case 4: fwht_stage<TC, 4>(buf, B, lo); break;
@@ -202,7 +230,29 @@ __global__ void __launch_bounds__(kSrhtThreads) srht_stage1(const TX* __restrict
   }
   __syncthreads();
   TC* zo = z + ((int64_t)col * T + t) * L;
-  for (int l = threadIdx.x; l < L; l += blockDim.x) zo[l] = buf[swz(lvals[l])];
+  for (int l = tid; l < L; l += blockDim.x) zo[l] = buf[swz(lvals[l])];
+}
+
+template <class TX, class TC>
+rbgs_status launch_stage1(dim3 grid, size_t smem, cudaStream_t st, const TX* X, int64_t ldx, int64_t n, int B,
+                          int logB, int T, uint2 key, const int* lvals, int L, TC* z, const int* active) {
+  const int E = B >= kSrhtThreads ? B / kSrhtThreads : 1;
+  auto go = [&](auto kern) -> rbgs_status {
+    RBGS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(TC) * kSrhtTile + 4 * kSrhtTile / 32)));
+    kern<<<grid, kSrhtThreads, smem, st>>>(X, ldx, n, B, logB, T, key, lvals, L, z, active);
+    RBGS_LAUNCH_CHECK();
+    return RBGS_OK;
+  };
+  switch (E) {
+    case 1: return go(srht_stage1<TX, TC, 1>);
+    case 2: return go(srht_stage1<TX, TC, 2>);
+    case 4: return go(srht_stage1<TX, TC, 4>);
+    case 8: return go(srht_stage1<TX, TC, 8>);
+    case 16: return go(srht_stage1<TX, TC, 16>);
+    case 32: return go(srht_stage1<TX, TC, 32>);
+    default: return RBGS_EINVAL;
+  }
 }
 
 // Stage 2: Y[r, col] = scale * sum_t (-1)^{popcount(rhi[r] & t)} z[col, t, rl[r]].
@@ -362,15 +412,12 @@ rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed
     int logB = 0;
     while ((1 << logB) < plan->B) ++logB;
     const size_t smem = sizeof(TC) * (size_t)plan->B + sizeof(uint32_t) * (size_t)((plan->B + 31) / 32);
-    RBGS_CUDA_TRY(cudaFuncSetAttribute(srht_stage1<TX, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(TC) * kSrhtTile + 4 * kSrhtTile / 32)));
     for (int64_t c0 = 0; c0 < ncols; c0 += 65535) {
       const int64_t nc = std::min<int64_t>(65535, ncols - c0);
       dim3 grid((unsigned)plan->T, (unsigned)nc);
-      srht_stage1<TX, TC><<<grid, kSrhtThreads, smem, st>>>(X + c0 * ldx, ldx, n, plan->B, logB, plan->T, key,
-                                                           plan->d_lvals, plan->L, z + c0 * plan->T * plan->L,
-                                                           active);
-      RBGS_LAUNCH_CHECK();
+      rbgs_status e = launch_stage1<TX, TC>(grid, smem, st, X + c0 * ldx, ldx, n, plan->B, logB, plan->T, key,
+                                            plan->d_lvals, plan->L, z + c0 * plan->T * plan->L, active);
+      if (e) return e;
     }
     const int64_t tot = k * ncols;
     srht_stage2<TC, TY><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(z, plan->T, plan->L, plan->d_rhi,

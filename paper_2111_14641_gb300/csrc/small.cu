@@ -95,94 +95,120 @@ __global__ void small_gemm_reduce(int64_t M, int N, int ks, const TACC* __restri
 }
 
 // ---------------------------------------------------------------- Cholesky --
-__global__ void chol_inv_kernel(int mb, const double* __restrict__ G, double* __restrict__ R,
-                                double* __restrict__ Rinv, int* flag, const int* active) {
+// G = R^T R (upper R, positive diagonal) of an mb x mb matrix, mb <= 64, and
+// R^{-1}, in the arithmetic of T, one CTA of 256 threads.  With shift != 0 the
+// factorization is of G + s I, s = shift * trace(G) (the shifted Cholesky QR
+// of Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020: keeps the first
+// round of Cholesky QR from breaking down on ill-conditioned blocks).
+template <class T>
+__global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restrict__ G, T* __restrict__ R,
+                                                       T* __restrict__ Rinv, double shift, int* flag,
+                                                       const int* active) {
   if (active && *active == 0) return;
-  __shared__ double Rs[64][65];
-  const int t = threadIdx.x;  // column index l
-  for (int e = t; e < mb * mb; e += blockDim.x) {
+  __shared__ T A[64][65];
+  __shared__ T X[64][65];
+  __shared__ T rinv_s;
+  __shared__ int bad_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < mb * mb; e += nt) {
     const int i = e % mb, l = e / mb;
-    Rs[i][l] = (i <= l) ? G[i + l * mb] : 0.0;
+    A[i][l] = (i <= l) ? G[i + l * mb] : (T)0;
   }
+  if (tid == 0) bad_s = 0;
   __syncthreads();
-  int bad = 0;
+  if (shift != 0.0) {
+    if (tid == 0) {
+      double tr = 0.0;
+      for (int i = 0; i < mb; ++i) tr += (double)A[i][i];
+      rinv_s = (T)(shift * tr);
+    }
+    __syncthreads();
+    if (tid < mb) A[tid][tid] += rinv_s;
+    __syncthreads();
+  }
   for (int j = 0; j < mb; ++j) {
-    // pivot: d = G_jj - sum_{i<j} R_ij^2 (kept in Rs[j][j] as it is updated)
-    if (t == 0) {
-      double d = Rs[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = 1;
-        d = 1.0;
+    if (tid == 0) {
+      T d = A[j][j];
+      if (!(d > (T)0) || !isfinite((double)d)) {
+        bad_s = 1;
+        d = (T)1;
       }
-      Rs[j][j] = sqrt(d);
+      const T r = sqrt(d);
+      A[j][j] = r;
+      rinv_s = (T)1 / r;
     }
     __syncthreads();
-    if (t > j && t < mb) Rs[j][t] /= Rs[j][j];
+    for (int l = j + 1 + tid; l < mb; l += nt) A[j][l] *= rinv_s;
     __syncthreads();
-    // trailing update: Rs[i][l] -= R_ji R_jl for j < i <= l
-    for (int e = t; e < mb * mb; e += blockDim.x) {
-      const int i = e % mb, l = e / mb;
-      if (i > j && i <= l) Rs[i][l] -= Rs[j][i] * Rs[j][l];
+    const int w = mb - j - 1;
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = j + 1 + e % w, l = j + 1 + e / w;
+      if (i <= l) A[i][l] -= A[j][i] * A[j][l];
     }
     __syncthreads();
   }
-  if (t == 0 && bad && flag) atomicOr(flag, 1);
-  for (int e = t; e < mb * mb; e += blockDim.x) {
+  // inverse, rows from the bottom: X[i][l] = (delta_il - sum_{t=i+1}^{l} R[i][t] X[t][l]) / R[i][i]
+  for (int e = tid; e < mb * mb; e += nt) X[e % mb][e / mb] = (T)0;
+  __syncthreads();
+  for (int i = mb - 1; i >= 0; --i) {
+    const T di = (T)1 / A[i][i];
+    for (int l = i + tid; l < mb; l += nt) {
+      T s = (l == i) ? (T)1 : (T)0;
+      for (int t = i + 1; t <= l; ++t) s -= A[i][t] * X[t][l];
+      X[i][l] = s * di;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < mb * mb; e += nt) {
     const int i = e % mb, l = e / mb;
-    R[i + l * mb] = (i <= l) ? Rs[i][l] : 0.0;
+    R[i + l * mb] = (i <= l) ? A[i][l] : (T)0;
+    Rinv[i + l * mb] = (i <= l) ? X[i][l] : (T)0;
   }
-  // inverse of the upper factor: column l solves R x = e_l by back substitution
-  if (t < mb) {
-    const int l = t;
-    double x[64];
-#pragma unroll 1
-    for (int i = mb - 1; i >= 0; --i) {
-      double s = (i == l) ? 1.0 : 0.0;
-      if (i <= l) {
-        for (int q = i + 1; q <= l; ++q) s -= Rs[i][q] * x[q];
-        x[i] = s / Rs[i][i];
-      } else {
-        x[i] = 0.0;
-      }
-    }
-    for (int i = 0; i < mb; ++i) Rinv[i + l * mb] = x[i];
-  }
+  if (tid == 0 && bad_s && flag) atomicOr(flag, 1);
 }
 
-template <class TS>
-__global__ void trmm_kernel(int64_t k, int mb, TS* A, int64_t lda, const double* __restrict__ U,
-                            const int* active) {
+// Out = A * U (A k x mb, U upper mb x mb): one thread per output entry.
+template <class TS, class TU>
+__global__ void trmm_kernel(int64_t k, int mb, const TS* __restrict__ A, int64_t lda, const TU* __restrict__ U,
+                            TS* __restrict__ Out, int64_t ldo, const int* active) {
   if (active && *active == 0) return;
-  __shared__ TS Us[64][64];
+  __shared__ TS Us[64][65];
   for (int e = threadIdx.x; e < mb * mb; e += blockDim.x) {
     const int i = e % mb, l = e / mb;
     Us[i][l] = (TS)U[i + l * mb];
   }
   __syncthreads();
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= k) return;
-  // in place, columns from the last: A[r][j] = sum_{i<=j} A[r][i] U[i][j]
-  for (int j = mb - 1; j >= 0; --j) {
-    TS s = 0;
-    for (int i = 0; i <= j; ++i) s += A[r + i * lda] * Us[i][j];
-    A[r + j * lda] = s;
-  }
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * mb) return;
+  const int64_t r = idx % k;
+  const int j = (int)(idx / k);
+  TS s = 0;
+  for (int i = 0; i <= j; ++i) s += A[r + i * lda] * Us[i][j];
+  Out[r + j * ldo] = s;
 }
 
-__global__ void tri_mul_kernel(int mb, const double* __restrict__ A, const double* __restrict__ B, double* C,
-                               const int* active) {
+// C = A * B for upper-triangular mb x mb matrices (ld mb).
+template <class T>
+__global__ void tri_mul_kernel(int mb, const T* __restrict__ A, const T* __restrict__ B, T* C, const int* active) {
   if (active && *active == 0) return;
+  __shared__ T As[64][65], Bs[64][65];
   for (int e = threadIdx.x; e < mb * mb; e += blockDim.x) {
     const int i = e % mb, j = e / mb;
-    double s = 0.0;
-    for (int t = i; t <= j; ++t) s += A[i + t * mb] * B[t + j * mb];
-    C[i + j * mb] = (i <= j) ? s : 0.0;
+    As[i][j] = A[i + j * mb];
+    Bs[i][j] = B[i + j * mb];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < mb * mb; e += blockDim.x) {
+    const int i = e % mb, j = e / mb;
+    T s = 0;
+    for (int t = i; t <= j; ++t) s += As[i][t] * Bs[t][j];
+    C[i + j * mb] = (i <= j) ? s : (T)0;
   }
 }
 
 template <class TS, class TG>
 __global__ void assemble_g_kernel(int64_t c, int mb, const TS* __restrict__ Rc, int64_t ldrc,
-                                  const double* __restrict__ Rii, const double* __restrict__ Riinv, TG* G,
+                                  const TS* __restrict__ Rii, const TS* __restrict__ Riinv, TG* G,
                                   int64_t ldg, double* R, int64_t ldr, const int* active) {
   if (active && *active == 0) return;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -193,20 +219,20 @@ __global__ void assemble_g_kernel(int64_t c, int mb, const TS* __restrict__ Rc, 
   double g;
   if (i < c) {
     double s = 0.0;
-    for (int t = 0; t <= j; ++t) s += (double)Rc[i + t * ldrc] * Riinv[t + j * mb];
+    for (int t = 0; t <= j; ++t) s += (double)Rc[i + t * ldrc] * (double)Riinv[t + j * mb];
     g = -s;
     if (R) R[i + (int64_t)j * ldr] = (double)Rc[i + (int64_t)j * ldrc];
   } else {
     const int ii = (int)(i - c);
-    g = (ii <= j) ? Riinv[ii + j * mb] : 0.0;
-    if (R) R[i + (int64_t)j * ldr] = (ii <= j) ? Rii[ii + j * mb] : 0.0;
+    g = (ii <= j) ? (double)Riinv[ii + j * mb] : 0.0;
+    if (R) R[i + (int64_t)j * ldr] = (ii <= j) ? (double)Rii[ii + j * mb] : 0.0;
   }
   G[i + (int64_t)j * ldg] = (TG)g;
 }
 
 template <class TS>
 __global__ void reorth_r_top(int64_t c, int mb, const TS* __restrict__ R2c, int64_t ldr2,
-                             const double* __restrict__ R2ii, double* Rcol, int64_t ldr, double* tmp,
+                             const TS* __restrict__ R2ii, double* Rcol, int64_t ldr, double* tmp,
                              const int* active) {
   if (active && *active == 0) return;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,7 +248,7 @@ __global__ void reorth_r_top(int64_t c, int mb, const TS* __restrict__ R2c, int6
   } else {
     const int ii = (int)(i - c);
     double s = 0.0;
-    for (int t = ii; t <= j; ++t) s += R2ii[ii + t * mb] * Rold[t + (int64_t)j * ldr];
+    for (int t = ii; t <= j; ++t) s += (double)R2ii[ii + t * mb] * Rold[t + (int64_t)j * ldr];
     tmp[ii + j * mb] = (ii <= j) ? s : 0.0;
   }
 }
@@ -239,12 +265,13 @@ __global__ void copy_diag_block(int64_t c, int mb, const double* __restrict__ tm
 template <class TS>
 __global__ void reorth_decide_kernel(int64_t c, int mb, const TS* __restrict__ X, int64_t ldx, double tol,
                                      int mode, int* active, int* count, int* blk_flag) {
-  __shared__ double red[256];
+  __shared__ double red[1024];
   double s = 0.0;
-  for (int64_t e = threadIdx.x; e < c * mb; e += blockDim.x) {
-    const double v = (double)X[(e % c) + (e / c) * ldx];
-    s += v * v;
-  }
+  for (int j = 0; j < mb; ++j)
+    for (int64_t i = threadIdx.x; i < c; i += blockDim.x) {
+      const double v = (double)X[i + j * ldx];
+      s += v * v;
+    }
   red[threadIdx.x] = s;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
@@ -348,35 +375,43 @@ INST_SG(float, float, float)
 INST_SG(float, double, double)
 #undef INST_SG
 
-rbgs_status chol_inv(int mb, const double* G, double* R, double* Rinv, int* flag, const int* active,
+template <class T>
+rbgs_status chol_inv(int mb, const T* G, T* R, T* Rinv, double shift, int* flag, const int* active,
                      cudaStream_t st) {
   if (mb < 1 || mb > 64) return RBGS_EINVAL;
-  chol_inv_kernel<<<1, 64, 0, st>>>(mb, G, R, Rinv, flag, active);
+  chol_inv_kernel<T><<<1, 256, 0, st>>>(mb, G, R, Rinv, shift, flag, active);
   RBGS_LAUNCH_CHECK();
   return RBGS_OK;
 }
+template rbgs_status chol_inv<double>(int, const double*, double*, double*, double, int*, const int*, cudaStream_t);
+template rbgs_status chol_inv<float>(int, const float*, float*, float*, double, int*, const int*, cudaStream_t);
 
 template <class TS>
-rbgs_status trmm_right_upper(int64_t k, int mb, TS* A, int64_t lda, const double* U, const int* active,
-                             cudaStream_t st) {
+rbgs_status trmm_right_upper(int64_t k, int mb, const TS* A, int64_t lda, const TS* U, TS* Out, int64_t ldo,
+                             const int* active, cudaStream_t st) {
   if (mb < 1 || mb > 64) return RBGS_EINVAL;
   if (k == 0) return RBGS_OK;
-  trmm_kernel<TS><<<(unsigned)((k + 127) / 128), 128, 0, st>>>(k, mb, A, lda, U, active);
+  const int64_t tot = k * mb;
+  trmm_kernel<TS, TS><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(k, mb, A, lda, U, Out, ldo, active);
   RBGS_LAUNCH_CHECK();
   return RBGS_OK;
 }
-template rbgs_status trmm_right_upper<double>(int64_t, int, double*, int64_t, const double*, const int*,
-                                              cudaStream_t);
-template rbgs_status trmm_right_upper<float>(int64_t, int, float*, int64_t, const double*, const int*, cudaStream_t);
+template rbgs_status trmm_right_upper<double>(int64_t, int, const double*, int64_t, const double*, double*, int64_t,
+                                              const int*, cudaStream_t);
+template rbgs_status trmm_right_upper<float>(int64_t, int, const float*, int64_t, const float*, float*, int64_t,
+                                             const int*, cudaStream_t);
 
-rbgs_status tri_mul(int mb, const double* A, const double* B, double* C, const int* active, cudaStream_t st) {
-  tri_mul_kernel<<<1, 256, 0, st>>>(mb, A, B, C, active);
+template <class T>
+rbgs_status tri_mul(int mb, const T* A, const T* B, T* C, const int* active, cudaStream_t st) {
+  tri_mul_kernel<T><<<1, 256, 0, st>>>(mb, A, B, C, active);
   RBGS_LAUNCH_CHECK();
   return RBGS_OK;
 }
+template rbgs_status tri_mul<double>(int, const double*, const double*, double*, const int*, cudaStream_t);
+template rbgs_status tri_mul<float>(int, const float*, const float*, float*, const int*, cudaStream_t);
 
 template <class TS, class TG>
-rbgs_status assemble_g(int64_t c, int mb, const TS* Rc, int64_t ldrc, const double* Rii, const double* Riinv, TG* G,
+rbgs_status assemble_g(int64_t c, int mb, const TS* Rc, int64_t ldrc, const TS* Rii, const TS* Riinv, TG* G,
                        int64_t ldg, double* R, int64_t ldr, const int* active, cudaStream_t st) {
   const int64_t tot = (c + mb) * mb;
   assemble_g_kernel<TS, TG><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(c, mb, Rc, ldrc, Rii, Riinv, G, ldg, R,
@@ -386,13 +421,13 @@ rbgs_status assemble_g(int64_t c, int mb, const TS* Rc, int64_t ldrc, const doub
 }
 template rbgs_status assemble_g<double, double>(int64_t, int, const double*, int64_t, const double*, const double*,
                                                 double*, int64_t, double*, int64_t, const int*, cudaStream_t);
-template rbgs_status assemble_g<float, double>(int64_t, int, const float*, int64_t, const double*, const double*,
+template rbgs_status assemble_g<float, double>(int64_t, int, const float*, int64_t, const float*, const float*,
                                                double*, int64_t, double*, int64_t, const int*, cudaStream_t);
-template rbgs_status assemble_g<float, float>(int64_t, int, const float*, int64_t, const double*, const double*,
+template rbgs_status assemble_g<float, float>(int64_t, int, const float*, int64_t, const float*, const float*,
                                               float*, int64_t, double*, int64_t, const int*, cudaStream_t);
 
 template <class TS>
-rbgs_status reorth_update_r(int64_t c, int mb, const TS* R2c, int64_t ldr2, const double* R2ii, double* Rcol,
+rbgs_status reorth_update_r(int64_t c, int mb, const TS* R2c, int64_t ldr2, const TS* R2ii, double* Rcol,
                             int64_t ldr, double* tmp, const int* active, cudaStream_t st) {
   const int64_t tot = (c + mb) * mb;
   reorth_r_top<TS><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(c, mb, R2c, ldr2, R2ii, Rcol, ldr, tmp, active);
@@ -403,13 +438,13 @@ rbgs_status reorth_update_r(int64_t c, int mb, const TS* R2c, int64_t ldr2, cons
 }
 template rbgs_status reorth_update_r<double>(int64_t, int, const double*, int64_t, const double*, double*, int64_t,
                                              double*, const int*, cudaStream_t);
-template rbgs_status reorth_update_r<float>(int64_t, int, const float*, int64_t, const double*, double*, int64_t,
+template rbgs_status reorth_update_r<float>(int64_t, int, const float*, int64_t, const float*, double*, int64_t,
                                             double*, const int*, cudaStream_t);
 
 template <class TS>
 rbgs_status reorth_decide(int64_t c, int mb, const TS* X, int64_t ldx, double tol, int mode, int* active, int* count,
                           int* blk_flag, cudaStream_t st) {
-  reorth_decide_kernel<TS><<<1, 256, 0, st>>>(c, mb, X, ldx, tol, mode, active, count, blk_flag);
+  reorth_decide_kernel<TS><<<1, 1024, 0, st>>>(c, mb, X, ldx, tol, mode, active, count, blk_flag);
   RBGS_LAUNCH_CHECK();
   return RBGS_OK;
 }

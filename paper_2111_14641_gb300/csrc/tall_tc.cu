@@ -10,15 +10,20 @@
 //   a g ~ a_hi g_hi + a_hi g_lo + a_lo g_hi     (error ~2^-22 |a g|).
 //
 // Persistent kernel, one CTA per SM, 128-row tiles, K in chunks of 32:
-//   warp 0      TMA producer: A chunk (128 rows x 32 columns, column-major
-//               source, no swizzle) + the pre-split G chunk (bulk copy)
+//   warp 0      TMA producer of the raw ring: A chunk (128 rows x 32 columns
+//               of the column-major source, no swizzle, 16 KB), 6 stages
 //   warp 1      TMEM allocation and the single MMA-issuing thread
-//   warps 2-5   converters: thread r reads row r of the raw chunk, writes the
-//               TF32 hi part in place and the lo part next to it, both in the
-//               K-major no-swizzle core-matrix layout (8 rows x 16 B cores,
-//               K-direction core stride 128 B, 8-row group stride 1024 B)
-//   warps 6-9   epilogue: TMEM -> registers -> column-major global stores
-// Four smem stages (48 KB each) and two TMEM accumulators (64 columns each).
+//   warp 2      bulk-copy producer of the pre-split G chunk (hi + lo, 16 KB)
+//               into the converted ring, 2 stages
+//   warps 3-6   converters: thread r reads row r of a raw chunk (the raw stage
+//               is released as soon as it is read), writes the TF32 hi and lo
+//               parts into the converted ring in the K-major no-swizzle
+//               core-matrix layout (8 rows x 16 B cores, K-direction core
+//               stride 128 B, 8-row group stride 1024 B)
+//   warps 7-10  epilogue: TMEM -> registers -> column-major global stores
+// The raw ring decouples HBM reads from MMA progress: up to 96 KB of A per SM
+// are in flight.  Two TMEM accumulators (64 columns each) overlap the
+// epilogue of one tile with the main loop of the next.
 // Every mbarrier wait is bounded; on expiry the kernel records an error flag,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -37,12 +42,14 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_N = 64;
 constexpr int TC_K = 32;  // fp32 elements per chunk
-constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 320;
+constexpr int RAW_STAGES = 6;   // TMA destinations (raw fp32 chunks)
+constexpr int CV_STAGES = 2;    // converted operands (A hi/lo + G hi/lo) for the MMA
+constexpr int TC_THREADS = 352; // 11 warps
 constexpr int A_BYTES = TC_M * TC_K * 4;      // 16 KB
 constexpr int B_BYTES = TC_N * TC_K * 4;      // 8 KB per part
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BAR_OFF = TC_STAGES * STAGE_BYTES;
+constexpr int CV_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int CV_OFF = RAW_STAGES * A_BYTES;
+constexpr int SMEM_BAR_OFF = CV_OFF + CV_STAGES * CV_BYTES;
 constexpr int SMEM_BYTES = SMEM_BAR_OFF + 256 + 1024;  // + barriers + alignment slack
 constexpr uint32_t kMaxSpin = 1u << 26;                // bounded waits (~seconds)
 constexpr int TMEM_COLS = 2 * TC_N;
@@ -103,17 +110,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
-// Named barrier 1 over the 128 converter threads with an OR-reduction of `pred`.
-__device__ __forceinline__ bool conv_bar_or(bool pred) {
-  uint32_t out;
-  asm volatile(
-      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, 1, 128, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
-      : "=r"(out)
-      : "r"((uint32_t)pred)
-      : "memory");
-  return out != 0;
-}
-
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -171,26 +167,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_BAR_OFF);
-  // barrier slots: full[4] conv[4] empty[4] accf[2] acce[2] fin[1]
+  // barrier slots: raw_full[6] raw_empty[6] cv_full[2] cv_bfull[2] cv_free[2] accf[2] acce[2] fin[1]
   const uint32_t bar0 = smem_u32(bars);
-  auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto conv_bar = [&](int s) { return bar0 + 8u * (4 + s); };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (8 + s); };
-  auto accf_bar = [&](int b) { return bar0 + 8u * (12 + b); };
-  auto acce_bar = [&](int b) { return bar0 + 8u * (14 + b); };
-  const uint32_t fin_bar = bar0 + 8u * 16;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 17);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 17 + 8);
+  auto raw_full = [&](int s) { return bar0 + 8u * s; };
+  auto raw_empty = [&](int s) { return bar0 + 8u * (6 + s); };
+  auto cv_full = [&](int s) { return bar0 + 8u * (12 + s); };
+  auto cv_bfull = [&](int s) { return bar0 + 8u * (14 + s); };
+  auto cv_free = [&](int s) { return bar0 + 8u * (16 + s); };
+  auto accf_bar = [&](int b) { return bar0 + 8u * (18 + b); };
+  auto acce_bar = [&](int b) { return bar0 + 8u * (20 + b); };
+  const uint32_t fin_bar = bar0 + 8u * 22;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 23);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 23 + 8);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int nchunks = p.nc1 + p.nc2;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
-      mbar_init(full_bar(s), 1);
-      mbar_init(conv_bar(s), 4);
-      mbar_init(empty_bar(s), 1);
+    for (int s = 0; s < RAW_STAGES; ++s) {
+      mbar_init(raw_full(s), 1);
+      mbar_init(raw_empty(s), 4);
+    }
+    for (int s = 0; s < CV_STAGES; ++s) {
+      mbar_init(cv_full(s), 4);
+      mbar_init(cv_bfull(s), 1);
+      mbar_init(cv_free(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf_bar(b), 1);
@@ -217,33 +219,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   };
 
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------- A producer (raw ring)
     if (lane == 0) {
       uint32_t it = 0;
-      int armed_phase[TC_STAGES];
-      for (int s = 0; s < TC_STAGES; ++s) armed_phase[s] = -1;
+      int armed_phase[RAW_STAGES];
+      for (int s = 0; s < RAW_STAGES; ++s) armed_phase[s] = -1;
       for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
         const int row0 = tile * TC_M;
         for (int ch = 0; ch < nchunks; ++ch, ++it) {
-          const int s = it % TC_STAGES;
-          const uint32_t ph = (it / TC_STAGES) & 1u;
-          if (!mbar_wait(empty_bar(s), ph ^ 1u)) {
+          const int s = it % RAW_STAGES;
+          const uint32_t ph = (it / RAW_STAGES) & 1u;
+          if (!mbar_wait(raw_empty(s), ph ^ 1u)) {
             fail();
             break;
           }
           if (*abort_flag) break;
-          unsigned char* st = smem + s * STAGE_BYTES;
-          mbar_expect_tx(full_bar(s), A_BYTES + 2 * B_BYTES);
-          if (ch < p.nc1) tma_load_2d(smem_u32(st), &tmA1, row0, ch * TC_K, full_bar(s));
-          else tma_load_2d(smem_u32(st), &tmA2, row0, (ch - p.nc1) * TC_K, full_bar(s));
-          bulk_load(smem_u32(st + 2 * A_BYTES), p.gsplit + (size_t)ch * (2 * TC_N * TC_K), 2 * B_BYTES,
-                    full_bar(s));
+          mbar_expect_tx(raw_full(s), A_BYTES);
+          const uint32_t dst = smem_u32(smem + s * A_BYTES);
+          if (ch < p.nc1) tma_load_2d(dst, &tmA1, row0, ch * TC_K, raw_full(s));
+          else tma_load_2d(dst, &tmA2, row0, (ch - p.nc1) * TC_K, raw_full(s));
           armed_phase[s] = (int)ph;
         }
       }
       // never leave with copies in flight into this CTA's shared memory
-      for (int s = 0; s < TC_STAGES; ++s)
-        if (armed_phase[s] >= 0 && !mbar_wait(full_bar(s), (uint32_t)armed_phase[s])) atomicExch(p.err, 2);
+      for (int s = 0; s < RAW_STAGES; ++s)
+        if (armed_phase[s] >= 0 && !mbar_wait(raw_full(s), (uint32_t)armed_phase[s])) atomicExch(p.err, 2);
+    }
+  } else if (warp == 2) {
+    // ------------------------------------ G producer (converted ring, B part)
+    if (lane == 0) {
+      uint32_t it = 0;
+      int armed_phase[CV_STAGES];
+      for (int s = 0; s < CV_STAGES; ++s) armed_phase[s] = -1;
+      for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
+        for (int ch = 0; ch < nchunks; ++ch, ++it) {
+          const int c = it % CV_STAGES;
+          const uint32_t ph = (it / CV_STAGES) & 1u;
+          if (!mbar_wait(cv_free(c), ph ^ 1u)) {
+            fail();
+            break;
+          }
+          if (*abort_flag) break;
+          mbar_expect_tx(cv_bfull(c), 2 * B_BYTES);
+          bulk_load(smem_u32(smem + CV_OFF + c * CV_BYTES + 2 * A_BYTES),
+                    p.gsplit + (size_t)ch * (2 * TC_N * TC_K), 2 * B_BYTES, cv_bfull(c));
+          armed_phase[c] = (int)ph;
+        }
+      }
+      for (int s = 0; s < CV_STAGES; ++s)
+        if (armed_phase[s] >= 0 && !mbar_wait(cv_bfull(s), (uint32_t)armed_phase[s])) atomicExch(p.err, 2);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
@@ -260,15 +284,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t dtm = tmem_base + (uint32_t)(b * TC_N);
         bool bad = false;
         for (int ch = 0; ch < nchunks; ++ch, ++it) {
-          const int s = it % TC_STAGES;
-          const uint32_t ph = (it / TC_STAGES) & 1u;
-          if (!mbar_wait(conv_bar(s), ph) || *abort_flag) {
+          const int c = it % CV_STAGES;
+          const uint32_t ph = (it / CV_STAGES) & 1u;
+          if (!mbar_wait(cv_full(c), ph) || !mbar_wait(cv_bfull(c), ph) || *abort_flag) {
             fail();
             bad = true;
             break;
           }
           tc_fence_after();
-          const uint32_t ahi = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t ahi = smem_u32(smem + CV_OFF + c * CV_BYTES);
           const uint32_t alo = ahi + A_BYTES;
           const uint32_t bhi = ahi + 2 * A_BYTES;
           const uint32_t blo = bhi + B_BYTES;
@@ -283,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             umma_tf32(dtm, dah, dbl, 1u);
             umma_tf32(dtm, dal, dbh, 1u);
           }
-          umma_commit(empty_bar(s));
+          umma_commit(cv_free(c));
         }
         if (bad) break;
         umma_commit(accf_bar(b));
@@ -292,28 +316,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       umma_commit(fin_bar);
       if (!mbar_wait(fin_bar, 0)) atomicExch(p.err, 3);
     }
-  } else if (warp < 6) {
-    // ----------------------------------------------------------- converters
-    const int r = threadIdx.x - 64;  // row of the tile
+  } else if (warp < 7) {
+    // ---------------------------------------------- converters (warps 3..6)
+    const int r = threadIdx.x - 96;  // row of the tile
+    const int rowoff = (r >> 3) * 1024 + (r & 7) * 16;
     uint32_t it = 0;
-    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-      bool stop = false;
+    bool stop = false;
+    for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x) {
       for (int ch = 0; ch < nchunks; ++ch, ++it) {
-        const int s = it % TC_STAGES;
-        const uint32_t ph = (it / TC_STAGES) & 1u;
-        const bool ok = mbar_wait(full_bar(s), ph);
-        if (!ok) fail();
-        // one decision for all 128 converter threads (the named barriers below need all of them)
-        stop = conv_bar_or(!ok || *abort_flag);
-        if (stop) break;
-        float* raw = reinterpret_cast<float*>(smem + s * STAGE_BYTES);
+        const int s = it % RAW_STAGES;
+        const uint32_t ph = (it / RAW_STAGES) & 1u;
+        const int c = it % CV_STAGES;
+        const uint32_t cph = (it / CV_STAGES) & 1u;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(raw_full(s), ph) && mbar_wait(cv_free(c), cph ^ 1u));
+        if (!ok && lane == 0) fail();
+        if (!ok || __shfl_sync(0xffffffffu, (int)*abort_flag, 0)) {
+          stop = true;
+          break;
+        }
+        const float* raw = reinterpret_cast<const float*>(smem + s * A_BYTES);
         float v[TC_K];
 #pragma unroll
         for (int k = 0; k < TC_K; ++k) v[k] = raw[k * TC_M + r];
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        unsigned char* hi = smem + s * STAGE_BYTES;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(raw_empty(s));  // the TMA may refill this raw stage now
+        unsigned char* hi = smem + CV_OFF + c * CV_BYTES;
         unsigned char* lo = hi + A_BYTES;
-        const int rowoff = (r >> 3) * 1024 + (r & 7) * 16;
 #pragma unroll
         for (int c4 = 0; c4 < TC_K / 4; ++c4) {
           uint32_t h[4], l[4];
@@ -328,12 +356,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(conv_bar(s));
+        if (lane == 0) mbar_arrive(cv_full(c));
       }
-      if (stop) break;
     }
   } else {
-    // ------------------------------------------------------------- epilogue
+    // ------------------------------------------------ epilogue (warps 7..10)
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
     uint32_t tcount = 0;
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++tcount) {
