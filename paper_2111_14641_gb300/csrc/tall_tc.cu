@@ -11,19 +11,22 @@
 //
 // Persistent kernel, one CTA per SM, 128-row tiles, K in chunks of 32:
 //   warp 0      TMA producer of the raw ring: A chunk (128 rows x 32 columns
-//               of the column-major source, no swizzle, 16 KB), 6 stages
+//               of the column-major source, no swizzle, 16 KB), 5 stages
 //   warp 1      TMEM allocation and the single MMA-issuing thread
-//   warp 2      bulk-copy producer of the pre-split G chunk (hi + lo, 16 KB)
-//               into the converted ring, 2 stages
+//   warp 2      bulk-copy producer of the pre-split G chunk (hi + lo, 16 KB),
+//               4 stages
 //   warps 3-6   converters: thread r reads row r of a raw chunk (the raw stage
 //               is released as soon as it is read), writes the TF32 hi and lo
-//               parts into the converted ring in the K-major no-swizzle
-//               core-matrix layout (8 rows x 16 B cores, K-direction core
-//               stride 128 B, 8-row group stride 1024 B)
-//   warps 7-10  epilogue: TMEM -> registers -> column-major global stores
-// The raw ring decouples HBM reads from MMA progress: up to 96 KB of A per SM
-// are in flight.  Two TMEM accumulators (64 columns each) overlap the
-// epilogue of one tile with the main loop of the next.
+//               parts (2 stages) in the K-major no-swizzle core-matrix layout
+//               (8 rows x 16 B cores, K-direction core stride 128 B, 8-row
+//               group stride 1024 B)
+//   warps 7-14  epilogue: drains TMEM into registers, stores the rows
+// Accuracy: the tensor cores truncate when they add into an FP32 accumulator,
+// so an accumulator that receives every product of a long K loop drifts by
+// ~(number of MMAs) * 2^-24.  Each chunk's a_hi g_hi product therefore lands
+// in a fresh TMEM slot (4 rotating slots) that the epilogue adds with
+// compensated FP32 summation; the two cross terms, 2^-11 smaller, share one
+// accumulator per tile (double-buffered across tiles).
 // Every mbarrier wait is bounded; on expiry the kernel records an error flag,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -41,18 +44,23 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr int TC_N = 64;
-constexpr int TC_K = 32;  // fp32 elements per chunk
-constexpr int RAW_STAGES = 6;   // TMA destinations (raw fp32 chunks)
-constexpr int CV_STAGES = 2;    // converted operands (A hi/lo + G hi/lo) for the MMA
-constexpr int TC_THREADS = 352; // 11 warps
+constexpr int TC_K = 32;        // fp32 elements per chunk
+constexpr int RAW_STAGES = 5;   // TMA destinations (raw fp32 A chunks, 16 KB)
+constexpr int CV_STAGES = 2;    // converted A (TF32 hi + lo, 32 KB) for the MMA
+constexpr int G_STAGES = 4;     // G chunks (TF32 hi + lo, 16 KB)
+constexpr int NSLOT = 4;        // TMEM slots for the per-chunk main products
+constexpr int TC_THREADS = 480; // 15 warps
 constexpr int A_BYTES = TC_M * TC_K * 4;      // 16 KB
 constexpr int B_BYTES = TC_N * TC_K * 4;      // 8 KB per part
-constexpr int CV_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int CV_BYTES = 2 * A_BYTES;
+constexpr int G_BYTES = 2 * B_BYTES;
 constexpr int CV_OFF = RAW_STAGES * A_BYTES;
-constexpr int SMEM_BAR_OFF = CV_OFF + CV_STAGES * CV_BYTES;
-constexpr int SMEM_BYTES = SMEM_BAR_OFF + 256 + 1024;  // + barriers + alignment slack
+constexpr int G_OFF = CV_OFF + CV_STAGES * CV_BYTES;
+constexpr int SMEM_BAR_OFF = G_OFF + G_STAGES * G_BYTES;
+constexpr int SMEM_BYTES = SMEM_BAR_OFF + 512 + 1024;  // + barriers + alignment slack
 constexpr uint32_t kMaxSpin = 1u << 26;                // bounded waits (~seconds)
-constexpr int TMEM_COLS = 2 * TC_N;
+constexpr int TMEM_COLS = 512;                         // 4 main slots + 2 cross accumulators of 64
+constexpr int CROSS_COL0 = NSLOT * TC_N;
 
 struct TcParams {
   int64_t n;
@@ -166,19 +174,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (p.active && *p.active == 0) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_BAR_OFF);
-  // barrier slots: raw_full[6] raw_empty[6] cv_full[2] cv_bfull[2] cv_free[2] accf[2] acce[2] fin[1]
-  const uint32_t bar0 = smem_u32(bars);
-  auto raw_full = [&](int s) { return bar0 + 8u * s; };
-  auto raw_empty = [&](int s) { return bar0 + 8u * (6 + s); };
-  auto cv_full = [&](int s) { return bar0 + 8u * (12 + s); };
-  auto cv_bfull = [&](int s) { return bar0 + 8u * (14 + s); };
-  auto cv_free = [&](int s) { return bar0 + 8u * (16 + s); };
-  auto accf_bar = [&](int b) { return bar0 + 8u * (18 + b); };
-  auto acce_bar = [&](int b) { return bar0 + 8u * (20 + b); };
-  const uint32_t fin_bar = bar0 + 8u * 22;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 23);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 23 + 8);
+  const uint32_t bar0 = smem_u32(smem + SMEM_BAR_OFF);
+  // barrier slots
+  auto raw_full = [&](int s) { return bar0 + 8u * s; };                 // 5
+  auto raw_empty = [&](int s) { return bar0 + 8u * (5 + s); };          // 5
+  auto cv_full = [&](int s) { return bar0 + 8u * (10 + s); };           // 2
+  auto cv_free = [&](int s) { return bar0 + 8u * (12 + s); };           // 2
+  auto g_full = [&](int s) { return bar0 + 8u * (14 + s); };            // 4
+  auto g_free = [&](int s) { return bar0 + 8u * (18 + s); };            // 4
+  auto slot_full = [&](int s) { return bar0 + 8u * (22 + s); };         // 4
+  auto slot_free = [&](int s) { return bar0 + 8u * (26 + s); };         // 4
+  auto cross_full = [&](int b) { return bar0 + 8u * (30 + b); };        // 2
+  auto cross_free = [&](int b) { return bar0 + 8u * (32 + b); };        // 2
+  const uint32_t fin_bar = bar0 + 8u * 34;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 36);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 36 + 8);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -191,12 +201,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int s = 0; s < CV_STAGES; ++s) {
       mbar_init(cv_full(s), 4);
-      mbar_init(cv_bfull(s), 1);
       mbar_init(cv_free(s), 1);
     }
+    for (int s = 0; s < G_STAGES; ++s) {
+      mbar_init(g_full(s), 1);
+      mbar_init(g_free(s), 1);
+    }
+    for (int s = 0; s < NSLOT; ++s) {
+      mbar_init(slot_full(s), 1);
+      mbar_init(slot_free(s), 8);
+    }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(accf_bar(b), 1);
-      mbar_init(acce_bar(b), 4);
+      mbar_init(cross_full(b), 1);
+      mbar_init(cross_free(b), 8);
     }
     mbar_init(fin_bar, 1);
     *abort_flag = 0;
@@ -246,28 +263,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (armed_phase[s] >= 0 && !mbar_wait(raw_full(s), (uint32_t)armed_phase[s])) atomicExch(p.err, 2);
     }
   } else if (warp == 2) {
-    // ------------------------------------ G producer (converted ring, B part)
+    // -------------------------------------------------------- G producer
     if (lane == 0) {
       uint32_t it = 0;
-      int armed_phase[CV_STAGES];
-      for (int s = 0; s < CV_STAGES; ++s) armed_phase[s] = -1;
+      int armed_phase[G_STAGES];
+      for (int s = 0; s < G_STAGES; ++s) armed_phase[s] = -1;
       for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
         for (int ch = 0; ch < nchunks; ++ch, ++it) {
-          const int c = it % CV_STAGES;
-          const uint32_t ph = (it / CV_STAGES) & 1u;
-          if (!mbar_wait(cv_free(c), ph ^ 1u)) {
+          const int g = it % G_STAGES;
+          const uint32_t ph = (it / G_STAGES) & 1u;
+          if (!mbar_wait(g_free(g), ph ^ 1u)) {
             fail();
             break;
           }
           if (*abort_flag) break;
-          mbar_expect_tx(cv_bfull(c), 2 * B_BYTES);
-          bulk_load(smem_u32(smem + CV_OFF + c * CV_BYTES + 2 * A_BYTES),
-                    p.gsplit + (size_t)ch * (2 * TC_N * TC_K), 2 * B_BYTES, cv_bfull(c));
-          armed_phase[c] = (int)ph;
+          mbar_expect_tx(g_full(g), G_BYTES);
+          bulk_load(smem_u32(smem + G_OFF + g * G_BYTES), p.gsplit + (size_t)ch * (2 * TC_N * TC_K), G_BYTES,
+                    g_full(g));
+          armed_phase[g] = (int)ph;
         }
       }
-      for (int s = 0; s < CV_STAGES; ++s)
-        if (armed_phase[s] >= 0 && !mbar_wait(cv_bfull(s), (uint32_t)armed_phase[s])) atomicExch(p.err, 2);
+      for (int s = 0; s < G_STAGES; ++s)
+        if (armed_phase[s] >= 0 && !mbar_wait(g_full(s), (uint32_t)armed_phase[s])) atomicExch(p.err, 2);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
@@ -275,26 +292,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t it = 0, tcount = 0;
       for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x, ++tcount) {
         const int b = tcount & 1;
-        const uint32_t aph = (tcount >> 1) & 1u;
-        if (!mbar_wait(acce_bar(b), aph ^ 1u)) {
+        const uint32_t bph = (tcount >> 1) & 1u;
+        if (!mbar_wait(cross_free(b), bph ^ 1u)) {
           fail();
           break;
         }
         tc_fence_after();
-        const uint32_t dtm = tmem_base + (uint32_t)(b * TC_N);
+        const uint32_t dcross = tmem_base + (uint32_t)(CROSS_COL0 + b * TC_N);
         bool bad = false;
         for (int ch = 0; ch < nchunks; ++ch, ++it) {
-          const int c = it % CV_STAGES;
-          const uint32_t ph = (it / CV_STAGES) & 1u;
-          if (!mbar_wait(cv_full(c), ph) || !mbar_wait(cv_bfull(c), ph) || *abort_flag) {
+          const int c = it % CV_STAGES, g = it % G_STAGES, sl = it % NSLOT;
+          const uint32_t cph = (it / CV_STAGES) & 1u, gph = (it / G_STAGES) & 1u, sph = (it / NSLOT) & 1u;
+          if (!mbar_wait(slot_free(sl), sph ^ 1u) || !mbar_wait(cv_full(c), cph) || !mbar_wait(g_full(g), gph) ||
+              *abort_flag) {
             fail();
             bad = true;
             break;
           }
           tc_fence_after();
+          const uint32_t dmain = tmem_base + (uint32_t)(sl * TC_N);
           const uint32_t ahi = smem_u32(smem + CV_OFF + c * CV_BYTES);
           const uint32_t alo = ahi + A_BYTES;
-          const uint32_t bhi = ahi + 2 * A_BYTES;
+          const uint32_t bhi = smem_u32(smem + G_OFF + g * G_BYTES);
           const uint32_t blo = bhi + B_BYTES;
 #pragma unroll
           for (int kk = 0; kk < TC_K / 8; ++kk) {
@@ -303,14 +322,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint64_t dal = umma_desc(alo + off, 128, 1024);
             const uint64_t dbh = umma_desc(bhi + off, 128, 1024);
             const uint64_t dbl = umma_desc(blo + off, 128, 1024);
-            umma_tf32(dtm, dah, dbh, (ch | kk) != 0);
-            umma_tf32(dtm, dah, dbl, 1u);
-            umma_tf32(dtm, dal, dbh, 1u);
+            umma_tf32(dmain, dah, dbh, kk != 0);              // this chunk's main product, fresh slot
+            umma_tf32(dcross, dah, dbl, (ch | kk) != 0);       // small cross terms, whole tile
+            umma_tf32(dcross, dal, dbh, 1u);
           }
           umma_commit(cv_free(c));
+          umma_commit(g_free(g));
+          umma_commit(slot_full(sl));
         }
         if (bad) break;
-        umma_commit(accf_bar(b));
+        umma_commit(cross_full(b));
       }
       // all issued MMAs complete before TMEM is released
       umma_commit(fin_bar);
@@ -360,30 +381,69 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else {
-    // ------------------------------------------------ epilogue (warps 7..10)
-    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
-    uint32_t tcount = 0;
-    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++tcount) {
-      const int b = tcount & 1;
-      const uint32_t aph = (tcount >> 1) & 1u;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(accf_bar(b), aph));
-      if (!ok && lane == 0) fail();
-      const int ab = __shfl_sync(0xffffffffu, (int)*abort_flag, 0);
-      if (!ok || ab) break;  // warp-uniform: the TMEM loads below are .sync.aligned
-      tc_fence_after();
-      float v[TC_N];
-      const uint32_t taddr = tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * TC_N);
+    // ------------------------------------------------ epilogue (warps 7..14)
+    // Per chunk: drain the chunk's TMEM slot into compensated FP32 sums;
+    // per tile: add the cross-term accumulator and store the rows.  Two
+    // warps share each TMEM lane quarter (warp % 4), 32 columns each.
+    const int quarter = warp & 3;
+    const int half = (warp - 7) >> 2;
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    const uint32_t col_off = (uint32_t)(32 * half);
+    uint32_t it = 0, tcount = 0;
+    bool stop = false;
+    for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++tcount) {
+      float acc[32], cmp[32];
 #pragma unroll
-      for (int j = 0; j < TC_N / 16; ++j) tmem_ld16(taddr + 16 * j, v + 16 * j);
+      for (int j = 0; j < 32; ++j) {
+        acc[j] = 0.f;
+        cmp[j] = 0.f;
+      }
+      for (int ch = 0; ch < nchunks; ++ch, ++it) {
+        const int sl = it % NSLOT;
+        const uint32_t sph = (it / NSLOT) & 1u;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(slot_full(sl), sph));
+        if (!ok && lane == 0) fail();
+        if (!ok || __shfl_sync(0xffffffffu, (int)*abort_flag, 0)) {
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        float v[32];
+        const uint32_t taddr = tmem_base + lane_off + (uint32_t)(sl * TC_N) + col_off;
+        tmem_ld16(taddr, v);
+        tmem_ld16(taddr + 16, v + 16);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(slot_free(sl));
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {  // Kahan-Babuska summation in FP32
+          const float y = v[j] - cmp[j];
+          const float t = acc[j] + y;
+          cmp[j] = (t - acc[j]) - y;
+          acc[j] = t;
+        }
+      }
+      if (stop) break;
+      const int b = tcount & 1;
+      const uint32_t bph = (tcount >> 1) & 1u;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(cross_full(b), bph));
+      if (!ok && lane == 0) fail();
+      if (!ok || __shfl_sync(0xffffffffu, (int)*abort_flag, 0)) break;
+      tc_fence_after();
+      float v[32];
+      const uint32_t taddr = tmem_base + lane_off + (uint32_t)(CROSS_COL0 + b * TC_N) + col_off;
+      tmem_ld16(taddr, v);
+      tmem_ld16(taddr + 16, v + 16);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acce_bar(b));
+      if (lane == 0) mbar_arrive(cross_free(b));
       const int64_t row = (int64_t)tile * TC_M + 32 * quarter + lane;
       if (row < p.n) {
 #pragma unroll
-        for (int j = 0; j < TC_N; ++j)
-          if (j < p.mb) p.qout[row + j * p.ldo] = v[j];
+        for (int j = 0; j < 32; ++j)
+          if ((int)col_off + j < p.mb) p.qout[row + (int64_t)(col_off + j) * p.ldo] = acc[j] + (v[j] - cmp[j]);
       }
     }
   }
