@@ -11,20 +11,22 @@
 //
 // Persistent kernel, one CTA per SM, 128-row tiles, K in chunks of 32:
 //   warp 0      TMA producer of the raw ring: A chunk (128 rows x 32 columns
-//               of the column-major source, no swizzle, 16 KB), 5 stages
+//               of the column-major source, no swizzle, 16 KB), 8 stages
 //   warp 1      TMEM allocation and the single MMA-issuing thread
-//   warp 2      bulk-copy producer of the pre-split G chunk (hi + lo, 16 KB),
-//               4 stages
-//   warps 3-6   converters: thread r reads row r of a raw chunk (the raw stage
-//               is released as soon as it is read), writes the TF32 hi and lo
-//               parts (2 stages) in the K-major no-swizzle core-matrix layout
-//               (8 rows x 16 B cores, K-direction core stride 128 B, 8-row
-//               group stride 1024 B)
-//   warps 7-14  epilogue: drains TMEM into registers, stores the rows
+//   warp 2      bulk-copy producer of the pre-split G chunk (hi + lo, 16 KB,
+//               K-major no-swizzle core-matrix layout), 4 stages
+//   warps 3-10  converters: the thread of TMEM lane r reads row r of half a
+//               raw chunk (the raw stage is released as soon as it is read),
+//               rounds it to TF32 hi and lo parts and stores them into tensor
+//               memory (stages of 64 columns), where the MMA reads A
+//   warps 11-26 epilogue: drains TMEM into registers, stores the rows
+// Keeping A in tensor memory halves the shared-memory traffic per chunk (the
+// tensor core would otherwise re-read the 128-row A operand from shared
+// memory for each of the 12 MMAs), which bounded the earlier designs.
 // Accuracy: the tensor cores truncate when they add into an FP32 accumulator,
 // so an accumulator that receives every product of a long K loop drifts by
 // ~(number of MMAs) * 2^-24.  Each chunk's a_hi g_hi product therefore lands
-// in a fresh TMEM slot (4 rotating slots) that the epilogue adds with
+// in a fresh TMEM slot (rotating slots) that the epilogue adds with
 // compensated FP32 summation; the two cross terms, 2^-11 smaller, share one
 // accumulator per tile (double-buffered across tiles).
 // Every mbarrier wait is bounded; on expiry the kernel records an error flag,
@@ -33,6 +35,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -45,22 +48,30 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_N = 64;
 constexpr int TC_K = 32;        // fp32 elements per chunk
-constexpr int RAW_STAGES = 5;   // TMA destinations (raw fp32 A chunks, 16 KB)
-constexpr int CV_STAGES = 2;    // converted A (TF32 hi + lo, 32 KB) for the MMA
-constexpr int G_STAGES = 4;     // G chunks (TF32 hi + lo, 16 KB)
-constexpr int NSLOT = 4;        // TMEM slots for the per-chunk main products
-constexpr int TC_THREADS = 480; // 15 warps
-constexpr int A_BYTES = TC_M * TC_K * 4;      // 16 KB
+constexpr int TC_THREADS = 864; // 27 warps
+constexpr int A_BYTES = TC_M * TC_K * 4;      // 16 KB raw fp32 chunk
 constexpr int B_BYTES = TC_N * TC_K * 4;      // 8 KB per part
-constexpr int CV_BYTES = 2 * A_BYTES;
 constexpr int G_BYTES = 2 * B_BYTES;
-constexpr int CV_OFF = RAW_STAGES * A_BYTES;
-constexpr int G_OFF = CV_OFF + CV_STAGES * CV_BYTES;
-constexpr int SMEM_BAR_OFF = G_OFF + G_STAGES * G_BYTES;
-constexpr int SMEM_BYTES = SMEM_BAR_OFF + 512 + 1024;  // + barriers + alignment slack
-constexpr uint32_t kMaxSpin = 1u << 26;                // bounded waits (~seconds)
-constexpr int TMEM_COLS = 512;                         // 4 main slots + 2 cross accumulators of 64
-constexpr int CROSS_COL0 = NSLOT * TC_N;
+constexpr uint64_t kMaxWaitNs = 2000000000ull;         // bounded waits: 2 s
+constexpr uint32_t kSuspendHintNs = 100000u;           // sleep hint per try_wait: 100 us
+constexpr int TMEM_COLS = 512;
+
+// Pipeline shape: RAW raw stages (TMA, shared memory), GS G stages (shared
+// memory), F chunks accumulated per TMEM slot before the epilogue drains it,
+// AS converted-A stages and NS main-product slots in tensor memory.
+// TMEM columns: NS x 64 slots | 2 x 64 cross accumulators | AS x 64 A stages.
+template <int RAW, int GS, int F, int AS, int NS>
+struct TcCfg {
+  static constexpr int RAW_STAGES = RAW, G_STAGES = GS, CHUNKS_PER_SLOT = F, A_STAGES = AS, NSLOT = NS;
+  static constexpr int G_OFF = RAW * A_BYTES;
+  static constexpr int SMEM_BAR_OFF = G_OFF + GS * G_BYTES;
+  static constexpr int SMEM_BYTES = SMEM_BAR_OFF + 512 + 1024;  // + barriers + alignment slack
+  static constexpr int SLOT_COL0 = 0;
+  static constexpr int CROSS_COL0 = NS * TC_N;
+  static constexpr int A_COL0 = CROSS_COL0 + 2 * TC_N;
+  static_assert(RAW <= 8 && GS <= 8 && AS <= 4 && NS <= 4, "barrier slots");
+  static_assert(A_COL0 + AS * 2 * TC_K <= TMEM_COLS, "TMEM budget");
+};
 
 struct TcParams {
   int64_t n;
@@ -88,21 +99,33 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware until
+// the phase completes or the hint (ns) elapses, so waiting warps do not take
+// issue slots from the converters.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
 
-// Bounded wait on the phase with the given parity; false on expiry.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on the phase with the given parity: false after kMaxWaitNs.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kMaxSpin; ++i)
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
     if (mbar_try(bar, parity)) return true;
-  return false;
+    if (global_ns() - t0 > kMaxWaitNs) return false;
+  }
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -124,6 +147,15 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
+// Round to TF32 (10 explicit mantissa bits), nearest with ties away from zero,
+// on the integer pipes: add half a unit of the kept precision to the
+// magnitude bits, then clear the 13 dropped bits (a carry moves into the
+// exponent as it should).  For finite inputs this is the same rounding as
+// tf32_rna.
+__device__ __forceinline__ uint32_t tf32_round_bits(float x) {
+  return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+}
+
 // Shared-memory matrix descriptor, K-major, no swizzle.
 __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -143,6 +175,37 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+
+// A operand read from tensor memory (rows in lanes, K along columns).
+__device__ __forceinline__ void umma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
       : "memory");
 }
 
@@ -169,26 +232,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <class Cfg>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tall_tc_kernel(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2, TcParams p) {
+  constexpr int RAW_STAGES = Cfg::RAW_STAGES, G_STAGES = Cfg::G_STAGES;
+  constexpr int F = Cfg::CHUNKS_PER_SLOT, A_STAGES = Cfg::A_STAGES, NSLOT = Cfg::NSLOT;
+  constexpr int G_OFF = Cfg::G_OFF, SMEM_BAR_OFF = Cfg::SMEM_BAR_OFF;
+  constexpr int SLOT_COL0 = Cfg::SLOT_COL0, CROSS_COL0 = Cfg::CROSS_COL0, A_COL0 = Cfg::A_COL0;
   if (p.active && *p.active == 0) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t bar0 = smem_u32(smem + SMEM_BAR_OFF);
-  // barrier slots
-  auto raw_full = [&](int s) { return bar0 + 8u * s; };                 // 5
-  auto raw_empty = [&](int s) { return bar0 + 8u * (5 + s); };          // 5
-  auto cv_full = [&](int s) { return bar0 + 8u * (10 + s); };           // 2
-  auto cv_free = [&](int s) { return bar0 + 8u * (12 + s); };           // 2
-  auto g_full = [&](int s) { return bar0 + 8u * (14 + s); };            // 4
-  auto g_free = [&](int s) { return bar0 + 8u * (18 + s); };            // 4
-  auto slot_full = [&](int s) { return bar0 + 8u * (22 + s); };         // 4
-  auto slot_free = [&](int s) { return bar0 + 8u * (26 + s); };         // 4
-  auto cross_full = [&](int b) { return bar0 + 8u * (30 + b); };        // 2
-  auto cross_free = [&](int b) { return bar0 + 8u * (32 + b); };        // 2
-  const uint32_t fin_bar = bar0 + 8u * 34;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 36);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 36 + 8);
+  auto raw_full = [&](int s) { return bar0 + 8u * s; };                 // 8 slots
+  auto raw_empty = [&](int s) { return bar0 + 8u * (8 + s); };          // 8
+  auto a_full = [&](int s) { return bar0 + 8u * (16 + s); };            // 4
+  auto a_free = [&](int s) { return bar0 + 8u * (20 + s); };            // 4
+  auto g_full = [&](int s) { return bar0 + 8u * (24 + s); };            // 8
+  auto g_free = [&](int s) { return bar0 + 8u * (32 + s); };            // 8
+  auto slot_full = [&](int s) { return bar0 + 8u * (40 + s); };         // 4
+  auto slot_free = [&](int s) { return bar0 + 8u * (44 + s); };         // 4
+  auto cross_full = [&](int b) { return bar0 + 8u * (48 + b); };        // 2
+  auto cross_free = [&](int b) { return bar0 + 8u * (50 + b); };        // 2
+  const uint32_t fin_bar = bar0 + 8u * 52;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 54);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 54 + 8);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -197,11 +264,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < RAW_STAGES; ++s) {
       mbar_init(raw_full(s), 1);
-      mbar_init(raw_empty(s), 4);
+      mbar_init(raw_empty(s), 8);
     }
-    for (int s = 0; s < CV_STAGES; ++s) {
-      mbar_init(cv_full(s), 4);
-      mbar_init(cv_free(s), 1);
+    for (int s = 0; s < A_STAGES; ++s) {
+      mbar_init(a_full(s), 8);
+      mbar_init(a_free(s), 1);
     }
     for (int s = 0; s < G_STAGES; ++s) {
       mbar_init(g_full(s), 1);
@@ -209,11 +276,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int s = 0; s < NSLOT; ++s) {
       mbar_init(slot_full(s), 1);
-      mbar_init(slot_free(s), 8);
+      mbar_init(slot_free(s), 16);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(cross_full(b), 1);
-      mbar_init(cross_free(b), 8);
+      mbar_init(cross_free(b), 16);
     }
     mbar_init(fin_bar, 1);
     *abort_flag = 0;
@@ -289,7 +356,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      uint32_t it = 0, tcount = 0;
+      uint32_t it = 0, tcount = 0, sbase = 0;
       for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x, ++tcount) {
         const int b = tcount & 1;
         const uint32_t bph = (tcount >> 1) & 1u;
@@ -301,106 +368,112 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t dcross = tmem_base + (uint32_t)(CROSS_COL0 + b * TC_N);
         bool bad = false;
         for (int ch = 0; ch < nchunks; ++ch, ++it) {
-          const int c = it % CV_STAGES, g = it % G_STAGES, sl = it % NSLOT;
-          const uint32_t cph = (it / CV_STAGES) & 1u, gph = (it / G_STAGES) & 1u, sph = (it / NSLOT) & 1u;
-          if (!mbar_wait(slot_free(sl), sph ^ 1u) || !mbar_wait(cv_full(c), cph) || !mbar_wait(g_full(g), gph) ||
-              *abort_flag) {
+          const int c = it % A_STAGES, g = it % G_STAGES;
+          const uint32_t cph = (it / A_STAGES) & 1u, gph = (it / G_STAGES) & 1u;
+          // slot u of this tile holds chunks [F u, F u + F); slots rotate over all tiles (sidx)
+          const bool first_in_slot = (ch % F) == 0;
+          const bool last_in_slot = (ch % F) == F - 1 || ch == nchunks - 1;
+          const uint32_t sidx = sbase + (uint32_t)(ch / F);
+          const int sl = sidx % NSLOT;
+          const uint32_t sph = (sidx / NSLOT) & 1u;
+          if ((first_in_slot && !mbar_wait(slot_free(sl), sph ^ 1u)) || !mbar_wait(a_full(c), cph) ||
+              !mbar_wait(g_full(g), gph) || *abort_flag) {
             fail();
             bad = true;
             break;
           }
           tc_fence_after();
-          const uint32_t dmain = tmem_base + (uint32_t)(sl * TC_N);
-          const uint32_t ahi = smem_u32(smem + CV_OFF + c * CV_BYTES);
-          const uint32_t alo = ahi + A_BYTES;
+          const uint32_t dmain = tmem_base + (uint32_t)(SLOT_COL0 + sl * TC_N);
+          const uint32_t ahi = tmem_base + (uint32_t)(A_COL0 + c * 2 * TC_K);
+          const uint32_t alo = ahi + TC_K;
           const uint32_t bhi = smem_u32(smem + G_OFF + g * G_BYTES);
           const uint32_t blo = bhi + B_BYTES;
+          // main products of the chunk (fresh slot every F chunks), then the small cross terms
+#pragma unroll
+          for (int kk = 0; kk < TC_K / 8; ++kk)
+            umma_tf32_ts(dmain, ahi + 8 * kk, umma_desc(bhi + kk * 256, 128, 1024), (!first_in_slot) || kk != 0);
 #pragma unroll
           for (int kk = 0; kk < TC_K / 8; ++kk) {
-            const uint32_t off = kk * 256;  // 8 tf32 = two 16-byte cores along K
-            const uint64_t dah = umma_desc(ahi + off, 128, 1024);
-            const uint64_t dal = umma_desc(alo + off, 128, 1024);
-            const uint64_t dbh = umma_desc(bhi + off, 128, 1024);
-            const uint64_t dbl = umma_desc(blo + off, 128, 1024);
-            umma_tf32(dmain, dah, dbh, kk != 0);              // this chunk's main product, fresh slot
-            umma_tf32(dcross, dah, dbl, (ch | kk) != 0);       // small cross terms, whole tile
-            umma_tf32(dcross, dal, dbh, 1u);
+            umma_tf32_ts(dcross, ahi + 8 * kk, umma_desc(blo + kk * 256, 128, 1024), (ch | kk) != 0);
+            umma_tf32_ts(dcross, alo + 8 * kk, umma_desc(bhi + kk * 256, 128, 1024), 1u);
           }
-          umma_commit(cv_free(c));
+          umma_commit(a_free(c));
           umma_commit(g_free(g));
-          umma_commit(slot_full(sl));
+          if (last_in_slot) umma_commit(slot_full(sl));
         }
         if (bad) break;
         umma_commit(cross_full(b));
+        sbase += (uint32_t)((nchunks + F - 1) / F);
       }
       // all issued MMAs complete before TMEM is released
       umma_commit(fin_bar);
       if (!mbar_wait(fin_bar, 0)) atomicExch(p.err, 3);
     }
-  } else if (warp < 7) {
-    // ---------------------------------------------- converters (warps 3..6)
-    const int r = threadIdx.x - 96;  // row of the tile
-    const int rowoff = (r >> 3) * 1024 + (r & 7) * 16;
+  } else if (warp < 11) {
+    // --------------------------------------------- converters (warps 3..10)
+    // A warp may only address TMEM lanes 32 (warp % 4) .. +31, so its rows are
+    // those; two warps share each lane quarter, one per half of the chunk's K.
+    const int quarter = warp & 3;
+    const int khalf = (warp - 3) >> 2;
+    const int r = 32 * quarter + lane;  // row of the tile == TMEM lane
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    constexpr int KH = TC_K / 2;
     uint32_t it = 0;
     bool stop = false;
     for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x) {
       for (int ch = 0; ch < nchunks; ++ch, ++it) {
         const int s = it % RAW_STAGES;
         const uint32_t ph = (it / RAW_STAGES) & 1u;
-        const int c = it % CV_STAGES;
-        const uint32_t cph = (it / CV_STAGES) & 1u;
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(raw_full(s), ph) && mbar_wait(cv_free(c), cph ^ 1u));
+        const int c = it % A_STAGES;
+        const uint32_t cph = (it / A_STAGES) & 1u;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(raw_full(s), ph) && mbar_wait(a_free(c), cph ^ 1u));
         if (!ok && lane == 0) fail();
         if (!ok || __shfl_sync(0xffffffffu, (int)*abort_flag, 0)) {
           stop = true;
           break;
         }
-        const float* raw = reinterpret_cast<const float*>(smem + s * A_BYTES);
-        float v[TC_K];
+        tc_fence_after();
+        const float* raw = reinterpret_cast<const float*>(smem + s * A_BYTES) + khalf * KH * TC_M;
+        uint32_t h[KH], l[KH];
 #pragma unroll
-        for (int k = 0; k < TC_K; ++k) v[k] = raw[k * TC_M + r];
+        for (int k = 0; k < KH; ++k) {
+          const float x = raw[k * TC_M + r];
+          h[k] = tf32_round_bits(x);
+          l[k] = tf32_round_bits(x - __uint_as_float(h[k]));
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(raw_empty(s));  // the TMA may refill this raw stage now
-        unsigned char* hi = smem + CV_OFF + c * CV_BYTES;
-        unsigned char* lo = hi + A_BYTES;
-#pragma unroll
-        for (int c4 = 0; c4 < TC_K / 4; ++c4) {
-          uint32_t h[4], l[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float x = v[4 * c4 + q];
-            h[q] = tf32_rna(x);
-            l[q] = tf32_rna(x - __uint_as_float(h[q]));
-          }
-          *reinterpret_cast<uint4*>(hi + rowoff + c4 * 128) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(lo + rowoff + c4 * 128) = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t abase = tmem_base + lane_off + (uint32_t)(A_COL0 + c * 2 * TC_K + khalf * KH);
+        tmem_st16(abase, h);
+        tmem_st16(abase + TC_K, l);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(cv_full(c));
+        if (lane == 0) mbar_arrive(a_full(c));
       }
     }
   } else {
-    // ------------------------------------------------ epilogue (warps 7..14)
-    // Per chunk: drain the chunk's TMEM slot into compensated FP32 sums;
-    // per tile: add the cross-term accumulator and store the rows.  Two
-    // warps share each TMEM lane quarter (warp % 4), 32 columns each.
+    // ----------------------------------------------- epilogue (warps 11..26)
+    // Per slot: drain the TMEM slot into compensated FP32 sums; per tile: add
+    // the cross-term accumulator and store the rows.  Four warps share each
+    // TMEM lane quarter (warp % 4), 16 columns each.
     const int quarter = warp & 3;
-    const int half = (warp - 7) >> 2;
+    const int part = (warp - 11) >> 2;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-    const uint32_t col_off = (uint32_t)(32 * half);
-    uint32_t it = 0, tcount = 0;
+    const uint32_t col_off = (uint32_t)(16 * part);
+    uint32_t sidx = 0, tcount = 0;
     bool stop = false;
+    const int nslots_tile = (nchunks + F - 1) / F;
     for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++tcount) {
-      float acc[32], cmp[32];
+      float acc[16], cmp[16];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < 16; ++j) {
         acc[j] = 0.f;
         cmp[j] = 0.f;
       }
-      for (int ch = 0; ch < nchunks; ++ch, ++it) {
-        const int sl = it % NSLOT;
-        const uint32_t sph = (it / NSLOT) & 1u;
+      for (int u = 0; u < nslots_tile; ++u, ++sidx) {
+        const int sl = sidx % NSLOT;
+        const uint32_t sph = (sidx / NSLOT) & 1u;
         const bool ok = __all_sync(0xffffffffu, mbar_wait(slot_full(sl), sph));
         if (!ok && lane == 0) fail();
         if (!ok || __shfl_sync(0xffffffffu, (int)*abort_flag, 0)) {
@@ -408,16 +481,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         tc_fence_after();
-        float v[32];
-        const uint32_t taddr = tmem_base + lane_off + (uint32_t)(sl * TC_N) + col_off;
-        tmem_ld16(taddr, v);
-        tmem_ld16(taddr + 16, v + 16);
+        float v[16];
+        tmem_ld16(tmem_base + lane_off + (uint32_t)(SLOT_COL0 + sl * TC_N) + col_off, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(slot_free(sl));
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {  // Kahan-Babuska summation in FP32
+        for (int j = 0; j < 16; ++j) {  // Kahan-Babuska summation in FP32
           const float y = v[j] - cmp[j];
           const float t = acc[j] + y;
           cmp[j] = (t - acc[j]) - y;
@@ -431,10 +502,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok && lane == 0) fail();
       if (!ok || __shfl_sync(0xffffffffu, (int)*abort_flag, 0)) break;
       tc_fence_after();
-      float v[32];
-      const uint32_t taddr = tmem_base + lane_off + (uint32_t)(CROSS_COL0 + b * TC_N) + col_off;
-      tmem_ld16(taddr, v);
-      tmem_ld16(taddr + 16, v + 16);
+      float v[16];
+      tmem_ld16(tmem_base + lane_off + (uint32_t)(CROSS_COL0 + b * TC_N) + col_off, v);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       tc_fence_before();
       __syncwarp();
@@ -442,7 +511,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int64_t row = (int64_t)tile * TC_M + 32 * quarter + lane;
       if (row < p.n) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
+        for (int j = 0; j < 16; ++j)
           if ((int)col_off + j < p.mb) p.qout[row + (int64_t)(col_off + j) * p.ldo] = acc[j] + (v[j] - cmp[j]);
       }
     }
@@ -516,6 +585,16 @@ bool make_map(CUtensorMap* map, const float* base, int64_t n, int64_t cols, int6
   return r == CUDA_SUCCESS;
 }
 
+// Pipeline configuration (see TcCfg); RBGS_TC_CONFIG=<index> selects another
+// shape for tuning measurements.
+int tc_config() {
+  static int cfg = []() {
+    const char* e = getenv("RBGS_TC_CONFIG");
+    return e ? atoi(e) : 0;
+  }();
+  return cfg;
+}
+
 }  // namespace
 
 size_t tc_gsplit_floats(int64_t K) { return (size_t)((K + TC_K - 1) / TC_K + 2) * 2 * TC_N * TC_K; }
@@ -558,11 +637,21 @@ rbgs_status tall_update_tc(int64_t n, int64_t c, int64_t mb, const float* A1, in
   p.ldo = ldo;
   p.active = active;
   p.err = err;
-  RBGS_CUDA_TRY(cudaFuncSetAttribute(tall_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   const int grid = std::min(p.ntiles, nsm);
-  tall_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, st>>>(m1, m2, p);
-  RBGS_LAUNCH_CHECK();
-  return RBGS_OK;
+  auto go = [&](auto cfg) -> rbgs_status {
+    using Cfg = decltype(cfg);
+    RBGS_CUDA_TRY(cudaFuncSetAttribute(tall_tc_kernel<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg::SMEM_BYTES));
+    tall_tc_kernel<Cfg><<<grid, TC_THREADS, Cfg::SMEM_BYTES, st>>>(m1, m2, p);
+    RBGS_LAUNCH_CHECK();
+    return RBGS_OK;
+  };
+  switch (tc_config()) {
+    case 1: return go(TcCfg<8, 4, 2, 4, 2>{});
+    case 2: return go(TcCfg<8, 4, 1, 4, 2>{});
+    case 3: return go(TcCfg<8, 4, 2, 3, 3>{});
+    default: return go(TcCfg<8, 4, 1, 3, 3>{});
+  }
 }
 
 }  // namespace rbgs
