@@ -183,7 +183,7 @@ def cpu_baseline(cfg, ls_iters, reorth):
     W = synth.svd_matrix(ns, ms, cfg["cond"], cfg["seed_w"])
     t0 = time.perf_counter()
     out = oracle.rbgs(W, cfg["mb"], cfg["sketch"], cfg["k"], cfg["seed_theta"], variant=5, ls="richardson",
-                      ls_iters=ls_iters, reorth=bool(reorth))
+                      ls_iters=ls_iters, reorth=bool(reorth), ls_iters_first=1)
     dt = time.perf_counter() - t0
     flops = algorithmic_flops(ns, ms, cfg["mb"], cfg["k"], cfg["sketch"], ls_iters, out["passes2"])
     del W

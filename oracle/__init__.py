@@ -77,7 +77,7 @@ def _load():
         lib.or_qr_full.argtypes = [i64, i64, dp, i64, dp, i64, dp, i64]
         lib.or_qr_full.restype = ctypes.c_int
         lib.or_rbgs.argtypes = [dp, i64, i64, i64, i64, ctypes.c_int, i64, u64, ctypes.c_int, ctypes.c_int,
-                                ctypes.c_int, ctypes.c_int, dp, i64, dp, i64, dp, dp, dp]
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, i64, dp, i64, dp, dp, dp]
         lib.or_rbgs.restype = ctypes.c_int
         lib.or_rcholqr.argtypes = [dp, i64, i64, i64, ctypes.c_int, i64, u64, dp, i64, dp, i64]
         lib.or_rcholqr.restype = ctypes.c_int
@@ -170,8 +170,9 @@ def householder_qr(A):
 
 
 def rbgs(W, mp: int, kind: str, k: int, seed: int, variant: int = 5, ls: str = "householder",
-         ls_iters: int = 5, reorth: bool = False):
-    """Alg. 2.  Returns dict(Q, R, S, P, delta, delta_tilde, passes2, rc)."""
+         ls_iters: int = 5, reorth: bool = False, ls_iters_first: int = 0):
+    """Alg. 2.  Returns dict(Q, R, S, P, delta, delta_tilde, passes2, rc).
+    With reorth, ls_iters_first > 0 sets the iterations of the first pass."""
     W = _f64(W)
     n, m = W.shape
     Q = np.zeros((n, m), order="F")
@@ -180,7 +181,8 @@ def rbgs(W, mp: int, kind: str, k: int, seed: int, variant: int = 5, ls: str = "
     P = np.zeros((k, m), order="F")
     st = np.zeros(3)
     rc = _load().or_rbgs(_ptr(W), n, m, n, int(mp), THETA[kind], int(k), int(seed), int(variant), LS[ls],
-                         int(ls_iters), int(bool(reorth)), _ptr(Q), n, _ptr(R), m, _ptr(S), _ptr(P), _ptr(st))
+                         int(ls_iters), int(ls_iters_first), int(bool(reorth)), _ptr(Q), n, _ptr(R), m, _ptr(S),
+                         _ptr(P), _ptr(st))
     if rc == -1:
         raise ValueError("bad RBGS arguments")
     return dict(Q=Q, R=R, S=S, P=P, delta=st[0], delta_tilde=st[1], passes2=int(st[2]), rc=rc)

@@ -661,11 +661,12 @@ static int interblock(int variant, int64_t n, int64_t mp, double* Qp, int64_t ld
 /* Alg. 2.  W n x m (ldw), block size mp, m = mp * p.  Outputs Q (n x m, ldq),
  * R (m x m, ldr, upper triangular), and, when non-NULL, S = Theta Q and
  * P = Theta W (k x m, ld k).  stats (when non-NULL) receives
- * {Delta, Delta~, number of second passes}.  Returns 0, -1 on bad
- * arguments, -2 on a breakdown (zero or non-finite R_ii diagonal).         */
+ * {Delta, Delta~, number of second passes}.  With reorth, ls_iters_first > 0
+ * sets the Richardson count of the first (provisional) pass.  Returns 0, -1
+ * on bad arguments, -2 on a breakdown (zero or non-finite R_ii diagonal).   */
 int or_rbgs(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int theta, int64_t k, uint64_t seed,
-            int variant, int ls, int ls_iters, int reorth, double* Q, int64_t ldq, double* R, int64_t ldr,
-            double* S_out, double* P_out, double* stats) {
+            int variant, int ls, int ls_iters, int ls_iters_first, int reorth, double* Q, int64_t ldq, double* R,
+            int64_t ldr, double* S_out, double* P_out, double* stats) {
   if (mp <= 0 || m % mp != 0 || n < 1 || k < m || ldw < n || ldq < n || ldr < m) return -1;
   if (theta == OR_THETA_SRHT && k > or_srht_padded(n)) return -1;
   if (theta != OR_THETA_SRHT && k > n) return -1;
@@ -692,8 +693,11 @@ int or_rbgs(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int 
     double* Si = S + c * k;
     /* step 1: P_i = Theta W_i */
     or_theta_apply(theta, k, n, seed, Wi, ldw, mp, Pi, k);
-    /* step 2: R_{1:i-1,i} = argmin ||S_{1:i-1} Y - P_i||_F */
-    if (c > 0 && solve_ls(ls, ls_iters, k, c, S, k, Pi, k, mp, Rc, m)) rc = -2;
+    /* step 2: R_{1:i-1,i} = argmin ||S_{1:i-1} Y - P_i||_F (with a second pass
+       to follow, the first may use its own iteration count) */
+    if (c > 0 && solve_ls(ls, (reorth && ls_iters_first > 0) ? ls_iters_first : ls_iters, k, c, S, k, Pi, k, mp, Rc,
+                          m))
+      rc = -2;
     /* step 3: Q'_i = W_i - Q_{1:i-1} R_{1:i-1,i} */
     project(n, c, mp, Wi, ldw, Q, ldq, Rc, m, Qi, ldq);
     /* implicit sketch for Alg. 5: S'_i = P_i - S_{1:i-1} R_{1:i-1,i} */

@@ -22,6 +22,8 @@ struct SrhtPlan {
   int* d_lvals = nullptr;    // [L]  distinct low indices (sorted)
   int* d_rhi = nullptr;      // [k]  i_hi of sample r
   int* d_rl = nullptr;       // [k]  position of i_lo(sample r) in lvals
+  int* d_off = nullptr;      // [L+1] CSR offsets: samples whose low index is lvals[l]
+  int* d_rs = nullptr;       // [k]  sample indices grouped by low index
   std::vector<int64_t> samples;
 };
 
@@ -42,6 +44,14 @@ template <class TX, class TY>
 rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed, const TX* X, int64_t ldx,
                            int64_t ncols, TY* Y, int64_t ldy, void* scratch, size_t scratch_bytes,
                            cudaStream_t st, const int* active = nullptr);
+
+// Two-source form: Y1 = Theta X1 and Y2 = Theta X2 in one pass (the SRHT
+// transforms all columns in the same launches).
+template <class TX, class TY>
+rbgs_status sketch_apply2_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed, const TX* X1, int64_t ldx1,
+                            int64_t nc1, TY* Y1, int64_t ldy1, const TX* X2, int64_t ldx2, int64_t nc2, TY* Y2,
+                            int64_t ldy2, void* scratch, size_t scratch_bytes, cudaStream_t st,
+                            const int* active = nullptr);
 
 // --------------------------------------------------------------- tall ops ---
 // Qout (n x mb) = [A1 (n x c) | A2 (n x mb)] * G ((c+mb) x mb, ldg).  Qout may
@@ -73,8 +83,11 @@ rbgs_status small_gemm(int trans, int64_t M, int64_t N, int64_t K, double alpha,
 // Cholesky G (+ shift * trace(G) I) = R^T R (upper R, positive diagonal) of an
 // mb x mb matrix and R^{-1}, in the arithmetic of T; sets *flag |= 1 on a
 // non-positive or non-finite pivot.
+// With Rprev != null (a second Cholesky QR round) R and Rinv receive the
+// products R_new Rprev and Rprev_inv R_new^{-1}.
 template <class T>
-rbgs_status chol_inv(int mb, const T* G, T* R, T* Rinv, double shift, int* flag, const int* active, cudaStream_t st);
+rbgs_status chol_inv(int mb, const T* G, T* R, T* Rinv, double shift, int* flag, const T* Rprev, const T* Rprev_inv,
+                     const int* active, cudaStream_t st);
 
 // Out (k x mb, ldo) = A (k x mb, lda) * U (U upper mb x mb, ld mb).
 template <class TS>

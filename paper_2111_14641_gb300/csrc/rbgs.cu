@@ -127,19 +127,31 @@ bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) 
 template <class TS>
 rbgs_status cholqr2(int64_t k, int mb, const TS* Sp, TS* Sp2, TS** sm, TS* part, int* flag, const int* active,
                     cudaStream_t st, TS* R, TS* Rinv) {
-  TS *gram = sm[0], *R1 = sm[1], *R1inv = sm[2], *R2 = sm[3], *R2inv = sm[4];
+  TS *gram = sm[0], *R1 = sm[1], *R1inv = sm[2];
   const double shift = sizeof(TS) == 4 ? 1e-6 : 0.0;
   rbgs_status s;
   s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
   if (s) return s;
-  if ((s = chol_inv<TS>(mb, gram, R1, R1inv, shift, flag, active, st))) return s;
+  if ((s = chol_inv<TS>(mb, gram, R1, R1inv, shift, flag, nullptr, nullptr, active, st))) return s;
   if ((s = trmm_right_upper<TS>(k, mb, Sp, k, R1inv, Sp2, k, active, st))) return s;
   s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp2, k, Sp2, k, 0.0, gram, mb, part, kPartElems, active, st);
   if (s) return s;
-  if ((s = chol_inv<TS>(mb, gram, R2, R2inv, 0.0, flag, active, st))) return s;
-  if ((s = tri_mul<TS>(mb, R2, R1, R, active, st))) return s;
-  if ((s = tri_mul<TS>(mb, R1inv, R2inv, Rinv, active, st))) return s;
+  // second round; the kernel also forms R = R2 R1 and R^{-1} = R1^{-1} R2^{-1}
+  if ((s = chol_inv<TS>(mb, gram, R, Rinv, 0.0, flag, R1, R1inv, active, st))) return s;
   return RBGS_OK;
+}
+
+// One round of Cholesky QR with the shift (the provisional first pass of a
+// two-pass block only needs an invertible R_ii).
+template <class TS>
+rbgs_status cholqr1(int64_t k, int mb, const TS* Sp, TS** sm, TS* part, int* flag, const int* active,
+                    cudaStream_t st, TS* R, TS* Rinv) {
+  TS* gram = sm[0];
+  const double shift = sizeof(TS) == 4 ? 1e-6 : 0.0;
+  rbgs_status s =
+      small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
+  if (s) return s;
+  return chol_inv<TS>(mb, gram, R, Rinv, shift, flag, nullptr, nullptr, active, st);
 }
 
 // Step 2 by l Richardson iterations from X = 0:  X <- X + S^T (P - S X).
@@ -169,7 +181,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
   const int64_t p = m / mb;
   const int l = o.ls_iters < 1 ? 1 : o.ls_iters;
   const bool fp64 = sizeof(T) == 8;
-  const size_t sk_bytes = sketch_scratch_bytes(sketch, k, n, mb, fp64) + 256;
+  const size_t sk_bytes = sketch_scratch_bytes(sketch, k, n, 2 * mb, fp64) + 256;
   const bool cert = o.certify != 0 && stats != nullptr;
 
   // ---- carve the workspace
@@ -273,24 +285,28 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       TS* Si = S + c * k;
       double* Rcol = R + c * ldr;
       // step 2 and the implicit sketch of Alg. 5
+      // With a second pass to follow, the first pass is provisional: one
+      // Richardson step and one (shifted) Cholesky QR round; the second pass
+      // (l steps, two rounds) settles the block.
+      const bool provisional = o.reorth != 0 && c > 0;
       if (c > 0) {
-        if ((s = richardson<TS>(k, c, mb, S, Pi, X, m, Res, l, partf, nullptr, st))) return s;
+        if ((s = richardson<TS>(k, c, mb, S, Pi, X, m, Res, provisional ? 1 : l, partf, nullptr, st))) return s;
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
         s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X, m, 1.0, Sp, k, partf, kPartElems, nullptr, st);
         if (s) return s;
       } else {
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
       }
-      if ((s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, nullptr, st, Rii, Riinv))) return s;
+      if (provisional) s = cholqr1<TS>(k, mb, Sp, sm, partf, brk, nullptr, st, Rii, Riinv);
+      else s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, nullptr, st, Rii, Riinv);
+      if (s) return s;
       if ((s = make_g(c, X, Rii, Riinv, Rcol, nullptr))) return s;
       // step 3 fused with the triangular solve
       if ((s = tall(c, Wi, ldw, Qi, nullptr))) return s;
-      // step 5, and step 1 of the next block
-      if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st))) return s;
-      if (blk + 1 < p) {
-        s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi + mb * ldw, ldw, mb, Pi + mb * k, k, skscr, sk_bytes, st);
-        if (s) return s;
-      }
+      // step 5, and step 1 of the next block, in one pass (the single reduction per block of Alg. 5)
+      s = sketch_apply2_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, Wi + mb * ldw, ldw, blk + 1 < p ? mb : 0,
+                                 Pi + mb * k, k, skscr, sk_bytes, st);
+      if (s) return s;
       // optional second projection pass
       if (o.reorth && c > 0) {
         s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Si, k, 0.0, X2, m, partf, kPartElems, nullptr, st);

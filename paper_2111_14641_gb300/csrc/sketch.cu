@@ -87,23 +87,36 @@ rbgs_status srht_plan_get(uint64_t seed, int64_t n, int64_t k, const SrhtPlan** 
   lv.erase(std::unique(lv.begin(), lv.end()), lv.end());
   for (int64_t r = 0; r < k; ++r) rl[r] = (int)(std::lower_bound(lv.begin(), lv.end(), lo[r]) - lv.begin());
   p->L = (int)lv.size();
-  cudaError_t e1 = cudaMalloc(&p->d_lvals, sizeof(int) * std::max<size_t>(1, lv.size()));
-  cudaError_t e2 = cudaMalloc(&p->d_rhi, sizeof(int) * std::max<int64_t>(1, k));
-  cudaError_t e3 = cudaMalloc(&p->d_rl, sizeof(int) * std::max<int64_t>(1, k));
-  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+  std::vector<int> off((size_t)p->L + 1, 0), rs((size_t)k);
+  for (int64_t r = 0; r < k; ++r) off[(size_t)rl[r] + 1] += 1;
+  for (int l = 0; l < p->L; ++l) off[(size_t)l + 1] += off[(size_t)l];
+  {
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (int64_t r = 0; r < k; ++r) rs[(size_t)fill[(size_t)rl[r]]++] = (int)r;
+  }
+  auto release = [&]() {
     cudaFree(p->d_lvals);
     cudaFree(p->d_rhi);
     cudaFree(p->d_rl);
+    cudaFree(p->d_off);
+    cudaFree(p->d_rs);
     delete p;
+  };
+  cudaError_t e1 = cudaMalloc(&p->d_lvals, sizeof(int) * std::max<size_t>(1, lv.size()));
+  cudaError_t e2 = cudaMalloc(&p->d_rhi, sizeof(int) * std::max<int64_t>(1, k));
+  cudaError_t e3 = cudaMalloc(&p->d_rl, sizeof(int) * std::max<int64_t>(1, k));
+  cudaError_t e4 = cudaMalloc(&p->d_off, sizeof(int) * off.size());
+  cudaError_t e5 = cudaMalloc(&p->d_rs, sizeof(int) * std::max<int64_t>(1, k));
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess) {
+    release();
     return RBGS_ENOMEM;
   }
   if (cudaMemcpy(p->d_lvals, lv.data(), sizeof(int) * lv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->d_rhi, rhi.data(), sizeof(int) * k, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(p->d_rl, rl.data(), sizeof(int) * k, cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaFree(p->d_lvals);
-    cudaFree(p->d_rhi);
-    cudaFree(p->d_rl);
-    delete p;
+      cudaMemcpy(p->d_rl, rl.data(), sizeof(int) * k, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->d_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->d_rs, rs.data(), sizeof(int) * k, cudaMemcpyHostToDevice) != cudaSuccess) {
+    release();
     return RBGS_ECUDA;
   }
   pc.plans.push_back({dev, p});
@@ -122,6 +135,8 @@ void srht_plans_release() {
       cudaFree(e.second->d_lvals);
       cudaFree(e.second->d_rhi);
       cudaFree(e.second->d_rl);
+      cudaFree(e.second->d_off);
+      cudaFree(e.second->d_rs);
       delete e.second;
     } else {
       keep.push_back(e);
@@ -275,6 +290,229 @@ __global__ void srht_stage2(const TC* __restrict__ z, int T, int L, const int* _
   Y[r + col * ldy] = (TY)(acc * scale);
 }
 
+// Persistent, double-buffered form of stage 1 for float data (all columns of
+// up to two sources): one CTA per SM walks the (column, tile) items; a bulk
+// asynchronous copy brings the next tile into the second buffer while the
+// current one is transformed in place.  The waits on the copies are bounded.
+struct SrhtSrc {
+  const float* x[2];
+  int64_t ld[2];
+  int64_t nc0;  // columns of source 0; the rest come from source 1
+};
+
+__device__ __forceinline__ uint32_t sk_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool sk_mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > 4000000000ull) return false;
+  }
+}
+
+template <int E>
+__global__ void __launch_bounds__(kSrhtThreads, 1)
+    srht_stage1_persist(SrhtSrc src, int64_t n, int B, int logB, int T, uint2 key, const int* __restrict__ lvals,
+                        int L, float* __restrict__ z, int64_t ncols, const int* active, int* err) {
+  if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* bufs = reinterpret_cast<float*>(smem_raw);            // 2 x B
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(bufs + 2 * B);   // B / 32
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  const int64_t nitems = ncols * T;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sk_smem_u32(&full[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sk_smem_u32(&full[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bad = 0;
+  }
+  __syncthreads();
+  // item -> (column, tile, source pointer, valid rows, bulk-copy bytes)
+  auto item = [&](int64_t w, const float*& p, int64_t& row0, int& valid, uint32_t& bytes) {
+    const int64_t col = w / T;
+    const int t = (int)(w % T);
+    const int sidx = col < src.nc0 ? 0 : 1;
+    const int64_t lc = sidx ? col - src.nc0 : col;
+    row0 = (int64_t)t * B;
+    p = src.x[sidx] + lc * src.ld[sidx] + row0;
+    const int64_t v = n - row0;
+    valid = v <= 0 ? 0 : (int)(v < B ? v : B);
+    bytes = ((((uintptr_t)p) & 15) == 0) ? (uint32_t)((valid * 4) & ~15) : 0u;
+  };
+  auto issue = [&](int64_t w, int b) {
+    const float* p;
+    int64_t row0;
+    int valid;
+    uint32_t bytes;
+    item(w, p, row0, valid, bytes);
+    const uint32_t bar = sk_smem_u32(&full[b]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    if (bytes)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       sk_smem_u32(bufs + (size_t)b * B)),
+                   "l"(p), "r"(bytes), "r"(bar)
+                   : "memory");
+  };
+  // copies issued into / consumed from each buffer; a buffer with issued >
+  // consumed has a copy in flight whose phase parity is (issued - 1) & 1
+  int issued[2] = {0, 0}, consumed[2] = {0, 0};
+  int64_t w = blockIdx.x;
+  if (w < nitems) {
+    if (tid == 0) issue(w, 0);
+    issued[0] = 1;
+  }
+  for (int idx = 0; w < nitems; w += gridDim.x, ++idx) {
+    const int b = idx & 1;
+    const int64_t wn = w + gridDim.x;
+    if (wn < nitems) {  // buffer b^1 was released at the end of the previous item
+      if (tid == 0) issue(wn, b ^ 1);
+      issued[b ^ 1] += 1;
+    }
+    const float* p;
+    int64_t row0;
+    int valid;
+    uint32_t bytes;
+    item(w, p, row0, valid, bytes);
+    // sign words of this tile
+    const int nwords = (B + 31) >> 5;
+    for (int q = tid; q < nwords; q += blockDim.x) {
+      const int64_t e0 = row0 + 32 * (int64_t)q;
+      const uint4 bits = srht_sign_bits(key, (uint32_t)(e0 >> 7));
+      sgn[q] = word_of(bits, (int)((e0 >> 5) & 3));
+    }
+    if (!sk_mbar_wait(sk_smem_u32(&full[b]), (uint32_t)(consumed[b] & 1))) bad = 1;
+    consumed[b] += 1;
+    __syncthreads();
+    if (bad) {
+      consumed[b] -= 1;  // that copy may still be in flight
+      break;
+    }
+    float* buf = bufs + (size_t)b * B;
+    const int done = (int)(bytes / 4);  // entries that arrived by the bulk copy
+    float v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = tid + kSrhtThreads * e;
+      float x = 0.f;
+      if (j < done) x = buf[j];
+      else if (j < valid) x = __ldg(p + j);
+      if (j < B && ((sgn[j >> 5] >> (j & 31)) & 1u)) x = -x;
+      v[e] = x;
+    }
+#pragma unroll
+    for (int h = 1; h < E; h <<= 1) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if ((e & h) == 0) {
+          const float a = v[e], c = v[e + h];
+          v[e] = a + c;
+          v[e + h] = a - c;
+        }
+      }
+    }
+    __syncthreads();  // all reads of the raw layout done before the in-place permutation
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = tid + kSrhtThreads * e;
+      if (j < B) buf[swz(j)] = v[e];
+    }
+    const int lowbits = logB < 9 ? logB : 9;
+    for (int lo = 0; lo < lowbits; lo += 5) {
+      __syncthreads();
+      const int r = min(5, lowbits - lo);
+      switch (r) {
+        case 5: fwht_stage<float, 5>(buf, B, lo); break;
+        case 4: fwht_stage<float, 4>(buf, B, lo); break;
+        case 3: fwht_stage<float, 3>(buf, B, lo); break;
+        case 2: fwht_stage<float, 2>(buf, B, lo); break;
+        default: fwht_stage<float, 1>(buf, B, lo); break;
+      }
+    }
+    __syncthreads();
+    float* zo = z + w * L;  // (col * T + t) * L
+    for (int l = tid; l < L; l += blockDim.x) zo[l] = buf[swz(lvals[l])];
+    __syncthreads();  // buffer b may be refilled from the next iteration on
+  }
+  // leave no copy in flight into shared memory
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b)
+      if (issued[b] > consumed[b] && !sk_mbar_wait(sk_smem_u32(&full[b]), (uint32_t)((issued[b] - 1) & 1))) bad = 1;
+    if (bad && err) atomicExch(err, 1);
+  }
+  __syncthreads();
+}
+
+// Stage 2 as a transform across tiles: for each column and distinct low
+// index l, the T values z[col, :, l] go through the T-point Hadamard
+// transform in registers, which yields entry (i_hi, l) of H (D x) for every
+// i_hi; the sampled rows with low index l pick theirs.
+template <class TC, class TY, int TT>
+__global__ void __launch_bounds__(128) srht_stage2_fwht(const TC* __restrict__ z, int L, const int* __restrict__ off,
+                                                        const int* __restrict__ rs, const int* __restrict__ rhi,
+                                                        int64_t ncols, int64_t nc0, TC scale, TY* __restrict__ Y1,
+                                                        int64_t ldy1, TY* __restrict__ Y2, int64_t ldy2,
+                                                        const int* active) {
+  if (active && *active == 0) return;
+  __shared__ TC sv[TT][129];
+  const int64_t col = blockIdx.y;
+  const int l = blockIdx.x * 128 + threadIdx.x;
+  TC v[TT];
+#pragma unroll
+  for (int t = 0; t < TT; ++t) v[t] = l < L ? z[((int64_t)col * TT + t) * L + l] : (TC)0;
+#pragma unroll
+  for (int h = 1; h < TT; h <<= 1) {
+#pragma unroll
+    for (int e = 0; e < TT; ++e) {
+      if ((e & h) == 0) {
+        const TC a = v[e], b = v[e + h];
+        v[e] = a + b;
+        v[e + h] = a - b;
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < TT; ++t) sv[t][threadIdx.x] = v[t];
+  __syncwarp();
+  if (l >= L) return;
+  TY* Y = col < nc0 ? Y1 + col * ldy1 : Y2 + (col - nc0) * ldy2;
+  for (int q = off[l]; q < off[l + 1]; ++q) {
+    const int r = rs[q];
+    Y[r] = (TY)(sv[rhi[r]][threadIdx.x] * scale);
+  }
+}
+
+template <class TC, class TY>
+rbgs_status launch_stage2_fwht(int T, int L, const SrhtPlan* plan, const TC* z, int64_t ncols, int64_t nc0, TC scale,
+                               TY* Y1, int64_t ldy1, TY* Y2, int64_t ldy2, const int* active, cudaStream_t st,
+                               bool* done) {
+  *done = true;
+  dim3 grid((unsigned)((L + 127) / 128), (unsigned)ncols);
+  switch (T) {
+#define S2(TT)                                                                                                   \
+  case TT:                                                                                                       \
+    srht_stage2_fwht<TC, TY, TT><<<grid, 128, 0, st>>>(z, L, plan->d_off, plan->d_rs, plan->d_rhi, ncols, nc0,   \
+                                                       scale, Y1, ldy1, Y2, ldy2, active);                      \
+    break;
+    S2(1) S2(2) S2(4) S2(8) S2(16) S2(32) S2(64)
+#undef S2
+    default:
+      *done = false;
+      return RBGS_OK;
+  }
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
+
 // ------------------------------------------------------- Gaussian/Rademacher
 
 constexpr int kDenseRows = 64;   // Theta rows per CTA
@@ -394,37 +632,106 @@ size_t sketch_scratch_bytes(rbgs_sketch kind, int64_t k, int64_t n, int64_t ncol
 }
 
 template <class TX, class TY>
+rbgs_status sketch_apply2_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed, const TX* X1, int64_t ldx1,
+                            int64_t nc1, TY* Y1, int64_t ldy1, const TX* X2, int64_t ldx2, int64_t nc2, TY* Y2,
+                            int64_t ldy2, void* scratch, size_t scratch_bytes, cudaStream_t st, const int* active) {
+  using TC = TX;  // arithmetic follows the input precision
+  const int64_t ncols = nc1 + nc2;
+  if (ncols == 0 || k == 0) return RBGS_OK;
+  if (kind != RBGS_SK_SRHT) {
+    rbgs_status s = sketch_apply_t<TX, TY>(kind, k, n, seed, X1, ldx1, nc1, Y1, ldy1, scratch, scratch_bytes, st,
+                                           active);
+    if (s || nc2 == 0) return s;
+    return sketch_apply_t<TX, TY>(kind, k, n, seed, X2, ldx2, nc2, Y2, ldy2, scratch, scratch_bytes, st, active);
+  }
+  const uint2 key = seed_key(seed);
+  const double dscale = 1.0 / std::sqrt((double)k);
+  const TC scale = (TC)dscale;
+  const SrhtPlan* plan = nullptr;
+  rbgs_status s = srht_plan_get(seed, n, k, &plan);
+  if (s != RBGS_OK) return s;
+  const size_t need = sizeof(TC) * (size_t)(ncols * plan->T) * (size_t)plan->L;
+  if (scratch_bytes < need) return RBGS_EINVAL;
+  TC* z = reinterpret_cast<TC*>(scratch);
+  int logB = 0;
+  while ((1 << logB) < plan->B) ++logB;
+  const int E = plan->B >= kSrhtThreads ? plan->B / kSrhtThreads : 1;
+  if (sizeof(TX) == 4) {
+    int dev = 0, nsm = 0;
+    RBGS_CUDA_TRY(cudaGetDevice(&dev));
+    RBGS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t nitems = ncols * plan->T;
+    const int grid = (int)std::min<int64_t>(nitems, nsm);
+    const size_t smem = sizeof(float) * 2 * (size_t)plan->B + sizeof(uint32_t) * (size_t)((plan->B + 31) / 32);
+    SrhtSrc sd;
+    sd.x[0] = reinterpret_cast<const float*>(X1);
+    sd.x[1] = reinterpret_cast<const float*>(nc2 ? X2 : X1);
+    sd.ld[0] = ldx1;
+    sd.ld[1] = nc2 ? ldx2 : ldx1;
+    sd.nc0 = nc1;
+    float* zf = reinterpret_cast<float*>(z);
+    auto go = [&](auto kern) -> rbgs_status {
+      RBGS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float) * 2 * kSrhtTile + 4 * kSrhtTile / 32)));
+      kern<<<grid, kSrhtThreads, smem, st>>>(sd, n, plan->B, logB, plan->T, key, plan->d_lvals, plan->L, zf, ncols,
+                                             active, nullptr);
+      RBGS_LAUNCH_CHECK();
+      return RBGS_OK;
+    };
+    switch (E) {
+      case 1: s = go(srht_stage1_persist<1>); break;
+      case 2: s = go(srht_stage1_persist<2>); break;
+      case 4: s = go(srht_stage1_persist<4>); break;
+      case 8: s = go(srht_stage1_persist<8>); break;
+      case 16: s = go(srht_stage1_persist<16>); break;
+      case 32: s = go(srht_stage1_persist<32>); break;
+      default: return RBGS_EINVAL;
+    }
+    if (s) return s;
+  } else {
+    const size_t smem = sizeof(TC) * (size_t)plan->B + sizeof(uint32_t) * (size_t)((plan->B + 31) / 32);
+    for (int src = 0; src < 2; ++src) {
+      const TX* X = src ? X2 : X1;
+      const int64_t ldx = src ? ldx2 : ldx1;
+      const int64_t nc = src ? nc2 : nc1;
+      TC* zs = z + (src ? nc1 : 0) * plan->T * plan->L;
+      for (int64_t c0 = 0; c0 < nc; c0 += 65535) {
+        const int64_t nn = std::min<int64_t>(65535, nc - c0);
+        dim3 grid((unsigned)plan->T, (unsigned)nn);
+        s = launch_stage1<TX, TC>(grid, smem, st, X + c0 * ldx, ldx, n, plan->B, logB, plan->T, key, plan->d_lvals,
+                                  plan->L, zs + c0 * plan->T * plan->L, active);
+        if (s) return s;
+      }
+    }
+  }
+  bool done = false;
+  s = launch_stage2_fwht<TC, TY>(plan->T, plan->L, plan, z, ncols, nc1, scale, Y1, ldy1, Y2, ldy2, active, st, &done);
+  if (s) return s;
+  if (!done) {
+    for (int src = 0; src < 2; ++src) {
+      const int64_t nc = src ? nc2 : nc1;
+      if (nc == 0) continue;
+      const int64_t tot = k * nc;
+      srht_stage2<TC, TY><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+          z + (src ? nc1 : 0) * plan->T * plan->L, plan->T, plan->L, plan->d_rhi, plan->d_rl, k, nc, scale,
+          src ? Y2 : Y1, src ? ldy2 : ldy1, active);
+      RBGS_LAUNCH_CHECK();
+    }
+  }
+  return RBGS_OK;
+}
+
+template <class TX, class TY>
 rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed, const TX* X, int64_t ldx,
                            int64_t ncols, TY* Y, int64_t ldy, void* scratch, size_t scratch_bytes, cudaStream_t st,
                            const int* active) {
   using TC = TX;  // arithmetic follows the input precision
   if (ncols == 0 || k == 0) return RBGS_OK;
+  if (kind == RBGS_SK_SRHT)
+    return sketch_apply2_t<TX, TY>(kind, k, n, seed, X, ldx, ncols, Y, ldy, X, ldx, 0, Y, ldy, scratch,
+                                   scratch_bytes, st, active);
   const uint2 key = seed_key(seed);
   const double dscale = 1.0 / std::sqrt((double)k);
-  const TC scale = (TC)dscale;
-  if (kind == RBGS_SK_SRHT) {
-    const SrhtPlan* plan = nullptr;
-    rbgs_status s = srht_plan_get(seed, n, k, &plan);
-    if (s != RBGS_OK) return s;
-    const size_t need = sizeof(TC) * (size_t)(ncols * plan->T) * (size_t)plan->L;
-    if (scratch_bytes < need) return RBGS_EINVAL;
-    TC* z = reinterpret_cast<TC*>(scratch);
-    int logB = 0;
-    while ((1 << logB) < plan->B) ++logB;
-    const size_t smem = sizeof(TC) * (size_t)plan->B + sizeof(uint32_t) * (size_t)((plan->B + 31) / 32);
-    for (int64_t c0 = 0; c0 < ncols; c0 += 65535) {
-      const int64_t nc = std::min<int64_t>(65535, ncols - c0);
-      dim3 grid((unsigned)plan->T, (unsigned)nc);
-      rbgs_status e = launch_stage1<TX, TC>(grid, smem, st, X + c0 * ldx, ldx, n, plan->B, logB, plan->T, key,
-                                            plan->d_lvals, plan->L, z + c0 * plan->T * plan->L, active);
-      if (e) return e;
-    }
-    const int64_t tot = k * ncols;
-    srht_stage2<TC, TY><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(z, plan->T, plan->L, plan->d_rhi,
-                                                                      plan->d_rl, k, ncols, scale, Y, ldy, active);
-    RBGS_LAUNCH_CHECK();
-    return RBGS_OK;
-  }
   if (kind != RBGS_SK_GAUSS && kind != RBGS_SK_RADEMACHER) return RBGS_EINVAL;
   const int nsplit = dense_nsplit(k, n);
   const int64_t rows_per_split = ((n + nsplit - 1) / nsplit + kDenseJ - 1) / kDenseJ * kDenseJ;
@@ -439,7 +746,8 @@ rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed
                                                                               dscale, rows_per_split, part, active);
     else
       dense_sketch_part<RBGS_SK_RADEMACHER, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
-                                                                                   dscale, rows_per_split, part, active);
+                                                                                   dscale, rows_per_split, part,
+                                                                                   active);
     RBGS_LAUNCH_CHECK();
     const int64_t tot = k * nc;
     dense_sketch_reduce<TC, TY><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nsplit, k, nc, Y + c0 * ldy, ldy,
@@ -458,5 +766,15 @@ template rbgs_status sketch_apply_t<float, double>(rbgs_sketch, int64_t, int64_t
 template rbgs_status sketch_apply_t<float, float>(rbgs_sketch, int64_t, int64_t, uint64_t, const float*, int64_t,
                                                   int64_t, float*, int64_t, void*, size_t, cudaStream_t,
                                                   const int*);
+
+template rbgs_status sketch_apply2_t<double, double>(rbgs_sketch, int64_t, int64_t, uint64_t, const double*, int64_t,
+                                                     int64_t, double*, int64_t, const double*, int64_t, int64_t,
+                                                     double*, int64_t, void*, size_t, cudaStream_t, const int*);
+template rbgs_status sketch_apply2_t<float, double>(rbgs_sketch, int64_t, int64_t, uint64_t, const float*, int64_t,
+                                                    int64_t, double*, int64_t, const float*, int64_t, int64_t,
+                                                    double*, int64_t, void*, size_t, cudaStream_t, const int*);
+template rbgs_status sketch_apply2_t<float, float>(rbgs_sketch, int64_t, int64_t, uint64_t, const float*, int64_t,
+                                                   int64_t, float*, int64_t, const float*, int64_t, int64_t, float*,
+                                                   int64_t, void*, size_t, cudaStream_t, const int*);
 
 }  // namespace rbgs

@@ -34,27 +34,41 @@ __global__ void __launch_bounds__(256) small_gemm_part(int trans, int64_t M, int
   const int split = blockIdx.y;
   const int64_t kb = (int64_t)split * kper;
   const int64_t ke = min(K, kb + kper);
+  constexpr int PER = (SG_K * SG_T) / 256;  // elements per thread per chunk (A and B alike)
+  TACC ra[PER], rb[PER];
+  // software pipeline: the global loads of chunk l0 + SG_K are in flight while chunk l0 is used
+  auto load = [&](int64_t l0) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      int il, ll;
+      if (trans) { ll = e % SG_K; il = e / SG_K; }   // A is K x M: contiguous in l
+      else { il = e % SG_T; ll = e / SG_T; }         // A is M x K: contiguous in i
+      const int64_t gi = i0 + il, gl = l0 + ll;
+      ra[q] = (gi < M && gl < ke) ? (TACC)(trans ? A[gl + gi * lda] : A[gi + gl * lda]) : (TACC)0;
+      const int lb = e % SG_K, j = e / SG_K;
+      const int64_t gb = l0 + lb;
+      rb[q] = (gb < ke && j < N) ? (TACC)B[gb + (int64_t)j * ldb] : (TACC)0;
+    }
+  };
   TACC acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[i][q] = 0;
+  if (kb < ke) load(kb);
   for (int64_t l0 = kb; l0 < ke; l0 += SG_K) {
-    for (int e = tid; e < SG_K * SG_T; e += 256) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
       int il, ll;
-      if (trans) { ll = e % SG_K; il = e / SG_K; }   // A is K x M: contiguous in l
-      else { il = e % SG_T; ll = e / SG_T; }         // A is M x K: contiguous in i
-      const int64_t gi = i0 + il, gl = l0 + ll;
-      TACC v = 0;
-      if (gi < M && gl < ke) v = (TACC)(trans ? A[gl + gi * lda] : A[gi + gl * lda]);
-      As[ll][il] = v;
-    }
-    for (int e = tid; e < SG_K * SG_N; e += 256) {
-      const int ll = e % SG_K, j = e / SG_K;
-      const int64_t gl = l0 + ll;
-      Bs[ll][j] = (gl < ke && j < N) ? (TACC)B[gl + (int64_t)j * ldb] : (TACC)0;
+      if (trans) { ll = e % SG_K; il = e / SG_K; }
+      else { il = e % SG_T; ll = e / SG_T; }
+      As[ll][il] = ra[q];
+      Bs[e % SG_K][e / SG_K] = rb[q];
     }
     __syncthreads();
+    if (l0 + SG_K < ke) load(l0 + SG_K);
 #pragma unroll
     for (int ll = 0; ll < SG_K; ++ll) {
       TACC a[4], b[4];
@@ -103,17 +117,27 @@ __global__ void small_gemm_reduce(int64_t M, int N, int ks, const TACC* __restri
 template <class T>
 __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restrict__ G, T* __restrict__ R,
                                                        T* __restrict__ Rinv, double shift, int* flag,
+                                                       const T* __restrict__ Rprev, const T* __restrict__ Rprev_inv,
                                                        const int* active) {
   if (active && *active == 0) return;
-  __shared__ T A[64][65];
-  __shared__ T X[64][65];
+  extern __shared__ __align__(16) unsigned char chol_smem[];
+  typedef T Row[65];
+  Row* A = reinterpret_cast<Row*>(chol_smem);   // 64 x 65
+  Row* X = A + 64;
+  Row* P = X + 64;    // Rprev
+  Row* PI = P + 64;   // Rprev_inv
   __shared__ T rinv_s;
   __shared__ int bad_s;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < mb * mb; e += nt) {
-    const int i = e % mb, l = e / mb;
-    A[i][l] = (i <= l) ? G[i + l * mb] : (T)0;
-  }
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // 16 x 16 thread grid
+  for (int l = ty; l < mb; l += 16)
+    for (int i = tx; i < mb; i += 16) {
+      A[i][l] = (i <= l) ? G[i + l * mb] : (T)0;
+      X[i][l] = (i == l) ? (T)1 : (T)0;
+      if (Rprev) {
+        P[i][l] = Rprev[i + l * mb];
+        PI[i][l] = Rprev_inv[i + l * mb];
+      }
+    }
   if (tid == 0) bad_s = 0;
   __syncthreads();
   if (shift != 0.0) {
@@ -126,6 +150,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
     if (tid < mb) A[tid][tid] += rinv_s;
     __syncthreads();
   }
+  // right-looking Cholesky, upper factor in A
   for (int j = 0; j < mb; ++j) {
     if (tid == 0) {
       T d = A[j][j];
@@ -138,31 +163,44 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
       rinv_s = (T)1 / r;
     }
     __syncthreads();
-    for (int l = j + 1 + tid; l < mb; l += nt) A[j][l] *= rinv_s;
+    for (int l = j + 1 + tid; l < mb; l += 256) A[j][l] *= rinv_s;
     __syncthreads();
-    const int w = mb - j - 1;
-    for (int e = tid; e < w * w; e += nt) {
-      const int i = j + 1 + e % w, l = j + 1 + e / w;
-      if (i <= l) A[i][l] -= A[j][i] * A[j][l];
+    for (int l = j + 1 + ty; l < mb; l += 16) {
+      const T ajl = A[j][l];
+      for (int i = j + 1 + tx; i <= l; i += 16) A[i][l] -= A[j][i] * ajl;
     }
     __syncthreads();
   }
-  // inverse, rows from the bottom: X[i][l] = (delta_il - sum_{t=i+1}^{l} R[i][t] X[t][l]) / R[i][i]
-  for (int e = tid; e < mb * mb; e += nt) X[e % mb][e / mb] = (T)0;
-  __syncthreads();
-  for (int i = mb - 1; i >= 0; --i) {
-    const T di = (T)1 / A[i][i];
-    for (int l = i + tid; l < mb; l += nt) {
-      T s = (l == i) ? (T)1 : (T)0;
-      for (int t = i + 1; t <= l; ++t) s -= A[i][t] * X[t][l];
-      X[i][l] = s * di;
+  // inverse by Gauss-Jordan elimination from the last pivot up (X = I to start):
+  // row j of X /= R_jj, then every row i < j subtracts R_ij times row j.
+  for (int j = mb - 1; j >= 0; --j) {
+    const T dj = (T)1 / A[j][j];
+    for (int l = j + tid; l < mb; l += 256) X[j][l] *= dj;
+    __syncthreads();
+    for (int l = j + ty; l < mb; l += 16) {
+      const T xjl = X[j][l];
+      for (int i = tx; i < j; i += 16) X[i][l] -= A[i][j] * xjl;
     }
     __syncthreads();
   }
-  for (int e = tid; e < mb * mb; e += nt) {
-    const int i = e % mb, l = e / mb;
-    R[i + l * mb] = (i <= l) ? A[i][l] : (T)0;
-    Rinv[i + l * mb] = (i <= l) ? X[i][l] : (T)0;
+  if (Rprev) {
+    // second round of Cholesky QR: R := R2 R1, R^{-1} := R1^{-1} R2^{-1} (upper triangular products)
+    for (int l = ty; l < mb; l += 16)
+      for (int i = tx; i < mb; i += 16) {
+        T s1 = 0, s2 = 0;
+        for (int t = i; t <= l; ++t) {
+          s1 += A[i][t] * P[t][l];
+          s2 += PI[i][t] * X[t][l];
+        }
+        R[i + l * mb] = (i <= l) ? s1 : (T)0;
+        Rinv[i + l * mb] = (i <= l) ? s2 : (T)0;
+      }
+  } else {
+    for (int l = ty; l < mb; l += 16)
+      for (int i = tx; i < mb; i += 16) {
+        R[i + l * mb] = (i <= l) ? A[i][l] : (T)0;
+        Rinv[i + l * mb] = (i <= l) ? X[i][l] : (T)0;
+      }
   }
   if (tid == 0 && bad_s && flag) atomicOr(flag, 1);
 }
@@ -218,9 +256,9 @@ __global__ void assemble_g_kernel(int64_t c, int mb, const TS* __restrict__ Rc, 
   const int j = (int)(idx / rows);
   double g;
   if (i < c) {
-    double s = 0.0;
-    for (int t = 0; t <= j; ++t) s += (double)Rc[i + t * ldrc] * (double)Riinv[t + j * mb];
-    g = -s;
+    TS s = 0;
+    for (int t = 0; t <= j; ++t) s += Rc[i + t * ldrc] * Riinv[t + j * mb];
+    g = -(double)s;
     if (R) R[i + (int64_t)j * ldr] = (double)Rc[i + (int64_t)j * ldrc];
   } else {
     const int ii = (int)(i - c);
@@ -242,9 +280,9 @@ __global__ void reorth_r_top(int64_t c, int mb, const TS* __restrict__ R2c, int6
   const int j = (int)(idx / rows);
   const double* Rold = Rcol + c;  // R_ii (old) at rows c..c+mb-1
   if (i < c) {
-    double s = 0.0;
-    for (int t = 0; t <= j; ++t) s += (double)R2c[i + t * ldr2] * Rold[t + (int64_t)j * ldr];
-    Rcol[i + (int64_t)j * ldr] += s;
+    TS s = 0;
+    for (int t = 0; t <= j; ++t) s += R2c[i + t * ldr2] * (TS)Rold[t + (int64_t)j * ldr];
+    Rcol[i + (int64_t)j * ldr] += (double)s;
   } else {
     const int ii = (int)(i - c);
     double s = 0.0;
@@ -267,11 +305,12 @@ __global__ void reorth_decide_kernel(int64_t c, int mb, const TS* __restrict__ X
                                      int mode, int* active, int* count, int* blk_flag) {
   __shared__ double red[1024];
   double s = 0.0;
-  for (int j = 0; j < mb; ++j)
-    for (int64_t i = threadIdx.x; i < c; i += blockDim.x) {
-      const double v = (double)X[i + j * ldx];
-      s += v * v;
-    }
+  const int64_t tot = c * mb;
+#pragma unroll 8
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const double v = (double)X[(e % c) + (e / c) * ldx];
+    s += v * v;
+  }
   red[threadIdx.x] = s;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
@@ -376,15 +415,19 @@ INST_SG(float, double, double)
 #undef INST_SG
 
 template <class T>
-rbgs_status chol_inv(int mb, const T* G, T* R, T* Rinv, double shift, int* flag, const int* active,
-                     cudaStream_t st) {
+rbgs_status chol_inv(int mb, const T* G, T* R, T* Rinv, double shift, int* flag, const T* Rprev, const T* Rprev_inv,
+                     const int* active, cudaStream_t st) {
   if (mb < 1 || mb > 64) return RBGS_EINVAL;
-  chol_inv_kernel<T><<<1, 256, 0, st>>>(mb, G, R, Rinv, shift, flag, active);
+  const int smem = (int)(4 * 64 * 65 * sizeof(T));
+  RBGS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  chol_inv_kernel<T><<<1, 256, smem, st>>>(mb, G, R, Rinv, shift, flag, Rprev, Rprev_inv, active);
   RBGS_LAUNCH_CHECK();
   return RBGS_OK;
 }
-template rbgs_status chol_inv<double>(int, const double*, double*, double*, double, int*, const int*, cudaStream_t);
-template rbgs_status chol_inv<float>(int, const float*, float*, float*, double, int*, const int*, cudaStream_t);
+template rbgs_status chol_inv<double>(int, const double*, double*, double*, double, int*, const double*,
+                                      const double*, const int*, cudaStream_t);
+template rbgs_status chol_inv<float>(int, const float*, float*, float*, double, int*, const float*, const float*,
+                                     const int*, cudaStream_t);
 
 template <class TS>
 rbgs_status trmm_right_upper(int64_t k, int mb, const TS* A, int64_t lda, const TS* U, TS* Out, int64_t ldo,

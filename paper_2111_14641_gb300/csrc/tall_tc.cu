@@ -25,10 +25,10 @@
 // memory for each of the 12 MMAs), which bounded the earlier designs.
 // Accuracy: the tensor cores truncate when they add into an FP32 accumulator,
 // so an accumulator that receives every product of a long K loop drifts by
-// ~(number of MMAs) * 2^-24.  Each chunk's a_hi g_hi product therefore lands
-// in a fresh TMEM slot (rotating slots) that the epilogue adds with
-// compensated FP32 summation; the two cross terms, 2^-11 smaller, share one
-// accumulator per tile (double-buffered across tiles).
+// ~(number of MMAs) * 2^-24.  Each chunk's products therefore land in a fresh
+// TMEM slot (rotating slots), the small cross terms first and the four main
+// products last, and the epilogue adds the slots with compensated FP32
+// summation.
 // Every mbarrier wait is bounded; on expiry the kernel records an error flag,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -57,19 +57,18 @@ constexpr uint32_t kSuspendHintNs = 100000u;           // sleep hint per try_wai
 constexpr int TMEM_COLS = 512;
 
 // Pipeline shape: RAW raw stages (TMA, shared memory), GS G stages (shared
-// memory), F chunks accumulated per TMEM slot before the epilogue drains it,
-// AS converted-A stages and NS main-product slots in tensor memory.
-// TMEM columns: NS x 64 slots | 2 x 64 cross accumulators | AS x 64 A stages.
-template <int RAW, int GS, int F, int AS, int NS>
+// memory), AS converted-A stages and NS product slots in tensor memory.
+// TMEM columns: NS x 64 slots | AS x 64 A stages.
+template <int RAW, int GS, int AS, int NS>
 struct TcCfg {
-  static constexpr int RAW_STAGES = RAW, G_STAGES = GS, CHUNKS_PER_SLOT = F, A_STAGES = AS, NSLOT = NS;
+  static constexpr int RAW_STAGES = RAW, G_STAGES = GS, A_STAGES = AS, NSLOT = NS;
   static constexpr int G_OFF = RAW * A_BYTES;
   static constexpr int SMEM_BAR_OFF = G_OFF + GS * G_BYTES;
-  static constexpr int SMEM_BYTES = SMEM_BAR_OFF + 512 + 1024;  // + barriers + alignment slack
+  static constexpr int BAR_BYTES = 1024;  // 65 mbarriers, the TMEM address slot and the abort flag
+  static constexpr int SMEM_BYTES = SMEM_BAR_OFF + BAR_BYTES + 1024;  // + alignment slack of the base
   static constexpr int SLOT_COL0 = 0;
-  static constexpr int CROSS_COL0 = NS * TC_N;
-  static constexpr int A_COL0 = CROSS_COL0 + 2 * TC_N;
-  static_assert(RAW <= 8 && GS <= 8 && AS <= 4 && NS <= 4, "barrier slots");
+  static constexpr int A_COL0 = NS * TC_N;
+  static_assert(RAW <= 8 && GS <= 8 && AS <= 8 && NS <= 8, "barrier slots");
   static_assert(A_COL0 + AS * 2 * TC_K <= TMEM_COLS, "TMEM budget");
 };
 
@@ -170,14 +169,6 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                             ((uint32_t)(TC_M >> 4) << 24);
 
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
-      : "memory");
-}
-
 // A operand read from tensor memory (rows in lanes, K along columns).
 __device__ __forceinline__ void umma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accum) {
   asm volatile(
@@ -194,18 +185,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
       "%15, %16};" ::"r"(taddr),
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
       "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
-}
-
-// 32 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
       : "memory");
 }
 
@@ -236,26 +215,25 @@ template <class Cfg>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tall_tc_kernel(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2, TcParams p) {
   constexpr int RAW_STAGES = Cfg::RAW_STAGES, G_STAGES = Cfg::G_STAGES;
-  constexpr int F = Cfg::CHUNKS_PER_SLOT, A_STAGES = Cfg::A_STAGES, NSLOT = Cfg::NSLOT;
+  constexpr int A_STAGES = Cfg::A_STAGES, NSLOT = Cfg::NSLOT;
   constexpr int G_OFF = Cfg::G_OFF, SMEM_BAR_OFF = Cfg::SMEM_BAR_OFF;
-  constexpr int SLOT_COL0 = Cfg::SLOT_COL0, CROSS_COL0 = Cfg::CROSS_COL0, A_COL0 = Cfg::A_COL0;
+  constexpr int SLOT_COL0 = Cfg::SLOT_COL0, A_COL0 = Cfg::A_COL0;
   if (p.active && *p.active == 0) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t bar0 = smem_u32(smem + SMEM_BAR_OFF);
   auto raw_full = [&](int s) { return bar0 + 8u * s; };                 // 8 slots
   auto raw_empty = [&](int s) { return bar0 + 8u * (8 + s); };          // 8
-  auto a_full = [&](int s) { return bar0 + 8u * (16 + s); };            // 4
-  auto a_free = [&](int s) { return bar0 + 8u * (20 + s); };            // 4
-  auto g_full = [&](int s) { return bar0 + 8u * (24 + s); };            // 8
-  auto g_free = [&](int s) { return bar0 + 8u * (32 + s); };            // 8
-  auto slot_full = [&](int s) { return bar0 + 8u * (40 + s); };         // 4
-  auto slot_free = [&](int s) { return bar0 + 8u * (44 + s); };         // 4
-  auto cross_full = [&](int b) { return bar0 + 8u * (48 + b); };        // 2
-  auto cross_free = [&](int b) { return bar0 + 8u * (50 + b); };        // 2
-  const uint32_t fin_bar = bar0 + 8u * 52;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 54);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 54 + 8);
+  auto a_full = [&](int s) { return bar0 + 8u * (16 + s); };            // 8
+  auto a_free = [&](int s) { return bar0 + 8u * (24 + s); };            // 8
+  auto g_full = [&](int s) { return bar0 + 8u * (32 + s); };            // 8
+  auto g_free = [&](int s) { return bar0 + 8u * (40 + s); };            // 8
+  auto slot_full = [&](int s) { return bar0 + 8u * (48 + s); };         // 8
+  auto slot_free = [&](int s) { return bar0 + 8u * (56 + s); };         // 8
+  const uint32_t fin_bar = bar0 + 8u * 64;
+  static_assert(8 * 66 + 16 <= Cfg::BAR_BYTES, "barrier area");
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + SMEM_BAR_OFF + 8 * 66);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SMEM_BAR_OFF + 8 * 66 + 8);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -277,10 +255,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int s = 0; s < NSLOT; ++s) {
       mbar_init(slot_full(s), 1);
       mbar_init(slot_free(s), 16);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(cross_full(b), 1);
-      mbar_init(cross_free(b), 16);
     }
     mbar_init(fin_bar, 1);
     *abort_flag = 0;
@@ -355,55 +329,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
+    // Each chunk's products go to a fresh TMEM slot: the small cross terms
+    // a_hi g_lo + a_lo g_hi first, then the four a_hi g_hi products, so the
+    // truncating accumulation adds to a small value first and to the large
+    // one only four times.
     if (lane == 0) {
-      uint32_t it = 0, tcount = 0, sbase = 0;
-      for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x, ++tcount) {
-        const int b = tcount & 1;
-        const uint32_t bph = (tcount >> 1) & 1u;
-        if (!mbar_wait(cross_free(b), bph ^ 1u)) {
-          fail();
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dcross = tmem_base + (uint32_t)(CROSS_COL0 + b * TC_N);
-        bool bad = false;
+      uint32_t it = 0;
+      bool bad = false;
+      for (int tile = blockIdx.x; tile < p.ntiles && !bad; tile += gridDim.x) {
         for (int ch = 0; ch < nchunks; ++ch, ++it) {
-          const int c = it % A_STAGES, g = it % G_STAGES;
-          const uint32_t cph = (it / A_STAGES) & 1u, gph = (it / G_STAGES) & 1u;
-          // slot u of this tile holds chunks [F u, F u + F); slots rotate over all tiles (sidx)
-          const bool first_in_slot = (ch % F) == 0;
-          const bool last_in_slot = (ch % F) == F - 1 || ch == nchunks - 1;
-          const uint32_t sidx = sbase + (uint32_t)(ch / F);
-          const int sl = sidx % NSLOT;
-          const uint32_t sph = (sidx / NSLOT) & 1u;
-          if ((first_in_slot && !mbar_wait(slot_free(sl), sph ^ 1u)) || !mbar_wait(a_full(c), cph) ||
-              !mbar_wait(g_full(g), gph) || *abort_flag) {
+          const int c = it % A_STAGES, g = it % G_STAGES, sl = it % NSLOT;
+          const uint32_t cph = (it / A_STAGES) & 1u, gph = (it / G_STAGES) & 1u, sph = (it / NSLOT) & 1u;
+          if (!mbar_wait(slot_free(sl), sph ^ 1u) || !mbar_wait(a_full(c), cph) || !mbar_wait(g_full(g), gph) ||
+              *abort_flag) {
             fail();
             bad = true;
             break;
           }
           tc_fence_after();
-          const uint32_t dmain = tmem_base + (uint32_t)(SLOT_COL0 + sl * TC_N);
+          const uint32_t dslot = tmem_base + (uint32_t)(SLOT_COL0 + sl * TC_N);
           const uint32_t ahi = tmem_base + (uint32_t)(A_COL0 + c * 2 * TC_K);
           const uint32_t alo = ahi + TC_K;
           const uint32_t bhi = smem_u32(smem + G_OFF + g * G_BYTES);
           const uint32_t blo = bhi + B_BYTES;
-          // main products of the chunk (fresh slot every F chunks), then the small cross terms
-#pragma unroll
-          for (int kk = 0; kk < TC_K / 8; ++kk)
-            umma_tf32_ts(dmain, ahi + 8 * kk, umma_desc(bhi + kk * 256, 128, 1024), (!first_in_slot) || kk != 0);
 #pragma unroll
           for (int kk = 0; kk < TC_K / 8; ++kk) {
-            umma_tf32_ts(dcross, ahi + 8 * kk, umma_desc(blo + kk * 256, 128, 1024), (ch | kk) != 0);
-            umma_tf32_ts(dcross, alo + 8 * kk, umma_desc(bhi + kk * 256, 128, 1024), 1u);
+            umma_tf32_ts(dslot, ahi + 8 * kk, umma_desc(blo + kk * 256, 128, 1024), kk != 0);
+            umma_tf32_ts(dslot, alo + 8 * kk, umma_desc(bhi + kk * 256, 128, 1024), 1u);
           }
+#pragma unroll
+          for (int kk = 0; kk < TC_K / 8; ++kk)
+            umma_tf32_ts(dslot, ahi + 8 * kk, umma_desc(bhi + kk * 256, 128, 1024), 1u);
           umma_commit(a_free(c));
           umma_commit(g_free(g));
-          if (last_in_slot) umma_commit(slot_full(sl));
+          umma_commit(slot_full(sl));
         }
-        if (bad) break;
-        umma_commit(cross_full(b));
-        sbase += (uint32_t)((nchunks + F - 1) / F);
       }
       // all issued MMAs complete before TMEM is released
       umma_commit(fin_bar);
@@ -454,26 +414,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     // ----------------------------------------------- epilogue (warps 11..26)
-    // Per slot: drain the TMEM slot into compensated FP32 sums; per tile: add
-    // the cross-term accumulator and store the rows.  Four warps share each
-    // TMEM lane quarter (warp % 4), 16 columns each.
+    // Per chunk: drain its TMEM slot into compensated FP32 sums; per tile:
+    // store the rows.  Four warps share each TMEM lane quarter (warp % 4),
+    // 16 columns each.
     const int quarter = warp & 3;
     const int part = (warp - 11) >> 2;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
     const uint32_t col_off = (uint32_t)(16 * part);
-    uint32_t sidx = 0, tcount = 0;
+    uint32_t it = 0;
     bool stop = false;
-    const int nslots_tile = (nchunks + F - 1) / F;
-    for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x, ++tcount) {
+    for (int tile = blockIdx.x; tile < p.ntiles && !stop; tile += gridDim.x) {
       float acc[16], cmp[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         acc[j] = 0.f;
         cmp[j] = 0.f;
       }
-      for (int u = 0; u < nslots_tile; ++u, ++sidx) {
-        const int sl = sidx % NSLOT;
-        const uint32_t sph = (sidx / NSLOT) & 1u;
+      for (int ch = 0; ch < nchunks; ++ch, ++it) {
+        const int sl = it % NSLOT;
+        const uint32_t sph = (it / NSLOT) & 1u;
         const bool ok = __all_sync(0xffffffffu, mbar_wait(slot_full(sl), sph));
         if (!ok && lane == 0) fail();
         if (!ok || __shfl_sync(0xffffffffu, (int)*abort_flag, 0)) {
@@ -496,23 +455,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       if (stop) break;
-      const int b = tcount & 1;
-      const uint32_t bph = (tcount >> 1) & 1u;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(cross_full(b), bph));
-      if (!ok && lane == 0) fail();
-      if (!ok || __shfl_sync(0xffffffffu, (int)*abort_flag, 0)) break;
-      tc_fence_after();
-      float v[16];
-      tmem_ld16(tmem_base + lane_off + (uint32_t)(CROSS_COL0 + b * TC_N) + col_off, v);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(cross_free(b));
       const int64_t row = (int64_t)tile * TC_M + 32 * quarter + lane;
       if (row < p.n) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if ((int)col_off + j < p.mb) p.qout[row + (int64_t)(col_off + j) * p.ldo] = acc[j] + (v[j] - cmp[j]);
+          if ((int)col_off + j < p.mb) p.qout[row + (int64_t)(col_off + j) * p.ldo] = acc[j] - cmp[j];
       }
     }
   }
@@ -647,10 +594,10 @@ rbgs_status tall_update_tc(int64_t n, int64_t c, int64_t mb, const float* A1, in
     return RBGS_OK;
   };
   switch (tc_config()) {
-    case 1: return go(TcCfg<8, 4, 2, 4, 2>{});
-    case 2: return go(TcCfg<8, 4, 1, 4, 2>{});
-    case 3: return go(TcCfg<8, 4, 2, 3, 3>{});
-    default: return go(TcCfg<8, 4, 1, 3, 3>{});
+    case 1: return go(TcCfg<8, 4, 5, 3>{});
+    case 2: return go(TcCfg<8, 4, 6, 2>{});
+    case 3: return go(TcCfg<6, 6, 4, 4>{});
+    default: return go(TcCfg<8, 4, 4, 4>{});
   }
 }
 
