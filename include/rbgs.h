@@ -45,7 +45,8 @@ typedef enum {
   RBGS_ENOTCERTIFIED = 5,  /* Delta or Delta~ > 0.1, Thm. 4.1 cannot certify (on request)    */
   RBGS_ETIMEOUT = 6,       /* a bounded device-side wait expired                            */
   RBGS_ENOCONV = 7,        /* an iterative solver stopped before its tolerance               */
-  RBGS_ENODEV = 8          /* no usable sm_103 device                                        */
+  RBGS_ENODEV = 8,         /* no usable sm_103 device                                        */
+  RBGS_ETOOLARGE = 9       /* c + mb > RBGS_NOALLOC_MAX_K in rbgs_tall_update_noalloc        */
 } rbgs_status;
 
 /* Sketching matrices Theta (k x n).  Sec. 2.3 uses Rademacher and SRHT; the
@@ -131,6 +132,25 @@ RBGS_API rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n,
 RBGS_API rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_t mb, const void* Qprev, int64_t ldq,
                              const void* X, int64_t ldx, const double* G, int64_t ldg, void* Qout, int64_t ldo,
                              void* stream, int32_t sync);
+
+/* rbgs_tall_update without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot let a library call cudaMalloc
+ * or cudaFree -- those whose device memory is all handed out by their own
+ * allocator (a framework pool reserving most of HBM), and those on a latency
+ * path where an allocation or free may synchronise the device.  Arguments,
+ * results and precisions are those of rbgs_tall_update.
+ * Limit: c + mb <= RBGS_NOALLOC_MAX_K, else RBGS_ETOOLARGE (checked before any
+ * CUDA call).  The scratch (the FP32 copy or TF32 split of G and an error flag,
+ * about 4.03 MiB) is a fixed __device__ array inside the library, present on
+ * every device that loads it until the process exits.  The first call on a
+ * device looks up that array's device address (with the device current);
+ * make that first call before any stream capture on the device.  All calls
+ * share the array: calls whose GPU work overlaps (unordered streams, or host
+ * threads calling at once) race on it and give wrong results.            */
+#define RBGS_NOALLOC_MAX_K 8192
+RBGS_API rbgs_status rbgs_tall_update_noalloc(int32_t prec, int64_t n, int64_t c, int64_t mb, const void* Qprev,
+                                     int64_t ldq, const void* X, int64_t ldx, const double* G, int64_t ldg,
+                                     void* Qout, int64_t ldo, void* stream, int32_t sync);
 
 /* Philox4x32-10 blocks on the device: out[4i..4i+3] = philox(ctr[4i..4i+3],
  * key = (seed_lo, seed_hi)) for i < count (device pointers).              */

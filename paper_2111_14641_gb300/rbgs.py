@@ -20,8 +20,11 @@ _HDR = Path(__file__).resolve().parent.parent / "include" / "rbgs.h"
 
 SKETCH = {"gauss": 0, "rademacher": 1, "srht": 2}
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2}
+# Largest c + mb that rbgs_tall_update_noalloc accepts (its fixed scratch).
+NOALLOC_MAX_K = int(re.search(r"#define RBGS_NOALLOC_MAX_K (\d+)", _HDR.read_text()).group(1))
 STATUS = {0: "RBGS_OK", 1: "RBGS_EINVAL", 2: "RBGS_ENOMEM", 3: "RBGS_ECUDA", 4: "RBGS_EBREAKDOWN",
-          5: "RBGS_ENOTCERTIFIED", 6: "RBGS_ETIMEOUT", 7: "RBGS_ENOCONV", 8: "RBGS_ENODEV"}
+          5: "RBGS_ENOTCERTIFIED", 6: "RBGS_ETIMEOUT", 7: "RBGS_ENOCONV", 8: "RBGS_ENODEV",
+          9: "RBGS_ETOOLARGE"}
 
 
 class RbgsError(RuntimeError):
@@ -78,11 +81,13 @@ def load(build_if_missing: bool = False):
                             ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
     lib.rbgs_sketch_apply.argtypes = [ctypes.c_int, i64, i64, u64, i32, vp, i64, i64, vp, i64, vp, i32]
     lib.rbgs_tall_update.argtypes = [i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i32]
+    lib.rbgs_tall_update_noalloc.argtypes = [i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i32]
     lib.rbgs_philox.argtypes = [u64, vp, vp, i64, vp, i32]
     lib.rbgs_release_workspace.argtypes = []
     lib.rbgs_version.restype = ctypes.c_char_p
     lib.rbgs_launch_count.restype = ctypes.c_int64
-    for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_philox", "rbgs_release_workspace"):
+    for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
+                 "rbgs_release_workspace"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -185,6 +190,26 @@ def tall_update(Qprev: torch.Tensor | None, X: torch.Tensor, G: torch.Tensor, pr
                                 Gc.data_ptr(), _ld(Gc, "G"), out.data_ptr(), _ld(out, "out"), _stream_ptr(stream),
                                 int(sync))
     _check(code, "rbgs_tall_update")
+    return out
+
+
+def tall_update_noalloc(Qprev: torch.Tensor | None, X: torch.Tensor, G: torch.Tensor, out: torch.Tensor,
+                        prec: str | None = None, stream=None, sync: bool = True) -> torch.Tensor:
+    """Qout = [Qprev | X] G like tall_update, through the entry point that
+    allocates no device memory (scratch is a fixed buffer inside the library;
+    c + mb <= NOALLOC_MAX_K).  G must already be a column-major float64 CUDA
+    tensor and out must be given, so this call allocates nothing either."""
+    lib = load()
+    prec = _prec_of(X, prec)
+    n, mb = X.shape
+    c = 0 if Qprev is None else Qprev.shape[1]
+    if not (G.is_cuda and G.dtype == torch.float64):
+        raise ValueError("G must be a float64 CUDA tensor")
+    code = lib.rbgs_tall_update_noalloc(PREC[prec], n, c, mb, 0 if Qprev is None else Qprev.data_ptr(),
+                                        n if Qprev is None else _ld(Qprev, "Qprev"), X.data_ptr(), _ld(X, "X"),
+                                        G.data_ptr(), _ld(G, "G"), out.data_ptr(), _ld(out, "out"),
+                                        _stream_ptr(stream), int(sync))
+    _check(code, "rbgs_tall_update_noalloc")
     return out
 
 
