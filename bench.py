@@ -8,8 +8,11 @@ resident in HBM, through the C ABI of librbgs.
 Default workload (mixed precision): n = 1,000,000 rows, m = 1000 columns,
 block size m_p = 50, SRHT sketch k = 2000, W in FP32 with singular values
 log-spaced from 1 to 1e-6 (W = U diag(sigma) V^T from seeded N(0,1) factors).
-The tall products run in 3xTF32 on the tcgen05 tensor cores; the sketch-space
-least squares in FP32 and the small factorizations in FP64.
+The tall products and the sketches run in FP32 storage with 3xTF32 tensor-core
+products (tcgen05); the sketch-space steps (least squares, block Cholesky QR,
+R) run in FP64 (--fine 0 runs them in FP32; the line reports the other choice
+as a variant).  Step 2 takes one Richardson iteration per pass; every block
+after the first takes a second projection pass (--reorth 1).
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -154,16 +157,48 @@ def quality(rb, W, Q, R, cfg):
         den += float((Wc * Wc).sum())
     Q64 = rb.colmajor(Q.double())
     S = rb.sketch_apply(Q64, cfg["sketch"], cfg["k"], cfg["seed_theta"], prec="fp64")
-    Gs = S.t() @ S
-    Ei = torch.eye(m, dtype=torch.float64, device=W.device) - Gs
-    d_fro = float(torch.linalg.norm(Ei))
-    d_two = float(torch.linalg.matrix_norm(Ei, ord=2))
-    Gq = Q64.t() @ Q64
-    ev = torch.linalg.eigvalsh(Gq)
-    condq = float(torch.sqrt(ev.max() / ev.min()))
-    del Q64, S, Gq
+    import numpy as np
+
+    # m x m spectral quantities on the host (numpy LAPACK)
+    Ei = np.eye(m) - (S.t() @ S).cpu().numpy()
+    d_fro = float(np.linalg.norm(Ei))
+    d_two = float(np.linalg.norm(Ei, 2))
+    ev = np.linalg.eigvalsh((Q64.t() @ Q64).cpu().numpy())
+    condq = float(np.sqrt(ev.max() / ev.min()))
+    del Q64, S
     return {"rel_factorization_error": math.sqrt(num / den), "sketched_orthogonality_fro": d_fro,
             "sketched_orthogonality_2": d_two, "cond_Q": condq}
+
+
+def tall_traffic(prec, bytes_per_launch):
+    """DRAM bytes per tall-update launch: the ratio of ncu's measured
+    dram__bytes_read + dram__bytes_write to the algorithmic bytes of one
+    captured launch (profiles/tall_tc_kernel_*.md), scaled to the average
+    launch here; None unless that capture was taken from the kernel source
+    as it is now."""
+    import glob
+    import hashlib
+
+    if prec != "tf32x3":
+        return None
+    src = os.path.join(ROOT, "paper_2111_14641_gb300", "csrc", "tall_tc.cu")
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "tall_tc_kernel_*.md"))):
+        fields = {}
+        with open(path) as f:
+            for ln in f:
+                if ":" in ln and not ln.startswith(("|", " ", "#", "-")):
+                    key, _, val = ln.partition(":")
+                    fields[key.strip()] = val.strip()
+        ratio = fields.get("traffic_over_algorithmic")
+        prefix = fields.get("kernel_source_sha256_prefix")
+        if ratio and prefix and digest.startswith(prefix):
+            return float(ratio) * bytes_per_launch
+    return None
 
 
 def cpu_baseline(cfg, ls_iters, reorth):
@@ -241,7 +276,8 @@ def run_ours(args, cfg):
 
     def step(timing=False):
         return rb.rbgs_qr(W, mb, cfg["sketch"], k, cfg["seed_theta"], prec=prec, ls_iters=args.ls_iters,
-                          reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q, R=R, sync=True, timing=timing)[2]
+                          reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q, R=R, sync=True, timing=timing,
+                          fine=args.fine)[2]
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -290,12 +326,7 @@ def run_ours(args, cfg):
     if peak is None:
         peak, peak_src = 6800.0, "fallback"
     achieved = tall_bytes / (tall_ms * 1e-3) / 1e9 if tall_ms > 0 else None
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get(f"{args.workload}:{prec}")
-    except (OSError, ValueError):
-        traffic = None
+    traffic = tall_traffic(prec, tall_bytes / max(tall_launches, 1))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel": "tall_tc_kernel" if prec == "tf32x3" else "tall_simt_kernel",
@@ -334,7 +365,8 @@ def run_ours(args, cfg):
                                            "fp64": "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": cfg["desc"], "n": n, "m": m, "mb": mb, "sketch": cfg["sketch"], "k": k,
-                       "prec": prec, "ls_iters": args.ls_iters, "reorth": args.reorth,
+                       "prec": prec, "sketch_space": "fp64" if (args.fine or prec == "fp64") else "fp32",
+                       "ls_iters": args.ls_iters, "reorth": args.reorth,
                        "reorth_tol": args.reorth_tol, "passes2": passes2,
                        "l2": "inputs larger than L2 (W and Q are GBs; no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -343,6 +375,11 @@ def run_ours(args, cfg):
 
     if rank == 0 and not args.no_quality:
         line["quality"] = quality(rb, W if args.no_e2e else _refill(W, cfg, dev, dtype), Q, R, cfg)
+
+    if rank == 0 and world == 1 and not args.no_variant and prec != "fp64":
+        other = 0 if args.fine else 1
+        line[f"variant_sketch_space_{'fp64' if other else 'fp32'}"] = sketch_space_variant(
+            rb, W, Q, R, cfg, args, prec, other, flops)
 
     if rank == 0 and world == 1 and not args.no_fp64_compare and prec != "fp64":
         line["fp64_path"] = fp64_compare(rb, cfg, args, dev)
@@ -355,6 +392,35 @@ def run_ours(args, cfg):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def sketch_space_variant(rb, W, Q, R, cfg, args, prec, fine, flops_ref):
+    """The same factorization with the other precision of the sketch-space
+    steps (FP32 or FP64), 3 warm-up and up to 5 timed steps, with its quality."""
+    import torch
+
+    def step():
+        return rb.rbgs_qr(W, cfg["mb"], cfg["sketch"], cfg["k"], cfg["seed_theta"], prec=prec,
+                          ls_iters=args.ls_iters, reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q, R=R,
+                          sync=True, fine=bool(fine))[2]
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        st = step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    out = {"ms_per_step": ms, "steps": steps, "sketch_space": "fp64" if fine else "fp32",
+           "value": algorithmic_flops(cfg["n"], cfg["m"], cfg["mb"], cfg["k"], cfg["sketch"], args.ls_iters,
+                                      st.passes2) / (ms * 1e-3) / 1e9, "unit": "GFLOP/s"}
+    if not args.no_quality:
+        out["quality"] = quality(rb, W, Q, R, cfg)
+    return out
 
 
 def _refill(W, cfg, dev, dtype):
@@ -399,15 +465,23 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--prec", choices=["tf32x3", "fp32", "fp64"], default=None)
-    ap.add_argument("--ls-iters", type=int, default=2)
+    ap.add_argument("--ls-iters", type=int, default=1)
     ap.add_argument("--reorth", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--reorth-tol", type=float, default=1e-6)
+    ap.add_argument("--fine", type=int, default=1, choices=[0, 1],
+                    help="mixed precision: 1 = sketch-space steps (least squares, block QR, R) in FP64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="skip the measurement with the other sketch-space precision")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=None,
+                    help="override n (smaller cases for profiler captures; recorded in config.workload)")
     args = ap.parse_args(argv)
     cfg = WORKLOADS[args.workload]
+    if args.rows:
+        cfg = dict(cfg, n=args.rows, desc=cfg["desc"] + f" [n overridden: {args.rows} rows]")
     if args.prec is None:
         args.prec = "fp64" if args.workload == "c1" else "tf32x3"
     if args.impl == "reference":

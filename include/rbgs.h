@@ -59,8 +59,9 @@ typedef enum { RBGS_SK_GAUSS = 0, RBGS_SK_RADEMACHER = 1, RBGS_SK_SRHT = 2 } rbg
 /* Arithmetic of the tall (n-row) operations: the projection of step 3 fused
  * with R_ii^{-1}, and the sketches.
  *  FP64    double storage, double arithmetic everywhere.
- *  FP32    float storage of W and Q; SIMT FP32 tall product; sketch-space
- *          products in FP32, small m_p x m_p factorizations in FP64.
+ *  FP32    float storage of W and Q; SIMT FP32 tall product; sketches
+ *          computed in FP32.  The sketch-space steps (least squares, block
+ *          Cholesky QR, R) run in FP64 with opts->fine = 1, else in FP32.
  *  TF32X3  as FP32, but the tall product runs on the tcgen05 tensor cores
  *          with split operands (a = a_hi + a_lo in TF32, three products),
  *          accurate to about 2^-22 relative per product.                  */
@@ -77,7 +78,10 @@ typedef struct {
   void* stream;        /* cudaStream_t                                                   */
   int32_t sync;        /* 1: wait and report device-side status; 0: enqueue only        */
   int32_t timing;      /* 1: time the tall-update launches with CUDA events (needs sync) */
-  int32_t reserved[2];
+  int32_t fine;        /* FP32 / TF32X3 only: 1 = the sketch-space steps (P and S stored,
+                          step-2 least squares, block Cholesky QR, R) in FP64 (the
+                          paper's u_fine); 0 = in FP32                                  */
+  int32_t reserved;
 } rbgs_opts;
 
 typedef struct {

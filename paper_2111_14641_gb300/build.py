@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     if force or procs or not LIB.exists():
         tmp = LIB.with_suffix(f".{os.getpid()}.tmp.so")
         cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", str(tmp), *map(str, objs),
-               "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+               "-Xlinker", "-rpath=/usr/local/cuda/lib64", "-Xlinker", "--no-undefined"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB

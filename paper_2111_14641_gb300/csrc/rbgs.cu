@@ -456,14 +456,15 @@ rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb
   if (o.prec == RBGS_P_FP64)
     return qr_impl<double, double>((const double*)W, n, m, ldw, (int)mb, sketch, k, seed, (double*)Q, ldq, R, ldr, o,
                                    stats, false);
-  if (o.prec == RBGS_P_TF32X3) {
-    // tensor-core path: TMA needs 16-byte aligned bases and leading dimensions
-    if (((uintptr_t)W & 15) || ((uintptr_t)Q & 15) || (ldw % 4) || (ldq % 4)) return RBGS_EINVAL;
-    return qr_impl<float, float>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o,
-                                 stats, true);
-  }
+  if (o.fine < 0 || o.fine > 1) return RBGS_EINVAL;
+  const bool tensor = o.prec == RBGS_P_TF32X3;
+  // tensor-core path: TMA needs 16-byte aligned bases and leading dimensions
+  if (tensor && (((uintptr_t)W & 15) || ((uintptr_t)Q & 15) || (ldw % 4) || (ldq % 4))) return RBGS_EINVAL;
+  if (o.fine)
+    return qr_impl<float, double>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o,
+                                  stats, tensor);
   return qr_impl<float, float>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o, stats,
-                               false);
+                               tensor);
 }
 
 rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,

@@ -468,6 +468,8 @@ template rbgs_status assemble_g<float, double>(int64_t, int, const float*, int64
                                                double*, int64_t, double*, int64_t, const int*, cudaStream_t);
 template rbgs_status assemble_g<float, float>(int64_t, int, const float*, int64_t, const float*, const float*,
                                               float*, int64_t, double*, int64_t, const int*, cudaStream_t);
+template rbgs_status assemble_g<double, float>(int64_t, int, const double*, int64_t, const double*, const double*,
+                                               float*, int64_t, double*, int64_t, const int*, cudaStream_t);
 
 template <class TS>
 rbgs_status reorth_update_r(int64_t c, int mb, const TS* R2c, int64_t ldr2, const TS* R2ii, double* Rcol,

@@ -38,6 +38,21 @@ def svd_matrix(n: int, m: int, cond: float, seed: int, dtype=np.float64) -> np.n
     return np.asfortranarray(W.astype(dtype))
 
 
+def _orthonormal_cols_torch(G):
+    """Orthonormal basis of the columns of the FP64 device matrix G (n x m,
+    well conditioned): two Cholesky-QR rounds, Gram products on the device and
+    the m x m Cholesky factor on the host, which in exact arithmetic is the Q
+    factor of G with positive-diagonal R (the Householder-QR factor)."""
+    import torch
+
+    for _ in range(2):
+        C = (G.t() @ G).cpu().numpy()
+        L = np.linalg.cholesky(C)
+        Rinv = np.linalg.inv(L.T)
+        G = G @ torch.from_numpy(Rinv).to(G.device)
+    return G
+
+
 def svd_matrix_torch(n: int, m: int, cond: float, seed: int, device="cuda", dtype=None):
     """Same recipe drawn with torch on ``device`` (for sizes too large for the
     host).  Returns a column-major (n x m) tensor: shape (n, m), strides (1, n)."""
@@ -47,10 +62,10 @@ def svd_matrix_torch(n: int, m: int, cond: float, seed: int, device="cuda", dtyp
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     G = torch.randn((m, n), generator=g, device=device, dtype=torch.float64).t()  # column-major n x m
-    U, _ = torch.linalg.qr(G)
+    U = _orthonormal_cols_torch(G)
     del G
     H = torch.randn((m, m), generator=g, device=device, dtype=torch.float64)
-    V, _ = torch.linalg.qr(H)
+    V = torch.from_numpy(np.linalg.qr(H.cpu().numpy())[0]).to(device)
     s = torch.as_tensor(sigmas(m, cond), device=device, dtype=torch.float64)
     Wt = (V * s) @ U.t()  # (m x n) row-major == W column-major
     del U

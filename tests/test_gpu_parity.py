@@ -1,5 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
 same seeded inputs.  Paper references: Balabanov & Grigori, arXiv 2111.14641."""
+import os
+
 import numpy as np
 import pytest
 
@@ -218,13 +220,16 @@ def test_tall_update_tc_matches_numpy(rb, n, c, mb, inplace):
 
 @pytest.mark.parametrize("kind", ["gauss", "srht"])
 @pytest.mark.parametrize("reorth", [False, True])
-def test_rbgs_tf32x3_matches_oracle(rb, kind, reorth):
+@pytest.mark.parametrize("fine", [False, True])
+def test_rbgs_tf32x3_matches_oracle(rb, kind, reorth, fine):
+    """fine=True keeps the sketch-space steps in FP64 (the paper's u_fine)."""
     n, m, mb, k = 6000, 48, 8, 240
     cond = 1e3
     W = synth.svd_matrix(n, m, cond, 3).astype(np.float32).astype(np.float64)
     Wd = dev_ld(W, torch.float32, n + 4)
     Qd = dev_ld(np.zeros((n, m)), torch.float32, n + 4)
-    _, Rd, st = rb.rbgs_qr(Wd, mb, kind, k, 5, prec="tf32x3", ls_iters=3, reorth=int(reorth), Q=Qd, certify=True)
+    _, Rd, st = rb.rbgs_qr(Wd, mb, kind, k, 5, prec="tf32x3", ls_iters=3, reorth=int(reorth), Q=Qd, certify=True,
+                           fine=fine)
     Q, R = host(Qd), host(Rd)
     ref = oracle.rbgs(W, mb, kind, k, 5, variant=5, ls="richardson", ls_iters=3, reorth=reorth, ls_iters_first=1)
     assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
@@ -233,3 +238,35 @@ def test_rbgs_tf32x3_matches_oracle(rb, kind, reorth):
     assert ortho < (1e-4 if reorth else 1e-3)
     assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
     assert st.passes2 == (m // mb - 1 if reorth else 0)
+
+
+# ------------------------------------------------ full-size mixed workload --
+
+def test_c2_full_size_properties(rb):
+    """n = 1e6, m = 1000, m_p = 50, SRHT k = 2000, W in FP32 with sigma from 1
+    to 1e-6, in the launch configuration bench.py times (3xTF32 tall products,
+    FP64 sketch space, one Richardson iteration, second pass on every block).
+    The oracle cannot factor this size, so the test checks what holds at any
+    size, with the oracle's own Theta: sketched orthogonality of Q, W = QR,
+    and the triangular structure of R."""
+    n, m, mb, k, seed = 1_000_000, 1000, 50, 2000, 1
+    W = synth.svd_matrix_torch(n, m, 1e6, 7, device="cuda", dtype=torch.float32)
+    Q, R, st = rb.rbgs_qr(W, mb, "srht", k, seed, prec="tf32x3", ls_iters=1, reorth=1, fine=True)
+    assert st.passes2 == m // mb - 1
+    Rh = host(R)
+    assert np.allclose(np.tril(Rh, -1), 0.0) and np.all(np.diag(Rh) > 0)
+    # ||W - QR||_F / ||W||_F in FP64 on the device, 1e5 rows at a time
+    num = den = 0.0
+    R64 = R.double()
+    for r0 in range(0, n, 100_000):
+        Wc = W[r0:r0 + 100_000].double()
+        E = Wc - Q[r0:r0 + 100_000].double() @ R64
+        num += float((E * E).sum())
+        den += float((Wc * Wc).sum())
+    assert np.sqrt(num / den) <= 1e-6
+    # sketched orthogonality with the oracle's SRHT (independent of the GPU sketch)
+    oracle.set_threads(os.cpu_count() or 1)
+    S = oracle.theta_apply("srht", k, seed, host(Q))
+    E = np.eye(m) - S.T @ S
+    assert np.linalg.norm(E, 2) <= 1e-6
+    assert np.linalg.norm(E) <= 2e-5
