@@ -42,6 +42,8 @@ WORKLOADS = {
 CPU_SAMPLE_ROWS = 16384
 CPU_SAMPLE_COLS = 500
 METRIC = "RBGS QR GFLOP/s & roofline frac, mixed vs FP64 on GB300 at stated orthogonality"
+TALL_KERNEL = {"f16x3": "tall_h3_kernel", "tf32x3": "tall_tc_kernel"}
+TALL_SOURCE = {"f16x3": "tall_h3.cu", "tf32x3": "tall_tc.cu"}
 
 
 def algorithmic_flops(n, m, mb, k, sketch, ls_iters, reorth_blocks):
@@ -179,15 +181,16 @@ def tall_traffic(prec, bytes_per_launch):
     import glob
     import hashlib
 
-    if prec != "tf32x3":
+    if prec not in TALL_KERNEL:
         return None
-    src = os.path.join(ROOT, "paper_2111_14641_gb300", "csrc", "tall_tc.cu")
+    kernel = TALL_KERNEL[prec]
+    src = os.path.join(ROOT, "paper_2111_14641_gb300", "csrc", TALL_SOURCE[prec])
     try:
         with open(src, "rb") as f:
             digest = hashlib.sha256(f.read()).hexdigest()
     except OSError:
         return None
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "tall_tc_kernel_*.md"))):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
         fields = {}
         with open(path) as f:
             for ln in f:
@@ -329,7 +332,7 @@ def run_ours(args, cfg):
     traffic = tall_traffic(prec, tall_bytes / max(tall_launches, 1))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "kernel": "tall_tc_kernel" if prec == "tf32x3" else "tall_simt_kernel",
+                "kernel": TALL_KERNEL.get(prec, "tall_simt_kernel"),
                 "peak_source": peak_src, "launch_ms_avg": tall_ms / max(tall_launches, 1),
                 "bytes_per_launch_avg": tall_bytes / max(tall_launches, 1)}
 
@@ -361,7 +364,8 @@ def run_ours(args, cfg):
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"tf32x3": "f32 (3xTF32 tensor products)", "fp32": "f32",
+            "vs_baseline": None, "dtype": {"f16x3": "f32 (3x FP16-split tensor products)",
+                                           "tf32x3": "f32 (3xTF32 tensor products)", "fp32": "f32",
                                            "fp64": "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": cfg["desc"], "n": n, "m": m, "mb": mb, "sketch": cfg["sketch"], "k": k,
@@ -464,7 +468,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
-    ap.add_argument("--prec", choices=["tf32x3", "fp32", "fp64"], default=None)
+    ap.add_argument("--prec", choices=["f16x3", "tf32x3", "fp32", "fp64"], default=None)
     ap.add_argument("--ls-iters", type=int, default=1)
     ap.add_argument("--reorth", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--reorth-tol", type=float, default=1e-6)

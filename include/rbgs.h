@@ -64,8 +64,13 @@ typedef enum { RBGS_SK_GAUSS = 0, RBGS_SK_RADEMACHER = 1, RBGS_SK_SRHT = 2 } rbg
  *          Cholesky QR, R) run in FP64 with opts->fine = 1, else in FP32.
  *  TF32X3  as FP32, but the tall product runs on the tcgen05 tensor cores
  *          with split operands (a = a_hi + a_lo in TF32, three products),
- *          accurate to about 2^-22 relative per product.                  */
-typedef enum { RBGS_P_FP64 = 0, RBGS_P_FP32 = 1, RBGS_P_TF32X3 = 2 } rbgs_prec;
+ *          accurate to about 2^-22 relative per product.
+ *  F16X3   as TF32X3, with FP16 hi/lo splits under power-of-two column
+ *          scales (three kind::f16 products, also about 2^-22).  rbgs_qr
+ *          keeps the split of the finished Q columns in its workspace, so the
+ *          previous basis streams into the tensor cores without conversion.
+ *          The workspace grows by 4 bytes per element of Q.                 */
+typedef enum { RBGS_P_FP64 = 0, RBGS_P_FP32 = 1, RBGS_P_TF32X3 = 2, RBGS_P_F16X3 = 3 } rbgs_prec;
 
 typedef struct {
   int32_t prec;        /* rbgs_prec                                                      */
@@ -78,7 +83,7 @@ typedef struct {
   void* stream;        /* cudaStream_t                                                   */
   int32_t sync;        /* 1: wait and report device-side status; 0: enqueue only        */
   int32_t timing;      /* 1: time the tall-update launches with CUDA events (needs sync) */
-  int32_t fine;        /* FP32 / TF32X3 only: 1 = the sketch-space steps (P and S stored,
+  int32_t fine;        /* FP32 / TF32X3 / F16X3: 1 = the sketch-space steps (P and S stored,
                           step-2 least squares, block Cholesky QR, R) in FP64 (the
                           paper's u_fine); 0 = in FP32                                  */
   int32_t reserved;
@@ -142,7 +147,8 @@ RBGS_API rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_
  * or cudaFree -- those whose device memory is all handed out by their own
  * allocator (a framework pool reserving most of HBM), and those on a latency
  * path where an allocation or free may synchronise the device.  Arguments,
- * results and precisions are those of rbgs_tall_update.
+ * results and precisions are those of rbgs_tall_update, except that F16X3 is
+ * not offered (RBGS_EINVAL).
  * Limit: c + mb <= RBGS_NOALLOC_MAX_K, else RBGS_ETOOLARGE (checked before any
  * CUDA call).  The scratch (the FP32 copy or TF32 split of G and an error flag,
  * about 4.03 MiB) is a fixed __device__ array inside the library, present on

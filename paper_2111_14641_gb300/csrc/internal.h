@@ -71,6 +71,30 @@ size_t tc_gsplit_floats(int64_t K);  // floats needed for the split G of K rows
 rbgs_status tc_split_g(int64_t K, int64_t mb, const double* G, int64_t ldg, float* Gsplit, const int* active,
                        cudaStream_t st);
 
+// FP16 hi/lo split tensor-core version (tall_h3.cu).  The previous basis is
+// pre-split in a tiled layout (per 128-row tile, h3_nch_row(m) chunks of 64
+// columns, 32 KB each); the block's own columns `raw` (FP32) are split in the
+// kernel.  h3_prepare builds the split G (B) and the scales from the sketch of
+// the raw block (Sraw, k x mb) or from its column maxima (rawmax); qscale are
+// the per-column scales of the pre-split basis (null: 2^9 for every column).
+int64_t h3_nch_row(int64_t m);
+size_t h3_qs_bytes(int64_t n, int64_t m);
+size_t h3_b_bytes(int64_t c);
+// Output-column shift that aligns the split copy of columns cs_out.. to 8-column groups.
+int h3_shift(int64_t cs_out, int64_t mb, bool split_out);
+template <class TS>
+rbgs_status h3_prepare(int64_t c, int64_t mb, const double* G, int64_t ldg, const TS* Sraw, int64_t k,
+                       const float* rawmax, const float* qscale, int jsh, unsigned char* B, float* scales,
+                       const int* active, cudaStream_t st);
+rbgs_status tall_update_h3(int64_t n, int64_t c, int64_t mb, const unsigned char* qs, int64_t nch_row,
+                           const float* raw, int64_t ldr, const unsigned char* B, const float* scales, float* Qout,
+                           int64_t ldo, unsigned char* qs_out, int64_t cs_out, int jsh, const int* active, int* err,
+                           cudaStream_t st);
+rbgs_status h3_colmax(int64_t n, int64_t cols, const float* A, int64_t lda, unsigned int* mx, cudaStream_t st);
+rbgs_status h3_scales_from_max(int64_t cols, const unsigned int* mx, float* scale, cudaStream_t st);
+rbgs_status h3_split(int64_t n, int64_t cols, const float* A, int64_t lda, const float* scale, int64_t nch_row,
+                     unsigned char* qs, cudaStream_t st);
+
 // ------------------------------------------------------------ sketch space --
 // out (M x N, ldo) = alpha * op(A) * B + beta * out, op(A) = A (TRANS=0, A M x K)
 // or A^T (TRANS=1, A K x M); B K x N; N <= 64.  TA/TB input, TO output type,

@@ -176,7 +176,9 @@ rbgs_status richardson(int64_t k, int64_t c, int mb, const TS* S, const TS* Pi, 
 template <class T, class TS>
 rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_sketch sketch, int64_t k,
                     uint64_t seed, T* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts& o, rbgs_stats* stats,
-                    bool tensor) {
+                    int mode) {
+  // mode 0: SIMT tall product; 1: TF32X3 tensor cores; 2: F16X3 tensor cores with the pre-split basis
+  const bool tensor = mode != 0;
   cudaStream_t st = (cudaStream_t)o.stream;
   const int64_t p = m / mb;
   const int l = o.ls_iters < 1 ? 1 : o.ls_iters;
@@ -204,7 +206,10 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     double* tmp = cv.take<double>(64 * 64);
     T* Gmat = cv.take<T>((size_t)m * mb);
     double* Gd = tensor ? cv.take<double>((size_t)m * mb) : nullptr;
-    float* Gsplit = tensor ? cv.take<float>(tc_gsplit_floats(m)) : nullptr;
+    float* Gsplit = mode == 1 ? cv.take<float>(tc_gsplit_floats(m)) : nullptr;
+    unsigned char* Qs = mode == 2 ? cv.take<unsigned char>(h3_qs_bytes(n, m)) : nullptr;
+    unsigned char* Bh = mode == 2 ? cv.take<unsigned char>(h3_b_bytes(m)) : nullptr;
+    float* hsc = mode == 2 ? cv.take<float>(192) : nullptr;
     double* part = cv.take<double>(kPartElems);
     TS* partf = cv.take<TS>(kPartElems);
     void* skscr = cv.take<char>(sk_bytes);
@@ -243,7 +248,15 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     RBGS_CUDA_TRY(cudaMemset2DAsync(R, ldr * sizeof(double), 0, m * sizeof(double), m, st));
 
     rbgs_status s;
-    auto tall_raw = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act) -> rbgs_status {
+    auto tall_raw = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act, const TS* sraw,
+                        bool split_out) -> rbgs_status {
+      if (mode == 2) {
+        const int jsh = h3_shift(c, mb, split_out);
+        rbgs_status e = h3_prepare<TS>(c, mb, Gd, c + mb, sraw, k, nullptr, nullptr, jsh, Bh, hsc, act, st);
+        if (e) return e;
+        return tall_update_h3(n, c, mb, Qs, h3_nch_row(m), (const float*)X2src, ldx2, Bh, hsc, (float*)out, ldq,
+                              split_out ? Qs : nullptr, c, jsh, act, tmo, st);
+      }
       if (tensor) {
         rbgs_status e = tc_split_g(c + mb, mb, Gd, c + mb, Gsplit, act, st);
         if (e) return e;
@@ -252,8 +265,9 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       }
       return tall_update_simt<T>(n, c, mb, Q, ldq, X2src, ldx2, Gmat, c + mb, out, ldq, act, st);
     };
-    auto tall = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act) -> rbgs_status {
-      if (!timing) return tall_raw(c, X2src, ldx2, out, act);
+    auto tall = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act, const TS* sraw,
+                    bool split_out) -> rbgs_status {
+      if (!timing) return tall_raw(c, X2src, ldx2, out, act, sraw, split_out);
       TallEv e;
       e.bytes = (double)sizeof(T) * (double)n * (double)(c + 2 * mb);
       e.blk = c / mb;
@@ -265,7 +279,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       }
       evs.push_back(e);
       RBGS_CUDA_TRY(cudaEventRecord(e.a, st));
-      rbgs_status r = tall_raw(c, X2src, ldx2, out, act);
+      rbgs_status r = tall_raw(c, X2src, ldx2, out, act, sraw, split_out);
       RBGS_CUDA_TRY(cudaEventRecord(e.b, st));
       return r;
     };
@@ -302,7 +316,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       if (s) return s;
       if ((s = make_g(c, X, Rii, Riinv, Rcol, nullptr))) return s;
       // step 3 fused with the triangular solve
-      if ((s = tall(c, Wi, ldw, Qi, nullptr))) return s;
+      // (the split copy of a provisional result is not kept: the second pass rereads it as FP32)
+      if ((s = tall(c, Wi, ldw, Qi, nullptr, Pi, !(o.reorth == 1 && c > 0)))) return s;
       // step 5, and step 1 of the next block, in one pass (the single reduction per block of Alg. 5)
       s = sketch_apply2_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, Wi + mb * ldw, ldw, blk + 1 < p ? mb : 0,
                                  Pi + mb * k, k, skscr, sk_bytes, st);
@@ -324,7 +339,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         if (s) return s;
         if ((s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, active, st, R2ii, R2iinv))) return s;
         if ((s = make_g(c, X2, R2ii, R2iinv, nullptr, active))) return s;
-        if ((s = tall(c, Qi, ldq, Qi, active))) return s;
+        if ((s = tall(c, Qi, ldq, Qi, active, Si, true))) return s;
         if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st, active))) return s;
         if ((s = reorth_update_r<TS>(c, mb, X2, m, R2ii, Rcol, ldr, tmp, active, st))) return s;
       }
@@ -440,7 +455,7 @@ rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb
   if (!W || !Q || !R) return RBGS_EINVAL;
   if (n < 1 || n >= ((int64_t)1 << 31) || m < 1 || mb < 1 || mb > 64 || m % mb != 0) return RBGS_EINVAL;
   if (ldw < n || ldq < n || ldr < m || k < m) return RBGS_EINVAL;
-  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_TF32X3 || o.reorth < 0 || o.reorth > 2) return RBGS_EINVAL;
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2) return RBGS_EINVAL;
   if (sketch == RBGS_SK_SRHT) {
     int64_t np = 1;
     while (np < n) np <<= 1;
@@ -455,22 +470,22 @@ rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb
   if (ranges_overlap(R, 8 * (size_t)(ldr * (m - 1) + m), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
   if (o.prec == RBGS_P_FP64)
     return qr_impl<double, double>((const double*)W, n, m, ldw, (int)mb, sketch, k, seed, (double*)Q, ldq, R, ldr, o,
-                                   stats, false);
+                                   stats, 0);
   if (o.fine < 0 || o.fine > 1) return RBGS_EINVAL;
-  const bool tensor = o.prec == RBGS_P_TF32X3;
-  // tensor-core path: TMA needs 16-byte aligned bases and leading dimensions
-  if (tensor && (((uintptr_t)W & 15) || ((uintptr_t)Q & 15) || (ldw % 4) || (ldq % 4))) return RBGS_EINVAL;
+  const int mode = o.prec == RBGS_P_TF32X3 ? 1 : (o.prec == RBGS_P_F16X3 ? 2 : 0);
+  // tensor-core paths: TMA needs 16-byte aligned bases and leading dimensions
+  if (mode && (((uintptr_t)W & 15) || ((uintptr_t)Q & 15) || (ldw % 4) || (ldq % 4))) return RBGS_EINVAL;
   if (o.fine)
     return qr_impl<float, double>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o,
-                                  stats, tensor);
+                                  stats, mode);
   return qr_impl<float, float>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o, stats,
-                               tensor);
+                               mode);
 }
 
 rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,
                               int64_t ldx, int64_t ncols, double* Y, int64_t ldy, void* stream, int32_t sync) {
   if (!X || !Y || n < 1 || k < 1 || ncols < 0 || ldx < n || ldy < k) return RBGS_EINVAL;
-  if (prec < RBGS_P_FP64 || prec > RBGS_P_TF32X3) return RBGS_EINVAL;
+  if (prec < RBGS_P_FP64 || prec > RBGS_P_F16X3) return RBGS_EINVAL;
   if (sketch == RBGS_SK_SRHT) {
     int64_t np = 1;
     while (np < n) np <<= 1;
@@ -497,10 +512,49 @@ rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_t mb, con
   if (!X || !G || !Qout || (c > 0 && !Qprev)) return RBGS_EINVAL;
   if (n < 1 || c < 0 || mb < 1 || mb > 64 || ldx < n || ldo < n || (c > 0 && ldq < n) || ldg < c + mb)
     return RBGS_EINVAL;
-  if (prec < RBGS_P_FP64 || prec > RBGS_P_TF32X3) return RBGS_EINVAL;
+  if (prec < RBGS_P_FP64 || prec > RBGS_P_F16X3) return RBGS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t K = c + mb;
   rbgs_status s;
+  if (prec == RBGS_P_F16X3) {
+    // the basis carries no sketch here: split it with scales from its column maxima
+    if (((uintptr_t)X & 15) || (ldx % 4)) return RBGS_EINVAL;
+    if (ranges_overlap(Qout, 4 * (size_t)(ldo * (mb - 1) + n), Qprev, c > 0 ? 4 * (size_t)(ldq * (c - 1) + n) : 0))
+      return RBGS_EINVAL;
+    const int64_t nch = h3_nch_row(c);
+    const size_t qs_bytes = h3_qs_bytes(n, c), b_bytes = h3_b_bytes(c);
+    const size_t need = 256 + qs_bytes + b_bytes + 4 * (192 + (size_t)c + (size_t)c + 64) + 1024;
+    void* scr = nullptr;
+    if ((s = workspace(need, &scr))) return s;
+    char* w = (char*)scr;
+    int* err = (int*)w;
+    unsigned char* Qs = (unsigned char*)(w + 256);
+    unsigned char* B = Qs + qs_bytes;
+    float* sc = (float*)(B + b_bytes);
+    float* qscale = sc + 192;
+    unsigned int* mxq = (unsigned int*)(qscale + c);
+    unsigned int* mxx = mxq + c;
+    RBGS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    if (c > 0) {
+      if ((s = h3_colmax(n, c, (const float*)Qprev, ldq, mxq, st))) return s;
+      if ((s = h3_scales_from_max(c, mxq, qscale, st))) return s;
+      if ((s = h3_split(n, c, (const float*)Qprev, ldq, qscale, nch, Qs, st))) return s;
+    }
+    if ((s = h3_colmax(n, mb, (const float*)X, ldx, mxx, st))) return s;
+    s = h3_prepare<float>(c, mb, G, ldg, nullptr, 0, (const float*)mxx, c > 0 ? qscale : nullptr, 0, B, sc,
+                          nullptr, st);
+    if (s) return s;
+    s = tall_update_h3(n, c, mb, c > 0 ? Qs : nullptr, nch, (const float*)X, ldx, B, sc, (float*)Qout, ldo, nullptr,
+                       0, 0, nullptr, err, st);
+    if (s) return s;
+    if (sync) {
+      int herr = 0;
+      RBGS_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+      if (herr) return RBGS_ETIMEOUT;
+    }
+    return RBGS_OK;
+  }
   if (prec == RBGS_P_FP64) {
     s = tall_update_simt<double>(n, c, mb, (const double*)Qprev, ldq, (const double*)X, ldx, G, ldg, (double*)Qout,
                                  ldo, nullptr, st);

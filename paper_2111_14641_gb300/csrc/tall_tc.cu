@@ -572,7 +572,7 @@ rbgs_status tall_update_tc(int64_t n, int64_t c, int64_t mb, const float* A1, in
   RBGS_CUDA_TRY(cudaGetDevice(&dev));
   RBGS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   if (!err) return RBGS_EINVAL;
-  TcParams p;
+  TcParams p{};
   p.n = n;
   p.c = (int)c;
   p.mb = (int)mb;

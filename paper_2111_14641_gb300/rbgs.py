@@ -19,7 +19,7 @@ from . import build as _build
 _HDR = Path(__file__).resolve().parent.parent / "include" / "rbgs.h"
 
 SKETCH = {"gauss": 0, "rademacher": 1, "srht": 2}
-PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2}
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "f16x3": 3}
 # Largest c + mb that rbgs_tall_update_noalloc accepts (its fixed scratch).
 NOALLOC_MAX_K = int(re.search(r"#define RBGS_NOALLOC_MAX_K (\d+)", _HDR.read_text()).group(1))
 STATUS = {0: "RBGS_OK", 1: "RBGS_EINVAL", 2: "RBGS_ENOMEM", 3: "RBGS_ECUDA", 4: "RBGS_EBREAKDOWN",

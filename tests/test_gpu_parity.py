@@ -240,6 +240,62 @@ def test_rbgs_tf32x3_matches_oracle(rb, kind, reorth, fine):
     assert st.passes2 == (m // mb - 1 if reorth else 0)
 
 
+# ------------------------------------------- FP16 hi/lo split tensor path --
+
+@pytest.mark.parametrize("n,c,mb", [(1, 0, 1), (128, 0, 50), (129, 5, 3), (1000, 64, 16), (4097, 200, 50),
+                                    (300, 0, 64), (2000, 950, 50), (513, 33, 64), (700, 130, 7)])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_tall_update_f16x3_matches_numpy(rb, n, c, mb, inplace):
+    """FP16 hi/lo split tcgen05 product (power-of-two column scales):
+    Qout = [Qprev | X] G with FP32-level accuracy."""
+    rng = np.random.default_rng(11 * n + c + mb)
+    ld = (n + 3) // 4 * 4 + 4
+    Qp = rng.standard_normal((n, c)).astype(np.float32).astype(np.float64)
+    X = (rng.standard_normal((n, mb)) * np.logspace(0, -6, mb)).astype(np.float32).astype(np.float64)
+    G = rng.standard_normal((c + mb, mb)) * np.logspace(0, 5, mb)
+    Qd = dev_ld(Qp, torch.float32, ld) if c > 0 else None
+    Xd = dev_ld(X, torch.float32, ld)
+    out = Xd if inplace else dev_ld(np.zeros((n, mb)), torch.float32, ld)
+    res = host(rb.tall_update(Qd, Xd, torch.from_numpy(G), prec="f16x3", out=out))
+    ref = np.hstack([Qp, X]) @ G
+    scale = np.abs(np.hstack([Qp, X])) @ np.abs(G) + 1e-300
+    assert (np.abs(res - ref) / scale).max() <= 2e-6
+
+
+F16_QR_CASES = [
+    # n, m, mb, kind, k
+    (6000, 48, 8, "gauss", 240),
+    (3000, 150, 50, "srht", 400),
+    (5000, 128, 64, "srht", 300),
+    (2049, 39, 13, "rademacher", 120),
+]
+
+
+@pytest.mark.parametrize("n,m,mb,kind,k", F16_QR_CASES)
+@pytest.mark.parametrize("reorth", [0, 1, 2])
+@pytest.mark.parametrize("fine", [False, True])
+def test_rbgs_f16x3_matches_oracle(rb, n, m, mb, kind, k, reorth, fine):
+    """RBGS with the pre-split basis: block boundaries that do not fall on the
+    64-column chunks, all second-pass modes, FP32 or FP64 sketch space."""
+    cond = 1e3
+    W = synth.svd_matrix(n, m, cond, 5 + m).astype(np.float32).astype(np.float64)
+    ld = (n + 3) // 4 * 4 + 4  # the tensor-core paths need ld % 4 == 0
+    Wd = dev_ld(W, torch.float32, ld)
+    Qd = dev_ld(np.zeros((n, m)), torch.float32, ld)
+    _, Rd, st = rb.rbgs_qr(Wd, mb, kind, k, 5, prec="f16x3", ls_iters=3, reorth=reorth, reorth_tol=1e-6, Q=Qd,
+                           certify=True, fine=fine)
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, 5, variant=5, ls="richardson", ls_iters=3, reorth=bool(reorth),
+                      ls_iters_first=1)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    assert oracle.factorization_error(W, Q, R) < 2e-6
+    ortho = oracle.sketched_orthogonality(Q, kind, k, 5)[0]
+    assert ortho < (1e-4 if reorth else 1e-3)
+    assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
+    if reorth == 1:
+        assert st.passes2 == m // mb - 1
+
+
 # ------------------------------------------------ full-size mixed workload --
 
 def test_c2_full_size_properties(rb):
