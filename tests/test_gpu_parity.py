@@ -300,14 +300,14 @@ def test_rbgs_f16x3_matches_oracle(rb, n, m, mb, kind, k, reorth, fine):
 
 def test_c2_full_size_properties(rb):
     """n = 1e6, m = 1000, m_p = 50, SRHT k = 2000, W in FP32 with sigma from 1
-    to 1e-6, in the launch configuration bench.py times (3xTF32 tall products,
+    to 1e-6, in the launch configuration bench.py times (FP16-split tall products,
     FP64 sketch space, one Richardson iteration, second pass on every block).
     The oracle cannot factor this size, so the test checks what holds at any
     size, with the oracle's own Theta: sketched orthogonality of Q, W = QR,
     and the triangular structure of R."""
     n, m, mb, k, seed = 1_000_000, 1000, 50, 2000, 1
     W = synth.svd_matrix_torch(n, m, 1e6, 7, device="cuda", dtype=torch.float32)
-    Q, R, st = rb.rbgs_qr(W, mb, "srht", k, seed, prec="tf32x3", ls_iters=1, reorth=1, fine=True)
+    Q, R, st = rb.rbgs_qr(W, mb, "srht", k, seed, prec="f16x3", ls_iters=1, reorth=1, fine=True)
     assert st.passes2 == m // mb - 1
     Rh = host(R)
     assert np.allclose(np.tril(Rh, -1), 0.0) and np.all(np.diag(Rh) > 0)
