@@ -172,6 +172,20 @@ rbgs_status richardson(int64_t k, int64_t c, int mb, const TS* S, const TS* Pi, 
   return RBGS_OK;
 }
 
+// A non-blocking stream per device for work that can run beside the caller's
+// stream (ordered with events).
+rbgs_status side_stream(cudaStream_t* out) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  RBGS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return RBGS_ENODEV;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev]) RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+  *out = streams[dev];
+  return RBGS_OK;
+}
+
 // T: storage of W and Q; TS: storage/arithmetic of the sketch space.
 template <class T, class TS>
 rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_sketch sketch, int64_t k,
@@ -213,6 +227,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     double* part = cv.take<double>(kPartElems);
     TS* partf = cv.take<TS>(kPartElems);
     void* skscr = cv.take<char>(sk_bytes);
+    void* skscr2 = cv.take<char>(sk_bytes);  // the side stream's sketches of the next blocks of W
     int* flags = cv.take<int>(64);
     int* blk_on = cv.take<int>((size_t)p);
     double* cert_buf = cert ? cv.take<double>((size_t)k * m * 3 + (size_t)m * 64 + 8) : nullptr;
@@ -293,8 +308,28 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       return assemble_g<TS, T>(c, mb, Rc, m, Rd, Rdinv, Gmat, c + mb, Rcol, ldr, act, st);
     };
 
+    // Step 1 of block i + 1 (the sketch of W_{i+1}) depends on nothing in block
+    // i, so it runs on a side stream while block i's sketch-space steps run
+    // here (those keep few SMs busy); an event hands P_{i+1} over.
+    cudaStream_t st2 = nullptr;
+    std::vector<cudaEvent_t> evw;
+    struct EvGuard {
+      std::vector<cudaEvent_t>* v;
+      ~EvGuard() {
+        for (auto e : *v) cudaEventDestroy(e);
+      }
+    } evguard{&evw};
+    if (p > 1) {
+      if ((s = side_stream(&st2))) return s;
+      evw.resize((size_t)p + 1, nullptr);
+      for (auto& e : evw) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     // step 1 of the first block
     if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, W, ldw, mb, P, k, skscr, sk_bytes, st))) return s;
+    if (p > 1) {  // the side stream starts after everything enqueued here so far
+      RBGS_CUDA_TRY(cudaEventRecord(evw[p], st));
+      RBGS_CUDA_TRY(cudaStreamWaitEvent(st2, evw[p], 0));
+    }
     for (int64_t blk = 0; blk < p; ++blk) {
       const int64_t c = blk * mb;
       const T* Wi = W + c * ldw;
@@ -302,6 +337,12 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       TS* Pi = P + c * k;
       TS* Si = S + c * k;
       double* Rcol = R + c * ldr;
+      if (blk + 1 < p) {
+        s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi + mb * ldw, ldw, mb, Pi + mb * k, k, skscr2, sk_bytes, st2);
+        if (s) return s;
+        RBGS_CUDA_TRY(cudaEventRecord(evw[blk + 1], st2));
+      }
+      if (blk > 0) RBGS_CUDA_TRY(cudaStreamWaitEvent(st, evw[blk], 0));
       // step 2 and the implicit sketch of Alg. 5
       // With a second pass to follow, the first pass is provisional: one
       // Richardson step and one (shifted) Cholesky QR round; the second pass
@@ -322,10 +363,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       // step 3 fused with the triangular solve
       // (the split copy of a provisional result is not kept: the second pass rereads it as FP32)
       if ((s = tall(c, Wi, ldw, Qi, nullptr, Pi, !(o.reorth == 1 && c > 0)))) return s;
-      // step 5, and step 1 of the next block, in one pass (the single reduction per block of Alg. 5)
-      s = sketch_apply2_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, Wi + mb * ldw, ldw, blk + 1 < p ? mb : 0,
-                                 Pi + mb * k, k, skscr, sk_bytes, st);
-      if (s) return s;
+      // step 5 (the sketch of W_{i+1}, step 1 of the next block, runs on the side stream)
+      if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st))) return s;
       // optional second projection pass
       if (o.reorth && c > 0) {
         s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Si, k, 0.0, X2, m, partf, kPartElems, nullptr, st);

@@ -29,7 +29,12 @@ __global__ void __launch_bounds__(256) small_gemm_part(int trans, int64_t M, int
   __shared__ TACC As[SG_K][SG_T + 1];
   __shared__ TACC Bs[SG_K][SG_N + 1];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  // Warp w owns output columns 8w .. 8w + 7, lane l rows l and l + 32: a warp
+  // whose columns are all >= N does no arithmetic (N = m_p is often not a
+  // multiple of 16, and the FP64 pipe is the bottleneck).
+  const int warp = tid >> 5, lane = tid & 31;
+  const int jw = 8 * warp;
+  const bool busy = jw < N;
   const int64_t i0 = (int64_t)blockIdx.x * SG_T;
   const int split = blockIdx.y;
   const int64_t kb = (int64_t)split * kper;
@@ -51,11 +56,11 @@ __global__ void __launch_bounds__(256) small_gemm_part(int trans, int64_t M, int
       rb[q] = (gb < ke && j < N) ? (TACC)B[gb + (int64_t)j * ldb] : (TACC)0;
     }
   };
-  TACC acc[4][4];
+  TACC acc[2][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[i][q] = 0;
+    for (int q = 0; q < 8; ++q) acc[i][q] = 0;
   if (kb < ke) load(kb);
   for (int64_t l0 = kb; l0 < ke; l0 += SG_K) {
 #pragma unroll
@@ -69,28 +74,30 @@ __global__ void __launch_bounds__(256) small_gemm_part(int trans, int64_t M, int
     }
     __syncthreads();
     if (l0 + SG_K < ke) load(l0 + SG_K);
+    if (busy) {
 #pragma unroll
-    for (int ll = 0; ll < SG_K; ++ll) {
-      TACC a[4], b[4];
+      for (int ll = 0; ll < SG_K; ++ll) {
+        const TACC a0 = As[ll][lane], a1 = As[ll][lane + 32];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[ll][ty + 16 * i];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = Bs[ll][tx + 16 * q];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] += a[i] * b[q];
+        for (int q = 0; q < 8; ++q) {
+          const TACC b = Bs[ll][jw + q];
+          acc[0][q] += a0 * b;
+          acc[1][q] += a1 * b;
+        }
+      }
     }
     __syncthreads();
   }
+  if (busy) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t gi = i0 + ty + 16 * i;
-      const int j = tx + 16 * q;
-      if (gi < M && j < N) part[((int64_t)split * N + j) * M + gi] = acc[i][q];
-    }
+      for (int q = 0; q < 8; ++q) {
+        const int64_t gi = i0 + lane + 32 * i;
+        const int j = jw + q;
+        if (gi < M && j < N) part[((int64_t)split * N + j) * M + gi] = acc[i][q];
+      }
+  }
 }
 
 template <class TACC, class TO>
