@@ -108,8 +108,20 @@ __global__ void small_gemm_reduce(int64_t M, int N, int ks, const TACC* __restri
   if (idx >= M * N) return;
   const int64_t i = idx % M;
   const int64_t j = idx / M;
-  TACC s = 0;
-  for (int p = 0; p < ks; ++p) s += part[((int64_t)p * N + j) * M + i];
+  // eight independent loads in flight (the partial slices live in L2); the
+  // slices are added in a fixed order, so the result is reproducible
+  const TACC* pp = part + j * M + i;
+  const int64_t stride = (int64_t)N * M;
+  TACC s8[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) s8[u] = 0;
+  int p = 0;
+  for (; p + 8 <= ks; p += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s8[u] += pp[(int64_t)(p + u) * stride];
+  }
+  for (; p < ks; ++p) s8[p & 7] += pp[(int64_t)p * stride];
+  TACC s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
   TO* o = out + i + j * ldo;
   const double v = alpha * (double)s;
   *o = (TO)(beta == 0.0 ? v : v + beta * (double)(*o));
@@ -153,6 +165,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
   Row* P = X + 64;                             // Rprev
   Row* PI = P + 64;                            // Rprev_inv
   __shared__ T xscale[64];                     // row j of R^{-1} = X[j][:] * xscale[j]
+  __shared__ T pivot_s[2];                     // 1 / sqrt of the current and the next pivot
   __shared__ T shift_s;
   __shared__ int bad_s;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // 16 x 16 thread grid
@@ -184,18 +197,20 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
   // SM's FP64 pipe is narrow and a warp instruction costs the same with idle
   // lanes, so the triangle is walked by a linear index (full warps); the
   // pivot's reciprocal square root is taken once per warp and broadcast.
-  const int lane = tid & 31;
-  for (int j = 0; j < mb; ++j) {
-    T rinv = 0;
-    if (lane == 0) {
-      T d = A[j][j];
-      if (!(d > (T)0) || !isfinite((double)d)) {
-        if (tid == 0) bad_s = 1;
-        d = (T)1;
-      }
-      rinv = rsqrt(d);
+  // The next pivot's reciprocal square root is taken by the thread that
+  // finishes that pivot (the first entry of the trailing triangle) while the
+  // other warps still update: it stays off the step's critical path.
+  if (tid == 0) {
+    T d = A[0][0];
+    if (!(d > (T)0) || !isfinite((double)d)) {
+      bad_s = 1;
+      d = (T)1;
     }
-    rinv = __shfl_sync(0xffffffffu, rinv, 0);
+    pivot_s[0] = rsqrt(d);
+  }
+  __syncthreads();
+  for (int j = 0; j < mb; ++j) {
+    const T rinv = pivot_s[j & 1];
     const T dinv = rinv * rinv;
     if (tid == 0) xscale[j] = rinv;  // 1 / R_jj, used by the inverse below
     for (int l = j + tid; l < mb; l += 256) F[j][l] = (l == j) ? (T)1 / rinv : A[j][l] * rinv;
@@ -204,7 +219,16 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
     for (int e = tid; e < tot; e += 256) {
       const int b = tri_col(e), a = e - b * (b + 1) / 2;  // a <= b < nt
       const int i = j + 1 + a, l = j + 1 + b;
-      A[i][l] -= A[j][i] * dinv * A[j][l];
+      const T v = A[i][l] - A[j][i] * dinv * A[j][l];
+      A[i][l] = v;
+      if (e == 0) {  // (j + 1, j + 1): the next pivot is final now
+        T d = v;
+        if (!(d > (T)0) || !isfinite((double)d)) {
+          bad_s = 1;
+          d = (T)1;
+        }
+        pivot_s[(j + 1) & 1] = rsqrt(d);
+      }
     }
     __syncthreads();
   }
@@ -220,6 +244,12 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
     }
     __syncthreads();
   }
+  // rows of R^{-1} = X[j][:] / R_jj, scaled once
+  for (int e = tid; e < mb * mb; e += 256) {
+    const int i = e / mb, l = e % mb;
+    if (i <= l) X[i][l] *= xscale[i];
+  }
+  __syncthreads();
   // Outputs by diagonals (equal dot-product lengths within a warp).
   const int ntri = mb * (mb + 1) / 2;
   if (Rprev) {
@@ -230,7 +260,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
       T s1 = 0, s2 = 0;
       for (int t = i; t <= l; ++t) {
         s1 += F[i][t] * P[t][l];
-        s2 += PI[i][t] * X[t][l] * xscale[t];
+        s2 += PI[i][t] * X[t][l];
       }
       R[i + l * mb] = s1;
       Rinv[i + l * mb] = s2;
@@ -240,7 +270,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
       int d = diag_of(e, mb), i = e - diag_start(d, mb);
       const int l = i + d;
       R[i + l * mb] = F[i][l];
-      Rinv[i + l * mb] = X[i][l] * xscale[i];
+      Rinv[i + l * mb] = X[i][l];
     }
   }
   for (int e = tid; e < mb * mb; e += 256) {  // strictly lower parts are zero

@@ -69,12 +69,18 @@ constexpr float kQScale = 512.f;          // 2^9: scale of the sketch-orthonorma
 constexpr uint64_t kMaxWaitNs = 2000000000ull;  // bounded waits: 2 s
 constexpr uint32_t kSuspendHintNs = 100000u;
 
-template <int AST, int RST, int BST, int NS = 4>
+// ATM > 0: the A chunk is copied into ATM tensor-memory stages (tcgen05.cp)
+// and the MMAs read A from there; 0: the MMAs read A from shared memory.
+template <int AST, int RST, int BST, int NS = 4, int ATM = 0>
 struct H3Cfg {
   static constexpr int A_STAGES = AST, R_STAGES = RST, B_STAGES = BST;
   static constexpr int NSLOT = NS;              // TMEM accumulator slots of 64 FP32 columns
-  static constexpr int TMEM_COLS = NS * 64;     // 256 or 512
-  static_assert(NS == 4 || NS == 8, "TMEM allocation is a power of two");
+  static constexpr int A_TMEM = ATM;
+  static constexpr int A_COL0 = NS * 64;        // TMEM A stages: 64 columns each (hi 32 | lo 32)
+  static constexpr int TMEM_USED = NS * 64 + ATM * 64;
+  static constexpr int TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
+  static_assert(TMEM_USED <= 512, "TMEM budget");
+  static_assert(ATM == 0 || ATM == 2 || ATM == 4, "TMEM A stages");
   static constexpr int R_OFF = AST * H_ACHUNK;
   static constexpr int B_OFF = R_OFF + RST * H_ACHUNK;
   static constexpr int BAR_OFF = B_OFF + BST * H_BCHUNK;
@@ -171,6 +177,18 @@ __device__ __forceinline__ void umma_f16_ss(uint32_t tmem_d, uint64_t adesc, uin
       "l"(adesc), "l"(bdesc), "r"(kIdescF16), "r"(accum)
       : "memory");
 }
+// A operand from tensor memory (rows in lanes, K pairs along the columns).
+__device__ __forceinline__ void umma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(kIdescF16), "r"(accum)
+      : "memory");
+}
+// 128 rows x 256 bits (16 fp16 of K) from shared memory (matrix descriptor) into 8 TMEM columns.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
+  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -224,10 +242,11 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   auto conv_full = [&](int s) { return bar0 + 8u * (50 + s); };  // 2
   auto raw_empty = [&](int s) { return bar0 + 8u * (52 + s); };  // 2
   const uint32_t fin_bar = bar0 + 8u * 54;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::BAR_OFF + 8 * 56);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + Cfg::BAR_OFF + 8 * 56 + 8);
-  float* sm_scale = reinterpret_cast<float*>(smem + Cfg::BAR_OFF + 8 * 56 + 16);  // 128 floats
-  static_assert(8 * 56 + 16 + 128 * 4 <= Cfg::BAR_BYTES, "barrier area");
+  auto atm_free = [&](int s) { return bar0 + 8u * (55 + s); };   // 4
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::BAR_OFF + 8 * 60);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + Cfg::BAR_OFF + 8 * 60 + 8);
+  float* sm_scale = reinterpret_cast<float*>(smem + Cfg::BAR_OFF + 8 * 60 + 16);  // 128 floats
+  static_assert(8 * 60 + 16 + 128 * 4 <= Cfg::BAR_BYTES, "barrier area");
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -252,6 +271,7 @@ __global__ void __launch_bounds__(H_THREADS, 1)
       mbar_init(raw_empty(s), 1);
     }
     mbar_init(fin_bar, 1);
+    for (int s = 0; s < 4; ++s) mbar_init(atm_free(s), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -367,18 +387,46 @@ __global__ void __launch_bounds__(H_THREADS, 1)
           const uint32_t alo = ahi + H_PART;
           const uint32_t bhi = smem_u32(smem + Cfg::B_OFF + bs * H_BCHUNK);
           const uint32_t blo = bhi + H_BPART;
-          // 4 K steps of 16: cross terms first, then the main products
+          if constexpr (Cfg::A_TMEM > 0) {
+            // A into tensor memory once (tcgen05.cp, 128 rows x 16 K per copy), then
+            // the MMAs read it there: the chunk crosses shared memory once, not three times
+            const int ts = (int)(sit % Cfg::A_TMEM);
+            const uint32_t tph = (sit / Cfg::A_TMEM) & 1u;
+            if (!mbar_wait(atm_free(ts), tph ^ 1u)) {  // the MMAs of chunk sit - A_TMEM are done with it
+              fail(1);
+              bad = true;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t ta = tmem_base + (uint32_t)(Cfg::A_COL0 + ts * 64);
 #pragma unroll
-          for (int kk = 0; kk < H_K / 16; ++kk) {
-            umma_f16_ss(dslot, umma_desc(ahi + kk * 2 * kALbo, kALbo, kASbo),
-                        umma_desc(blo + kk * 2 * kBLbo, kBLbo, kBSbo), kk != 0);
-            umma_f16_ss(dslot, umma_desc(alo + kk * 2 * kALbo, kALbo, kASbo),
-                        umma_desc(bhi + kk * 2 * kBLbo, kBLbo, kBSbo), 1u);
+            for (int kk = 0; kk < H_K / 16; ++kk) {
+              tmem_cp_128x256b(ta + 8 * kk, umma_desc(ahi + kk * 2 * kALbo, kALbo, kASbo));
+              tmem_cp_128x256b(ta + 32 + 8 * kk, umma_desc(alo + kk * 2 * kALbo, kALbo, kASbo));
+            }
+#pragma unroll
+            for (int kk = 0; kk < H_K / 16; ++kk) {
+              umma_f16_ts(dslot, ta + 8 * kk, umma_desc(blo + kk * 2 * kBLbo, kBLbo, kBSbo), kk != 0);
+              umma_f16_ts(dslot, ta + 32 + 8 * kk, umma_desc(bhi + kk * 2 * kBLbo, kBLbo, kBSbo), 1u);
+            }
+#pragma unroll
+            for (int kk = 0; kk < H_K / 16; ++kk)
+              umma_f16_ts(dslot, ta + 8 * kk, umma_desc(bhi + kk * 2 * kBLbo, kBLbo, kBSbo), 1u);
+            umma_commit(atm_free(ts));
+          } else {
+            // 4 K steps of 16: cross terms first, then the main products
+#pragma unroll
+            for (int kk = 0; kk < H_K / 16; ++kk) {
+              umma_f16_ss(dslot, umma_desc(ahi + kk * 2 * kALbo, kALbo, kASbo),
+                          umma_desc(blo + kk * 2 * kBLbo, kBLbo, kBSbo), kk != 0);
+              umma_f16_ss(dslot, umma_desc(alo + kk * 2 * kALbo, kALbo, kASbo),
+                          umma_desc(bhi + kk * 2 * kBLbo, kBLbo, kBSbo), 1u);
+            }
+#pragma unroll
+            for (int kk = 0; kk < H_K / 16; ++kk)
+              umma_f16_ss(dslot, umma_desc(ahi + kk * 2 * kALbo, kALbo, kASbo),
+                          umma_desc(bhi + kk * 2 * kBLbo, kBLbo, kBSbo), 1u);
           }
-#pragma unroll
-          for (int kk = 0; kk < H_K / 16; ++kk)
-            umma_f16_ss(dslot, umma_desc(ahi + kk * 2 * kALbo, kALbo, kASbo),
-                        umma_desc(bhi + kk * 2 * kBLbo, kBLbo, kBSbo), 1u);
           umma_commit(raw ? raw_empty(as) : a_empty(as));
           umma_commit(b_empty(bs));
           umma_commit(slot_full(sl));
@@ -815,6 +863,15 @@ int h3_slots() {
   return v;
 }
 
+// RBGS_H3_ATMEM=1: A through tensor memory (tcgen05.cp) in the long-K shape.
+int h3_a_tmem() {
+  static int v = []() {
+    const char* e = getenv("RBGS_H3_ATMEM");
+    return e ? atoi(e) : 0;
+  }();
+  return v;
+}
+
 }  // namespace
 
 int64_t h3_nch_row(int64_t m) { return (m + H_K - 1) / H_K; }
@@ -929,6 +986,8 @@ rbgs_status tall_update_h3(int64_t n, int64_t c, int64_t mb, const unsigned char
   if (qch == 0) return go(H3Cfg<1, 2, 2>{});
   if (qch <= 2) return go(H3Cfg<3, 2, 2>{});
   if (h3_slots() == 8) return go(H3Cfg<4, 1, 3, 8>{});
+  if (h3_a_tmem() == 2) return go(H3Cfg<4, 1, 3, 4, 2>{});
+  if (h3_a_tmem() == 4) return go(H3Cfg<4, 1, 3, 4, 4>{});
   return go(H3Cfg<4, 1, 3>{});
 }
 
