@@ -83,6 +83,17 @@ def _load():
         lib.or_rcholqr.restype = ctypes.c_int
         lib.or_ls_solve.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, dp, i64, dp, i64, i64, dp, i64]
         lib.or_ls_solve.restype = ctypes.c_int
+        dd = ctypes.c_double
+        lib.or_stencil5_apply.argtypes = [ctypes.c_void_p, dp, i64, i64, dp, i64]
+        lib.or_stencil5_apply.restype = None
+        lib.or_rbgs_arnoldi.argtypes = [i64, i64, dd, dd, dp, i64, i64, i64, ctypes.c_int, i64, ctypes.c_uint64,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, i64,
+                                        dp, i64, dp]
+        lib.or_rbgs_arnoldi.restype = ctypes.c_int
+        lib.or_block_krylov.argtypes = [ctypes.c_int, i64, i64, dd, dd, dp, i64, dp, i64, i64, i64, ctypes.c_int, i64,
+                                        ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, dd, i64, dp]
+        lib.or_block_krylov.restype = ctypes.c_int
         lib.or_set_threads.argtypes = [ctypes.c_int]
         lib.or_get_threads.restype = ctypes.c_int
         _lib = lib
@@ -211,6 +222,65 @@ def rcholqr(W, kind: str, k: int, seed: int):
     if rc == -1:
         raise ValueError("bad arguments")
     return Q, R, rc
+
+
+# ---- Sec. 5: the stencil operator, Alg. 7 (RBGS-Arnoldi), block GMRES / FOM ----
+
+class _Stencil(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("bx", ctypes.c_double), ("by", ctypes.c_double)]
+
+
+def stencil5_apply(nx: int, ny: int, bx: float, by: float, X) -> np.ndarray:
+    """Y = A X for the 5-point convection-diffusion operator (-Laplace + b . grad,
+    nx x ny interior points of the unit square, zero Dirichlet boundary)."""
+    X = _f64(X)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1, order="F")
+    n, c = X.shape
+    Y = np.zeros((n, c), order="F")
+    op = _Stencil(nx, ny, bx, by)
+    _load().or_stencil5_apply(ctypes.byref(op), _ptr(X), n, c, _ptr(Y), n)
+    return Y
+
+
+def rbgs_arnoldi(nx: int, ny: int, bx: float, by: float, B, p: int, kind: str, k: int, seed: int, variant: int = 5,
+                 ls: str = "householder", ls_iters: int = 5, reorth: bool = False, ls_iters_first: int = 0):
+    """Alg. 7: Q (n x p mp), R (p mp x p mp); H = R[:, mp:].  Returns dict(Q, R, delta, delta_tilde, rc)."""
+    B = _f64(B)
+    n, mp = B.shape
+    m = p * mp
+    Q = np.zeros((n, m), order="F")
+    R = np.zeros((m, m), order="F")
+    st = np.zeros(3)
+    rc = _load().or_rbgs_arnoldi(nx, ny, bx, by, _ptr(B), n, mp, p, THETA[kind], int(k), int(seed), int(variant),
+                                 LS[ls], int(ls_iters), int(ls_iters_first), int(bool(reorth)), _ptr(Q), n, _ptr(R),
+                                 m, _ptr(st))
+    if rc == -1:
+        raise ValueError("bad Arnoldi arguments")
+    return dict(Q=Q, R=R, delta=st[0], delta_tilde=st[1], rc=rc)
+
+
+def block_krylov(method: str, nx: int, ny: int, bx: float, by: float, B, X0, p: int, kind: str, k: int, seed: int,
+                 rtol: float, max_cycles: int, variant: int = 5, ls: str = "householder", ls_iters: int = 5,
+                 reorth: bool = False, ls_iters_first: int = 0):
+    """Restarted randomized block GMRES (method "gmres") or FOM ("fom") with p
+    Arnoldi blocks per cycle.  Returns (X, cycles, relres)."""
+    B = _f64(B)
+    X = np.array(_f64(X0), order="F", copy=True)
+    n, mp = B.shape
+    relres = np.zeros(mp)
+    cyc = _load().or_block_krylov({"gmres": 0, "fom": 1}[method], nx, ny, bx, by, _ptr(B), n, _ptr(X), n, mp, p,
+                                  THETA[kind], int(k), int(seed), int(variant), LS[ls], int(ls_iters),
+                                  int(ls_iters_first), int(bool(reorth)), float(rtol), int(max_cycles), _ptr(relres))
+    if cyc < 0:
+        raise np.linalg.LinAlgError(f"block Krylov solver failed ({cyc})")
+    return X, int(cyc), relres
+
+
+def stencil5_dense(nx: int, ny: int, bx: float, by: float) -> np.ndarray:
+    """The operator as a dense matrix, column by column through stencil5_apply."""
+    n = nx * ny
+    return stencil5_apply(nx, ny, bx, by, np.eye(n))
 
 
 # ---- quality measures, computed in FP64 with the oracle's own Theta ----------

@@ -26,6 +26,8 @@
  *             (S'_i = P_i - S_{1:i-1} R_{1:i-1,i}).
  *   Alg. 6    steps 4-5 by l2 Householder QR followed by RCholeskyQR.
  *   Step 6    Delta = ||I - S^T S||_F, Delta~ = ||P - S R||_F / ||P||_F.
+ *   Alg. 7    RBGS-Arnoldi for the 5-point convection-diffusion operator;
+ *   Sec. 5.2  restarted randomized block GMRES, Sec. 5.3 block FOM.
  *
  * One extension that the paper does not contain is offered behind a flag:
  * a second projection pass per block ("reorth"), the sketched analogue of
@@ -664,9 +666,40 @@ static int interblock(int variant, int64_t n, int64_t mp, double* Qp, int64_t ld
  * {Delta, Delta~, number of second passes}.  With reorth, ls_iters_first > 0
  * sets the Richardson count of the first (provisional) pass.  Returns 0, -1
  * on bad arguments, -2 on a breakdown (zero or non-finite R_ii diagonal).   */
-int or_rbgs(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int theta, int64_t k, uint64_t seed,
-            int variant, int ls, int ls_iters, int ls_iters_first, int reorth, double* Q, int64_t ldq, double* R,
-            int64_t ldr, double* S_out, double* P_out, double* stats) {
+/* ------------------------------------------------------------------------ */
+/* The 5-point convection-diffusion operator A u = -Laplace(u) + b . grad(u) on
+ * the unit square, nx x ny interior points with spacing hx = 1/(nx+1),
+ * hy = 1/(ny+1), zero Dirichlet boundary, central differences; point (x, y)
+ * is row x + nx y.  (The synthetic operator of the Krylov experiments.)     */
+typedef struct {
+  int64_t nx, ny;
+  double bx, by;
+} or_stencil;
+
+void or_stencil5_apply(const or_stencil* op, const double* X, int64_t ldx, int64_t ncols, double* Y, int64_t ldy) {
+  const int64_t nx = op->nx, ny = op->ny;
+  const double hx = 1.0 / (double)(nx + 1), hy = 1.0 / (double)(ny + 1);
+  const double cx = 1.0 / (hx * hx), cy = 1.0 / (hy * hy);
+  const double ax = op->bx / (2.0 * hx), ay = op->by / (2.0 * hy);
+  for (int64_t j = 0; j < ncols; ++j) {
+    const double* x = X + j * ldx;
+    double* y = Y + j * ldy;
+    for (int64_t iy = 0; iy < ny; ++iy)
+      for (int64_t ix = 0; ix < nx; ++ix) {
+        const int64_t i = ix + nx * iy;
+        const double w = ix > 0 ? x[i - 1] : 0.0, e = ix + 1 < nx ? x[i + 1] : 0.0;
+        const double so = iy > 0 ? x[i - nx] : 0.0, no = iy + 1 < ny ? x[i + nx] : 0.0;
+        y[i] = cx * (2.0 * x[i] - w - e) + cy * (2.0 * x[i] - so - no) + ax * (e - w) + ay * (no - so);
+      }
+  }
+}
+
+/* RBGS, optionally as the block Arnoldi process of Alg. 7: with op, block 1
+ * is W_1 = B (the given W) and every later block is W_i = A Q_{i-1}.       */
+static int rbgs_core(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int theta, int64_t k,
+                     uint64_t seed, int variant, int ls, int ls_iters, int ls_iters_first, int reorth,
+                     const or_stencil* op, double* Q, int64_t ldq, double* R, int64_t ldr, double* S_out,
+                     double* P_out, double* stats) {
   if (mp <= 0 || m % mp != 0 || n < 1 || k < m || ldw < n || ldq < n || ldr < m) return -1;
   if (theta == OR_THETA_SRHT && k > or_srht_padded(n)) return -1;
   if (theta != OR_THETA_SRHT && k > n) return -1;
@@ -680,6 +713,7 @@ int or_rbgs(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int 
   double* R2ii = (double*)malloc(sizeof(double) * (size_t)(mp * mp));
   double* Tmp = (double*)malloc(sizeof(double) * (size_t)(m * mp));
   double* Qtmp = (double*)malloc(sizeof(double) * (size_t)(n * mp));
+  double* Wop = op ? (double*)malloc(sizeof(double) * (size_t)(n * mp)) : NULL;
   int rc = 0;
   int passes2 = 0;
   for (int64_t j = 0; j < m; ++j)
@@ -688,18 +722,24 @@ int or_rbgs(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int 
   for (int64_t blk = 0; blk < p; ++blk) {
     int64_t c = blk * mp; /* columns already orthogonalized */
     const double* Wi = W + c * ldw;
+    int64_t ldwi = ldw;
+    if (op && blk > 0) { /* Alg. 7, step 2: W_i = A Q_{i-1} */
+      or_stencil5_apply(op, Q + (c - mp) * ldq, ldq, mp, Wop, n);
+      Wi = Wop;
+      ldwi = n;
+    }
     double* Qi = Q + c * ldq;
     double* Pi = P + c * k;
     double* Si = S + c * k;
     /* step 1: P_i = Theta W_i */
-    or_theta_apply(theta, k, n, seed, Wi, ldw, mp, Pi, k);
+    or_theta_apply(theta, k, n, seed, Wi, ldwi, mp, Pi, k);
     /* step 2: R_{1:i-1,i} = argmin ||S_{1:i-1} Y - P_i||_F (with a second pass
        to follow, the first may use its own iteration count) */
     if (c > 0 && solve_ls(ls, (reorth && ls_iters_first > 0) ? ls_iters_first : ls_iters, k, c, S, k, Pi, k, mp, Rc,
                           m))
       rc = -2;
     /* step 3: Q'_i = W_i - Q_{1:i-1} R_{1:i-1,i} */
-    project(n, c, mp, Wi, ldw, Q, ldq, Rc, m, Qi, ldq);
+    project(n, c, mp, Wi, ldwi, Q, ldq, Rc, m, Qi, ldq);
     /* implicit sketch for Alg. 5: S'_i = P_i - S_{1:i-1} R_{1:i-1,i} */
     if (c > 0) gemm(0, 0, k, mp, c, 1.0, S, k, Rc, m, 0.0, Spp, k);
     for (int64_t j = 0; j < mp; ++j)
@@ -756,8 +796,112 @@ int or_rbgs(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int 
   }
   if (S_out) memcpy(S_out, S, sizeof(double) * (size_t)(k * m));
   if (P_out) memcpy(P_out, P, sizeof(double) * (size_t)(k * m));
-  free(S); free(P); free(Spp); free(Rc); free(Rii); free(R2); free(R2ii); free(Tmp); free(Qtmp);
+  free(S); free(P); free(Spp); free(Rc); free(Rii); free(R2); free(R2ii); free(Tmp); free(Qtmp); free(Wop);
   return rc;
+}
+
+int or_rbgs(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int theta, int64_t k, uint64_t seed,
+            int variant, int ls, int ls_iters, int ls_iters_first, int reorth, double* Q, int64_t ldq, double* R,
+            int64_t ldr, double* S_out, double* P_out, double* stats) {
+  return rbgs_core(W, n, m, ldw, mp, theta, k, seed, variant, ls, ls_iters, ls_iters_first, reorth, NULL, Q, ldq, R,
+                   ldr, S_out, P_out, stats);
+}
+
+/* Alg. 7 (RBGS-Arnoldi) for the stencil operator: Q = Q_(1:p) (n x p mp) and
+ * R = R_(1:p,1:p); the block Hessenberg matrix is H = R_(1:p,2:p), so that
+ * A Q_(1:p-1) = Q_(1:p) H.                                                  */
+int or_rbgs_arnoldi(int64_t nx, int64_t ny, double bx, double by, const double* B, int64_t ldb, int64_t mp,
+                    int64_t p, int theta, int64_t k, uint64_t seed, int variant, int ls, int ls_iters,
+                    int ls_iters_first, int reorth, double* Q, int64_t ldq, double* R, int64_t ldr, double* stats) {
+  or_stencil op = {nx, ny, bx, by};
+  return rbgs_core(B, nx * ny, p * mp, ldb, mp, theta, k, seed, variant, ls, ls_iters, ls_iters_first, reorth, &op, Q,
+                   ldq, R, ldr, NULL, NULL, stats);
+}
+
+/* Least squares min ||A z - b|| (A m x n, m >= n, full rank) for nrhs right
+ * sides by Householder QR; A and B are overwritten, Z (n x nrhs) receives z. */
+static int householder_ls(int64_t m, int64_t n, double* A, int64_t lda, double* B, int64_t ldb, int64_t nrhs,
+                          double* Z, int64_t ldz) {
+  double* tau = (double*)malloc(sizeof(double) * (size_t)n);
+  or_householder_qr(m, n, A, lda, tau);
+  householder_apply_qt(m, n, A, lda, tau, B, ldb, nrhs);
+  free(tau);
+  for (int64_t r = 0; r < nrhs; ++r)
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double s = B[i + r * ldb];
+      for (int64_t t = i + 1; t < n; ++t) s -= A[i + t * lda] * Z[t + r * ldz];
+      if (A[i + i * lda] == 0.0) return -2;
+      Z[i + r * ldz] = s / A[i + i * lda];
+    }
+  return 0;
+}
+
+/* Restarted randomized block GMRES (Sec. 5.2) or FOM (Sec. 5.3) for A X = B
+ * (n x mp, FP64).  Each cycle runs Alg. 7 on the residual block r = B - A X
+ * with p blocks and takes the coordinates z of the correction in Q_(1:p-1):
+ *   GMRES: z = argmin || H z - R_(1:p,1) ||   (H = R_(1:p,2:p), eq. GMRESsol)
+ *   FOM:   z = H_(1:p-1,1:p-1)^{-1} R_(1:p-1,1)                 (eq. RFOMsol)
+ * then X += Q_(1:p-1) z.  Stops when max_j ||r_j|| / ||b_j|| <= rtol or after
+ * max_cycles cycles; relres (mp) receives the final relative residuals.
+ * method: 0 = GMRES, 1 = FOM.  Returns the number of cycles run, or < 0.   */
+int or_block_krylov(int method, int64_t nx, int64_t ny, double bx, double by, const double* B, int64_t ldb,
+                    double* X, int64_t ldx, int64_t mp, int64_t p, int theta, int64_t k, uint64_t seed, int variant,
+                    int ls, int ls_iters, int ls_iters_first, int reorth, double rtol, int64_t max_cycles,
+                    double* relres) {
+  or_stencil op = {nx, ny, bx, by};
+  const int64_t n = nx * ny, m = p * mp, nk = m - mp;
+  if (p < 2 || mp < 1 || k < m) return -1;
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n * mp));
+  double* Q = (double*)malloc(sizeof(double) * (size_t)(n * m));
+  double* R = (double*)malloc(sizeof(double) * (size_t)(m * m));
+  double* H = (double*)malloc(sizeof(double) * (size_t)(m * nk));
+  double* rhs = (double*)malloc(sizeof(double) * (size_t)(m * mp));
+  double* Z = (double*)malloc(sizeof(double) * (size_t)(nk * mp));
+  double* bn = (double*)malloc(sizeof(double) * (size_t)mp);
+  int64_t cyc = 0;
+  int rc = 0;
+  for (int64_t j = 0; j < mp; ++j) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += B[i + j * ldb] * B[i + j * ldb];
+    bn[j] = sqrt(s) > 0.0 ? sqrt(s) : 1.0;
+  }
+  for (;;) {
+    or_stencil5_apply(&op, X, ldx, mp, r, n);
+    double worst = 0.0;
+    for (int64_t j = 0; j < mp; ++j) {
+      double s = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        r[i + j * n] = B[i + j * ldb] - r[i + j * n];
+        s += r[i + j * n] * r[i + j * n];
+      }
+      relres[j] = sqrt(s) / bn[j];
+      if (relres[j] > worst) worst = relres[j];
+    }
+    if (worst <= rtol || cyc >= max_cycles) break;
+    if (rbgs_core(r, n, m, n, mp, theta, k, seed, variant, ls, ls_iters, ls_iters_first, reorth, &op, Q, n, R, m, NULL,
+                  NULL, NULL)) {
+      rc = -2;
+      break;
+    }
+    if (method == 0) {
+      for (int64_t j = 0; j < nk; ++j)
+        for (int64_t i = 0; i < m; ++i) H[i + j * m] = R[i + (mp + j) * m];
+      for (int64_t j = 0; j < mp; ++j)
+        for (int64_t i = 0; i < m; ++i) rhs[i + j * m] = R[i + j * m];
+      if (householder_ls(m, nk, H, m, rhs, m, mp, Z, nk)) { rc = -2; break; }
+    } else {
+      for (int64_t j = 0; j < nk; ++j)
+        for (int64_t i = 0; i < nk; ++i) H[i + j * nk] = R[i + (mp + j) * m];
+      for (int64_t j = 0; j < mp; ++j)
+        for (int64_t i = 0; i < nk; ++i) rhs[i + j * nk] = R[i + j * m];
+      if (householder_ls(nk, nk, H, nk, rhs, nk, mp, Z, nk)) { rc = -2; break; }
+    }
+    /* X += Q_(1:p-1) z */
+    gemm(0, 0, n, mp, nk, 1.0, Q, n, Z, nk, 1.0, X, ldx);
+    ++cyc;
+  }
+  free(r); free(Q); free(R); free(H); free(rhs); free(Z); free(bn);
+  return rc ? rc : (int)cyc;
 }
 
 /* Closed form of RBGS in exact arithmetic: R = R factor (positive diagonal)

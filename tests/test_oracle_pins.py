@@ -344,3 +344,125 @@ def test_theta_golden(fname, kind, k, n, seed):
     T = oracle.theta_dense(kind, k, n, seed)
     tol = 0.0 if kind != "gauss" else 1e-15
     np.testing.assert_allclose(T, ref, rtol=tol, atol=tol)
+
+
+# ------------------------------------------- Sec. 5: Arnoldi, GMRES, FOM --
+
+def _kron_stencil(nx, ny, bx, by):
+    """The convection-diffusion matrix written as a Kronecker sum of the 1-D
+    central-difference operators (independent of the oracle's loop)."""
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+
+    def one_d(nn, h, b):
+        T = np.zeros((nn, nn))
+        for i in range(nn):
+            T[i, i] = 2.0 / h ** 2
+            if i > 0:
+                T[i, i - 1] = -1.0 / h ** 2 - b / (2 * h)
+            if i + 1 < nn:
+                T[i, i + 1] = -1.0 / h ** 2 + b / (2 * h)
+        return T
+
+    return np.kron(np.eye(ny), one_d(nx, hx, bx)) + np.kron(one_d(ny, hy, by), np.eye(nx))
+
+
+@pytest.mark.parametrize("nx,ny,bx,by", [(6, 5, 100.0, 50.0), (9, 9, 3.0, 1.5), (4, 7, 0.0, 0.0)])
+def test_stencil_matches_kronecker_form(nx, ny, bx, by):
+    A = oracle.stencil5_dense(nx, ny, bx, by)
+    np.testing.assert_allclose(A, _kron_stencil(nx, ny, bx, by), rtol=1e-14, atol=1e-10)
+
+
+def test_stencil_eigenvalues_closed_form():
+    """With cell Peclet numbers P = b h / 2 < 1 the spectrum is real:
+    lambda_jl = (2/h^2) [2 - sqrt(1 - Px^2) cos(j pi h) - sqrt(1 - Py^2) cos(l pi h)]."""
+    nx = ny = 12
+    bx, by = 10.0, 5.0
+    h = 1.0 / (nx + 1)
+    px, py = bx * h / 2, by * h / 2
+    ev = np.sort(np.linalg.eigvals(oracle.stencil5_dense(nx, ny, bx, by)).real)
+    j = np.arange(1, nx + 1)
+    lam = (2 / h ** 2) * (2 - np.sqrt(1 - px ** 2) * np.cos(j[:, None] * np.pi * h)
+                          - np.sqrt(1 - py ** 2) * np.cos(j[None, :] * np.pi * h))
+    np.testing.assert_allclose(ev, np.sort(lam.ravel()), rtol=1e-10)
+
+
+def test_arnoldi_identity_and_sketched_orthonormality():
+    """Alg. 7: A Q_(1:p-1) = Q H with H = R_(1:p,2:p), Theta Q orthonormal, B = Q_1 R_11."""
+    nx, ny, mp, p = 10, 8, 3, 6
+    B = synth.gaussian(nx * ny, mp, 4)
+    out = oracle.rbgs_arnoldi(nx, ny, 30.0, 10.0, B, p, "gauss", 60, 2)
+    Q, R = out["Q"], out["R"]
+    A = _kron_stencil(nx, ny, 30.0, 10.0)
+    AQ = A @ Q[:, : (p - 1) * mp]
+    assert np.abs(AQ - Q @ R[:, mp:]).max() <= 1e-13 * np.abs(AQ).max()
+    np.testing.assert_allclose(Q[:, :mp] @ R[:mp, :mp], B, atol=1e-13 * np.abs(B).max())
+    assert np.allclose(np.tril(R, -1), 0.0)
+    S = oracle.theta_apply("gauss", 60, 2, Q)
+    assert np.abs(S.T @ S - np.eye(p * mp)).max() < 1e-12
+
+
+def _krylov_basis(A, B, blocks):
+    K = [B]
+    for _ in range(blocks - 1):
+        K.append(A @ K[-1])
+    return np.hstack(K)
+
+
+def test_gmres_identity_sketch_is_textbook_minimal_residual():
+    """With Theta = I one cycle of randomized block GMRES is block GMRES: each
+    column minimizes ||b - A u|| over K_(p-1)(A, B) (brute force on an
+    explicit Krylov basis)."""
+    nx, ny, mp, p = 6, 6, 2, 5
+    n = nx * ny
+    B = synth.gaussian(n, mp, 9)
+    A = _kron_stencil(nx, ny, 20.0, 10.0)
+    X, cyc, _ = oracle.block_krylov("gmres", nx, ny, 20.0, 10.0, B, np.zeros((n, mp)), p, "identity", n, 0, 0.0, 1)
+    assert cyc == 1
+    K = _krylov_basis(A, B, p - 1)
+    for i in range(mp):
+        y, *_ = np.linalg.lstsq(A @ K, B[:, i], rcond=None)
+        u_star = K @ y
+        assert np.linalg.norm(B[:, i] - A @ X[:, i]) <= np.linalg.norm(B[:, i] - A @ u_star) * (1 + 1e-8) + 1e-12
+        np.testing.assert_allclose(X[:, i], u_star, rtol=1e-6, atol=1e-9 * np.abs(u_star).max())
+
+
+def test_gmres_minimizes_the_sketched_residual():
+    """Sec. 5.2: u_i = argmin over K_(p-1) of ||Theta (b_i - A u)||."""
+    nx, ny, mp, p, k = 7, 6, 2, 5, 30
+    n = nx * ny
+    B = synth.gaussian(n, mp, 12)
+    A = _kron_stencil(nx, ny, 15.0, 5.0)
+    X, _, _ = oracle.block_krylov("gmres", nx, ny, 15.0, 5.0, B, np.zeros((n, mp)), p, "gauss", k, 5, 0.0, 1)
+    T = oracle.theta_dense("gauss", k, n, 5)
+    K = _krylov_basis(A, B, p - 1)
+    for i in range(mp):
+        y, *_ = np.linalg.lstsq(T @ A @ K, T @ B[:, i], rcond=None)
+        r_star = np.linalg.norm(T @ (B[:, i] - A @ (K @ y)))
+        r_got = np.linalg.norm(T @ (B[:, i] - A @ X[:, i]))
+        assert r_got <= r_star * (1 + 1e-7)
+        assert abs(r_got - r_star) <= 1e-7 * r_star
+
+
+def test_fom_satisfies_sketched_galerkin():
+    """Sec. 5.3: <Theta v, Theta r(u_i)> = 0 for all v in K_(p-1)."""
+    nx, ny, mp, p, k = 7, 6, 2, 5, 30
+    n = nx * ny
+    B = synth.gaussian(n, mp, 13)
+    A = _kron_stencil(nx, ny, 15.0, 5.0)
+    X, _, _ = oracle.block_krylov("fom", nx, ny, 15.0, 5.0, B, np.zeros((n, mp)), p, "gauss", k, 6, 0.0, 1)
+    T = oracle.theta_dense("gauss", k, n, 6)
+    K = _krylov_basis(A, B, p - 1)
+    Kq, _ = np.linalg.qr(T @ K)
+    G = Kq.T @ (T @ (B - A @ X))
+    assert np.abs(G).max() <= 1e-9 * np.linalg.norm(T @ B)
+
+
+@pytest.mark.parametrize("method", ["gmres", "fom"])
+def test_restarted_solver_reaches_direct_solution(method):
+    nx, ny, mp = 10, 9, 2
+    n = nx * ny
+    B = synth.gaussian(n, mp, 21)
+    X, cyc, rel = oracle.block_krylov(method, nx, ny, 12.0, 6.0, B, np.zeros((n, mp)), 8, "gauss", 64, 8, 1e-11, 200)
+    assert rel.max() <= 1e-11 and cyc >= 1
+    Xd = np.linalg.solve(_kron_stencil(nx, ny, 12.0, 6.0), B)
+    assert np.abs(X - Xd).max() <= 1e-8 * np.abs(Xd).max()
