@@ -162,6 +162,57 @@ RBGS_API rbgs_status rbgs_tall_update_noalloc(int32_t prec, int64_t n, int64_t c
                                      int64_t ldq, const void* X, int64_t ldx, const double* G, int64_t ldg,
                                      void* Qout, int64_t ldo, void* stream, int32_t sync);
 
+/* ------------------------------------------------------------------------
+ * Randomized block Krylov methods (Sec. 5).
+ *
+ * Operator: the 5-point convection-diffusion operator
+ *   A u = -(u_xx + u_yy) + bx u_x + by u_y
+ * on nx x ny interior points of the unit square (spacing 1/(nx+1) and
+ * 1/(ny+1)), zero Dirichlet boundary, central differences.  Point (x, y) is
+ * row x + nx y, so n = nx ny.                                              */
+typedef enum { RBGS_OP_STENCIL5 = 0 } rbgs_op_kind;
+typedef struct {
+  int32_t kind;      /* rbgs_op_kind                                                   */
+  int32_t reserved;
+  int64_t nx, ny;    /* interior points                                                */
+  double bx, by;     /* convection velocity                                            */
+} rbgs_op;
+
+/* Y = A X for ncols columns (device, column-major).  X and Y are double if
+ * prec == RBGS_P_FP64, else float.  X and Y must not overlap.               */
+RBGS_API rbgs_status rbgs_op_apply(const rbgs_op* op, int32_t prec, const void* X, int64_t ldx, int64_t ncols, void* Y,
+                          int64_t ldy, void* stream, int32_t sync);
+
+/* RBGS-Arnoldi, Alg. 7: W_1 = B, then W_i = A Q_{i-1} for i = 2..p, each
+ * block orthogonalized by one step of RBGS (Alg. 2 with Alg. 5, options as in
+ * rbgs_qr).  B (n x mb, ldb) and Q (n x p mb, ldq) are device arrays of the
+ * prec type; R (p mb x p mb, ldr) is device double.  The block Hessenberg
+ * matrix is H = R(:, mb:), so that A Q(:, 0:(p-1) mb) = Q H.  Errors as rbgs_qr. */
+RBGS_API rbgs_status rbgs_block_arnoldi(const rbgs_op* op, const void* B, int64_t ldb, int64_t mb, int64_t p,
+                               rbgs_sketch sketch, int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R,
+                               int64_t ldr, const rbgs_opts* opts, rbgs_stats* stats);
+
+/* Restarted randomized block GMRES (Sec. 5.2) for A X = B, B and X n x mb
+ * device double (X holds the initial guess and receives the solution).  Each
+ * cycle runs Alg. 7 with p blocks on the residual block r = B - A X (basis
+ * in opts->prec; r, X and the projected problem in FP64) and sets
+ *   X += Q(:, 0:(p-1) mb) z,   z = argmin || H z - R(:, 0:mb) ||
+ * (eq. GMRESsol; H = R(:, mb:) block upper Hessenberg, solved by Householder
+ * reflectors in FP64).  Stops when max_j ||r_j|| / ||b_j|| <= rtol or after
+ * max_cycles cycles.  *cycles (host) receives the cycles run, relres (host,
+ * mb values) the final relative residuals.  Returns RBGS_ENOCONV if rtol
+ * was not reached; other errors as rbgs_qr.  Synchronous.                  */
+RBGS_API rbgs_status rbgs_block_gmres(const rbgs_op* op, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t mb,
+                             int64_t p, double rtol, int64_t max_cycles, rbgs_sketch sketch, int64_t k,
+                             uint64_t seed, const rbgs_opts* opts, int64_t* cycles, double* relres);
+
+/* Restarted randomized block FOM (Sec. 5.3): as rbgs_block_gmres with
+ *   z = H(0:(p-1) mb, :)^{-1} R(0:(p-1) mb, 0:mb)   (eq. RFOMsol),
+ * whose residual satisfies the sketched Galerkin condition.                  */
+RBGS_API rbgs_status rbgs_block_fom(const rbgs_op* op, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t mb,
+                           int64_t p, double rtol, int64_t max_cycles, rbgs_sketch sketch, int64_t k, uint64_t seed,
+                           const rbgs_opts* opts, int64_t* cycles, double* relres);
+
 /* Philox4x32-10 blocks on the device: out[4i..4i+3] = philox(ctr[4i..4i+3],
  * key = (seed_lo, seed_hi)) for i < count (device pointers).              */
 RBGS_API rbgs_status rbgs_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t count, void* stream, int32_t sync);

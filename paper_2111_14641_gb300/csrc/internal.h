@@ -95,6 +95,24 @@ rbgs_status h3_scales_from_max(int64_t cols, const unsigned int* mx, float* scal
 rbgs_status h3_split(int64_t n, int64_t cols, const float* A, int64_t lda, const float* scale, int64_t nch_row,
                      unsigned char* qs, cudaStream_t st);
 
+// --------------------------------------------------------- Krylov (Sec. 5) --
+template <class TI, class TO>
+rbgs_status stencil_apply_t(const rbgs_op& op, const TI* X, int64_t ldx, int64_t ncols, TO* Y, int64_t ldy,
+                            cudaStream_t st);
+size_t residual_part_elems(int64_t n, int64_t ncols);
+// r = B - A X (FP64) and norms[j] = ||r_j|| (part: residual_part_elems scratch)
+rbgs_status residual_t(const rbgs_op& op, const double* B, int64_t ldb, const double* X, int64_t ldx,
+                       int64_t ncols, double* r, int64_t ldr, double* part, double* norms, cudaStream_t st);
+rbgs_status colnorms_t(int64_t n, int64_t ncols, const double* A, int64_t lda, double* part, double* norms,
+                       cudaStream_t st);
+template <class TI, class TO>
+rbgs_status cast_cols_t(int64_t n, int64_t ncols, const TI* A, int64_t lda, TO* B, int64_t ldb, cudaStream_t st);
+template <class TD>
+rbgs_status add_cols_t(int64_t n, int64_t ncols, const TD* D, int64_t ldd, double* X, int64_t ldx, cudaStream_t st);
+// min ||H z - F|| with H (M x N) zero below its bw-th subdiagonal (overwrites H, F)
+rbgs_status banded_ls(int M, int N, int bw, double* H, int ldh, double* F, int ldf, int nrhs, double* Z, int ldz,
+                      int* flag, cudaStream_t st);
+
 // ------------------------------------------------------------ sketch space --
 // out (M x N, ldo) = alpha * op(A) * B + beta * out, op(A) = A (TRANS=0, A M x K)
 // or A^T (TRANS=1, A K x M); B K x N; N <= 64.  TA/TB input, TO output type,

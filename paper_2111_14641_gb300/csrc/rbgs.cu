@@ -9,6 +9,7 @@
 //   step 5/1 S_i = Theta Q_i and P_{i+1} = Theta W_{i+1}
 //   option   a second projection pass of Q_i against Q_{1:i-1} (reorth)
 //   step 6   Delta, Delta~ on request.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -190,7 +191,9 @@ rbgs_status side_stream(cudaStream_t* out) {
 template <class T, class TS>
 rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_sketch sketch, int64_t k,
                     uint64_t seed, T* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts& o, rbgs_stats* stats,
-                    int mode) {
+                    int mode, const rbgs_op* op = nullptr) {
+  // With op (Alg. 7, RBGS-Arnoldi): W holds only the first block B; every
+  // later block is W_i = A Q_{i-1}, formed in the columns of Q_i.
   // mode 0: SIMT tall product; 1: TF32X3 tensor cores; 2: F16X3 tensor cores with the pre-split basis
   const bool tensor = mode != 0;
   cudaStream_t st = (cudaStream_t)o.stream;
@@ -319,30 +322,38 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         for (auto e : *v) cudaEventDestroy(e);
       }
     } evguard{&evw};
-    if (p > 1) {
+    const bool ahead = p > 1 && op == nullptr;  // the next block of W is known in advance
+    if (ahead) {
       if ((s = side_stream(&st2))) return s;
       evw.resize((size_t)p + 1, nullptr);
       for (auto& e : evw) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     // step 1 of the first block
     if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, W, ldw, mb, P, k, skscr, sk_bytes, st))) return s;
-    if (p > 1) {  // the side stream starts after everything enqueued here so far
+    if (ahead) {  // the side stream starts after everything enqueued here so far
       RBGS_CUDA_TRY(cudaEventRecord(evw[p], st));
       RBGS_CUDA_TRY(cudaStreamWaitEvent(st2, evw[p], 0));
     }
     for (int64_t blk = 0; blk < p; ++blk) {
       const int64_t c = blk * mb;
       const T* Wi = W + c * ldw;
+      int64_t ldwi = ldw;
       T* Qi = Q + c * ldq;
       TS* Pi = P + c * k;
       TS* Si = S + c * k;
       double* Rcol = R + c * ldr;
-      if (blk + 1 < p) {
+      if (op && blk > 0) {  // Alg. 7, step 2: W_i = A Q_{i-1}, then its sketch (step 1 of the block)
+        if ((s = stencil_apply_t<T, T>(*op, Qi - mb * ldq, ldq, mb, Qi, ldq, st))) return s;
+        Wi = Qi;
+        ldwi = ldq;
+        if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi, ldwi, mb, Pi, k, skscr, sk_bytes, st))) return s;
+      }
+      if (ahead && blk + 1 < p) {
         s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi + mb * ldw, ldw, mb, Pi + mb * k, k, skscr2, sk_bytes, st2);
         if (s) return s;
         RBGS_CUDA_TRY(cudaEventRecord(evw[blk + 1], st2));
       }
-      if (blk > 0) RBGS_CUDA_TRY(cudaStreamWaitEvent(st, evw[blk], 0));
+      if (ahead && blk > 0) RBGS_CUDA_TRY(cudaStreamWaitEvent(st, evw[blk], 0));
       // step 2 and the implicit sketch of Alg. 5
       // With a second pass to follow, the first pass is provisional: one
       // Richardson step and one (shifted) Cholesky QR round; the second pass
@@ -362,7 +373,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       if ((s = make_g(c, X, Rii, Riinv, Rcol, nullptr))) return s;
       // step 3 fused with the triangular solve
       // (the split copy of a provisional result is not kept: the second pass rereads it as FP32)
-      if ((s = tall(c, Wi, ldw, Qi, nullptr, Pi, !(o.reorth == 1 && c > 0)))) return s;
+      if ((s = tall(c, Wi, ldwi, Qi, nullptr, Pi, !(o.reorth == 1 && c > 0)))) return s;
       // step 5 (the sketch of W_{i+1}, step 1 of the next block, runs on the side stream)
       if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st))) return s;
       // optional second projection pass
@@ -665,3 +676,207 @@ rbgs_status rbgs_release_workspace(void) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ Sec. 5 --
+
+namespace {
+
+rbgs_status check_op(const rbgs_op* op) {
+  if (!op || op->kind != RBGS_OP_STENCIL5 || op->nx < 1 || op->ny < 1) return RBGS_EINVAL;
+  if (op->nx * op->ny >= ((int64_t)1 << 31)) return RBGS_EINVAL;
+  if (!std::isfinite(op->bx) || !std::isfinite(op->by)) return RBGS_EINVAL;
+  return RBGS_OK;
+}
+
+rbgs_status check_sketch(rbgs_sketch sketch, int64_t n, int64_t k, int64_t m) {
+  if (k < m) return RBGS_EINVAL;
+  if (sketch == RBGS_SK_SRHT) {
+    int64_t np = 1;
+    while (np < n) np <<= 1;
+    return k > np ? RBGS_EINVAL : RBGS_OK;
+  }
+  if (sketch == RBGS_SK_GAUSS || sketch == RBGS_SK_RADEMACHER) return k > n ? RBGS_EINVAL : RBGS_OK;
+  return RBGS_EINVAL;
+}
+
+// Alg. 7 on (W = B, Q): dispatch by precision (the arguments are checked).
+rbgs_status arnoldi_run(const rbgs_op& op, const void* B, int64_t ldb, int64_t mb, int64_t p, rbgs_sketch sketch,
+                        int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts& o,
+                        rbgs_stats* stats) {
+  const int64_t n = op.nx * op.ny, m = p * mb;
+  if (o.prec == RBGS_P_FP64)
+    return qr_impl<double, double>((const double*)B, n, m, ldb, (int)mb, sketch, k, seed, (double*)Q, ldq, R, ldr, o,
+                                   stats, 0, &op);
+  const int mode = o.prec == RBGS_P_TF32X3 ? 1 : (o.prec == RBGS_P_F16X3 ? 2 : 0);
+  if (o.fine)
+    return qr_impl<float, double>((const float*)B, n, m, ldb, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o,
+                                  stats, mode, &op);
+  return qr_impl<float, float>((const float*)B, n, m, ldb, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o, stats,
+                               mode, &op);
+}
+
+// Device buffers owned by one solver call.
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+// Restarted randomized block GMRES (method 0) or FOM (method 1).
+rbgs_status krylov_solve(int method, const rbgs_op* op, const double* B, int64_t ldb, double* X, int64_t ldx,
+                         int64_t mb, int64_t p, double rtol, int64_t max_cycles, rbgs_sketch sketch, int64_t k,
+                         uint64_t seed, const rbgs_opts* opts, int64_t* cycles, double* relres) {
+  rbgs_status s;
+  if ((s = check_op(op))) return s;
+  const int64_t n = op->nx * op->ny, m = p * mb, nk = m - mb;
+  if (!B || !X || !relres || mb < 1 || mb > 64 || p < 2 || ldb < n || ldx < n || max_cycles < 0 || !(rtol >= 0.0))
+    return RBGS_EINVAL;
+  if ((s = check_sketch(sketch, n, k, m))) return s;
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1)
+    return RBGS_EINVAL;
+  o.sync = 1;  // one synchronisation per cycle (breakdown and convergence are read on the host)
+  o.timing = 0;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const bool f64 = o.prec == RBGS_P_FP64;
+  const size_t es = f64 ? 8 : 4;
+  // buffers: basis Q (n x m), residual r (n x mb), correction D (n x mb, basis type), the
+  // Arnoldi R (m x m), H and F copies, z, G in float, norms and partial sums, a flag
+  const size_t part_elems = residual_part_elems(n, mb);
+  const size_t bytes_q = es * (size_t)n * (size_t)m, bytes_r = 8 * (size_t)n * (size_t)mb,
+               bytes_d = es * (size_t)n * (size_t)mb;
+  const size_t small = 8 * ((size_t)m * m + (size_t)m * nk + (size_t)m * mb + (size_t)nk * mb + 2 * mb + part_elems) +
+                       4 * ((size_t)nk * mb) + 1024;
+  DevBuf buf;
+  if (cudaMalloc(&buf.p, bytes_q + bytes_r + bytes_d + small + 4096) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  char* w = (char*)buf.p;
+  auto take = [&](size_t b) {
+    char* r = w;
+    w += (b + 255) & ~(size_t)255;
+    return (void*)r;
+  };
+  void* Qb = take(bytes_q);
+  double* r = (double*)take(bytes_r);
+  void* D = take(bytes_d);
+  double* Rm = (double*)take(8 * (size_t)m * m);
+  double* Hb = (double*)take(8 * (size_t)m * nk);
+  double* Fb = (double*)take(8 * (size_t)m * mb);
+  double* Z = (double*)take(8 * (size_t)nk * mb);
+  float* Zf = (float*)take(4 * (size_t)nk * mb);
+  double* norms = (double*)take(8 * (size_t)mb);
+  double* bnorm = (double*)take(8 * (size_t)mb);
+  double* part = (double*)take(8 * part_elems);
+  int* flag = (int*)take(256);
+  RBGS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  std::vector<double> hb((size_t)mb), hn((size_t)mb);
+  if ((s = colnorms_t(n, mb, B, ldb, part, bnorm, st))) return s;
+  RBGS_CUDA_TRY(cudaMemcpyAsync(hb.data(), bnorm, 8 * mb, cudaMemcpyDeviceToHost, st));
+  RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  for (auto& v : hb)
+    if (!(v > 0.0)) v = 1.0;
+  int64_t cyc = 0;
+  for (;;) {
+    if ((s = residual_t(*op, B, ldb, X, ldx, mb, r, n, part, norms, st))) return s;
+    RBGS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, 8 * mb, cudaMemcpyDeviceToHost, st));
+    RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+    double worst = 0.0;
+    for (int64_t j = 0; j < mb; ++j) {
+      relres[j] = hn[(size_t)j] / hb[(size_t)j];
+      worst = std::max(worst, relres[j]);
+    }
+    if (!(worst > rtol) || cyc >= max_cycles) {
+      if (cycles) *cycles = cyc;
+      return worst <= rtol ? RBGS_OK : RBGS_ENOCONV;
+    }
+    // Alg. 7 on the residual block (W_1 = r in the basis precision)
+    if (f64) s = cast_cols_t<double, double>(n, mb, r, n, (double*)Qb, n, st);
+    else s = cast_cols_t<double, float>(n, mb, r, n, (float*)Qb, n, st);
+    if (s) return s;
+    if ((s = arnoldi_run(*op, Qb, n, mb, p, sketch, k, seed, Qb, n, Rm, m, o, nullptr))) return s;
+    // the projected problem in FP64: H = R(:, mb:), F = R(:, 0:mb) (GMRES) or their top nk rows (FOM)
+    const int64_t M = method == 0 ? m : nk;
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(Hb, 8 * M, Rm + mb * m, 8 * m, 8 * M, nk, cudaMemcpyDeviceToDevice, st));
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(Fb, 8 * M, Rm, 8 * m, 8 * M, mb, cudaMemcpyDeviceToDevice, st));
+    if ((s = banded_ls((int)M, (int)nk, (int)mb, Hb, (int)M, Fb, (int)M, (int)mb, Z, (int)nk, flag, st))) return s;
+    // X += Q(:, 0:nk) z, the product on the tall kernel of the basis type
+    const int64_t c = nk - mb;
+    if (f64) {
+      s = tall_update_simt<double>(n, c, mb, (const double*)Qb, n, (const double*)Qb + c * n, n, Z, nk,
+                                   (double*)D, n, nullptr, st);
+    } else {
+      if ((s = cast_cols_t<double, float>(nk, mb, Z, nk, Zf, nk, st))) return s;
+      s = tall_update_simt<float>(n, c, mb, (const float*)Qb, n, (const float*)Qb + c * n, n, Zf, nk, (float*)D, n,
+                                  nullptr, st);
+    }
+    if (s) return s;
+    if (f64) s = add_cols_t<double>(n, mb, (const double*)D, n, X, ldx, st);
+    else s = add_cols_t<float>(n, mb, (const float*)D, n, X, ldx, st);
+    if (s) return s;
+    int hflag = 0;
+    RBGS_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hflag) return RBGS_EBREAKDOWN;
+    ++cyc;
+  }
+}
+
+}  // namespace
+
+rbgs_status rbgs_op_apply(const rbgs_op* op, int32_t prec, const void* X, int64_t ldx, int64_t ncols, void* Y,
+                          int64_t ldy, void* stream, int32_t sync) {
+  rbgs_status s;
+  if ((s = check_op(op))) return s;
+  const int64_t n = op->nx * op->ny;
+  if (!X || !Y || ncols < 0 || ldx < n || ldy < n) return RBGS_EINVAL;
+  if (prec < RBGS_P_FP64 || prec > RBGS_P_F16X3) return RBGS_EINVAL;
+  const size_t es = prec == RBGS_P_FP64 ? 8 : 4;
+  if (ncols > 0 && ranges_overlap(X, es * (size_t)(ldx * (ncols - 1) + n), Y, es * (size_t)(ldy * (ncols - 1) + n)))
+    return RBGS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == RBGS_P_FP64) s = stencil_apply_t<double, double>(*op, (const double*)X, ldx, ncols, (double*)Y, ldy, st);
+  else s = stencil_apply_t<float, float>(*op, (const float*)X, ldx, ncols, (float*)Y, ldy, st);
+  if (s) return s;
+  if (sync) RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  return RBGS_OK;
+}
+
+rbgs_status rbgs_block_arnoldi(const rbgs_op* op, const void* B, int64_t ldb, int64_t mb, int64_t p,
+                               rbgs_sketch sketch, int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R,
+                               int64_t ldr, const rbgs_opts* opts, rbgs_stats* stats) {
+  rbgs_status s;
+  if ((s = check_op(op))) return s;
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  const int64_t n = op->nx * op->ny, m = p * mb;
+  if (!B || !Q || !R || mb < 1 || mb > 64 || p < 1 || ldb < n || ldq < n || ldr < m) return RBGS_EINVAL;
+  if ((s = check_sketch(sketch, n, k, m))) return s;
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1)
+    return RBGS_EINVAL;
+  const size_t es = o.prec == RBGS_P_FP64 ? 8 : 4;
+  if (o.prec >= RBGS_P_TF32X3 && (((uintptr_t)B & 15) || ((uintptr_t)Q & 15) || (ldb % 4) || (ldq % 4)))
+    return RBGS_EINVAL;
+  if (ranges_overlap(R, 8 * (size_t)(ldr * (m - 1) + m), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
+  // B may be the first block of Q itself (it is read before Q_1 is written)
+  if (B != Q && ranges_overlap(B, es * (size_t)(ldb * (mb - 1) + n), Q, es * (size_t)(ldq * (m - 1) + n)))
+    return RBGS_EINVAL;
+  return arnoldi_run(*op, B, ldb, mb, p, sketch, k, seed, Q, ldq, R, ldr, o, stats);
+}
+
+rbgs_status rbgs_block_gmres(const rbgs_op* op, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t mb,
+                             int64_t p, double rtol, int64_t max_cycles, rbgs_sketch sketch, int64_t k,
+                             uint64_t seed, const rbgs_opts* opts, int64_t* cycles, double* relres) {
+  return krylov_solve(0, op, B, ldb, X, ldx, mb, p, rtol, max_cycles, sketch, k, seed, opts, cycles, relres);
+}
+
+rbgs_status rbgs_block_fom(const rbgs_op* op, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t mb,
+                           int64_t p, double rtol, int64_t max_cycles, rbgs_sketch sketch, int64_t k, uint64_t seed,
+                           const rbgs_opts* opts, int64_t* cycles, double* relres) {
+  return krylov_solve(1, op, B, ldb, X, ldx, mb, p, rtol, max_cycles, sketch, k, seed, opts, cycles, relres);
+}

@@ -40,6 +40,16 @@ class Opts(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class Op(ctypes.Structure):
+    """rbgs_op: the 5-point convection-diffusion operator on nx x ny interior points."""
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nx", ctypes.c_int64),
+                ("ny", ctypes.c_int64), ("bx", ctypes.c_double), ("by", ctypes.c_double)]
+
+
+def stencil_op(nx: int, ny: int, bx: float, by: float) -> Op:
+    return Op(0, 0, nx, ny, bx, by)
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("delta_tilde", ctypes.c_double), ("passes2", ctypes.c_int32),
                 ("certified", ctypes.c_int32), ("tall_ms", ctypes.c_double), ("tall_bytes", ctypes.c_double),
@@ -84,11 +94,19 @@ def load(build_if_missing: bool = False):
     lib.rbgs_tall_update.argtypes = [i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i32]
     lib.rbgs_tall_update_noalloc.argtypes = [i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i32]
     lib.rbgs_philox.argtypes = [u64, vp, vp, i64, vp, i32]
+    opp = ctypes.POINTER(Op)
+    lib.rbgs_op_apply.argtypes = [opp, i32, vp, i64, i64, vp, i64, vp, i32]
+    lib.rbgs_block_arnoldi.argtypes = [opp, vp, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
+                                       ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
+    for fn in ("rbgs_block_gmres", "rbgs_block_fom"):
+        getattr(lib, fn).argtypes = [opp, vp, i64, vp, i64, i64, i64, ctypes.c_double, i64, ctypes.c_int, i64, u64,
+                                     ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_int64), vp]
     lib.rbgs_release_workspace.argtypes = []
     lib.rbgs_version.restype = ctypes.c_char_p
     lib.rbgs_launch_count.restype = ctypes.c_int64
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
-                 "rbgs_release_workspace"):
+                 "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
+                 "rbgs_block_fom"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -214,6 +232,86 @@ def tall_update_noalloc(Qprev: torch.Tensor | None, X: torch.Tensor, G: torch.Te
                                         _stream_ptr(stream), int(sync))
     _check(code, "rbgs_tall_update_noalloc")
     return out
+
+
+def op_apply(op: Op, X: torch.Tensor, prec: str | None = None, stream=None) -> torch.Tensor:
+    """Y = A X (column-major CUDA tensors; float64 for fp64, else float32)."""
+    lib = load()
+    prec = _prec_of(X, prec)
+    n, c = X.shape
+    Y = torch.empty((c, n), dtype=X.dtype, device=X.device).t()
+    _check(lib.rbgs_op_apply(ctypes.byref(op), PREC[prec], X.data_ptr(), _ld(X, "X"), c, Y.data_ptr(), n,
+                             _stream_ptr(stream), 1), "rbgs_op_apply")
+    return Y
+
+
+def _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream):
+    o = Opts()
+    load().rbgs_opts_default(ctypes.byref(o))
+    o.prec, o.ls_iters, o.reorth, o.reorth_tol = PREC[prec], ls_iters, reorth, reorth_tol
+    o.stream, o.fine = _stream_ptr(stream), int(fine)
+    return o
+
+
+def block_arnoldi(op: Op, B: torch.Tensor, p: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
+                  prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
+                  fine: bool = False, Q: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None):
+    """Alg. 7: returns (Q, R) with A Q[:, :(p-1) mb] = Q R[:, mb:]."""
+    lib = load()
+    prec = _prec_of(B, prec)
+    n, mb = B.shape
+    m = p * mb
+    k = 2 * m if k is None else k
+    if Q is None:
+        Q = torch.empty((m, n), dtype=B.dtype, device=B.device).t()
+    if R is None:
+        R = torch.empty((m, m), dtype=torch.float64, device=B.device).t()
+    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream)
+    st = Stats()
+    _check(lib.rbgs_block_arnoldi(ctypes.byref(op), B.data_ptr(), _ld(B, "B"), mb, p, SKETCH[sketch], k, seed,
+                                  Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(), _ld(R, "R"), ctypes.byref(o),
+                                  ctypes.byref(st)), "rbgs_block_arnoldi")
+    return Q, R
+
+
+def _block_solve(fn: str, op: Op, B: torch.Tensor, X: torch.Tensor | None, p: int, rtol: float, max_cycles: int,
+                 sketch: str, k: int | None, seed: int, prec: str, ls_iters: int, reorth: int, reorth_tol: float,
+                 fine: bool, stream, raise_on_noconv: bool):
+    lib = load()
+    n, mb = B.shape
+    if B.dtype != torch.float64:
+        raise ValueError("B must be float64")
+    if X is None:
+        X = torch.zeros((mb, n), dtype=torch.float64, device=B.device).t()
+    k = 2 * p * mb if k is None else k
+    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream)
+    cyc = ctypes.c_int64(0)
+    rel = (ctypes.c_double * mb)()
+    code = getattr(lib, fn)(ctypes.byref(op), B.data_ptr(), _ld(B, "B"), X.data_ptr(), _ld(X, "X"), mb, p,
+                            float(rtol), int(max_cycles), SKETCH[sketch], k, seed, ctypes.byref(o),
+                            ctypes.byref(cyc), ctypes.cast(rel, ctypes.c_void_p))
+    if code == 7 and not raise_on_noconv:
+        code = 0
+    _check(code, fn)
+    return X, int(cyc.value), [float(v) for v in rel]
+
+
+def block_gmres(op: Op, B: torch.Tensor, X: torch.Tensor | None = None, p: int = 10, rtol: float = 1e-8,
+                max_cycles: int = 100, sketch: str = "srht", k: int | None = None, seed: int = 0,
+                prec: str = "fp64", ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
+                fine: bool = False, stream=None, raise_on_noconv: bool = False):
+    """Restarted randomized block GMRES (Sec. 5.2): returns (X, cycles, relres)."""
+    return _block_solve("rbgs_block_gmres", op, B, X, p, rtol, max_cycles, sketch, k, seed, prec, ls_iters, reorth,
+                        reorth_tol, fine, stream, raise_on_noconv)
+
+
+def block_fom(op: Op, B: torch.Tensor, X: torch.Tensor | None = None, p: int = 10, rtol: float = 1e-8,
+              max_cycles: int = 100, sketch: str = "srht", k: int | None = None, seed: int = 0,
+              prec: str = "fp64", ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
+              fine: bool = False, stream=None, raise_on_noconv: bool = False):
+    """Restarted randomized block FOM (Sec. 5.3): returns (X, cycles, relres)."""
+    return _block_solve("rbgs_block_fom", op, B, X, p, rtol, max_cycles, sketch, k, seed, prec, ls_iters, reorth,
+                        reorth_tol, fine, stream, raise_on_noconv)
 
 
 def philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:

@@ -73,3 +73,26 @@ def test_argument_checks_need_no_device(lib):
     assert lib.rbgs_qr(fake, 1000, 128, 1000, 128, 0, 256, 0, other, 1000, rr, 128, None, None) == 1
     # W and Q overlap
     assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 16, 0, fake, 100, rr, 8, None, None) == 1
+
+
+def test_krylov_argument_checks_need_no_device(lib):
+    """The Sec. 5 entry points refuse bad descriptors before any CUDA call."""
+    import ctypes
+
+    from paper_2111_14641_gb300 import rbgs as rbmod
+
+    rbmod.load()
+    bad = rbmod.Op(5, 0, 8, 8, 1.0, 1.0)          # unknown operator kind
+    empty = rbmod.Op(0, 0, 0, 8, 1.0, 1.0)        # empty grid
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.rbgs_op_apply(ctypes.byref(bad), 0, fake, 64, 1, fake, 64, None, 1) == 1
+    assert lib.rbgs_op_apply(None, 0, fake, 64, 1, fake, 64, None, 1) == 1
+    assert lib.rbgs_block_arnoldi(ctypes.byref(empty), fake, 64, 2, 4, 0, 16, 0, fake, 64, fake, 8, None, None) == 1
+    cyc = ctypes.c_int64(0)
+    rel = (ctypes.c_double * 2)()
+    good = rbmod.Op(0, 0, 8, 8, 1.0, 1.0)
+    # p < 2, then k < m
+    assert lib.rbgs_block_gmres(ctypes.byref(good), fake, 64, fake, 64, 2, 1, 1e-8, 10, 0, 16, 0, None,
+                                ctypes.byref(cyc), ctypes.cast(rel, ctypes.c_void_p)) == 1
+    assert lib.rbgs_block_fom(ctypes.byref(good), fake, 64, fake, 64, 2, 8, 1e-8, 10, 0, 8, 0, None,
+                              ctypes.byref(cyc), ctypes.cast(rel, ctypes.c_void_p)) == 1
