@@ -81,7 +81,7 @@ def test_krylov_argument_checks_need_no_device(lib):
 
     from paper_2111_14641_gb300 import rbgs as rbmod
 
-    rbmod.load()
+    lib = rbmod.load()  # the binding's handle: argument types declared
     bad = rbmod.Op(5, 0, 8, 8, 1.0, 1.0)          # unknown operator kind
     empty = rbmod.Op(0, 0, 0, 8, 1.0, 1.0)        # empty grid
     fake = ctypes.c_void_p(1 << 20)
