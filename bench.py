@@ -389,6 +389,9 @@ def run_ours(args, cfg):
     if rank == 0 and world == 1 and not args.no_fp64_compare and prec != "fp64":
         line["fp64_path"] = fp64_compare(rb, cfg, args, dev)
 
+    if rank == 0 and world == 1 and not args.no_krylov:
+        line["krylov_c4"] = krylov_c4(rb, dev, prec if prec != "fp64" else "f16x3")
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(cfg, args.ls_iters, args.reorth)
         line["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
@@ -425,6 +428,40 @@ def sketch_space_variant(rb, W, Q, R, cfg, args, prec, fine, flops_ref):
                                       st.passes2) / (ms * 1e-3) / 1e9, "unit": "GFLOP/s"}
     if not args.no_quality:
         out["quality"] = quality(rb, W, Q, R, cfg)
+    return out
+
+
+def krylov_c4(rb, dev, prec):
+    """Restarted randomized block GMRES (Sec. 5.2) on the 2-D convection-
+    diffusion operator: 1024 x 1024 interior points, b = (100, 50), 8 right
+    sides N(0,1), 40 blocks per cycle, SRHT with k = 4 x 320.  Unpreconditioned
+    restarted GMRES converges slowly on this operator, so the line reports the
+    time per cycle and the residuals after a fixed number of cycles, for the
+    mixed basis and for the FP64 path (same cycles, same residual history)."""
+    import torch
+
+    nx = ny = 1024
+    n, mb, restart = nx * ny, 8, 40
+    p, k = restart + 1, 4 * restart * mb
+    op = rb.stencil_op(nx, ny, 100.0, 50.0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(3)
+    B = torch.randn((mb, n), generator=g, device=dev, dtype=torch.float64).t()
+    out = {"workload": "block GMRES(40 blocks), 5-point convection-diffusion 1024^2, b=(100,50), 8 RHS, SRHT k=1280",
+           "n": n, "rhs": mb, "blocks_per_cycle": restart}
+    for label, pr, fine, cycles in (("mixed", prec, True, 5), ("fp64", "fp64", False, 1)):
+        rb.block_gmres(op, B, None, p=p, rtol=0.0, max_cycles=1, sketch="srht", k=k, seed=1, prec=pr, ls_iters=1,
+                       reorth=1, fine=fine)  # warm-up cycle
+        X = torch.zeros((mb, n), device=dev, dtype=torch.float64).t()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, cyc, rel = rb.block_gmres(op, B, X, p=p, rtol=0.0, max_cycles=cycles, sketch="srht", k=k, seed=1,
+                                     prec=pr, ls_iters=1, reorth=1, fine=fine)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[label] = {"prec": pr, "sketch_space": "fp64", "cycles": cyc, "s_per_cycle": dt / max(cyc, 1),
+                      "relres_max": max(rel)}
+    out["fp64_over_mixed_time_per_cycle"] = out["fp64"]["s_per_cycle"] / out["mixed"]["s_per_cycle"]
     return out
 
 
@@ -481,6 +518,7 @@ def main(argv=None):
                     help="skip the measurement with the other sketch-space precision")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-krylov", action="store_true", help="skip the block GMRES measurement on the stencil")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (smaller cases for profiler captures; recorded in config.workload)")
     args = ap.parse_args(argv)
