@@ -97,7 +97,9 @@ typedef struct {
   double tall_ms;      /* with opts->timing: summed duration of the tall-update launches */
   double tall_bytes;   /* algorithmic bytes those launches move (A read + Q_i written)  */
   int32_t tall_launches; /* tall-update launches that did work                          */
-  int32_t reserved;
+  int32_t chol_rounds2;  /* block Cholesky QR factorizations that took a second round
+                            (always, in the FP32 sketch space; in FP64 only where
+                            ||R1||_F ||R1^{-1}||_F > 4 m_p after the first round)       */
 } rbgs_stats;
 
 /* Fill *opts with the defaults: FP64, 2 Richardson iterations, reorth 0,

@@ -159,6 +159,14 @@ template <class TS>
 rbgs_status reorth_decide(int64_t c, int mb, const TS* X, int64_t ldx, double tol, int mode, int* active,
                           int* count, int* blk_flag, cudaStream_t st);
 
+// Whether a Cholesky QR round may be the last one: with R1 and R1^{-1} from
+// one round, need2 = (active) and ||R1||_F ||R1^{-1}||_F > thr.  When the round
+// is the last one, R1 and R1inv are copied into R and Rinv (mb x mb, ld mb);
+// count is incremented for every second round that will run.
+template <class T>
+rbgs_status round2_decide(int mb, const T* R1, const T* R1inv, T* R, T* Rinv, double thr, const int* active,
+                          int* need2, int* count, cudaStream_t st);
+
 // Elementwise C = A - B (k x mb) in TS.
 template <class TS>
 rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,

@@ -124,21 +124,29 @@ bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) 
 // the sketch-space arithmetic TS.  The first round of the FP32 path factors the
 // Gram matrix with a small diagonal shift so that it cannot break down on a
 // nearly rank-deficient block; the second round removes the shift's effect.
+// In FP64 the first round is unshifted and leaves an orthogonality defect of
+// order eps64 kappa(Sp)^2, so the second round runs only where
+// kappa_F(R1) = ||R1||_F ||R1^{-1}||_F exceeds 4 mb (decided on the device,
+// flag need2; n2count counts the second rounds).
 // Sp2 is a k x mb scratch for Sp R1^{-1}.
 template <class TS>
 rbgs_status cholqr2(int64_t k, int mb, const TS* Sp, TS* Sp2, TS** sm, TS* part, int* flag, const int* active,
-                    cudaStream_t st, TS* R, TS* Rinv) {
+                    cudaStream_t st, TS* R, TS* Rinv, int* need2, int* n2count) {
   TS *gram = sm[0], *R1 = sm[1], *R1inv = sm[2];
-  const double shift = sizeof(TS) == 4 ? 1e-6 : 0.0;
+  const bool fp64 = sizeof(TS) == 8;
+  const double shift = fp64 ? 0.0 : 1e-6;
   rbgs_status s;
   s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
   if (s) return s;
   if ((s = chol_inv<TS>(mb, gram, R1, R1inv, shift, flag, nullptr, nullptr, active, st))) return s;
-  if ((s = trmm_right_upper<TS>(k, mb, Sp, k, R1inv, Sp2, k, active, st))) return s;
-  s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp2, k, Sp2, k, 0.0, gram, mb, part, kPartElems, active, st);
+  // (the FP32 round is shifted and always followed by a second one: thr < 0)
+  if ((s = round2_decide<TS>(mb, R1, R1inv, R, Rinv, fp64 ? 4.0 * mb : -1.0, active, need2, n2count, st))) return s;
+  const int* act2 = need2;
+  if ((s = trmm_right_upper<TS>(k, mb, Sp, k, R1inv, Sp2, k, act2, st))) return s;
+  s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp2, k, Sp2, k, 0.0, gram, mb, part, kPartElems, act2, st);
   if (s) return s;
   // second round; the kernel also forms R = R2 R1 and R^{-1} = R1^{-1} R2^{-1}
-  if ((s = chol_inv<TS>(mb, gram, R, Rinv, 0.0, flag, R1, R1inv, active, st))) return s;
+  if ((s = chol_inv<TS>(mb, gram, R, Rinv, 0.0, flag, R1, R1inv, act2, st))) return s;
   return RBGS_OK;
 }
 
@@ -229,6 +237,12 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     float* hsc = mode == 2 ? cv.take<float>(320) : nullptr;
     double* part = cv.take<double>(kPartElems);
     TS* partf = cv.take<TS>(kPartElems);
+    // look-ahead of step 2 on the side stream (second X buffer, the partial
+    // residuals of the next block, the side stream's partial-sum scratch)
+    const bool look = p > 1 && op == nullptr && (o.reorth != 0 || l == 1);
+    TS* Xalt = look ? cv.take<TS>((size_t)m * mb) : nullptr;
+    TS* Spo[2] = {look ? cv.take<TS>((size_t)k * mb) : nullptr, look ? cv.take<TS>((size_t)k * mb) : nullptr};
+    TS* partf2 = look ? cv.take<TS>(kPartElems) : nullptr;
     void* skscr = cv.take<char>(sk_bytes);
     void* skscr2 = cv.take<char>(sk_bytes);  // the side stream's sketches of the next blocks of W
     int* flags = cv.take<int>(64);
@@ -243,6 +257,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     int* active = flags + 1;   // second pass on/off for this block
     int* npass2 = flags + 2;   // number of second passes
     int* tmo = flags + 3;      // bounded device wait expired
+    int* need2 = flags + 4;    // second Cholesky QR round on/off (FP64 sketch space)
+    int* n2count = flags + 5;  // second Cholesky QR rounds taken
     struct TallEv {
       cudaEvent_t a, b;
       double bytes;
@@ -325,7 +341,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     const bool ahead = p > 1 && op == nullptr;  // the next block of W is known in advance
     if (ahead) {
       if ((s = side_stream(&st2))) return s;
-      evw.resize((size_t)p + 1, nullptr);
+      evw.resize((size_t)p + 2, nullptr);  // [p]: start, [p + 1]: end of the previous block
       for (auto& e : evw) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     // step 1 of the first block
@@ -351,6 +367,26 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       if (ahead && blk + 1 < p) {
         s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi + mb * ldw, ldw, mb, Pi + mb * k, k, skscr2, sk_bytes, st2);
         if (s) return s;
+        if (look) {
+          // Step 2 of block i + 1 (one Richardson step, X = S^T P_{i+1}) over
+          // the columns of S that are final once block i - 1 is done:
+          // X_old = S_{1:i-1}^T P_{i+1} and Sp_old = P_{i+1} - S_{1:i-1} X_old.
+          // Block i + 1 adds the block row of S_i itself.
+          const TS* Pn = Pi + mb * k;
+          TS* Xn = ((blk + 1) & 1) ? Xalt : X;
+          TS* So = Spo[(blk + 1) & 1];
+          if (c > 0) {  // everything enqueued here so far is block i - 1 and before
+            RBGS_CUDA_TRY(cudaEventRecord(evw[p + 1], st));
+            RBGS_CUDA_TRY(cudaStreamWaitEvent(st2, evw[p + 1], 0));
+            s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Pn, k, 0.0, Xn, m, partf2, kPartElems, nullptr, st2);
+            if (s) return s;
+          }
+          RBGS_CUDA_TRY(cudaMemcpyAsync(So, Pn, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st2));
+          if (c > 0) {
+            s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, Xn, m, 1.0, So, k, partf2, kPartElems, nullptr, st2);
+            if (s) return s;
+          }
+        }
         RBGS_CUDA_TRY(cudaEventRecord(evw[blk + 1], st2));
       }
       if (ahead && blk > 0) RBGS_CUDA_TRY(cudaStreamWaitEvent(st, evw[blk], 0));
@@ -359,7 +395,19 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       // Richardson step and one (shifted) Cholesky QR round; the second pass
       // (l steps, two rounds) settles the block.
       const bool provisional = o.reorth != 0 && c > 0;
-      if (c > 0) {
+      TS* Xc = X;   // R_{1:i-1,i}
+      TS* Spc = Sp; // S'_i = P_i - S_{1:i-1} R_{1:i-1,i}
+      if (c > 0 && look) {  // finish the look-ahead with the block row of S_{i-1}
+        const int64_t c0 = c - mb;
+        Xc = (blk & 1) ? Xalt : X;
+        Spc = Spo[blk & 1];
+        s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, S + c0 * k, k, Pi, k, 0.0, Xc + c0, m, partf, kPartElems,
+                                   nullptr, st);
+        if (s) return s;
+        s = small_gemm<TS, TS, TS>(0, k, mb, mb, -1.0, S + c0 * k, k, Xc + c0, m, 1.0, Spc, k, partf, kPartElems,
+                                   nullptr, st);
+        if (s) return s;
+      } else if (c > 0) {
         if ((s = richardson<TS>(k, c, mb, S, Pi, X, m, Res, provisional ? 1 : l, partf, nullptr, st))) return s;
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
         s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X, m, 1.0, Sp, k, partf, kPartElems, nullptr, st);
@@ -367,10 +415,10 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       } else {
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
       }
-      if (provisional) s = cholqr1<TS>(k, mb, Sp, sm, partf, brk, nullptr, st, Rii, Riinv);
-      else s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, nullptr, st, Rii, Riinv);
+      if (provisional) s = cholqr1<TS>(k, mb, Spc, sm, partf, brk, nullptr, st, Rii, Riinv);
+      else s = cholqr2<TS>(k, mb, Spc, Res, sm, partf, brk, nullptr, st, Rii, Riinv, need2, n2count);
       if (s) return s;
-      if ((s = make_g(c, X, Rii, Riinv, Rcol, nullptr))) return s;
+      if ((s = make_g(c, Xc, Rii, Riinv, Rcol, nullptr))) return s;
       // step 3 fused with the triangular solve
       // (the split copy of a provisional result is not kept: the second pass rereads it as FP32)
       if ((s = tall(c, Wi, ldwi, Qi, nullptr, Pi, !(o.reorth == 1 && c > 0)))) return s;
@@ -391,7 +439,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
         s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Sp, k, partf, kPartElems, active, st);
         if (s) return s;
-        if ((s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, active, st, R2ii, R2iinv))) return s;
+        if ((s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, active, st, R2ii, R2iinv, need2, n2count))) return s;
         if ((s = make_g(c, X2, R2ii, R2iinv, nullptr, active))) return s;
         if ((s = tall(c, Qi, ldq, Qi, active, Si, true))) return s;
         if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st, active))) return s;
@@ -443,11 +491,12 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       stats->certified = (stats->delta <= 0.1 && stats->delta_tilde <= 0.1) ? 1 : 0;
     }
     if (o.sync || stats) {
-      int hf[4] = {0, 0, 0, 0};
+      int hf[6] = {0, 0, 0, 0, 0, 0};
       RBGS_CUDA_TRY(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
       RBGS_CUDA_TRY(cudaStreamSynchronize(st));
       if (stats) {
         stats->passes2 = hf[2];
+        stats->chol_rounds2 = hf[5];
         stats->tall_ms = 0.0;
         stats->tall_bytes = 0.0;
         stats->tall_launches = 0;

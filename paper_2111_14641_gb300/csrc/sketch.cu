@@ -13,6 +13,7 @@
 // accumulates Theta_tile * X_tile; slice partials are summed in fixed order.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <unordered_set>
 #include <vector>
@@ -318,14 +319,18 @@ __device__ __forceinline__ bool sk_mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
-template <int E>
-__global__ void __launch_bounds__(kSrhtThreads, 1)
+// NB = 2: one CTA per SM prefetches the next tile into its second buffer
+// while transforming the current one.  NB = 1: two CTAs per SM with one
+// buffer each; the co-resident CTA computes while the other one loads.
+template <int E, int NB>
+__global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
     srht_stage1_persist(SrhtSrc src, int64_t n, int B, int logB, int T, uint2 key, const int* __restrict__ lvals,
                         int L, float* __restrict__ z, int64_t ncols, const int* active, int* err) {
+  static_assert(NB == 1 || NB == 2, "buffers");
   if (active && *active == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* bufs = reinterpret_cast<float*>(smem_raw);            // 2 x B
-  uint32_t* sgn = reinterpret_cast<uint32_t*>(bufs + 2 * B);   // B / 32
+  float* bufs = reinterpret_cast<float*>(smem_raw);            // NB x B
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(bufs + NB * B);  // B / 32
   __shared__ __align__(8) uint64_t full[2];
   __shared__ int bad;
   const int tid = threadIdx.x;
@@ -372,9 +377,9 @@ __global__ void __launch_bounds__(kSrhtThreads, 1)
     issued[0] = 1;
   }
   for (int idx = 0; w < nitems; w += gridDim.x, ++idx) {
-    const int b = idx & 1;
+    const int b = NB == 2 ? (idx & 1) : 0;
     const int64_t wn = w + gridDim.x;
-    if (wn < nitems) {  // buffer b^1 was released at the end of the previous item
+    if (NB == 2 && wn < nitems) {  // buffer b^1 was released at the end of the previous item
       if (tid == 0) issue(wn, b ^ 1);
       issued[b ^ 1] += 1;
     }
@@ -442,6 +447,10 @@ __global__ void __launch_bounds__(kSrhtThreads, 1)
     float* zo = z + w * L;  // (col * T + t) * L
     for (int l = tid; l < L; l += blockDim.x) zo[l] = buf[swz(lvals[l])];
     __syncthreads();  // buffer b may be refilled from the next iteration on
+    if (NB == 1 && wn < nitems) {
+      if (tid == 0) issue(wn, 0);
+      issued[0] += 1;
+    }
   }
   // leave no copy in flight into shared memory
   if (tid == 0) {
@@ -450,6 +459,226 @@ __global__ void __launch_bounds__(kSrhtThreads, 1)
     if (bad && err) atomicExch(err, 1);
   }
   __syncthreads();
+}
+
+// Stage 1 for tiles of B = 16384 entries (every n' >= 2^14), with all indices
+// known at compile time.  Entry j of a tile has 14 bits; thread t holds 32
+// entries as 8 float4 and the transform runs in four register passes:
+//   A: bits 0, 1 (inside a float4) and 11..13, read from the raw tile
+//      (j = 4 t + 2048 q + c), with the signs of D applied on the way;
+//   B: bits 2..4;  C: bits 5..7;  D: bits 8..10.
+// Between the passes the tile sits in shared memory with float4 slot bits
+// 0..2 xor-ed by bits 3..5 (entry bits 2..4 by 5..7), which keeps every pass's
+// 16-byte accesses free of bank conflicts.  Butterflies over float4 halves use
+// the packed FP32 add.
+constexpr int kB16 = 16384;
+
+__device__ __forceinline__ int b16_phys(int j) { return j ^ (((j >> 5) & 7) << 2); }
+
+__device__ __forceinline__ void b16_bfly(float& a0, float& a1, float& b0, float& b1) {
+  const float2 a = make_float2(a0, a1), b = make_float2(b0, b1);
+  const float2 s = __fadd2_rn(a, b);
+  const float2 d = __fadd2_rn(a, make_float2(-b0, -b1));
+  a0 = s.x;
+  a1 = s.y;
+  b0 = d.x;
+  b1 = d.y;
+}
+
+// the three levels over the index q of v[q]
+__device__ __forceinline__ void b16_levels_q(float4 (&v)[8]) {
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if ((q & h) == 0) {
+        b16_bfly(v[q].x, v[q].y, v[q + h].x, v[q + h].y);
+        b16_bfly(v[q].z, v[q].w, v[q + h].z, v[q + h].w);
+      }
+    }
+  }
+}
+
+// the two levels inside each float4 (entry bits 0 and 1)
+__device__ __forceinline__ void b16_levels_in(float4 (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    b16_bfly(v[q].x, v[q].y, v[q].z, v[q].w);  // bit 1
+    const float x = v[q].x, y = v[q].y, z = v[q].z, w = v[q].w;
+    v[q] = make_float4(x + y, x - y, z + w, z - w);  // bit 0
+  }
+}
+
+__device__ __forceinline__ float b16_sign(float x, uint32_t bit_at_31) {
+  return __int_as_float(__float_as_int(x) ^ (int)(bit_at_31 & 0x80000000u));
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
+    srht_stage1_b16k(SrhtSrc src, int64_t n, int T, uint2 key, const int* __restrict__ lvals, int L,
+                     float* __restrict__ z, int64_t ncols, const int* active, int* err) {
+  static_assert(NB == 1 || NB == 2, "buffers");
+  static_assert(kSrhtThreads == 512, "the passes assume 512 threads x 32 entries");
+  constexpr int B = kB16;
+  if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* bufs = reinterpret_cast<float*>(smem_raw);            // NB x B
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(bufs + NB * B);  // B / 32
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  const int64_t nitems = ncols * T;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sk_smem_u32(&full[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sk_smem_u32(&full[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bad = 0;
+  }
+  __syncthreads();
+  auto item = [&](int64_t w, const float*& p, int64_t& row0, int& valid, uint32_t& bytes) {
+    const int64_t col = w / T;
+    const int t = (int)(w % T);
+    const int sidx = col < src.nc0 ? 0 : 1;
+    const int64_t lc = sidx ? col - src.nc0 : col;
+    row0 = (int64_t)t * B;
+    p = src.x[sidx] + lc * src.ld[sidx] + row0;
+    const int64_t v = n - row0;
+    valid = v <= 0 ? 0 : (int)(v < B ? v : B);
+    bytes = ((((uintptr_t)p) & 15) == 0) ? (uint32_t)((valid * 4) & ~15) : 0u;
+  };
+  auto issue = [&](int64_t w, int b) {
+    const float* p;
+    int64_t row0;
+    int valid;
+    uint32_t bytes;
+    item(w, p, row0, valid, bytes);
+    const uint32_t bar = sk_smem_u32(&full[b]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    if (bytes)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       sk_smem_u32(bufs + (size_t)b * B)),
+                   "l"(p), "r"(bytes), "r"(bar)
+                   : "memory");
+  };
+  int issued[2] = {0, 0}, consumed[2] = {0, 0};
+  int64_t w = blockIdx.x;
+  if (w < nitems) {
+    if (tid == 0) issue(w, 0);
+    issued[0] = 1;
+  }
+  // per-thread slot bases (float4 units) of the four passes
+  const int t7 = tid & 7, t37 = (tid >> 3) & 7;
+  const int slotA = tid ^ t37;                        // + 512 q   (raw slot tid + 512 q)
+  const int slotB = 8 * tid;                          // + (q ^ t7)
+  const int slotC = 64 * (tid >> 3);                  // + 8 q + (t7 ^ q)
+  const int slotD = (t7 ^ t37) + 8 * t37 + 512 * (tid >> 6);  // + 64 q
+  for (int idx = 0; w < nitems; w += gridDim.x, ++idx) {
+    const int b = NB == 2 ? (idx & 1) : 0;
+    const int64_t wn = w + gridDim.x;
+    if (NB == 2 && wn < nitems) {
+      if (tid == 0) issue(wn, b ^ 1);
+      issued[b ^ 1] += 1;
+    }
+    const float* p;
+    int64_t row0;
+    int valid;
+    uint32_t bytes;
+    item(w, p, row0, valid, bytes);
+    // the signs of D for this tile: one Philox block per 128 rows
+    if (tid < B / 128) {
+      const uint4 bits = srht_sign_bits(key, (uint32_t)((row0 >> 7) + tid));
+      reinterpret_cast<uint4*>(sgn)[tid] = bits;
+    }
+    if (!sk_mbar_wait(sk_smem_u32(&full[b]), (uint32_t)(consumed[b] & 1))) bad = 1;
+    consumed[b] += 1;
+    __syncthreads();
+    if (bad) {
+      consumed[b] -= 1;
+      break;
+    }
+    float* buf = bufs + (size_t)b * B;
+    float4* buf4 = reinterpret_cast<float4*>(buf);
+    const int done = (int)(bytes / 4);
+    float4 v[8];
+    // pass A
+    if (done == B) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = buf4[tid + 512 * q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = 4 * tid + 2048 * q;
+        if (j + 4 <= done) {
+          v[q] = buf4[tid + 512 * q];
+        } else {
+          float e[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) e[c] = (j + c < valid) ? __ldg(p + j + c) : 0.f;
+          v[q] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      // entries 4 tid + 2048 q + c: bits 4 (tid & 7) + c of sign word (tid >> 3) + 64 q
+      const uint32_t sw = sgn[(tid >> 3) + 64 * q] >> (4 * t7);
+      v[q].x = b16_sign(v[q].x, sw << 31);
+      v[q].y = b16_sign(v[q].y, sw << 30);
+      v[q].z = b16_sign(v[q].z, sw << 29);
+      v[q].w = b16_sign(v[q].w, sw << 28);
+    }
+    b16_levels_in(v);
+    b16_levels_q(v);
+    __syncwarp();  // the slots written below were read by lanes of this warp only
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf4[slotA + 512 * q] = v[q];
+    __syncthreads();
+    // pass B: slots 8 tid + (q ^ t7)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = buf4[slotB + (q ^ t7)];
+    b16_levels_q(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf4[slotB + (q ^ t7)] = v[q];
+    __syncthreads();
+    // pass C
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = buf4[slotC + 8 * q + (t7 ^ q)];
+    b16_levels_q(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf4[slotC + 8 * q + (t7 ^ q)] = v[q];
+    __syncthreads();
+    // pass D
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = buf4[slotD + 64 * q];
+    b16_levels_q(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf4[slotD + 64 * q] = v[q];
+    __syncthreads();
+    float* zo = z + w * L;  // (col * T + t) * L
+    for (int l = tid; l < L; l += blockDim.x) zo[l] = buf[b16_phys(__ldg(lvals + l))];
+    __syncthreads();  // buffer b may be refilled from here on
+    if (NB == 1 && wn < nitems) {
+      if (tid == 0) issue(wn, 0);
+      issued[0] += 1;
+    }
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b)
+      if (issued[b] > consumed[b] && !sk_mbar_wait(sk_smem_u32(&full[b]), (uint32_t)((issued[b] - 1) & 1))) bad = 1;
+    if (bad && err) atomicExch(err, 1);
+  }
+  __syncthreads();
+}
+
+// Buffers of the persistent stage 1: 1 (two CTAs per SM, measured faster on
+// GB300) or 2 (RBGS_SRHT_BUFFERS=2, one CTA per SM that prefetches).
+int srht_buffers() {
+  static int v = []() {
+    const char* e = getenv("RBGS_SRHT_BUFFERS");
+    const int b = e ? atoi(e) : 1;
+    return b == 1 ? 1 : 2;
+  }();
+  return v;
 }
 
 // Stage 2 as a transform across tiles: for each column and distinct low
@@ -661,8 +890,9 @@ rbgs_status sketch_apply2_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t see
     RBGS_CUDA_TRY(cudaGetDevice(&dev));
     RBGS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int64_t nitems = ncols * plan->T;
-    const int grid = (int)std::min<int64_t>(nitems, nsm);
-    const size_t smem = sizeof(float) * 2 * (size_t)plan->B + sizeof(uint32_t) * (size_t)((plan->B + 31) / 32);
+    const int nb = srht_buffers();
+    const int grid = (int)std::min<int64_t>(nitems, (int64_t)nsm * (nb == 1 ? 2 : 1));
+    const size_t smem = sizeof(float) * nb * (size_t)plan->B + sizeof(uint32_t) * (size_t)((plan->B + 31) / 32);
     SrhtSrc sd;
     sd.x[0] = reinterpret_cast<const float*>(X1);
     sd.x[1] = reinterpret_cast<const float*>(nc2 ? X2 : X1);
@@ -672,20 +902,38 @@ rbgs_status sketch_apply2_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t see
     float* zf = reinterpret_cast<float*>(z);
     auto go = [&](auto kern) -> rbgs_status {
       RBGS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float) * 2 * kSrhtTile + 4 * kSrhtTile / 32)));
+                                         (int)(sizeof(float) * nb * kSrhtTile + 4 * kSrhtTile / 32)));
       kern<<<grid, kSrhtThreads, smem, st>>>(sd, n, plan->B, logB, plan->T, key, plan->d_lvals, plan->L, zf, ncols,
                                              active, nullptr);
       RBGS_LAUNCH_CHECK();
       return RBGS_OK;
     };
-    switch (E) {
-      case 1: s = go(srht_stage1_persist<1>); break;
-      case 2: s = go(srht_stage1_persist<2>); break;
-      case 4: s = go(srht_stage1_persist<4>); break;
-      case 8: s = go(srht_stage1_persist<8>); break;
-      case 16: s = go(srht_stage1_persist<16>); break;
-      case 32: s = go(srht_stage1_persist<32>); break;
-      default: return RBGS_EINVAL;
+    if (plan->B == kB16) {
+      auto k16 = nb == 1 ? srht_stage1_b16k<1> : srht_stage1_b16k<2>;
+      RBGS_CUDA_TRY(cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k16<<<grid, kSrhtThreads, smem, st>>>(sd, n, plan->T, key, plan->d_lvals, plan->L, zf, ncols, active, nullptr);
+      RBGS_LAUNCH_CHECK();
+      s = RBGS_OK;
+    } else if (nb == 1) {
+      switch (E) {
+        case 1: s = go(srht_stage1_persist<1, 1>); break;
+        case 2: s = go(srht_stage1_persist<2, 1>); break;
+        case 4: s = go(srht_stage1_persist<4, 1>); break;
+        case 8: s = go(srht_stage1_persist<8, 1>); break;
+        case 16: s = go(srht_stage1_persist<16, 1>); break;
+        case 32: s = go(srht_stage1_persist<32, 1>); break;
+        default: return RBGS_EINVAL;
+      }
+    } else {
+      switch (E) {
+        case 1: s = go(srht_stage1_persist<1, 2>); break;
+        case 2: s = go(srht_stage1_persist<2, 2>); break;
+        case 4: s = go(srht_stage1_persist<4, 2>); break;
+        case 8: s = go(srht_stage1_persist<8, 2>); break;
+        case 16: s = go(srht_stage1_persist<16, 2>); break;
+        case 32: s = go(srht_stage1_persist<32, 2>); break;
+        default: return RBGS_EINVAL;
+      }
     }
     if (s) return s;
   } else {

@@ -403,6 +403,47 @@ __global__ void reorth_decide_kernel(int64_t c, int mb, const TS* __restrict__ X
   }
 }
 
+template <class T>
+__global__ void round2_decide_kernel(int mb, const T* __restrict__ R1, const T* __restrict__ R1inv, T* R, T* Rinv,
+                                     double thr, const int* active, int* need2, int* count) {
+  __shared__ double red[2][256];
+  __shared__ int on_s;
+  if (active && *active == 0) {
+    if (threadIdx.x == 0) *need2 = 0;
+    return;
+  }
+  const int tot = mb * mb;
+  double a = 0.0, b = 0.0;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const double x = (double)R1[e], y = (double)R1inv[e];
+    a += x * x;
+    b += y * y;
+  }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + h];
+      red[1][threadIdx.x] += red[1][threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double kf = sqrt(red[0][0] * red[1][0]);
+    const int on = !(kf <= thr);  // a NaN estimate keeps the second round
+    on_s = on;
+    *need2 = on;
+    if (on && count) *count += 1;
+  }
+  __syncthreads();
+  if (on_s) return;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    R[e] = R1[e];
+    Rinv[e] = R1inv[e];
+  }
+}
+
 template <class TS>
 __global__ void sub_mat_kernel(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C,
                                int64_t ldc, const int* active) {
@@ -576,6 +617,19 @@ template rbgs_status reorth_decide<double>(int64_t, int, const double*, int64_t,
                                            cudaStream_t);
 template rbgs_status reorth_decide<float>(int64_t, int, const float*, int64_t, double, int, int*, int*, int*,
                                           cudaStream_t);
+
+template <class T>
+rbgs_status round2_decide(int mb, const T* R1, const T* R1inv, T* R, T* Rinv, double thr, const int* active,
+                          int* need2, int* count, cudaStream_t st) {
+  if (mb < 1) return RBGS_EINVAL;
+  round2_decide_kernel<T><<<1, 256, 0, st>>>(mb, R1, R1inv, R, Rinv, thr, active, need2, count);
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
+template rbgs_status round2_decide<double>(int, const double*, const double*, double*, double*, double, const int*,
+                                           int*, int*, cudaStream_t);
+template rbgs_status round2_decide<float>(int, const float*, const float*, float*, float*, double, const int*,
+                                          int*, int*, cudaStream_t);
 
 template <class TS>
 rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,

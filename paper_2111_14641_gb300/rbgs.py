@@ -53,7 +53,7 @@ def stencil_op(nx: int, ny: int, bx: float, by: float) -> Op:
 class Stats(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("delta_tilde", ctypes.c_double), ("passes2", ctypes.c_int32),
                 ("certified", ctypes.c_int32), ("tall_ms", ctypes.c_double), ("tall_bytes", ctypes.c_double),
-                ("tall_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tall_launches", ctypes.c_int32), ("chol_rounds2", ctypes.c_int32)]
 
 
 @dataclass
@@ -65,6 +65,7 @@ class QRStats:
     tall_ms: float = 0.0
     tall_bytes: float = 0.0
     tall_launches: int = 0
+    chol_rounds2: int = 0
 
 
 _lib = None
@@ -179,7 +180,7 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
                        R.data_ptr(), _ld(R, "R"), ctypes.byref(o), ctypes.byref(st) if sync else None)
     _check(code, "rbgs_qr")
     stats = (QRStats(st.delta, st.delta_tilde, st.passes2, bool(st.certified), st.tall_ms, st.tall_bytes,
-                     st.tall_launches) if sync else None)
+                     st.tall_launches, st.chol_rounds2) if sync else None)
     return Q, R, stats
 
 
