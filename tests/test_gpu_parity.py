@@ -139,6 +139,38 @@ def test_rbgs_fp64_matches_oracle(rb, n, m, mb, kind, k, reorth):
     assert st.passes2 == (m // mb - 1 if reorth else 0)
 
 
+@pytest.mark.parametrize("reorth", [False, True])
+def test_fp64_second_cholesky_round_only_where_needed(rb, reorth):
+    """FP64 sketch space: Alg. 5's Cholesky QR takes its second round only where
+    the first round's R has ||R||_F ||R^{-1}||_F > 4 m_p.  Columns u_j sigma_j
+    make every block as ill-conditioned as its sigmas (about 10^2.9), so each
+    first pass that settles a block needs the second round, while the second
+    projection pass (a nearly orthonormal block) does not; the factors match
+    the oracle's either way."""
+    n, m, mb, k = 4000, 32, 16, 200
+    rng = np.random.Generator(np.random.PCG64(11))
+    U, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    cond = 1e6
+    W = np.asfortranarray(U * synth.sigmas(m, cond))
+    Q, R, ref, fact, ortho, st = _check_qr_against_oracle(rb, W, mb, "gauss", k, 99, 3, reorth, cond)
+    tol = 1e-13 * cond
+    assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+    assert np.abs(Q - ref["Q"]).max() <= tol * np.abs(ref["Q"]).max()
+    assert fact < 1e-14
+    assert st.chol_rounds2 == (1 if reorth else m // mb)
+
+
+def test_fp64_single_cholesky_round_when_well_conditioned(rb):
+    """A well-conditioned W (cond 2) needs no second Cholesky QR round in FP64;
+    the FP32 sketch space, whose first round is shifted, always takes it."""
+    n, m, mb, k = 3000, 40, 10, 200
+    W = synth.svd_matrix(n, m, 2.0, 21)
+    _, _, ref, fact, ortho, st = _check_qr_against_oracle(rb, W, mb, "srht", k, 3, 1, False, 2.0)
+    assert st.chol_rounds2 == 0 and fact < 1e-14 and ortho < 1e-13
+    _, _, st32 = rb.rbgs_qr(dev(W, torch.float32), mb, "srht", k, 3, prec="fp32", ls_iters=1, reorth=0)
+    assert st32.chol_rounds2 == m // mb
+
+
 def test_c1_config_fp64(rb):
     """n = 1e4, m = 100, m_p = 10, Gaussian k = 200, cond(W) = 1e8:
     ||W - QR||/||W|| <= 1e-13 and sketched orthogonality <= 1e-12 with the
