@@ -215,6 +215,30 @@ RBGS_API rbgs_status rbgs_block_fom(const rbgs_op* op, const double* B, int64_t 
                            int64_t p, double rtol, int64_t max_cycles, rbgs_sketch sketch, int64_t k, uint64_t seed,
                            const rbgs_opts* opts, int64_t* cycles, double* relres);
 
+/* Randomized Rayleigh-Ritz with restarting, Alg. 8 (Sec. 5.4), for extreme
+ * eigenpairs of the operator.  Each of the n_iter iterations runs Alg. 7 with
+ * p blocks from B (basis in opts->prec; B0 is the first B), sets
+ * H = R(:, mb:), and takes the mb extreme eigenpairs (mu, y) of the
+ * (p-1) mb x (p-1) mb matrix H_(1:p-1,1:p-1) (which: 0 = largest real part,
+ * 1 = smallest); the next B is Q(:, 0:(p-1) mb) Y.  The paper leaves the
+ * choice and the scaling of y open; here each y has unit 2-norm with its first
+ * largest-modulus entry real and positive, a real eigenvalue gives one column
+ * y of Y, a conjugate pair a +- ib the two columns Re y, Im y (Re y alone if
+ * one column is left), ordered by real part (ties: positive imaginary part
+ * first).  On return X (n x mb, ldx, device double) holds the last B with
+ * unit columns (step 5); ritz_re, ritz_im and resid_est (host, mb values)
+ * hold the Ritz value of each column and the estimate ||H_(p,1:p-1) y|| of
+ * its residual (step 3).  (p-1) mb <= RBGS_RITZ_MAX_N.  The small
+ * eigenproblem runs on one CTA in FP64 (Hessenberg reduction, Francis
+ * double-shift QR, inverse iteration); RBGS_ENOCONV if its QR iteration does
+ * not converge within 30 (p-1) mb sweeps; other errors as rbgs_block_gmres.
+ * Synchronous.                                                               */
+#define RBGS_RITZ_MAX_N 1024
+RBGS_API rbgs_status rbgs_rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int64_t mb, int64_t p,
+                                        int64_t n_iter, int32_t which, rbgs_sketch sketch, int64_t k, uint64_t seed,
+                                        const rbgs_opts* opts, double* X, int64_t ldx, double* ritz_re,
+                                        double* ritz_im, double* resid_est);
+
 /* Philox4x32-10 blocks on the device: out[4i..4i+3] = philox(ctr[4i..4i+3],
  * key = (seed_lo, seed_hi)) for i < count (device pointers).              */
 RBGS_API rbgs_status rbgs_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t count, void* stream, int32_t sync);

@@ -17,6 +17,9 @@ What each function follows (Balabanov & Grigori, arXiv 2111.14641):
 * ``rcholqr``: the closed form that RBGS reaches in exact arithmetic
   (R = R factor of Theta W with a positive diagonal, Q = W R^{-1}).
 * ``householder_qr``: textbook Householder QR with a positive diagonal.
+* ``rbgs_arnoldi`` / ``block_krylov`` / ``rayleigh_ritz``: Alg. 7, the
+  restarted randomized block GMRES and FOM of Sec. 5.2-5.3, and Alg. 8
+  (Sec. 5.4) on the 5-point convection-diffusion stencil.
 
 Every array is float64, column-major (Fortran order).
 """
@@ -275,6 +278,86 @@ def block_krylov(method: str, nx: int, ny: int, bx: float, by: float, B, X0, p: 
     if cyc < 0:
         raise np.linalg.LinAlgError(f"block Krylov solver failed ({cyc})")
     return X, int(cyc), relres
+
+
+RITZ_WHICH = ("LR", "SR")
+
+
+def ritz_select(mu, V, mp: int, which: str):
+    """Step 2 of Alg. 8: the m_p extreme Ritz pairs of the projected matrix, as
+    a real basis.  The paper leaves the selection and the scaling open; the
+    conventions (shared with the GPU path, written separately there) are:
+
+    * order: by real part, descending for "LR" and ascending for "SR"; among
+      equal real parts the eigenvalue with positive imaginary part comes first,
+      and each conjugate pair is considered once;
+    * each eigenvector y is scaled to unit 2-norm with its largest-modulus entry
+      (the first one, on ties) real and positive;
+    * a real eigenvalue takes one column y, a conjugate pair a +- ib two
+      columns Re y and Im y (only Re y if one slot is left).
+
+    Returns (values (complex, per column), Y (N x mp, real), vecs (the complex
+    unit eigenvector of each column's value: y, and conj(y) for the second
+    column of a pair))."""
+    mu = np.asarray(mu)
+    cand = [i for i in range(mu.size) if mu[i].imag >= 0.0]
+    if which == "LR":
+        cand.sort(key=lambda i: (-mu[i].real, -mu[i].imag))
+    elif which == "SR":
+        cand.sort(key=lambda i: (mu[i].real, -mu[i].imag))
+    else:
+        raise ValueError("which must be 'LR' or 'SR'")
+    N = V.shape[0]
+    Y = np.zeros((N, mp), order="F")
+    vals, vecs = [], []
+    col = 0
+    for i in cand:
+        if col >= mp:
+            break
+        y = V[:, i].astype(np.complex128)
+        y = y / np.linalg.norm(y)
+        j = int(np.argmax(np.abs(y)))
+        y = y * (np.conj(y[j]) / abs(y[j]))
+        Y[:, col] = y.real
+        vals.append(mu[i])
+        vecs.append(y)
+        col += 1
+        if mu[i].imag > 0.0 and col < mp:
+            Y[:, col] = y.imag
+            vals.append(np.conj(mu[i]))
+            vecs.append(np.conj(y))
+            col += 1
+    return np.array(vals), Y, vecs
+
+
+def rayleigh_ritz(nx: int, ny: int, bx: float, by: float, B0, p: int, n_iter: int, which: str, kind: str, k: int,
+                  seed: int, variant: int = 5, ls: str = "householder", ls_iters: int = 5, reorth: bool = False,
+                  ls_iters_first: int = 0):
+    """Alg. 8 (Sec. 5.4): randomized Rayleigh-Ritz with restarting.  Each
+    iteration runs Alg. 7 from B, sets H = R_(1:p,2:p), takes the m_p extreme
+    eigenpairs (mu, y) of H_(1:p-1,1:p-1) (numpy's eig as the library step;
+    selection and scaling per ``ritz_select``), estimates each residual by
+    ||H_(p,1:p-1) y|| and restarts from B = Q_(1:p-1) Y.  Step 5 scales the
+    columns of the last B to unit 2-norm.
+
+    Returns dict(values (complex, m_p), X (n x m_p), resid (m_p), Q, R of the
+    last iteration)."""
+    B = _f64(B0)
+    n, mp = B.shape
+    N = (p - 1) * mp
+    out = None
+    for _ in range(n_iter):
+        out = rbgs_arnoldi(nx, ny, bx, by, B, p, kind, k, seed, variant=variant, ls=ls, ls_iters=ls_iters,
+                           reorth=reorth, ls_iters_first=ls_iters_first)
+        if out["rc"] != 0:
+            raise np.linalg.LinAlgError(f"Arnoldi breakdown ({out['rc']})")
+        H = out["R"][:, mp:]
+        mu, V = np.linalg.eig(H[:N, :N])
+        vals, Y, vecs = ritz_select(mu, V, mp, which)
+        resid = np.array([np.linalg.norm(H[N:, :N] @ y) for y in vecs])
+        B = np.asfortranarray(out["Q"][:, :N] @ Y)
+    X = np.asfortranarray(B / np.linalg.norm(B, axis=0))
+    return dict(values=vals, X=X, resid=resid, Q=out["Q"], R=out["R"])
 
 
 def stencil5_dense(nx: int, ny: int, bx: float, by: float) -> np.ndarray:

@@ -167,6 +167,18 @@ template <class T>
 rbgs_status round2_decide(int mb, const T* R1, const T* R1inv, T* R, T* Rinv, double thr, const int* active,
                           int* need2, int* count, cudaStream_t st);
 
+// Alg. 8, step 2-3: the mp extreme eigenpairs of the N x N matrix H (ld ldh,
+// N + mb rows: rows N.. are H_(p,1:p-1)); which 0 = largest real part, 1 =
+// smallest.  vals: 2 mp doubles (re, im per column), Y: N x mp (ld N), resid:
+// mp residual estimates; *status = 0 or 1 (QR iteration did not converge).
+// scratch: ritz_eig_scratch_bytes(N).  One CTA, FP64.
+constexpr int kRitzMaxN = RBGS_RITZ_MAX_N;
+size_t ritz_eig_scratch_bytes(int N);
+rbgs_status ritz_eig(int N, int mb, int mp, int which, const double* H, int64_t ldh, double* vals, double* Y,
+                     double* resid, void* scratch, int* status, cudaStream_t st);
+// X[:, j] /= norms[j] (n x ncols, double)
+rbgs_status scale_cols(int64_t n, int64_t ncols, const double* norms, double* X, int64_t ldx, cudaStream_t st);
+
 // Elementwise C = A - B (k x mb) in TS.
 template <class TS>
 rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,

@@ -253,6 +253,8 @@ template rbgs_status cast_cols_t<double, float>(int64_t, int64_t, const double*,
                                                 cudaStream_t);
 template rbgs_status cast_cols_t<double, double>(int64_t, int64_t, const double*, int64_t, double*, int64_t,
                                                  cudaStream_t);
+template rbgs_status cast_cols_t<float, double>(int64_t, int64_t, const float*, int64_t, double*, int64_t,
+                                                cudaStream_t);
 
 template <class TD>
 rbgs_status add_cols_t(int64_t n, int64_t ncols, const TD* D, int64_t ldd, double* X, int64_t ldx, cudaStream_t st) {

@@ -875,6 +875,97 @@ rbgs_status krylov_solve(int method, const rbgs_op* op, const double* B, int64_t
   }
 }
 
+// Alg. 8: randomized Rayleigh-Ritz with restarting.
+rbgs_status rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int64_t mb, int64_t p, int64_t n_iter,
+                          int32_t which, rbgs_sketch sketch, int64_t k, uint64_t seed, const rbgs_opts* opts,
+                          double* X, int64_t ldx, double* ritz_re, double* ritz_im, double* resid_est) {
+  rbgs_status s;
+  if ((s = check_op(op))) return s;
+  const int64_t n = op->nx * op->ny, m = p * mb, N = m - mb;
+  if (!B0 || !X || !ritz_re || !ritz_im || !resid_est || mb < 1 || mb > 64 || p < 2 || n_iter < 1 || ldb < n ||
+      ldx < n || (which != 0 && which != 1) || N > kRitzMaxN)
+    return RBGS_EINVAL;
+  if ((s = check_sketch(sketch, n, k, m))) return s;
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1)
+    return RBGS_EINVAL;
+  o.sync = 1;
+  o.timing = 0;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const bool f64 = o.prec == RBGS_P_FP64;
+  const size_t es = f64 ? 8 : 4;
+  // buffers: basis Q (n x m), block B (n x mb, basis type), the Arnoldi R (m x m), Y (N x mb) in FP64
+  // and the basis type, Ritz values and residual estimates, column norms, the eigen-solver's scratch
+  const size_t part_elems = residual_part_elems(n, mb);
+  const size_t bytes = es * (size_t)n * (size_t)m + es * (size_t)n * (size_t)mb + 8 * (size_t)m * m +
+                       (8 + es) * (size_t)N * mb + 8 * (4 * (size_t)mb + part_elems) + ritz_eig_scratch_bytes((int)N) +
+                       16 * 256;
+  DevBuf buf;
+  if (cudaMalloc(&buf.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  char* w = (char*)buf.p;
+  auto take = [&](size_t b) {
+    char* r = w;
+    w += (b + 255) & ~(size_t)255;
+    return (void*)r;
+  };
+  void* Qb = take(es * (size_t)n * m);
+  void* Bb = take(es * (size_t)n * mb);
+  double* Rm = (double*)take(8 * (size_t)m * m);
+  double* Y = (double*)take(8 * (size_t)N * mb);
+  void* Yt = take(es * (size_t)N * mb);
+  double* vals = (double*)take(16 * (size_t)mb);
+  double* res = (double*)take(8 * (size_t)mb);
+  double* norms = (double*)take(8 * (size_t)mb);
+  double* part = (double*)take(8 * part_elems);
+  void* scr = take(ritz_eig_scratch_bytes((int)N));
+  int* status = (int*)take(256);
+  if (f64) s = cast_cols_t<double, double>(n, mb, B0, ldb, (double*)Bb, n, st);
+  else s = cast_cols_t<double, float>(n, mb, B0, ldb, (float*)Bb, n, st);
+  if (s) return s;
+  const int64_t c = N - mb;
+  for (int64_t it = 0; it < n_iter; ++it) {
+    // step 1: Alg. 7 from B; H = R(:, mb:)
+    if ((s = arnoldi_run(*op, Bb, n, mb, p, sketch, k, seed, Qb, n, Rm, m, o, nullptr))) return s;
+    // steps 2-3 on H_(1:p-1,1:p-1) and H_(p,1:p-1)
+    RBGS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+    if ((s = ritz_eig((int)N, (int)mb, (int)mb, which, Rm + mb * m, m, vals, Y, res, scr, status, st))) return s;
+    int hs = 0;
+    RBGS_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs) return RBGS_ENOCONV;
+    // step 4: B = Q(:, 0:N) Y on the tall kernel of the basis type
+    if (f64) {
+      s = tall_update_simt<double>(n, c, mb, (const double*)Qb, n, (const double*)Qb + c * n, n, Y, N, (double*)Bb, n,
+                                   nullptr, st);
+    } else {
+      if ((s = cast_cols_t<double, float>(N, mb, Y, N, (float*)Yt, N, st))) return s;
+      s = tall_update_simt<float>(n, c, mb, (const float*)Qb, n, (const float*)Qb + c * n, n, (const float*)Yt, N,
+                                  (float*)Bb, n, nullptr, st);
+    }
+    if (s) return s;
+  }
+  // step 5: X = B with unit columns
+  if (f64) s = cast_cols_t<double, double>(n, mb, (const double*)Bb, n, X, ldx, st);
+  else s = cast_cols_t<float, double>(n, mb, (const float*)Bb, n, X, ldx, st);
+  if (s) return s;
+  if ((s = colnorms_t(n, mb, X, ldx, part, norms, st))) return s;
+  if ((s = scale_cols(n, mb, norms, X, ldx, st))) return s;
+  std::vector<double> hv(2 * (size_t)mb);
+  RBGS_CUDA_TRY(cudaMemcpyAsync(hv.data(), vals, 16 * (size_t)mb, cudaMemcpyDeviceToHost, st));
+  RBGS_CUDA_TRY(cudaMemcpyAsync(resid_est, res, 8 * (size_t)mb, cudaMemcpyDeviceToHost, st));
+  RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int64_t j = 0; j < mb; ++j) {
+    ritz_re[j] = hv[2 * (size_t)j];
+    ritz_im[j] = hv[2 * (size_t)j + 1];
+  }
+  return RBGS_OK;
+}
+
 }  // namespace
 
 rbgs_status rbgs_op_apply(const rbgs_op* op, int32_t prec, const void* X, int64_t ldx, int64_t ncols, void* Y,
@@ -928,4 +1019,12 @@ rbgs_status rbgs_block_fom(const rbgs_op* op, const double* B, int64_t ldb, doub
                            int64_t p, double rtol, int64_t max_cycles, rbgs_sketch sketch, int64_t k, uint64_t seed,
                            const rbgs_opts* opts, int64_t* cycles, double* relres) {
   return krylov_solve(1, op, B, ldb, X, ldx, mb, p, rtol, max_cycles, sketch, k, seed, opts, cycles, relres);
+}
+
+rbgs_status rbgs_rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int64_t mb, int64_t p,
+                               int64_t n_iter, int32_t which, rbgs_sketch sketch, int64_t k, uint64_t seed,
+                               const rbgs_opts* opts, double* X, int64_t ldx, double* ritz_re, double* ritz_im,
+                               double* resid_est) {
+  return rayleigh_ritz(op, B0, ldb, mb, p, n_iter, which, sketch, k, seed, opts, X, ldx, ritz_re, ritz_im,
+                       resid_est);
 }

@@ -102,12 +102,14 @@ def load(build_if_missing: bool = False):
     for fn in ("rbgs_block_gmres", "rbgs_block_fom"):
         getattr(lib, fn).argtypes = [opp, vp, i64, vp, i64, i64, i64, ctypes.c_double, i64, ctypes.c_int, i64, u64,
                                      ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_int64), vp]
+    lib.rbgs_rayleigh_ritz.argtypes = [opp, vp, i64, i64, i64, i64, i32, ctypes.c_int, i64, u64, ctypes.POINTER(Opts),
+                                       vp, i64, vp, vp, vp]
     lib.rbgs_release_workspace.argtypes = []
     lib.rbgs_version.restype = ctypes.c_char_p
     lib.rbgs_launch_count.restype = ctypes.c_int64
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
                  "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
-                 "rbgs_block_fom"):
+                 "rbgs_block_fom", "rbgs_rayleigh_ritz"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -313,6 +315,32 @@ def block_fom(op: Op, B: torch.Tensor, X: torch.Tensor | None = None, p: int = 1
     """Restarted randomized block FOM (Sec. 5.3): returns (X, cycles, relres)."""
     return _block_solve("rbgs_block_fom", op, B, X, p, rtol, max_cycles, sketch, k, seed, prec, ls_iters, reorth,
                         reorth_tol, fine, stream, raise_on_noconv)
+
+
+RITZ_WHICH = {"LR": 0, "SR": 1}
+
+
+def rayleigh_ritz(op: Op, B0: torch.Tensor, p: int = 10, n_iter: int = 1, which: str = "LR", sketch: str = "srht",
+                  k: int | None = None, seed: int = 0, prec: str = "fp64", ls_iters: int = 2, reorth: int = 0,
+                  reorth_tol: float = 1e-8, fine: bool = False, X: torch.Tensor | None = None, stream=None):
+    """Randomized Rayleigh-Ritz with restarting (Alg. 8, Sec. 5.4).  B0: n x mb
+    float64 on the device.  Returns (values (complex, mb), X (n x mb float64,
+    unit columns), resid (mb estimates ||H_(p,1:p-1) y||))."""
+    lib = load()
+    n, mb = B0.shape
+    if B0.dtype != torch.float64:
+        raise ValueError("B0 must be float64")
+    if X is None:
+        X = torch.empty((mb, n), dtype=torch.float64, device=B0.device).t()
+    k = 2 * p * mb if k is None else k
+    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream)
+    re, im, rs = (ctypes.c_double * mb)(), (ctypes.c_double * mb)(), (ctypes.c_double * mb)()
+    _check(lib.rbgs_rayleigh_ritz(ctypes.byref(op), B0.data_ptr(), _ld(B0, "B0"), mb, p, n_iter, RITZ_WHICH[which],
+                                  SKETCH[sketch], k, seed, ctypes.byref(o), X.data_ptr(), _ld(X, "X"),
+                                  ctypes.cast(re, ctypes.c_void_p), ctypes.cast(im, ctypes.c_void_p),
+                                  ctypes.cast(rs, ctypes.c_void_p)), "rbgs_rayleigh_ritz")
+    vals = [complex(re[j], im[j]) for j in range(mb)]
+    return vals, X, [float(v) for v in rs]
 
 
 def philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:

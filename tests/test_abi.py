@@ -96,3 +96,30 @@ def test_krylov_argument_checks_need_no_device(lib):
                                 ctypes.byref(cyc), ctypes.cast(rel, ctypes.c_void_p)) == 1
     assert lib.rbgs_block_fom(ctypes.byref(good), fake, 64, fake, 64, 2, 8, 1e-8, 10, 0, 8, 0, None,
                               ctypes.byref(cyc), ctypes.cast(rel, ctypes.c_void_p)) == 1
+
+
+def test_rayleigh_ritz_argument_checks_need_no_device(lib):
+    """rbgs_rayleigh_ritz refuses bad arguments before any CUDA call."""
+    import ctypes
+
+    from paper_2111_14641_gb300 import rbgs as rbmod
+
+    lib = rbmod.load()
+    good = rbmod.Op(0, 0, 8, 8, 1.0, 1.0)
+    fake = ctypes.c_void_p(1 << 20)
+    out = [(ctypes.c_double * 2)() for _ in range(3)]
+    ptrs = [ctypes.cast(o, ctypes.c_void_p) for o in out]
+
+    def call(op, mb, p, n_iter, which, k, ldx=64):
+        return lib.rbgs_rayleigh_ritz(ctypes.byref(op), fake, 64, mb, p, n_iter, which, 0, k, 0, None, fake, ldx,
+                                      *ptrs)
+
+    assert call(good, 2, 1, 1, 0, 16) == 1            # p < 2
+    assert call(good, 2, 4, 0, 0, 16) == 1            # no iteration
+    assert call(good, 2, 4, 1, 2, 16) == 1            # which is 0 or 1
+    assert call(good, 2, 4, 1, 0, 4) == 1             # k < p mb
+    assert call(good, 2, 4, 1, 0, 16, ldx=10) == 1    # ldx < n
+    big = rbmod.Op(0, 0, 256, 256, 1.0, 1.0)          # (p - 1) mb > RBGS_RITZ_MAX_N
+    assert lib.rbgs_rayleigh_ritz(ctypes.byref(big), fake, 65536, 64, 18, 1, 0, 0, 2048, 0, None, fake, 65536,
+                                  *ptrs) == 1
+    assert lib.rbgs_rayleigh_ritz(None, fake, 64, 2, 4, 1, 0, 0, 16, 0, None, fake, 64, *ptrs) == 1

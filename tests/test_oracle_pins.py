@@ -466,3 +466,114 @@ def test_restarted_solver_reaches_direct_solution(method):
     assert rel.max() <= 1e-11 and cyc >= 1
     Xd = np.linalg.solve(_kron_stencil(nx, ny, 12.0, 6.0), B)
     assert np.abs(X - Xd).max() <= 1e-8 * np.abs(Xd).max()
+
+
+# ------------------------------------------------ Alg. 8: Rayleigh-Ritz --
+
+def _closed_form_eigs(nx, ny, bx, by):
+    """Eigenvalues of the convection-diffusion stencil for cell Peclet
+    numbers below 1 (separable: the 1-D tridiagonal Toeplitz spectra add)."""
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+    px, py = bx * hx / 2, by * hy / 2
+    ex = (2.0 - 2.0 * np.sqrt(1 - px ** 2) * np.cos(np.arange(1, nx + 1) * np.pi * hx)) / hx ** 2
+    ey = (2.0 - 2.0 * np.sqrt(1 - py ** 2) * np.cos(np.arange(1, ny + 1) * np.pi * hy)) / hy ** 2
+    return np.sort((ex[:, None] + ey[None, :]).ravel())
+
+
+def _ritz_vectors(out, mp, p):
+    """Complex Ritz pairs (mu, y) of the last iteration, recomputed from its H."""
+    N = (p - 1) * mp
+    H = out["R"][:, mp:]
+    mu, V = np.linalg.eig(H[:N, :N])
+    return oracle.ritz_select(mu, V, mp, "LR")
+
+
+def test_rr_identity_sketch_is_classical_rayleigh_ritz():
+    """With Theta = I the Ritz values are the eigenvalues of V^T A V for an
+    orthonormal basis V of the block Krylov space K_(p-1)(A, B) (brute force
+    on an explicit Krylov basis)."""
+    nx, ny, bx, by, mp, p = 7, 6, 8.0, 4.0, 2, 6
+    n = nx * ny
+    B = synth.gaussian(n, mp, 41)
+    A = _kron_stencil(nx, ny, bx, by)
+    out = oracle.rayleigh_ritz(nx, ny, bx, by, B, p, 1, "LR", "identity", n, 0)
+    V, _ = np.linalg.qr(_krylov_basis(A, B, p - 1))
+    ev = np.linalg.eigvals(V.T @ A @ V)
+    order = sorted(range(ev.size), key=lambda i: (-ev[i].real, -ev[i].imag))
+    want = [ev[i] for i in order if ev[i].imag >= 0][:mp]
+    got = [v for v in out["values"] if v.imag >= 0][: len(want)]
+    np.testing.assert_allclose(np.array(got), np.array(want)[: len(got)], rtol=1e-9)
+
+
+def test_rr_sketched_galerkin_and_residual_estimate():
+    """Sec. 5.4: a Ritz pair (mu, u = Q_(1:p-1) y) satisfies the sketched
+    Galerkin condition <Theta v, Theta (A u - mu u)> = 0 on range(Q_(1:p-1)),
+    and ||H_(p,1:p-1) y|| equals ||Theta (A u - mu u)|| (Arnoldi identity with
+    Theta Q orthonormal).  Checked with the dense Theta and operator."""
+    nx, ny, bx, by, mp, p, k = 9, 7, 10.0, 5.0, 3, 6, 50
+    n = nx * ny
+    B = synth.gaussian(n, mp, 43)
+    out = oracle.rayleigh_ritz(nx, ny, bx, by, B, p, 1, "LR", "gauss", k, 8)
+    T = oracle.theta_dense("gauss", k, n, 8)
+    A = _kron_stencil(nx, ny, bx, by)
+    N = (p - 1) * mp
+    Qn = out["Q"][:, :N]
+    vals, _, vecs = _ritz_vectors(out, mp, p)
+    np.testing.assert_allclose(vals, out["values"], rtol=1e-12)
+    for j, (mu, y) in enumerate(zip(vals, vecs)):
+        u = Qn @ y
+        r = T @ (A @ u - mu * u)
+        g = (T @ Qn).T @ r
+        assert np.abs(g).max() <= 1e-9 * np.linalg.norm(T @ (A @ u))
+        assert abs(np.linalg.norm(r) - out["resid"][j]) <= 1e-9 * np.linalg.norm(T @ (A @ u))
+
+
+@pytest.mark.parametrize("which", ["LR", "SR"])
+def test_rr_restarts_converge_to_closed_form_eigenvalues(which):
+    """Restarted Alg. 8 on a small grid with cell Peclet numbers below 1: the
+    leading Ritz value reaches the extreme eigenvalue of the closed form, its
+    residual estimate vanishes, and its returned vector (unit 2-norm) is an
+    eigenvector of the dense operator."""
+    nx, ny, bx, by, mp, p = 10, 8, 12.0, 6.0, 3, 6
+    n = nx * ny
+    ev = _closed_form_eigs(nx, ny, bx, by)
+    B = synth.gaussian(n, mp, 31)
+    out = oracle.rayleigh_ritz(nx, ny, bx, by, B, p, 60, which, "gauss", 60, 4)
+    target = ev[-1] if which == "LR" else ev[0]
+    mu = out["values"][0]
+    assert abs(mu.imag) == 0.0
+    assert abs(mu.real - target) <= 1e-11 * ev[-1]
+    assert out["resid"][0] <= 1e-9 * ev[-1]
+    x = out["X"][:, 0]
+    assert abs(np.linalg.norm(x) - 1.0) <= 1e-14
+    A = _kron_stencil(nx, ny, bx, by)
+    assert np.linalg.norm(A @ x - mu.real * x) <= 1e-8 * ev[-1]
+    # the Ritz values ordered as requested, each extreme in its set
+    re = [v.real for v in out["values"]]
+    assert re == sorted(re, reverse=(which == "LR"))
+
+
+def test_ritz_select_conventions():
+    """The selection and scaling rules on a matrix with a known spectrum:
+    a conjugate pair takes two columns (Re y, Im y), each y has unit norm and a
+    real positive largest entry, and the last slot keeps only Re y."""
+    rng = np.random.default_rng(5)
+    S = rng.standard_normal((5, 5))
+    D = np.zeros((5, 5))
+    D[0, 0] = 5.0
+    D[1:3, 1:3] = [[3.0, 2.0], [-2.0, 3.0]]     # 3 +- 2i
+    D[3, 3], D[4, 4] = 1.0, -1.0
+    M = S @ D @ np.linalg.inv(S)
+    mu, V = np.linalg.eig(M)
+    vals, Y, vecs = oracle.ritz_select(mu, V, 3, "LR")
+    np.testing.assert_allclose(vals, [5.0, 3.0 + 2.0j, 3.0 - 2.0j], atol=1e-10)
+    for y in vecs:
+        assert abs(np.linalg.norm(y) - 1.0) < 1e-14
+        j = int(np.argmax(np.abs(y)))
+        assert abs(y[j].imag) < 1e-15 and y[j].real > 0
+    np.testing.assert_allclose(Y[:, 1], vecs[1].real)
+    np.testing.assert_allclose(Y[:, 2], vecs[1].imag)
+    vals2, Y2, _ = oracle.ritz_select(mu, V, 2, "LR")
+    np.testing.assert_allclose(vals2, [5.0, 3.0 + 2.0j], atol=1e-10)
+    vals3, _, _ = oracle.ritz_select(mu, V, 2, "SR")
+    np.testing.assert_allclose(vals3, [-1.0, 1.0], atol=1e-10)
