@@ -171,9 +171,9 @@ rbgs_status round2_decide(int mb, const T* R1, const T* R1inv, T* R, T* Rinv, do
 // N + mb rows: rows N.. are H_(p,1:p-1)); which 0 = largest real part, 1 =
 // smallest.  vals: 2 mp doubles (re, im per column), Y: N x mp (ld N), resid:
 // mp residual estimates; *status = 0 or 1 (QR iteration did not converge).
-// scratch: ritz_eig_scratch_bytes(N).  One CTA, FP64.
+// scratch: ritz_eig_scratch_bytes(N, mb, mp).  One CTA (FP32 estimates, FP64 refinement).
 constexpr int kRitzMaxN = RBGS_RITZ_MAX_N;
-size_t ritz_eig_scratch_bytes(int N);
+size_t ritz_eig_scratch_bytes(int N, int mb, int mp);
 rbgs_status ritz_eig(int N, int mb, int mp, int which, const double* H, int64_t ldh, double* vals, double* Y,
                      double* resid, void* scratch, int* status, cudaStream_t st);
 // X[:, j] /= norms[j] (n x ncols, double)

@@ -900,7 +900,7 @@ rbgs_status rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int6
   // and the basis type, Ritz values and residual estimates, column norms, the eigen-solver's scratch
   const size_t part_elems = residual_part_elems(n, mb);
   const size_t bytes = es * (size_t)n * (size_t)m + es * (size_t)n * (size_t)mb + 8 * (size_t)m * m +
-                       (8 + es) * (size_t)N * mb + 8 * (4 * (size_t)mb + part_elems) + ritz_eig_scratch_bytes((int)N) +
+                       (8 + es) * (size_t)N * mb + 8 * (4 * (size_t)mb + part_elems) + ritz_eig_scratch_bytes((int)N, (int)mb, (int)mb) +
                        16 * 256;
   DevBuf buf;
   if (cudaMalloc(&buf.p, bytes) != cudaSuccess) {
@@ -922,7 +922,7 @@ rbgs_status rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int6
   double* res = (double*)take(8 * (size_t)mb);
   double* norms = (double*)take(8 * (size_t)mb);
   double* part = (double*)take(8 * part_elems);
-  void* scr = take(ritz_eig_scratch_bytes((int)N));
+  void* scr = take(ritz_eig_scratch_bytes((int)N, (int)mb, (int)mb));
   int* status = (int*)take(256);
   if (f64) s = cast_cols_t<double, double>(n, mb, B0, ldb, (double*)Bb, n, st);
   else s = cast_cols_t<double, float>(n, mb, B0, ldb, (float*)Bb, n, st);
