@@ -86,7 +86,10 @@ typedef struct {
   int32_t fine;        /* FP32 / TF32X3 / F16X3: 1 = the sketch-space steps (P and S stored,
                           step-2 least squares, block Cholesky QR, R) in FP64 (the
                           paper's u_fine); 0 = in FP32                                  */
-  int32_t reserved;
+  int32_t interblock;  /* steps 4-5: 0 or 5 = Alg. 5 (the sketch of Q'_i taken implicitly as
+                          P_i - S R, one tall pass per block); 4 = Alg. 4 (RCholeskyQR on
+                          the explicit sketch Theta Q'_i: the projection, a sketch, and an
+                          in-place scaling by R_ii^{-1}, two tall passes per block)      */
 } rbgs_opts;
 
 typedef struct {

@@ -252,7 +252,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       need = cv.off + 256;
       continue;
     }
-    TS *Rii = sm[5], *Riinv = sm[6], *R2ii = sm[7], *R2iinv = sm[8];
+    TS *Rii = sm[5], *Riinv = sm[6], *R2ii = sm[7], *R2iinv = sm[8], *Ieye = sm[9];
+    const bool alg4 = o.interblock == 4;
     int* brk = flags;          // breakdown
     int* active = flags + 1;   // second pass on/off for this block
     int* npass2 = flags + 2;   // number of second passes
@@ -284,31 +285,33 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     rbgs_status s;
     // The tall update in two parts: the small preparation of its G operand
     // (splits and scales) and the tall kernel itself, which alone is timed.
-    auto tall_prep = [&](int64_t c, const int* act, const TS* sraw, bool split_out) -> rbgs_status {
+    // c: basis columns read; cout: the column of Q the result occupies (where
+    // the pre-split copy goes).
+    auto tall_prep = [&](int64_t c, int64_t cout, const int* act, const TS* sraw, bool split_out) -> rbgs_status {
       if (mode == 2)
-        return h3_prepare<TS>(c, mb, Gd, c + mb, sraw, k, nullptr, nullptr, h3_shift(c, mb, split_out), Bh, hsc,
+        return h3_prepare<TS>(c, mb, Gd, c + mb, sraw, k, nullptr, nullptr, h3_shift(cout, mb, split_out), Bh, hsc,
                               act, st);
       if (mode == 1) return tc_split_g(c + mb, mb, Gd, c + mb, Gsplit, act, st);
       return RBGS_OK;
     };
-    auto tall_run = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act,
+    auto tall_run = [&](int64_t c, int64_t cout, const T* X2src, int64_t ldx2, T* out, const int* act,
                         bool split_out) -> rbgs_status {
       if (mode == 2)
         return tall_update_h3(n, c, mb, Qs, h3_nch_row(m), (const float*)X2src, ldx2, Bh, hsc, (float*)out, ldq,
-                              split_out ? Qs : nullptr, c, h3_shift(c, mb, split_out), act, tmo, st);
+                              split_out ? Qs : nullptr, cout, h3_shift(cout, mb, split_out), act, tmo, st);
       if (mode == 1)
         return tall_update_tc(n, c, mb, (const float*)Q, ldq, (const float*)X2src, ldx2, Gsplit, (float*)out, ldq,
                               act, tmo, st);
       return tall_update_simt<T>(n, c, mb, Q, ldq, X2src, ldx2, Gmat, c + mb, out, ldq, act, st);
     };
-    auto tall = [&](int64_t c, const T* X2src, int64_t ldx2, T* out, const int* act, const TS* sraw,
+    auto tall = [&](int64_t c, int64_t cout, const T* X2src, int64_t ldx2, T* out, const int* act, const TS* sraw,
                     bool split_out) -> rbgs_status {
-      rbgs_status r0 = tall_prep(c, act, sraw, split_out);
+      rbgs_status r0 = tall_prep(c, cout, act, sraw, split_out);
       if (r0) return r0;
-      if (!timing) return tall_run(c, X2src, ldx2, out, act, split_out);
+      if (!timing) return tall_run(c, cout, X2src, ldx2, out, act, split_out);
       TallEv e;
       e.bytes = (double)sizeof(T) * (double)n * (double)(c + 2 * mb);
-      e.blk = c / mb;
+      e.blk = cout / mb;
       e.pass2 = act != nullptr;
       RBGS_CUDA_TRY(cudaEventCreate(&e.a));
       if (cudaEventCreate(&e.b) != cudaSuccess) {
@@ -317,7 +320,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       }
       evs.push_back(e);
       RBGS_CUDA_TRY(cudaEventRecord(e.a, st));
-      rbgs_status r = tall_run(c, X2src, ldx2, out, act, split_out);
+      rbgs_status r = tall_run(c, cout, X2src, ldx2, out, act, split_out);
       RBGS_CUDA_TRY(cudaEventRecord(e.b, st));
       return r;
     };
@@ -325,6 +328,30 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
                       const int* act) -> rbgs_status {
       if (tensor) return assemble_g<TS, double>(c, mb, Rc, m, Rd, Rdinv, Gd, c + mb, Rcol, ldr, act, st);
       return assemble_g<TS, T>(c, mb, Rc, m, Rd, Rdinv, Gmat, c + mb, Rcol, ldr, act, st);
+    };
+    if (alg4) {  // the identity, for the projection G = [-X; I]
+      std::vector<TS> eye((size_t)mb * mb, (TS)0);
+      for (int j = 0; j < mb; ++j) eye[(size_t)j * mb + j] = (TS)1;
+      RBGS_CUDA_TRY(cudaMemcpyAsync(Ieye, eye.data(), sizeof(TS) * eye.size(), cudaMemcpyHostToDevice, st));
+      RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    // Steps 4-5 by Alg. 4 (RCholeskyQR on the explicit sketch) for the block
+    // src - Q_{1:c} Xc written to Qo (column c of Q): the projection with
+    // G = [-Xc; I], its sketch S'_i = Theta Q'_i, Cholesky QR of S'_i (one or two
+    // rounds) giving Rd and Rd^{-1}, the in-place scaling Q_i = Q'_i Rd^{-1}, and
+    // step 5, Sout = Theta Q_i.
+    auto alg4_pass = [&](int64_t c, const TS* Xc, const T* src, int64_t ldsrc, T* Qo, const TS* sraw, bool one_round,
+                         TS* Rd, TS* Rdinv, TS* Sout, bool split_final, const int* act) -> rbgs_status {
+      rbgs_status r;
+      if ((r = make_g(c, Xc, Ieye, Ieye, nullptr, act))) return r;
+      if ((r = tall(c, c, src, ldsrc, Qo, act, sraw, false))) return r;
+      if ((r = sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sp, k, skscr, sk_bytes, st, act))) return r;
+      if (one_round) r = cholqr1<TS>(k, mb, Sp, sm, partf, brk, act, st, Rd, Rdinv);
+      else r = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, act, st, Rd, Rdinv, need2, n2count);
+      if (r) return r;
+      if ((r = make_g(0, nullptr, Rd, Rdinv, nullptr, act))) return r;
+      if ((r = tall(0, c, Qo, ldq, Qo, act, Sp, split_final))) return r;
+      return sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sout, k, skscr, sk_bytes, st, act);
     };
 
     // Step 1 of block i + 1 (the sketch of W_{i+1}) depends on nothing in block
@@ -415,15 +442,21 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       } else {
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
       }
-      if (provisional) s = cholqr1<TS>(k, mb, Spc, sm, partf, brk, nullptr, st, Rii, Riinv);
-      else s = cholqr2<TS>(k, mb, Spc, Res, sm, partf, brk, nullptr, st, Rii, Riinv, need2, n2count);
-      if (s) return s;
-      if ((s = make_g(c, Xc, Rii, Riinv, Rcol, nullptr))) return s;
-      // step 3 fused with the triangular solve
       // (the split copy of a provisional result is not kept: the second pass rereads it as FP32)
-      if ((s = tall(c, Wi, ldwi, Qi, nullptr, Pi, !(o.reorth == 1 && c > 0)))) return s;
-      // step 5 (the sketch of W_{i+1}, step 1 of the next block, runs on the side stream)
-      if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st))) return s;
+      const bool split1 = !(o.reorth == 1 && c > 0);
+      if (alg4) {
+        if ((s = alg4_pass(c, Xc, Wi, ldwi, Qi, Pi, provisional, Rii, Riinv, Si, split1, nullptr))) return s;
+        if ((s = make_g(c, Xc, Rii, Riinv, Rcol, nullptr))) return s;  // the R column (G is not used again)
+      } else {
+        if (provisional) s = cholqr1<TS>(k, mb, Spc, sm, partf, brk, nullptr, st, Rii, Riinv);
+        else s = cholqr2<TS>(k, mb, Spc, Res, sm, partf, brk, nullptr, st, Rii, Riinv, need2, n2count);
+        if (s) return s;
+        if ((s = make_g(c, Xc, Rii, Riinv, Rcol, nullptr))) return s;
+        // step 3 fused with the triangular solve
+        if ((s = tall(c, c, Wi, ldwi, Qi, nullptr, Pi, split1))) return s;
+        // step 5 (the sketch of W_{i+1}, step 1 of the next block, runs on the side stream)
+        if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st))) return s;
+      }
       // optional second projection pass
       if (o.reorth && c > 0) {
         s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Si, k, 0.0, X2, m, partf, kPartElems, nullptr, st);
@@ -436,13 +469,18 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
           s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Res, k, 1.0, X2, m, partf, kPartElems, active, st);
           if (s) return s;
         }
-        RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
-        s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Sp, k, partf, kPartElems, active, st);
-        if (s) return s;
-        if ((s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, active, st, R2ii, R2iinv, need2, n2count))) return s;
-        if ((s = make_g(c, X2, R2ii, R2iinv, nullptr, active))) return s;
-        if ((s = tall(c, Qi, ldq, Qi, active, Si, true))) return s;
-        if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st, active))) return s;
+        if (alg4) {
+          if ((s = alg4_pass(c, X2, Qi, ldq, Qi, Si, false, R2ii, R2iinv, Si, true, active))) return s;
+        } else {
+          RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
+          s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Sp, k, partf, kPartElems, active, st);
+          if (s) return s;
+          if ((s = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, active, st, R2ii, R2iinv, need2, n2count))) return s;
+          if ((s = make_g(c, X2, R2ii, R2iinv, nullptr, active))) return s;
+          if ((s = tall(c, c, Qi, ldq, Qi, active, Si, true))) return s;
+          if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Qi, ldq, mb, Si, k, skscr, sk_bytes, st, active)))
+            return s;
+        }
         if ((s = reorth_update_r<TS>(c, mb, X2, m, R2ii, Rcol, ldr, tmp, active, st))) return s;
       }
     }
@@ -559,6 +597,7 @@ rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb
   if (n < 1 || n >= ((int64_t)1 << 31) || m < 1 || mb < 1 || mb > 64 || m % mb != 0) return RBGS_EINVAL;
   if (ldw < n || ldq < n || ldr < m || k < m) return RBGS_EINVAL;
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2) return RBGS_EINVAL;
+  if (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) return RBGS_EINVAL;
   if (sketch == RBGS_SK_SRHT) {
     int64_t np = 1;
     while (np < n) np <<= 1;
@@ -785,7 +824,8 @@ rbgs_status krylov_solve(int method, const rbgs_op* op, const double* B, int64_t
   rbgs_opts o;
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
-  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1)
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5))
     return RBGS_EINVAL;
   o.sync = 1;  // one synchronisation per cycle (breakdown and convergence are read on the host)
   o.timing = 0;
@@ -889,7 +929,8 @@ rbgs_status rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int6
   rbgs_opts o;
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
-  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1)
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5))
     return RBGS_EINVAL;
   o.sync = 1;
   o.timing = 0;
@@ -997,7 +1038,8 @@ rbgs_status rbgs_block_arnoldi(const rbgs_op* op, const void* B, int64_t ldb, in
   const int64_t n = op->nx * op->ny, m = p * mb;
   if (!B || !Q || !R || mb < 1 || mb > 64 || p < 1 || ldb < n || ldq < n || ldr < m) return RBGS_EINVAL;
   if ((s = check_sketch(sketch, n, k, m))) return s;
-  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1)
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5))
     return RBGS_EINVAL;
   const size_t es = o.prec == RBGS_P_FP64 ? 8 : 4;
   if (o.prec >= RBGS_P_TF32X3 && (((uintptr_t)B & 15) || ((uintptr_t)Q & 15) || (ldb % 4) || (ldq % 4)))

@@ -171,6 +171,38 @@ def test_fp64_single_cholesky_round_when_well_conditioned(rb):
     assert st32.chol_rounds2 == m // mb
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f16x3", "tf32x3"])
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_rbgs_alg4_matches_oracle(rb, prec, reorth):
+    """Steps 4-5 by Alg. 4 (RCholeskyQR on the explicit sketch Theta Q'_i:
+    projection, sketch, Cholesky QR, in-place scaling by R_ii^{-1}) against
+    the oracle's Alg. 4."""
+    n, m, mb, kind, k = 3000, 48, 16, "srht", 200
+    cond = 1e4 if prec == "fp64" else 1e3
+    W = synth.svd_matrix(n, m, cond, 77)
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Qd, Rd, st = rb.rbgs_qr(dev(W, td), mb, kind, k, 5, prec=prec, ls_iters=3, reorth=reorth, interblock=4,
+                            certify=True, fine=prec != "fp64")
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, 5, variant=4, ls="richardson", ls_iters=3, reorth=bool(reorth),
+                      ls_iters_first=1)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    fact = oracle.factorization_error(W, Q, R)
+    ortho = oracle.sketched_orthogonality(Q, kind, k, 5)[0]
+    if prec == "fp64":
+        tol = 1e-13 * cond
+        assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+        assert np.abs(Q - ref["Q"]).max() <= tol * np.abs(ref["Q"]).max()
+        assert fact < 1e-14 and ortho < 1e-12
+    else:
+        assert fact < 2e-6 and ortho < (1e-4 if reorth else 1e-3)
+        assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
+    if reorth:
+        assert st.passes2 == m // mb - 1
+
+
 def test_c1_config_fp64(rb):
     """n = 1e4, m = 100, m_p = 10, Gaussian k = 200, cond(W) = 1e8:
     ||W - QR||/||W|| <= 1e-13 and sketched orthogonality <= 1e-12 with the
