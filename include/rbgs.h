@@ -116,7 +116,8 @@ RBGS_API void rbgs_opts_default(rbgs_opts* opts);
  *  W    device, n x m, ld ldw >= n, float or double per opts->prec (read only)
  *  n    rows, 1 <= n < 2^31
  *  m    columns, m = mb * p
- *  mb   block size m_p, 1 <= mb <= 64, mb divides m
+ *  mb   block size m_p, 1 <= mb <= 64; when mb does not divide m the last of
+ *       the p = ceil(m / mb) blocks holds the m - (p - 1) mb remaining columns
  *  sketch, k, seed   Theta (k x n); m <= k; k <= n (Gaussian, Rademacher) or
  *       k <= n' = 2^ceil(log2 n) (SRHT)
  *  Q    device, n x m, ld ldq >= n, same type as W; receives the

@@ -660,7 +660,8 @@ static int interblock(int variant, int64_t n, int64_t mp, double* Qp, int64_t ld
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 2.  W n x m (ldw), block size mp, m = mp * p.  Outputs Q (n x m, ldq),
+/* Alg. 2.  W n x m (ldw), block size mp (the last of the p = ceil(m / mp)
+ * blocks takes the remaining columns).  Outputs Q (n x m, ldq),
  * R (m x m, ldr, upper triangular), and, when non-NULL, S = Theta Q and
  * P = Theta W (k x m, ld k).  stats (when non-NULL) receives
  * {Delta, Delta~, number of second passes}.  With reorth, ls_iters_first > 0
@@ -700,10 +701,13 @@ static int rbgs_core(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t
                      uint64_t seed, int variant, int ls, int ls_iters, int ls_iters_first, int reorth,
                      const or_stencil* op, double* Q, int64_t ldq, double* R, int64_t ldr, double* S_out,
                      double* P_out, double* stats) {
-  if (mp <= 0 || m % mp != 0 || n < 1 || k < m || ldw < n || ldq < n || ldr < m) return -1;
+  /* m need not be a multiple of mp: the last block takes the m - (p-1) mp
+     remaining columns (the Arnoldi process needs equal blocks) */
+  if (mp <= 0 || n < 1 || k < m || ldw < n || ldq < n || ldr < m) return -1;
+  if (op && m % mp != 0) return -1;
   if (theta == OR_THETA_SRHT && k > or_srht_padded(n)) return -1;
   if (theta != OR_THETA_SRHT && k > n) return -1;
-  int64_t p = m / mp;
+  int64_t p = (m + mp - 1) / mp;
   double* S = (double*)calloc((size_t)(k * m), sizeof(double));
   double* P = (double*)calloc((size_t)(k * m), sizeof(double));
   double* Spp = (double*)malloc(sizeof(double) * (size_t)(k * mp));
@@ -721,10 +725,11 @@ static int rbgs_core(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t
 
   for (int64_t blk = 0; blk < p; ++blk) {
     int64_t c = blk * mp; /* columns already orthogonalized */
+    const int64_t w = m - c < mp ? m - c : mp; /* this block's width */
     const double* Wi = W + c * ldw;
     int64_t ldwi = ldw;
     if (op && blk > 0) { /* Alg. 7, step 2: W_i = A Q_{i-1} */
-      or_stencil5_apply(op, Q + (c - mp) * ldq, ldq, mp, Wop, n);
+      or_stencil5_apply(op, Q + (c - mp) * ldq, ldq, w, Wop, n);
       Wi = Wop;
       ldwi = n;
     }
@@ -732,44 +737,44 @@ static int rbgs_core(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t
     double* Pi = P + c * k;
     double* Si = S + c * k;
     /* step 1: P_i = Theta W_i */
-    or_theta_apply(theta, k, n, seed, Wi, ldwi, mp, Pi, k);
+    or_theta_apply(theta, k, n, seed, Wi, ldwi, w, Pi, k);
     /* step 2: R_{1:i-1,i} = argmin ||S_{1:i-1} Y - P_i||_F (with a second pass
        to follow, the first may use its own iteration count) */
-    if (c > 0 && solve_ls(ls, (reorth && ls_iters_first > 0) ? ls_iters_first : ls_iters, k, c, S, k, Pi, k, mp, Rc,
+    if (c > 0 && solve_ls(ls, (reorth && ls_iters_first > 0) ? ls_iters_first : ls_iters, k, c, S, k, Pi, k, w, Rc,
                           m))
       rc = -2;
     /* step 3: Q'_i = W_i - Q_{1:i-1} R_{1:i-1,i} */
-    project(n, c, mp, Wi, ldwi, Q, ldq, Rc, m, Qi, ldq);
+    project(n, c, w, Wi, ldwi, Q, ldq, Rc, m, Qi, ldq);
     /* implicit sketch for Alg. 5: S'_i = P_i - S_{1:i-1} R_{1:i-1,i} */
-    if (c > 0) gemm(0, 0, k, mp, c, 1.0, S, k, Rc, m, 0.0, Spp, k);
-    for (int64_t j = 0; j < mp; ++j)
+    if (c > 0) gemm(0, 0, k, w, c, 1.0, S, k, Rc, m, 0.0, Spp, k);
+    for (int64_t j = 0; j < w; ++j)
       for (int64_t i = 0; i < k; ++i) Spp[i + j * k] = Pi[i + j * k] - (c > 0 ? Spp[i + j * k] : 0.0);
     /* steps 4-5 */
-    if (interblock(variant, n, mp, Qi, ldq, Spp, k, theta, k, seed, Rii, mp, Si, k)) rc = -2;
+    if (interblock(variant, n, w, Qi, ldq, Spp, k, theta, k, seed, Rii, mp, Si, k)) rc = -2;
 
     if (reorth && c > 0) {
       /* second pass (extension): treat Q_i as the block to orthogonalize. */
       ++passes2;
-      if (solve_ls(ls, ls_iters, k, c, S, k, Si, k, mp, R2, m)) rc = -2;
-      for (int64_t j = 0; j < mp; ++j)
+      if (solve_ls(ls, ls_iters, k, c, S, k, Si, k, w, R2, m)) rc = -2;
+      for (int64_t j = 0; j < w; ++j)
         for (int64_t i = 0; i < n; ++i) Qtmp[i + j * n] = Qi[i + j * ldq];
-      project(n, c, mp, Qtmp, n, Q, ldq, R2, m, Qi, ldq);
-      gemm(0, 0, k, mp, c, 1.0, S, k, R2, m, 0.0, Spp, k);
-      for (int64_t j = 0; j < mp; ++j)
+      project(n, c, w, Qtmp, n, Q, ldq, R2, m, Qi, ldq);
+      gemm(0, 0, k, w, c, 1.0, S, k, R2, m, 0.0, Spp, k);
+      for (int64_t j = 0; j < w; ++j)
         for (int64_t i = 0; i < k; ++i) Spp[i + j * k] = Si[i + j * k] - Spp[i + j * k];
-      if (interblock(variant, n, mp, Qi, ldq, Spp, k, theta, k, seed, R2ii, mp, Si, k)) rc = -2;
+      if (interblock(variant, n, w, Qi, ldq, Spp, k, theta, k, seed, R2ii, mp, Si, k)) rc = -2;
       /* R_{1:i-1,i} += R2 R_ii ; R_ii <- R2_ii R_ii */
-      gemm(0, 0, c, mp, mp, 1.0, R2, m, Rii, mp, 0.0, Tmp, m);
-      for (int64_t j = 0; j < mp; ++j)
+      gemm(0, 0, c, w, w, 1.0, R2, m, Rii, mp, 0.0, Tmp, m);
+      for (int64_t j = 0; j < w; ++j)
         for (int64_t i = 0; i < c; ++i) Rc[i + j * m] += Tmp[i + j * m];
-      gemm(0, 0, mp, mp, mp, 1.0, R2ii, mp, Rii, mp, 0.0, Tmp, mp);
-      for (int64_t j = 0; j < mp; ++j)
-        for (int64_t i = 0; i < mp; ++i) Rii[i + j * mp] = Tmp[i + j * mp];
+      gemm(0, 0, w, w, w, 1.0, R2ii, mp, Rii, mp, 0.0, Tmp, mp);
+      for (int64_t j = 0; j < w; ++j)
+        for (int64_t i = 0; i < w; ++i) Rii[i + j * mp] = Tmp[i + j * mp];
     }
     /* assemble column block i of R */
-    for (int64_t j = 0; j < mp; ++j) {
+    for (int64_t j = 0; j < w; ++j) {
       for (int64_t i = 0; i < c; ++i) R[i + (c + j) * ldr] = Rc[i + j * m];
-      for (int64_t i = 0; i < mp; ++i) R[c + i + (c + j) * ldr] = Rii[i + j * mp];
+      for (int64_t i = 0; i < w; ++i) R[c + i + (c + j) * ldr] = Rii[i + j * mp];
     }
   }
   if (stats) {

@@ -205,7 +205,11 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
   // mode 0: SIMT tall product; 1: TF32X3 tensor cores; 2: F16X3 tensor cores with the pre-split basis
   const bool tensor = mode != 0;
   cudaStream_t st = (cudaStream_t)o.stream;
-  const int64_t p = m / mb;
+  // m need not be a multiple of mb: the last of the p blocks takes the
+  // m - (p - 1) mb remaining columns.  Inside the block loop mb is the width of
+  // the current block (every helper below reads it); mbf is the full width.
+  const int mbf = mb;
+  const int64_t p = (m + mb - 1) / mb;
   const int l = o.ls_iters < 1 ? 1 : o.ls_iters;
   const bool fp64 = sizeof(T) == 8;
   const size_t sk_bytes = sketch_scratch_bytes(sketch, k, n, 2 * mb, fp64) + 256;
@@ -329,12 +333,15 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       if (tensor) return assemble_g<TS, double>(c, mb, Rc, m, Rd, Rdinv, Gd, c + mb, Rcol, ldr, act, st);
       return assemble_g<TS, T>(c, mb, Rc, m, Rd, Rdinv, Gmat, c + mb, Rcol, ldr, act, st);
     };
-    if (alg4) {  // the identity, for the projection G = [-X; I]
-      std::vector<TS> eye((size_t)mb * mb, (TS)0);
-      for (int j = 0; j < mb; ++j) eye[(size_t)j * mb + j] = (TS)1;
+    // the identity (ld w), for the projection G = [-X; I] of Alg. 4
+    auto set_eye = [&](int w) -> rbgs_status {
+      std::vector<TS> eye((size_t)w * w, (TS)0);
+      for (int j = 0; j < w; ++j) eye[(size_t)j * w + j] = (TS)1;
       RBGS_CUDA_TRY(cudaMemcpyAsync(Ieye, eye.data(), sizeof(TS) * eye.size(), cudaMemcpyHostToDevice, st));
       RBGS_CUDA_TRY(cudaStreamSynchronize(st));
-    }
+      return RBGS_OK;
+    };
+    if (alg4 && (s = set_eye(mb))) return s;
     // Steps 4-5 by Alg. 4 (RCholeskyQR on the explicit sketch) for the block
     // src - Q_{1:c} Xc written to Qo (column c of Q): the projection with
     // G = [-Xc; I], its sketch S'_i = Theta Q'_i, Cholesky QR of S'_i (one or two
@@ -372,13 +379,18 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       for (auto& e : evw) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     // step 1 of the first block
-    if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, W, ldw, mb, P, k, skscr, sk_bytes, st))) return s;
+    if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, W, ldw, (int64_t)std::min<int64_t>(mbf, m), P, k, skscr,
+                                   sk_bytes, st)))
+      return s;
     if (ahead) {  // the side stream starts after everything enqueued here so far
       RBGS_CUDA_TRY(cudaEventRecord(evw[p], st));
       RBGS_CUDA_TRY(cudaStreamWaitEvent(st2, evw[p], 0));
     }
     for (int64_t blk = 0; blk < p; ++blk) {
-      const int64_t c = blk * mb;
+      const int64_t c = blk * mbf;
+      mb = (int)std::min<int64_t>(mbf, m - c);  // this block's width
+      if (alg4 && mb != mbf && (s = set_eye(mb))) return s;  // the narrower last block
+      const int64_t wnext = blk + 1 < p ? std::min<int64_t>(mbf, m - c - mbf) : 0;
       const T* Wi = W + c * ldw;
       int64_t ldwi = ldw;
       T* Qi = Q + c * ldq;
@@ -386,31 +398,34 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       TS* Si = S + c * k;
       double* Rcol = R + c * ldr;
       if (op && blk > 0) {  // Alg. 7, step 2: W_i = A Q_{i-1}, then its sketch (step 1 of the block)
-        if ((s = stencil_apply_t<T, T>(*op, Qi - mb * ldq, ldq, mb, Qi, ldq, st))) return s;
+        if ((s = stencil_apply_t<T, T>(*op, Qi - mbf * ldq, ldq, mb, Qi, ldq, st))) return s;
         Wi = Qi;
         ldwi = ldq;
         if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi, ldwi, mb, Pi, k, skscr, sk_bytes, st))) return s;
       }
       if (ahead && blk + 1 < p) {
-        s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi + mb * ldw, ldw, mb, Pi + mb * k, k, skscr2, sk_bytes, st2);
+        s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi + mbf * ldw, ldw, wnext, Pi + mbf * k, k, skscr2, sk_bytes,
+                                  st2);
         if (s) return s;
         if (look) {
           // Step 2 of block i + 1 (one Richardson step, X = S^T P_{i+1}) over
           // the columns of S that are final once block i - 1 is done:
           // X_old = S_{1:i-1}^T P_{i+1} and Sp_old = P_{i+1} - S_{1:i-1} X_old.
           // Block i + 1 adds the block row of S_i itself.
-          const TS* Pn = Pi + mb * k;
+          const TS* Pn = Pi + mbf * k;
           TS* Xn = ((blk + 1) & 1) ? Xalt : X;
           TS* So = Spo[(blk + 1) & 1];
           if (c > 0) {  // everything enqueued here so far is block i - 1 and before
             RBGS_CUDA_TRY(cudaEventRecord(evw[p + 1], st));
             RBGS_CUDA_TRY(cudaStreamWaitEvent(st2, evw[p + 1], 0));
-            s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Pn, k, 0.0, Xn, m, partf2, kPartElems, nullptr, st2);
+            s = small_gemm<TS, TS, TS>(1, c, wnext, k, 1.0, S, k, Pn, k, 0.0, Xn, m, partf2, kPartElems, nullptr,
+                                       st2);
             if (s) return s;
           }
-          RBGS_CUDA_TRY(cudaMemcpyAsync(So, Pn, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st2));
+          RBGS_CUDA_TRY(cudaMemcpyAsync(So, Pn, sizeof(TS) * k * wnext, cudaMemcpyDeviceToDevice, st2));
           if (c > 0) {
-            s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, Xn, m, 1.0, So, k, partf2, kPartElems, nullptr, st2);
+            s = small_gemm<TS, TS, TS>(0, k, wnext, c, -1.0, S, k, Xn, m, 1.0, So, k, partf2, kPartElems, nullptr,
+                                       st2);
             if (s) return s;
           }
         }
@@ -425,13 +440,13 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       TS* Xc = X;   // R_{1:i-1,i}
       TS* Spc = Sp; // S'_i = P_i - S_{1:i-1} R_{1:i-1,i}
       if (c > 0 && look) {  // finish the look-ahead with the block row of S_{i-1}
-        const int64_t c0 = c - mb;
+        const int64_t c0 = c - mbf;  // the previous block is a full one
         Xc = (blk & 1) ? Xalt : X;
         Spc = Spo[blk & 1];
-        s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, S + c0 * k, k, Pi, k, 0.0, Xc + c0, m, partf, kPartElems,
+        s = small_gemm<TS, TS, TS>(1, mbf, mb, k, 1.0, S + c0 * k, k, Pi, k, 0.0, Xc + c0, m, partf, kPartElems,
                                    nullptr, st);
         if (s) return s;
-        s = small_gemm<TS, TS, TS>(0, k, mb, mb, -1.0, S + c0 * k, k, Xc + c0, m, 1.0, Spc, k, partf, kPartElems,
+        s = small_gemm<TS, TS, TS>(0, k, mb, mbf, -1.0, S + c0 * k, k, Xc + c0, m, 1.0, Spc, k, partf, kPartElems,
                                    nullptr, st);
         if (s) return s;
       } else if (c > 0) {
@@ -484,6 +499,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         if ((s = reorth_update_r<TS>(c, mb, X2, m, R2ii, Rcol, ldr, tmp, active, st))) return s;
       }
     }
+    mb = mbf;
     RBGS_LAUNCH_CHECK();
 
     // step 6 (optional): Delta = ||I - S^T S||_F, Delta~ = ||P - S R||_F / ||P||_F
@@ -594,7 +610,7 @@ rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
   if (!W || !Q || !R) return RBGS_EINVAL;
-  if (n < 1 || n >= ((int64_t)1 << 31) || m < 1 || mb < 1 || mb > 64 || m % mb != 0) return RBGS_EINVAL;
+  if (n < 1 || n >= ((int64_t)1 << 31) || m < 1 || mb < 1 || mb > 64) return RBGS_EINVAL;
   if (ldw < n || ldq < n || ldr < m || k < m) return RBGS_EINVAL;
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2) return RBGS_EINVAL;
   if (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) return RBGS_EINVAL;

@@ -59,8 +59,8 @@ def test_argument_checks_need_no_device(lib):
     fake = ctypes.c_void_p(0x1000)
     other = ctypes.c_void_p(0x10000000)
     rr = ctypes.c_void_p(0x20000000)
-    # m not a multiple of mb
-    assert lib.rbgs_qr(fake, 100, 10, 100, 4, 0, 20, 0, other, 100, rr, 10, None, None) == 1
+    # no block width
+    assert lib.rbgs_qr(fake, 100, 10, 100, 0, 0, 20, 0, other, 100, rr, 10, None, None) == 1
     # k < m
     assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 4, 0, other, 100, rr, 8, None, None) == 1
     # k > n for a dense sketch

@@ -203,6 +203,38 @@ def test_rbgs_alg4_matches_oracle(rb, prec, reorth):
         assert st.passes2 == m // mb - 1
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3", "tf32x3"])
+@pytest.mark.parametrize("interblock", [5, 4])
+@pytest.mark.parametrize("m,mb,reorth", [(50, 16, 0), (60, 50, 1), (9, 4, 1)])
+def test_rbgs_ragged_last_block_matches_oracle(rb, prec, interblock, m, mb, reorth):
+    """m not a multiple of m_p: the last block takes the remaining columns
+    (a narrower tall update, sketch and Cholesky QR) on every precision path."""
+    n, kind, k = 2048, "srht", 4 * m
+    cond = 1e4 if prec == "fp64" else 1e3
+    W = synth.svd_matrix(n, m, cond, 90 + m)
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Qd, Rd, st = rb.rbgs_qr(dev(W, td), mb, kind, k, 7, prec=prec, ls_iters=3, reorth=reorth,
+                            interblock=interblock, fine=prec != "fp64")
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, 7, variant=interblock, ls="richardson", ls_iters=3, reorth=bool(reorth),
+                      ls_iters_first=1)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    fact = oracle.factorization_error(W, Q, R)
+    ortho = oracle.sketched_orthogonality(Q, kind, k, 7)[0]
+    if prec == "fp64":
+        tol = 1e-13 * cond
+        assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+        assert np.abs(Q - ref["Q"]).max() <= tol * np.abs(ref["Q"]).max()
+        assert fact < 1e-14 and ortho < 1e-12
+    else:
+        assert fact < 2e-6 and ortho < (1e-4 if reorth else 1e-3)
+        assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
+    if reorth:
+        assert st.passes2 == (m + mb - 1) // mb - 1
+
+
 def test_c1_config_fp64(rb):
     """n = 1e4, m = 100, m_p = 10, Gaussian k = 200, cond(W) = 1e8:
     ||W - QR||/||W|| <= 1e-13 and sketched orthogonality <= 1e-12 with the
@@ -245,7 +277,7 @@ def test_breakdown_reported(rb):
 def test_invalid_arguments(rb):
     W = dev(synth.gaussian(100, 8, 1))
     with pytest.raises(rb.RbgsError):
-        rb.rbgs_qr(W, 3, "gauss", 16, 0, prec="fp64")     # m % mb != 0
+        rb.rbgs_qr(W, 65, "gauss", 16, 0, prec="fp64")    # mb > 64
     with pytest.raises(rb.RbgsError):
         rb.rbgs_qr(W, 4, "gauss", 101, 0, prec="fp64")    # k > n
     with pytest.raises(rb.RbgsError):

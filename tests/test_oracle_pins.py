@@ -240,6 +240,29 @@ def test_rbgs_reaches_closed_form(kind, variant):
     np.testing.assert_allclose(out["Q"], Qc, rtol=0, atol=1e-9 * np.abs(Qc).max())
 
 
+@pytest.mark.parametrize("variant", [4, 5, 6])
+@pytest.mark.parametrize("reorth", [False, True])
+@pytest.mark.parametrize("m,mp", [(23, 6), (25, 8), (7, 4)])
+def test_rbgs_ragged_last_block_reaches_closed_form(variant, reorth, m, mp):
+    """m not a multiple of m_p: the last block holds the remaining columns.
+    The closed form (R of Theta W, Q = W R^{-1}) does not depend on the
+    blocking, so the ragged factorization must reach it; with Theta = I it is
+    numpy's QR."""
+    n, k = 1200, 100
+    W = synth.svd_matrix(n, m, 1e3, m + mp)
+    out = oracle.rbgs(W, mp, "srht", k, 3, variant=variant, ls="householder", reorth=reorth)
+    Qc, Rc, rc = oracle.rcholqr(W, "srht", k, 3)
+    assert rc == 0 and out["rc"] == 0
+    np.testing.assert_allclose(out["R"], Rc, rtol=0, atol=1e-11 * np.abs(Rc).max())
+    np.testing.assert_allclose(out["Q"], Qc, rtol=0, atol=1e-9 * np.abs(Qc).max())
+    if reorth:
+        assert out["passes2"] == (m + mp - 1) // mp - 1
+    ident = oracle.rbgs(W[:200], mp, "identity", 200, 0, variant=variant)
+    Qn, Rn = np.linalg.qr(W[:200])
+    sg = np.sign(np.diag(Rn))
+    np.testing.assert_allclose(ident["R"], sg[:, None] * Rn, atol=1e-12 * np.abs(Rn).max())
+
+
 @pytest.mark.parametrize("ls,iters", [("householder", 0), ("richardson", 5), ("cg", 20)])
 def test_rbgs_invariants(ls, iters):
     n, m, mp, k = 4000, 40, 8, 200
@@ -325,7 +348,9 @@ def test_ex1_matrix_factorization_error_near_machine_precision():
 def test_bad_arguments_rejected():
     W = np.zeros((10, 6))
     with pytest.raises(ValueError):
-        oracle.rbgs(W, 4, "gauss", 6, 0)  # m not a multiple of mp
+        oracle.rbgs(W, 0, "gauss", 6, 0)  # no block width
+    with pytest.raises(ValueError):
+        oracle.rbgs(W, 3, "gauss", 5, 0)  # k < m
     with pytest.raises(ValueError):
         oracle.rbgs(W, 3, "gauss", 11, 0)  # k > n for a dense sketch
     with pytest.raises(ValueError):
