@@ -391,6 +391,8 @@ def run_ours(args, cfg):
 
     if rank == 0 and world == 1 and not args.no_krylov:
         line["krylov_c4"] = krylov_c4(rb, dev, prec if prec != "fp64" else "f16x3")
+    if rank == 0 and world == 1 and not args.no_batched:
+        line["batched_c3"] = batched_c3(rb, dev, prec if prec != "fp64" else "f16x3")
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(cfg, args.ls_iters, args.reorth)
@@ -481,6 +483,50 @@ def krylov_c4(rb, dev, prec):
     return out
 
 
+def batched_c3(rb, dev, prec, count=32):
+    """Many independent factorizations in one call (rbgs_qr_batched): the first
+    `count` problems of the 256-problem workload (n ~ U[2e4, 2e5], m in
+    {64..256}, m_p in {16, 32}, Gaussian k = 2m, near-duplicate columns),
+    timed on 1 and on 8 internal streams, for the mixed path and the FP64
+    path.  Quality is sampled on two problems: ||W - QR|| / ||W|| and cond(Q).
+    The near-duplicates sit at the FP32 rounding level, outside the stability
+    hypothesis u_crs cond(W) < 1 for FP32 storage; the FP64 path keeps it."""
+    import torch
+    import synth
+
+    specs = synth.batch_specs(count)
+    out = {"workload": f"{count} problems of the 256-problem batch: n~U[2e4,2e5], m in {{64..256}}, "
+                       "m_p in {16,32}, Gaussian k=2m, every 8th column a 1e-7-perturbed duplicate",
+           "problems": count}
+    for label, pr, dt in (("mixed", prec, torch.float32), ("fp64", "fp64", torch.float64)):
+        Ws = [synth.near_duplicate_matrix_torch(n, m, 11 + i, device=dev, dtype=dt) for i, (n, m, _) in enumerate(specs)]
+        mbs = [mp for _, _, mp in specs]
+        ks = [2 * m for _, m, _ in specs]
+        seeds = [7 + i for i in range(count)]
+        kw = dict(ls_iters=1, reorth=1, fine=pr != "fp64")
+        res = {"prec": pr}
+        for ns in (1, 8):
+            rb.rbgs_qr_batched(Ws[:2], mbs[:2], ks[:2], seeds[:2], "gauss", prec=pr, nstreams=ns, **kw)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Qs, Rs, status, _ = rb.rbgs_qr_batched(Ws, mbs, ks, seeds, "gauss", prec=pr, nstreams=ns, **kw)
+            torch.cuda.synchronize()
+            dts = time.perf_counter() - t0
+            res[f"streams_{ns}"] = {"s": dts, "problems_per_s": count / dts,
+                                    "statuses_ok": sum(1 for x in status if x == 0)}
+        qual = []
+        for i in range(2):
+            Q = Qs[i].double()
+            fe = float(torch.linalg.norm(Ws[i].double() - Q @ Rs[i]) / torch.linalg.norm(Ws[i].double()))
+            sv = torch.linalg.svdvals(Q)
+            qual.append({"rel_factorization_error": fe, "cond_Q": float(sv[0] / sv[-1])})
+        res["quality_sample"] = qual
+        out[label] = res
+        del Ws, Qs, Rs
+        torch.cuda.empty_cache()
+    return out
+
+
 def _refill(W, cfg, dev, dtype):
     """W was overwritten by the e2e copies of itself; it holds the same values."""
     return W
@@ -535,6 +581,7 @@ def main(argv=None):
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-krylov", action="store_true", help="skip the block GMRES measurement on the stencil")
+    ap.add_argument("--no-batched", action="store_true", help="skip the many-small-problems measurement")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (smaller cases for profiler captures; recorded in config.workload)")
     args = ap.parse_args(argv)

@@ -131,6 +131,31 @@ RBGS_API rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, i
                     uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts* opts,
                     rbgs_stats* stats);
 
+/* Many independent factorizations in one call (the same sketch kind and
+ * options for all).  Each problem gives W, Q, R and its sizes as for rbgs_qr,
+ * and receives status (RBGS_OK, RBGS_EBREAKDOWN or RBGS_ETIMEOUT) and
+ * passes2.  The problems run on min(nstreams, count, 32) internal streams,
+ * each with its own workspace and side stream, problem i on stream i mod
+ * nstreams, with no host synchronisation before the end of the batch; the
+ * batch starts after the work already on opts->stream and that stream waits
+ * for it.  Every problem is checked as in rbgs_qr before any work starts
+ * (RBGS_EINVAL).  opts->sync, timing and certify are ignored.  Returns the
+ * first problem's error, else RBGS_OK.  Synchronous.  The paper has no
+ * batched form; this serves many small factorizations at once.          */
+typedef struct {
+  const void* W;  /* n x m, ldw (device, prec type) */
+  int64_t n, m, ldw, mb, k;
+  uint64_t seed;
+  void* Q;        /* n x m, ldq (device, prec type) */
+  int64_t ldq;
+  double* R;      /* m x m, ldr (device) */
+  int64_t ldr;
+  int32_t status; /* out */
+  int32_t passes2; /* out */
+} rbgs_problem;
+RBGS_API rbgs_status rbgs_qr_batched(rbgs_problem* probs, int64_t count, rbgs_sketch sketch, const rbgs_opts* opts,
+                                     int32_t nstreams);
+
 /* Y = Theta X (Sec. 2.3), the sketch of steps 1 and 5 of Alg. 2.
  *  X device n x ncols (ldx), double if prec == RBGS_P_FP64 else float.
  *  Y device k x ncols (ldy), double.  FP64 sums in double; other precisions

@@ -195,11 +195,22 @@ rbgs_status side_stream(cudaStream_t* out) {
   return RBGS_OK;
 }
 
+// Resources of one factorization when several run side by side (rbgs_qr_batched):
+// its own workspace and side stream instead of the per-device ones, and a device
+// slot that receives its status words.  need_out alone asks for the workspace size.
+struct QrCtx {
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t side = nullptr;
+  int* status_out = nullptr;  // 8 ints: breakdown, -, passes2, timeout, -, Cholesky second rounds
+  size_t* need_out = nullptr;
+};
+
 // T: storage of W and Q; TS: storage/arithmetic of the sketch space.
 template <class T, class TS>
 rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_sketch sketch, int64_t k,
                     uint64_t seed, T* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts& o, rbgs_stats* stats,
-                    int mode, const rbgs_op* op = nullptr) {
+                    int mode, const rbgs_op* op = nullptr, const QrCtx* ctx = nullptr) {
   // With op (Alg. 7, RBGS-Arnoldi): W holds only the first block B; every
   // later block is W_i = A Q_{i-1}, formed in the columns of Q_i.
   // mode 0: SIMT tall product; 1: TF32X3 tensor cores; 2: F16X3 tensor cores with the pre-split basis
@@ -220,8 +231,17 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
   for (int pass = 0; pass < 2; ++pass) {
     void* base = nullptr;
     if (pass == 1) {
-      rbgs_status s = workspace(need, &base);
-      if (s) return s;
+      if (ctx && ctx->need_out) {
+        *ctx->need_out = need;
+        return RBGS_OK;
+      }
+      if (ctx && ctx->ws) {
+        if (need > ctx->ws_bytes) return RBGS_ENOMEM;
+        base = ctx->ws;
+      } else {
+        rbgs_status s = workspace(need, &base);
+        if (s) return s;
+      }
     }
     Carver cv(pass == 0 ? nullptr : base);
     TS* S = cv.take<TS>((size_t)k * m);
@@ -374,7 +394,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     } evguard{&evw};
     const bool ahead = p > 1 && op == nullptr;  // the next block of W is known in advance
     if (ahead) {
-      if ((s = side_stream(&st2))) return s;
+      if (ctx && ctx->side) st2 = ctx->side;
+      else if ((s = side_stream(&st2))) return s;
       evw.resize((size_t)p + 2, nullptr);  // [p]: start, [p + 1]: end of the previous block
       for (auto& e : evw) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
@@ -544,6 +565,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       stats->delta_tilde = hv[1] > 0 ? hv[0] / hv[1] : 0.0;
       stats->certified = (stats->delta <= 0.1 && stats->delta_tilde <= 0.1) ? 1 : 0;
     }
+    if (ctx && ctx->status_out)
+      RBGS_CUDA_TRY(cudaMemcpyAsync(ctx->status_out, flags, 8 * sizeof(int), cudaMemcpyDeviceToDevice, st));
     if (o.sync || stats) {
       int hf[6] = {0, 0, 0, 0, 0, 0};
       RBGS_CUDA_TRY(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
@@ -603,12 +626,13 @@ int64_t rbgs_launch_count(void) { return rbgs::g_launches.load(); }
 
 const char* rbgs_version(void) { return "librbgs 0.1 (sm_103a)"; }
 
-rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch, int64_t k,
-                    uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts* opts,
-                    rbgs_stats* stats) {
-  rbgs_opts o;
-  if (opts) o = *opts;
-  else rbgs_opts_default(&o);
+}  // extern "C"
+
+namespace {
+
+// The argument checks of rbgs_qr (also applied to every problem of a batch).
+rbgs_status check_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch, int64_t k,
+                     const void* Q, int64_t ldq, const double* R, int64_t ldr, const rbgs_opts& o) {
   if (!W || !Q || !R) return RBGS_EINVAL;
   if (n < 1 || n >= ((int64_t)1 << 31) || m < 1 || mb < 1 || mb > 64) return RBGS_EINVAL;
   if (ldw < n || ldq < n || ldr < m || k < m) return RBGS_EINVAL;
@@ -626,18 +650,149 @@ rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb
   const size_t es = o.prec == RBGS_P_FP64 ? 8 : 4;
   if (ranges_overlap(W, es * (size_t)(ldw * (m - 1) + n), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
   if (ranges_overlap(R, 8 * (size_t)(ldr * (m - 1) + m), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
+  if (o.prec == RBGS_P_FP64) return RBGS_OK;
+  if (o.fine < 0 || o.fine > 1) return RBGS_EINVAL;
+  // tensor-core paths: TMA needs 16-byte aligned bases and leading dimensions
+  if ((o.prec == RBGS_P_TF32X3 || o.prec == RBGS_P_F16X3) &&
+      (((uintptr_t)W & 15) || ((uintptr_t)Q & 15) || (ldw % 4) || (ldq % 4)))
+    return RBGS_EINVAL;
+  return RBGS_OK;
+}
+
+// rbgs_qr after its checks: the instance for the precisions.
+rbgs_status qr_dispatch(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch, int64_t k,
+                        uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts& o,
+                        rbgs_stats* stats, const QrCtx* ctx) {
   if (o.prec == RBGS_P_FP64)
     return qr_impl<double, double>((const double*)W, n, m, ldw, (int)mb, sketch, k, seed, (double*)Q, ldq, R, ldr, o,
-                                   stats, 0);
-  if (o.fine < 0 || o.fine > 1) return RBGS_EINVAL;
+                                   stats, 0, nullptr, ctx);
   const int mode = o.prec == RBGS_P_TF32X3 ? 1 : (o.prec == RBGS_P_F16X3 ? 2 : 0);
-  // tensor-core paths: TMA needs 16-byte aligned bases and leading dimensions
-  if (mode && (((uintptr_t)W & 15) || ((uintptr_t)Q & 15) || (ldw % 4) || (ldq % 4))) return RBGS_EINVAL;
   if (o.fine)
     return qr_impl<float, double>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o,
-                                  stats, mode);
+                                  stats, mode, nullptr, ctx);
   return qr_impl<float, float>((const float*)W, n, m, ldw, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o, stats,
-                               mode);
+                               mode, nullptr, ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch, int64_t k,
+                    uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts* opts,
+                    rbgs_stats* stats) {
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  rbgs_status s = check_qr(W, n, m, ldw, mb, sketch, k, Q, ldq, R, ldr, o);
+  if (s) return s;
+  return qr_dispatch(W, n, m, ldw, mb, sketch, k, seed, Q, ldq, R, ldr, o, stats, nullptr);
+}
+
+rbgs_status rbgs_qr_batched(rbgs_problem* probs, int64_t count, rbgs_sketch sketch, const rbgs_opts* opts,
+                            int32_t nstreams) {
+  if (!probs || count < 0 || nstreams < 1) return RBGS_EINVAL;
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  for (int64_t i = 0; i < count; ++i) {
+    const rbgs_problem& q = probs[i];
+    rbgs_status s = check_qr(q.W, q.n, q.m, q.ldw, q.mb, sketch, q.k, q.Q, q.ldq, q.R, q.ldr, o);
+    if (s) return s;
+  }
+  if (count == 0) return RBGS_OK;
+  o.sync = 0;
+  o.timing = 0;
+  o.certify = 0;
+  const int ns = (int)std::min<int64_t>(std::min<int64_t>(nstreams, count), 32);
+  // each stream's workspace holds the largest of its problems
+  std::vector<size_t> need((size_t)ns, 0);
+  for (int64_t i = 0; i < count; ++i) {
+    const rbgs_problem& q = probs[i];
+    size_t nd = 0;
+    QrCtx c;
+    c.need_out = &nd;
+    rbgs_status s = qr_dispatch(q.W, q.n, q.m, q.ldw, q.mb, sketch, q.k, q.seed, q.Q, q.ldq, q.R, q.ldr, o, nullptr,
+                                &c);
+    if (s) return s;
+    need[(size_t)(i % ns)] = std::max(need[(size_t)(i % ns)], nd);
+  }
+  struct Slot {
+    cudaStream_t st = nullptr, side = nullptr;
+    cudaEvent_t done = nullptr;
+    void* ws = nullptr;
+  };
+  std::vector<Slot> slots((size_t)ns);
+  int* dstat = nullptr;
+  cudaEvent_t start = nullptr;
+  struct Cleanup {
+    std::vector<Slot>* sl;
+    int** dstat;
+    cudaEvent_t* start;
+    ~Cleanup() {
+      for (auto& x : *sl) {
+        if (x.st) cudaStreamSynchronize(x.st);
+        if (x.side) cudaStreamSynchronize(x.side);
+        if (x.ws) cudaFree(x.ws);
+        if (x.done) cudaEventDestroy(x.done);
+        if (x.st) cudaStreamDestroy(x.st);
+        if (x.side) cudaStreamDestroy(x.side);
+      }
+      if (*dstat) cudaFree(*dstat);
+      if (*start) cudaEventDestroy(*start);
+    }
+  } cleanup{&slots, &dstat, &start};
+  for (auto& x : slots) {
+    RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking));
+    RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&x.side, cudaStreamNonBlocking));
+    RBGS_CUDA_TRY(cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming));
+  }
+  for (int j = 0; j < ns; ++j) {
+    if (cudaMalloc(&slots[(size_t)j].ws, need[(size_t)j]) != cudaSuccess) {
+      cudaGetLastError();
+      return RBGS_ENOMEM;
+    }
+  }
+  if (cudaMalloc(&dstat, sizeof(int) * 8 * (size_t)count) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  // the batch starts after the work already on the caller's stream, and that
+  // stream waits for the whole batch
+  cudaStream_t caller = (cudaStream_t)o.stream;
+  RBGS_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  RBGS_CUDA_TRY(cudaEventRecord(start, caller));
+  for (auto& x : slots) RBGS_CUDA_TRY(cudaStreamWaitEvent(x.st, start, 0));
+  for (int64_t i = 0; i < count; ++i) {
+    const rbgs_problem& q = probs[i];
+    Slot& x = slots[(size_t)(i % ns)];
+    QrCtx c;
+    c.ws = x.ws;
+    c.ws_bytes = need[(size_t)(i % ns)];
+    c.side = x.side;
+    c.status_out = dstat + 8 * i;
+    rbgs_opts oi = o;
+    oi.stream = x.st;
+    rbgs_status s = qr_dispatch(q.W, q.n, q.m, q.ldw, q.mb, sketch, q.k, q.seed, q.Q, q.ldq, q.R, q.ldr, oi, nullptr,
+                                &c);
+    if (s) return s;
+  }
+  for (auto& x : slots) {
+    RBGS_CUDA_TRY(cudaEventRecord(x.done, x.st));
+    RBGS_CUDA_TRY(cudaStreamWaitEvent(caller, x.done, 0));
+  }
+  std::vector<int> hs((size_t)count * 8);
+  RBGS_CUDA_TRY(cudaMemcpyAsync(hs.data(), dstat, sizeof(int) * hs.size(), cudaMemcpyDeviceToHost, caller));
+  RBGS_CUDA_TRY(cudaStreamSynchronize(caller));
+  rbgs_status first = RBGS_OK;
+  for (int64_t i = 0; i < count; ++i) {
+    const int* f = hs.data() + 8 * i;
+    const rbgs_status si = f[3] ? RBGS_ETIMEOUT : (f[0] ? RBGS_EBREAKDOWN : RBGS_OK);
+    probs[i].status = si;
+    probs[i].passes2 = f[2];
+    if (si && !first) first = si;
+  }
+  return first;
 }
 
 rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,

@@ -40,6 +40,13 @@ class Opts(ctypes.Structure):
                 ("interblock", ctypes.c_int32)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_void_p), ("n", ctypes.c_int64), ("m", ctypes.c_int64), ("ldw", ctypes.c_int64),
+                ("mb", ctypes.c_int64), ("k", ctypes.c_int64), ("seed", ctypes.c_uint64), ("Q", ctypes.c_void_p),
+                ("ldq", ctypes.c_int64), ("R", ctypes.c_void_p), ("ldr", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("passes2", ctypes.c_int32)]
+
+
 class Op(ctypes.Structure):
     """rbgs_op: the 5-point convection-diffusion operator on nx x ny interior points."""
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nx", ctypes.c_int64),
@@ -104,12 +111,13 @@ def load(build_if_missing: bool = False):
                                      ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_int64), vp]
     lib.rbgs_rayleigh_ritz.argtypes = [opp, vp, i64, i64, i64, i64, i32, ctypes.c_int, i64, u64, ctypes.POINTER(Opts),
                                        vp, i64, vp, vp, vp]
+    lib.rbgs_qr_batched.argtypes = [ctypes.POINTER(Problem), i64, ctypes.c_int, ctypes.POINTER(Opts), i32]
     lib.rbgs_release_workspace.argtypes = []
     lib.rbgs_version.restype = ctypes.c_char_p
     lib.rbgs_launch_count.restype = ctypes.c_int64
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
                  "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
-                 "rbgs_block_fom", "rbgs_rayleigh_ritz"):
+                 "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -158,6 +166,13 @@ def _prec_of(t: torch.Tensor, prec: str | None) -> str:
     return prec
 
 
+def _empty_cols(n: int, m: int, dtype, device) -> torch.Tensor:
+    """An n x m column-major tensor whose leading dimension is a multiple of 4
+    (the tensor-core paths read columns with 16-byte aligned copies)."""
+    ld = (n + 3) // 4 * 4
+    return torch.empty((m, ld), dtype=dtype, device=device).t()[:n]
+
+
 def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
             prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
             certify: bool = False, Q: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None,
@@ -170,7 +185,7 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
     n, m = W.shape
     k = 2 * m if k is None else k
     if Q is None:
-        Q = torch.empty((m, n), dtype=W.dtype, device=W.device).t()
+        Q = _empty_cols(n, m, W.dtype, W.device)
     if R is None:
         R = torch.empty((m, m), dtype=torch.float64, device=W.device).t()
     o = Opts()
@@ -186,6 +201,35 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
     stats = (QRStats(st.delta, st.delta_tilde, st.passes2, bool(st.certified), st.tall_ms, st.tall_bytes,
                      st.tall_launches, st.chol_rounds2) if sync else None)
     return Q, R, stats
+
+
+def rbgs_qr_batched(Ws: list, mbs, ks, seeds, sketch: str = "gauss", prec: str | None = None, ls_iters: int = 2,
+                    reorth: int = 0, reorth_tol: float = 1e-8, fine: bool = False, interblock: int = 5,
+                    nstreams: int = 8, Qs: list | None = None, Rs: list | None = None, stream=None):
+    """Independent RBGS factorizations of the column-major matrices Ws (one
+    mb, k and seed per problem, or one value for all) on nstreams internal
+    streams.  Returns (Qs, Rs, statuses, passes2)."""
+    lib = load()
+    cnt = len(Ws)
+    pick = (lambda v, i: v[i] if isinstance(v, (list, tuple)) else v)
+    prec = _prec_of(Ws[0], prec) if cnt else (prec or "fp64")
+    if Qs is None:
+        Qs = [_empty_cols(W.shape[0], W.shape[1], W.dtype, W.device) for W in Ws]
+    if Rs is None:
+        Rs = [torch.empty((W.shape[1], W.shape[1]), dtype=torch.float64, device=W.device).t() for W in Ws]
+    probs = (Problem * max(cnt, 1))()
+    for i, W in enumerate(Ws):
+        n, m = W.shape
+        probs[i] = Problem(W.data_ptr(), n, m, _ld(W, "W"), int(pick(mbs, i)), int(pick(ks, i)), int(pick(seeds, i)),
+                           Qs[i].data_ptr(), _ld(Qs[i], "Q"), Rs[i].data_ptr(), _ld(Rs[i], "R"), 0, 0)
+    o = Opts()
+    lib.rbgs_opts_default(ctypes.byref(o))
+    o.prec, o.ls_iters, o.reorth, o.reorth_tol = PREC[prec], ls_iters, reorth, reorth_tol
+    o.fine, o.interblock, o.stream = int(fine), int(interblock), _stream_ptr(stream)
+    code = lib.rbgs_qr_batched(probs, cnt, SKETCH[sketch], ctypes.byref(o), int(nstreams))
+    if code not in (0, 4, 6):  # per-problem breakdowns and timeouts are reported in the statuses
+        _check(code, "rbgs_qr_batched")
+    return Qs, Rs, [int(probs[i].status) for i in range(cnt)], [int(probs[i].passes2) for i in range(cnt)]
 
 
 def sketch_apply(X: torch.Tensor, sketch: str, k: int, seed: int, prec: str | None = None, stream=None,

@@ -10,6 +10,12 @@ prescribed structure.  Recipes:
   W_ij = sin(10(mu_j + x_i)) / (cos(100(mu_j - x_i)) + 1.1) on equispaced grids
   x_i = i/(n-1), mu_j = j/(m-1) (0-based), numerically rank-deficient.
 * ``gaussian``: seeded N(0,1) blocks.
+* ``batch_specs`` / ``near_duplicate_matrix_torch``: the many-small-problems
+  workload.  Per problem n ~ U[2e4, 2e5] and m in {64, 128, 192, 256}, m_p in
+  {16, 32}, drawn from numpy's Philox generator with seed 3; the columns are
+  N(0,1), and every 8th column j (j = 8, 16, ...) is replaced by column
+  j - 1 - (r mod j), r a seeded integer, plus Gaussian noise of relative size
+  1e-7 (a numerically rank-deficient matrix in FP32).
 
 CPU draws use numpy's PCG64; device draws (large sizes) use torch's generator
 on the given device, so the two do not produce the same numbers: a test that
@@ -84,3 +90,34 @@ def ex1_matrix(n: int, m: int, dtype=np.float64) -> np.ndarray:
 def gaussian(n: int, m: int, seed: int, dtype=np.float64) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.asfortranarray(rng.standard_normal((n, m)).astype(dtype))
+
+
+def batch_specs(count: int, seed: int = 3) -> list:
+    """(n, m, m_p) of each problem of the many-small-problems workload."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(20000, 200001))
+        m = int(rng.choice([64, 128, 192, 256]))
+        mp = int(rng.choice([16, 32]))
+        out.append((n, m, mp))
+    return out
+
+
+def near_duplicate_matrix_torch(n: int, m: int, seed: int, device="cuda", dtype=None):
+    """n x m column-major device matrix (leading dimension a multiple of 4):
+    N(0,1) columns, every 8th column j a copy of column j - 1 - (r mod j) plus
+    noise of relative size 1e-7."""
+    import torch
+
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    rng = np.random.Generator(np.random.Philox(seed))
+    ld = (n + 3) // 4 * 4
+    W = torch.randn((m, ld), device=device, generator=g, dtype=dtype).t()[:n]
+    for j in range(8, m, 8):
+        src = j - 1 - int(rng.integers(0, 1 << 30)) % j
+        scale = float(torch.linalg.norm(W[:, src])) / n ** 0.5
+        W[:, j] = W[:, src] + 1e-7 * scale * torch.randn(n, device=device, generator=g, dtype=dtype)
+    return W

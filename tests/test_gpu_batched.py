@@ -1,0 +1,85 @@
+"""Many independent factorizations in one call (rbgs_qr_batched): every problem
+equals its single rbgs_qr result bit for bit, whatever the number of streams,
+matches the oracle, and a breakdown stays local to its problem."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2111_14641_gb300 as rb
+    from paper_2111_14641_gb300 import build
+
+    build.build()
+    rb.load()
+    return rb
+
+
+def dev(A, dtype=torch.float64):
+    A = np.asarray(A)
+    return torch.from_numpy(np.ascontiguousarray(A.T)).to("cuda", dtype).t()
+
+
+def host(T):
+    return T.detach().double().cpu().numpy()
+
+
+SHAPES = [(2000, 16, 4), (3100, 24, 8), (4096, 40, 8), (2500, 12, 4), (5000, 32, 16), (2048, 20, 8), (3000, 9, 4)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+@pytest.mark.parametrize("nstreams", [1, 3, 8])
+def test_batched_equals_single_calls_and_oracle(rb, prec, nstreams):
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Ws = [synth.svd_matrix(n, m, 1e3, 40 + i) for i, (n, m, _) in enumerate(SHAPES)]
+    if prec != "fp64":
+        Ws = [W.astype(np.float32).astype(np.float64) for W in Ws]
+    mbs = [mb for _, _, mb in SHAPES]
+    ks = [2 * m for _, m, _ in SHAPES]
+    seeds = [100 + i for i in range(len(SHAPES))]
+    Wd = [dev(W, td) for W in Ws]
+    Qs, Rs, status, passes2 = rb.rbgs_qr_batched(Wd, mbs, ks, seeds, "gauss", prec=prec, ls_iters=2, reorth=1,
+                                                  fine=prec != "fp64", nstreams=nstreams)
+    assert status == [0] * len(SHAPES)
+    assert passes2 == [(m + mb - 1) // mb - 1 for _, m, mb in SHAPES]
+    for i, (n, m, mb) in enumerate(SHAPES):
+        Q1, R1, _ = rb.rbgs_qr(Wd[i], mbs[i], "gauss", ks[i], seeds[i], prec=prec, ls_iters=2, reorth=1,
+                               fine=prec != "fp64")
+        assert torch.equal(Qs[i], Q1) and torch.equal(Rs[i], R1)
+        ref = oracle.rbgs(Ws[i], mb, "gauss", ks[i], seeds[i], variant=5, ls="richardson", ls_iters=2, reorth=True,
+                          ls_iters_first=1)
+        R = host(Rs[i])
+        tol = 1e-10 if prec == "fp64" else 1e-2
+        assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+        assert oracle.factorization_error(Ws[i], host(Qs[i]), R) < (1e-14 if prec == "fp64" else 2e-6)
+
+
+def test_batched_breakdown_stays_local(rb):
+    """A zero column makes its problem's Cholesky pivot vanish: that problem
+    reports RBGS_EBREAKDOWN, the others are unaffected."""
+    Ws = [synth.svd_matrix(n, m, 1e2, 60 + i) for i, (n, m, _) in enumerate(SHAPES[:4])]
+    Ws[2] = Ws[2].copy()
+    Ws[2][:, 5] = 0.0
+    Wd = [dev(W) for W in Ws]
+    mbs = [mb for _, _, mb in SHAPES[:4]]
+    ks = [2 * m for _, m, _ in SHAPES[:4]]
+    Qs, Rs, status, _ = rb.rbgs_qr_batched(Wd, mbs, ks, 5, "gauss", prec="fp64", nstreams=2)
+    assert status[2] == 4 and [s for i, s in enumerate(status) if i != 2] == [0, 0, 0]
+    for i in (0, 1, 3):
+        Q1, R1, _ = rb.rbgs_qr(Wd[i], mbs[i], "gauss", ks[i], 5, prec="fp64")
+        assert torch.equal(Qs[i], Q1) and torch.equal(Rs[i], R1)
+
+
+def test_batched_rejects_a_bad_problem_before_any_work(rb):
+    Wd = [dev(synth.gaussian(100, 8, 1)), dev(synth.gaussian(120, 8, 2))]
+    with pytest.raises(rb.RbgsError):
+        rb.rbgs_qr_batched(Wd, [4, 4], [16, 200], 0, "gauss", prec="fp64")   # k > n in the second problem
