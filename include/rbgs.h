@@ -156,6 +156,20 @@ typedef struct {
 RBGS_API rbgs_status rbgs_qr_batched(rbgs_problem* probs, int64_t count, rbgs_sketch sketch, const rbgs_opts* opts,
                                      int32_t nstreams);
 
+/* rbgs_qr on HOST buffers: W (n x m, ldw), Q (n x m, ldq) and R (m x m, ldr)
+ * are host arrays of the prec type (R double).  The library keeps device
+ * copies (grown on demand, freed by rbgs_release_workspace).  Column block i
+ * of W goes to the device on a copy stream ahead of the factorization, block
+ * i of the factorization waits only for its own block, and each column block
+ * of Q is copied back as soon as it is final, while later blocks compute; R
+ * follows at the end.  With page-locked (pinned) host memory the copies
+ * overlap the computation; pageable memory gives the same result without the
+ * overlap.  Options and errors as rbgs_qr (no certification, no timing; stats
+ * receives passes2 and chol_rounds2).  Synchronous.                        */
+RBGS_API rbgs_status rbgs_qr_host(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch,
+                                  int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr,
+                                  const rbgs_opts* opts, rbgs_stats* stats);
+
 /* Y = Theta X (Sec. 2.3), the sketch of steps 1 and 5 of Alg. 2.
  *  X device n x ncols (ldx), double if prec == RBGS_P_FP64 else float.
  *  Y device k x ncols (ldy), double.  FP64 sums in double; other precisions

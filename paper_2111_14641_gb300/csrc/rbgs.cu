@@ -195,6 +195,78 @@ rbgs_status side_stream(cudaStream_t* out) {
   return RBGS_OK;
 }
 
+// Device copies of W, Q and R for the host-buffer entry point, kept per device
+// and grown on demand (freed by rbgs_release_workspace), and its two copy streams.
+struct HostPathBuf {
+  int dev = -1;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_hp_mu;
+std::vector<HostPathBuf> g_hp;
+
+rbgs_status host_path_buffer(size_t bytes, void** out) {
+  int dev = 0;
+  RBGS_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_hp_mu);
+  for (auto& b : g_hp) {
+    if (b.dev != dev) continue;
+    if (b.bytes >= bytes) {
+      *out = b.ptr;
+      return RBGS_OK;
+    }
+    cudaDeviceSynchronize();
+    cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return RBGS_ENOMEM;
+    }
+    b.bytes = bytes;
+    *out = b.ptr;
+    return RBGS_OK;
+  }
+  HostPathBuf b;
+  b.dev = dev;
+  if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  b.bytes = bytes;
+  g_hp.push_back(b);
+  *out = b.ptr;
+  return RBGS_OK;
+}
+
+void host_path_release() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lock(g_hp_mu);
+  for (auto& b : g_hp)
+    if (b.dev == dev && b.ptr) {
+      cudaDeviceSynchronize();
+      cudaFree(b.ptr);
+      b.ptr = nullptr;
+      b.bytes = 0;
+    }
+}
+
+// copy streams of the host-buffer entry point: [0] host to device, [1] device to host
+rbgs_status copy_streams(cudaStream_t* h2d, cudaStream_t* d2h) {
+  static std::mutex mu;
+  static cudaStream_t streams[64][2] = {};
+  int dev = 0;
+  RBGS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return RBGS_ENODEV;
+  std::lock_guard<std::mutex> lk(mu);
+  for (int i = 0; i < 2; ++i)
+    if (!streams[dev][i]) RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&streams[dev][i], cudaStreamNonBlocking));
+  *h2d = streams[dev][0];
+  *d2h = streams[dev][1];
+  return RBGS_OK;
+}
+
 // Resources of one factorization when several run side by side (rbgs_qr_batched):
 // its own workspace and side stream instead of the per-device ones, and a device
 // slot that receives its status words.  need_out alone asks for the workspace size.
@@ -204,6 +276,10 @@ struct QrCtx {
   cudaStream_t side = nullptr;
   int* status_out = nullptr;  // 8 ints: breakdown, -, passes2, timeout, -, Cholesky second rounds
   size_t* need_out = nullptr;
+  // host-buffer calls: block i of W may be read once w_ready[i] has fired, and
+  // q_done[i] is recorded once column block i of Q and of R is final
+  const cudaEvent_t* w_ready = nullptr;
+  const cudaEvent_t* q_done = nullptr;
 };
 
 // T: storage of W and Q; TS: storage/arithmetic of the sketch space.
@@ -400,6 +476,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       for (auto& e : evw) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     // step 1 of the first block
+    if (ctx && ctx->w_ready) RBGS_CUDA_TRY(cudaStreamWaitEvent(st, ctx->w_ready[0], 0));
     if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, W, ldw, (int64_t)std::min<int64_t>(mbf, m), P, k, skscr,
                                    sk_bytes, st)))
       return s;
@@ -411,6 +488,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       const int64_t c = blk * mbf;
       mb = (int)std::min<int64_t>(mbf, m - c);  // this block's width
       if (alg4 && mb != mbf && (s = set_eye(mb))) return s;  // the narrower last block
+      if (ctx && ctx->w_ready && op == nullptr) RBGS_CUDA_TRY(cudaStreamWaitEvent(st, ctx->w_ready[blk], 0));
       const int64_t wnext = blk + 1 < p ? std::min<int64_t>(mbf, m - c - mbf) : 0;
       const T* Wi = W + c * ldw;
       int64_t ldwi = ldw;
@@ -425,6 +503,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi, ldwi, mb, Pi, k, skscr, sk_bytes, st))) return s;
       }
       if (ahead && blk + 1 < p) {
+        if (ctx && ctx->w_ready) RBGS_CUDA_TRY(cudaStreamWaitEvent(st2, ctx->w_ready[blk + 1], 0));
         s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi + mbf * ldw, ldw, wnext, Pi + mbf * k, k, skscr2, sk_bytes,
                                   st2);
         if (s) return s;
@@ -519,6 +598,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         }
         if ((s = reorth_update_r<TS>(c, mb, X2, m, R2ii, Rcol, ldr, tmp, active, st))) return s;
       }
+      if (ctx && ctx->q_done) RBGS_CUDA_TRY(cudaEventRecord(ctx->q_done[blk], st));
     }
     mb = mbf;
     RBGS_LAUNCH_CHECK();
@@ -795,6 +875,107 @@ rbgs_status rbgs_qr_batched(rbgs_problem* probs, int64_t count, rbgs_sketch sket
   return first;
 }
 
+rbgs_status rbgs_qr_host(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch,
+                         int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts* opts,
+                         rbgs_stats* stats) {
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  if (!W || !Q || !R) return RBGS_EINVAL;
+  const size_t es = o.prec == RBGS_P_FP64 ? 8 : 4;
+  if (n >= 1 && m >= 1 && ldw >= n && ldq >= n &&
+      ranges_overlap(W, es * (size_t)(ldw * (m - 1) + n), Q, es * (size_t)(ldq * (m - 1) + n)))
+    return RBGS_EINVAL;
+  // the device copies: W and Q with a leading dimension that is a multiple of 4, R packed
+  const int64_t ldd = (n + 3) / 4 * 4;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t bw = up(es * (size_t)ldd * (size_t)std::max<int64_t>(m, 1));
+  const size_t br = up(8 * (size_t)std::max<int64_t>(m, 1) * (size_t)std::max<int64_t>(m, 1));
+  rbgs_opts oi = o;
+  oi.sync = 0;
+  oi.timing = 0;
+  oi.certify = 0;
+  // the same checks as rbgs_qr, on the device copies' layout
+  {
+    rbgs_status s0 = check_qr((const void*)(uintptr_t)256, n, m, ldd, mb, sketch, k,
+                              (const void*)(uintptr_t)(256 + bw), ldd, (const double*)(uintptr_t)(256 + 2 * bw), m, oi);
+    if (s0) return s0;
+    if (ldw < n || ldq < n || ldr < m) return RBGS_EINVAL;
+  }
+  void* buf = nullptr;
+  rbgs_status s = host_path_buffer(2 * bw + br + 256, &buf);
+  if (s) return s;
+  char* Wd = (char*)buf;
+  char* Qd = Wd + bw;
+  double* Rd = (double*)(Qd + bw);
+  int* dstat = nullptr;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  if ((s = copy_streams(&h2d, &d2h))) return s;
+  const int64_t p = (m + mb - 1) / mb;
+  std::vector<cudaEvent_t> ev((size_t)(2 * p + 2), nullptr);
+  struct EvFree {
+    std::vector<cudaEvent_t>* v;
+    int** d;
+    ~EvFree() {
+      for (auto e : *v)
+        if (e) cudaEventDestroy(e);
+      if (*d) cudaFree(*d);
+    }
+  } evfree{&ev, &dstat};
+  for (auto& e : ev) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEvent_t* w_ready = ev.data();
+  cudaEvent_t* q_done = ev.data() + p;
+  cudaEvent_t start = ev[(size_t)(2 * p)], copied = ev[(size_t)(2 * p + 1)];
+  if (cudaMalloc(&dstat, 8 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  cudaStream_t caller = (cudaStream_t)o.stream;
+  RBGS_CUDA_TRY(cudaEventRecord(start, caller));
+  RBGS_CUDA_TRY(cudaStreamWaitEvent(h2d, start, 0));
+  // W goes up block by block ahead of the factorization
+  for (int64_t b = 0; b < p; ++b) {
+    const int64_t c = b * mb, w = std::min<int64_t>(mb, m - c);
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(Wd + es * (size_t)(c * ldd), es * (size_t)ldd, (const char*)W + es * (size_t)(c * ldw),
+                                    es * (size_t)ldw, es * (size_t)n, (size_t)w, cudaMemcpyHostToDevice, h2d));
+    RBGS_CUDA_TRY(cudaEventRecord(w_ready[b], h2d));
+  }
+  QrCtx ctx;
+  ctx.status_out = dstat;
+  ctx.w_ready = w_ready;
+  ctx.q_done = q_done;
+  s = qr_dispatch(Wd, n, m, ldd, mb, sketch, k, seed, Qd, ldd, Rd, m, oi, nullptr, &ctx);
+  if (s) {
+    cudaStreamSynchronize(h2d);
+    cudaStreamSynchronize(caller);
+    return s;
+  }
+  // each finished block of Q comes down while the next ones are computed; R at the end
+  for (int64_t b = 0; b < p; ++b) {
+    const int64_t c = b * mb, w = std::min<int64_t>(mb, m - c);
+    RBGS_CUDA_TRY(cudaStreamWaitEvent(d2h, q_done[b], 0));
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync((char*)Q + es * (size_t)(c * ldq), es * (size_t)ldq, Qd + es * (size_t)(c * ldd),
+                                    es * (size_t)ldd, es * (size_t)n, (size_t)w, cudaMemcpyDeviceToHost, d2h));
+  }
+  RBGS_CUDA_TRY(cudaMemcpy2DAsync(R, 8 * (size_t)ldr, Rd, 8 * (size_t)m, 8 * (size_t)m, (size_t)m,
+                                  cudaMemcpyDeviceToHost, d2h));
+  int hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  RBGS_CUDA_TRY(cudaMemcpyAsync(hs, dstat, sizeof(hs), cudaMemcpyDeviceToHost, d2h));
+  RBGS_CUDA_TRY(cudaEventRecord(copied, d2h));
+  RBGS_CUDA_TRY(cudaStreamWaitEvent(caller, copied, 0));
+  RBGS_CUDA_TRY(cudaStreamSynchronize(caller));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->delta = -1.0;
+    stats->delta_tilde = -1.0;
+    stats->passes2 = hs[2];
+    stats->chol_rounds2 = hs[5];
+  }
+  if (hs[3]) return RBGS_ETIMEOUT;
+  if (hs[0]) return RBGS_EBREAKDOWN;
+  return RBGS_OK;
+}
+
 rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,
                               int64_t ldx, int64_t ncols, double* Y, int64_t ldy, void* stream, int32_t sync) {
   if (!X || !Y || n < 1 || k < 1 || ncols < 0 || ldx < n || ldy < k) return RBGS_EINVAL;
@@ -930,6 +1111,7 @@ rbgs_status rbgs_release_workspace(void) {
         w.bytes = 0;
       }
   }
+  host_path_release();
   srht_plans_release();
   return RBGS_OK;
 }

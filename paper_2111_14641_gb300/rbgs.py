@@ -112,12 +112,14 @@ def load(build_if_missing: bool = False):
     lib.rbgs_rayleigh_ritz.argtypes = [opp, vp, i64, i64, i64, i64, i32, ctypes.c_int, i64, u64, ctypes.POINTER(Opts),
                                        vp, i64, vp, vp, vp]
     lib.rbgs_qr_batched.argtypes = [ctypes.POINTER(Problem), i64, ctypes.c_int, ctypes.POINTER(Opts), i32]
+    lib.rbgs_qr_host.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
+                                 ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
     lib.rbgs_release_workspace.argtypes = []
     lib.rbgs_version.restype = ctypes.c_char_p
     lib.rbgs_launch_count.restype = ctypes.c_int64
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
                  "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
-                 "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched"):
+                 "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched", "rbgs_qr_host"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -201,6 +203,33 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
     stats = (QRStats(st.delta, st.delta_tilde, st.passes2, bool(st.certified), st.tall_ms, st.tall_bytes,
                      st.tall_launches, st.chol_rounds2) if sync else None)
     return Q, R, stats
+
+
+def rbgs_qr_host(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
+                 prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
+                 Q: torch.Tensor | None = None, R: torch.Tensor | None = None, fine: bool = False,
+                 interblock: int = 5, stream=None):
+    """rbgs_qr on host (CPU) tensors, column-major; pinned memory lets the
+    copies overlap the factorization.  Returns (Q, R, QRStats)."""
+    lib = load()
+    if W.is_cuda:
+        raise ValueError("W must be a host tensor")
+    prec = _prec_of(W, prec)
+    n, m = W.shape
+    k = 2 * m if k is None else k
+    pin = W.is_pinned()
+    if Q is None:
+        Q = torch.empty((m, n), dtype=W.dtype, pin_memory=pin).t()
+    if R is None:
+        R = torch.empty((m, m), dtype=torch.float64, pin_memory=pin).t()
+    o = Opts()
+    lib.rbgs_opts_default(ctypes.byref(o))
+    o.prec, o.ls_iters, o.reorth, o.reorth_tol = PREC[prec], ls_iters, reorth, reorth_tol
+    o.fine, o.interblock, o.stream = int(fine), int(interblock), _stream_ptr(stream)
+    st = Stats()
+    _check(lib.rbgs_qr_host(W.data_ptr(), n, m, _ld(W, "W"), mb, SKETCH[sketch], k, seed, Q.data_ptr(), _ld(Q, "Q"),
+                            R.data_ptr(), _ld(R, "R"), ctypes.byref(o), ctypes.byref(st)), "rbgs_qr_host")
+    return Q, R, QRStats(st.delta, st.delta_tilde, st.passes2, False, 0.0, 0.0, 0, st.chol_rounds2)
 
 
 def rbgs_qr_batched(Ws: list, mbs, ks, seeds, sketch: str = "gauss", prec: str | None = None, ls_iters: int = 2,

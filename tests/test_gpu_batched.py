@@ -83,3 +83,24 @@ def test_batched_rejects_a_bad_problem_before_any_work(rb):
     Wd = [dev(synth.gaussian(100, 8, 1)), dev(synth.gaussian(120, 8, 2))]
     with pytest.raises(rb.RbgsError):
         rb.rbgs_qr_batched(Wd, [4, 4], [16, 200], 0, "gauss", prec="fp64")   # k > n in the second problem
+
+
+@pytest.mark.parametrize("prec,pinned", [("fp64", True), ("f16x3", True), ("f16x3", False), ("fp32", True)])
+def test_host_buffer_path_equals_device_path(rb, prec, pinned):
+    """rbgs_qr_host (host W, Q, R; copies overlapped with the factorization)
+    gives bit for bit the device path's result, ragged last block included."""
+    n, m, mb, k = 5001, 70, 16, 160
+    td = torch.float64 if prec == "fp64" else torch.float32
+    W = synth.svd_matrix(n, m, 1e3, 21)
+    Wh = torch.from_numpy(np.ascontiguousarray(W.T)).to(td).t()
+    if pinned:
+        Wh = Wh.t().contiguous().pin_memory().t()
+    Qh, Rh, st = rb.rbgs_qr_host(Wh, mb, "srht", k, 3, prec=prec, ls_iters=1, reorth=1, fine=prec != "fp64")
+    Wd = Wh.t().contiguous().cuda().t()
+    if prec != "fp64":  # the tensor-core paths need a leading dimension that is a multiple of 4
+        buf = torch.zeros((m, (n + 3) // 4 * 4), dtype=td, device="cuda")
+        buf[:, :n] = Wd.t()
+        Wd = buf.t()[:n]
+    Qd, Rd, std = rb.rbgs_qr(Wd, mb, "srht", k, 3, prec=prec, ls_iters=1, reorth=1, fine=prec != "fp64")
+    assert torch.equal(Qh, Qd.cpu()) and torch.equal(Rh, Rd.cpu())
+    assert st.passes2 == std.passes2 == (m + mb - 1) // mb - 1
