@@ -170,6 +170,19 @@ RBGS_API rbgs_status rbgs_qr_host(const void* W, int64_t n, int64_t m, int64_t l
                                   int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr,
                                   const rbgs_opts* opts, rbgs_stats* stats);
 
+/* A posteriori check of the epsilon-embedding property (Sec. 4, the
+ * epsilon-embedding subsection): with a second, independent sketch Phi (the
+ * same kind and size, seed seed_phi), Y = R_phi^{-1} for R_phi the R factor of
+ * Phi Z, and (Theta Z) Y has orthonormal columns when Theta embeds range(Z)
+ * without distortion.  Y comes from RBGS of Z with Phi (Q_phi = Z R_phi^{-1};
+ * options as rbgs_qr), so (Theta Z) Y = Theta Q_phi.  *defect (host) receives
+ * ||I - (Theta Q_phi)^T (Theta Q_phi)||_F, which bounds the distortion of Theta
+ * on range(Z) up to that of Phi.  Z: n x m device array of the prec type.
+ * Errors as rbgs_qr.  Synchronous; allocates its buffers per call.          */
+RBGS_API rbgs_status rbgs_embedding_check(const void* Z, int64_t n, int64_t m, int64_t ldz, int64_t mb,
+                                          rbgs_sketch sketch, int64_t k, uint64_t seed_theta, uint64_t seed_phi,
+                                          const rbgs_opts* opts, double* defect);
+
 /* Y = Theta X (Sec. 2.3), the sketch of steps 1 and 5 of Alg. 2.
  *  X device n x ncols (ldx), double if prec == RBGS_P_FP64 else float.
  *  Y device k x ncols (ldy), double.  FP64 sums in double; other precisions

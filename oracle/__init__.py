@@ -14,6 +14,8 @@ What each function follows (Balabanov & Grigori, arXiv 2111.14641):
   generator).  Each side implements that convention separately.
 * ``rbgs``: Alg. 2 with steps 4-5 from Alg. 4, 5 or 6 and step-2 solvers
   from Sec. 3.1 and its supplement (Householder, Richardson, CG).
+* ``embedding_check``: the a posteriori check of Theta with an independent
+  sketch Phi (Sec. 4, the epsilon-embedding subsection).
 * ``rcholqr``: the closed form that RBGS reaches in exact arithmetic
   (R = R factor of Theta W with a positive diagonal, Q = W R^{-1}).
 * ``householder_qr``: textbook Householder QR with a positive diagonal.
@@ -278,6 +280,22 @@ def block_krylov(method: str, nx: int, ny: int, bx: float, by: float, B, X0, p: 
     if cyc < 0:
         raise np.linalg.LinAlgError(f"block Krylov solver failed ({cyc})")
     return X, int(cyc), relres
+
+
+def embedding_check(Z, mp: int, kind: str, k: int, seed_theta: int, seed_phi: int, variant: int = 5,
+                    ls: str = "householder", ls_iters: int = 5, reorth: bool = False, ls_iters_first: int = 0):
+    """The a posteriori check of the epsilon-embedding property (Sec. 4, the
+    epsilon-embedding subsection): with an independent sketch Phi, Y = the
+    inverse of the R factor of Phi Z, and (Theta Z) Y should have orthonormal
+    columns when Theta embeds range(Z) well.  Y is obtained from RBGS with the
+    sketch Phi (Q_phi = Z R_phi^{-1}, R_phi the R factor of Phi Z), so that
+    (Theta Z) Y = Theta Q_phi.  Returns ||I - (Theta Q_phi)^T (Theta Q_phi)||_F."""
+    out = rbgs(Z, mp, kind, k, seed_phi, variant=variant, ls=ls, ls_iters=ls_iters, reorth=reorth,
+               ls_iters_first=ls_iters_first)
+    if out["rc"] != 0:
+        raise np.linalg.LinAlgError(f"RBGS breakdown ({out['rc']})")
+    S = theta_apply(kind, k, seed_theta, out["Q"])
+    return float(np.linalg.norm(np.eye(S.shape[1]) - S.T @ S, "fro"))
 
 
 RITZ_WHICH = ("LR", "SR")

@@ -195,6 +195,14 @@ rbgs_status side_stream(cudaStream_t* out) {
   return RBGS_OK;
 }
 
+// Device buffers owned by one solver call.
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
 // Device copies of W, Q and R for the host-buffer entry point, kept per device
 // and grown on demand (freed by rbgs_release_workspace), and its two copy streams.
 struct HostPathBuf {
@@ -754,9 +762,85 @@ rbgs_status qr_dispatch(const void* W, int64_t n, int64_t m, int64_t ldw, int64_
                                mode, nullptr, ctx);
 }
 
+// The a posteriori check of the epsilon-embedding property (Sec. 4): RBGS of Z
+// with the sketch Phi gives Q_phi = Z R_phi^{-1}; Theta Q_phi = (Theta Z) R_phi^{-1}
+// should have orthonormal columns.  Returns ||I - (Theta Q_phi)^T Theta Q_phi||_F.
+template <class T>
+rbgs_status embedding_check_t(const T* Z, int64_t n, int64_t m, int64_t ldz, int64_t mb, rbgs_sketch sketch,
+                              int64_t k, uint64_t seed_theta, uint64_t seed_phi, const rbgs_opts& o, double* defect) {
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const bool fp64 = sizeof(T) == 8;
+  const int64_t ldq = (n + 3) / 4 * 4;
+  const int64_t chunk = 64;
+  const size_t sk = sketch_scratch_bytes(sketch, k, n, chunk, fp64) + 256;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t bq = up(sizeof(T) * (size_t)ldq * m), br = up(8 * (size_t)m * m), bs = up(8 * (size_t)k * m),
+               bg = up(8 * (size_t)m * chunk), bp = up(8 * (size_t)kPartElems);
+  DevBuf buf;
+  if (cudaMalloc(&buf.p, bq + br + bs + bg + bp + sk) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  char* w = (char*)buf.p;
+  T* Qp = (T*)w;
+  double* Rp = (double*)(w + bq);
+  double* S = (double*)(w + bq + br);
+  double* Gt = (double*)(w + bq + br + bs);
+  double* part = (double*)(w + bq + br + bs + bg);
+  void* scr = w + bq + br + bs + bg + bp;
+  rbgs_status s = qr_dispatch(Z, n, m, ldz, mb, sketch, k, seed_phi, Qp, ldq, Rp, m, o, nullptr, nullptr);
+  if (s) return s;
+  for (int64_t j0 = 0; j0 < m; j0 += chunk) {
+    const int64_t nc = std::min<int64_t>(chunk, m - j0);
+    if ((s = sketch_apply_t<T, double>(sketch, k, n, seed_theta, Qp + j0 * ldq, ldq, nc, S + j0 * k, k, scr, sk, st)))
+      return s;
+  }
+  double acc = 0.0;
+  std::vector<double> hG((size_t)m * chunk);
+  for (int64_t j0 = 0; j0 < m; j0 += chunk) {
+    const int64_t nc = std::min<int64_t>(chunk, m - j0);
+    s = small_gemm<double, double, double>(1, m, nc, k, 1.0, S, k, S + j0 * k, k, 0.0, Gt, m, part, kPartElems,
+                                           nullptr, st);
+    if (s) return s;
+    RBGS_CUDA_TRY(cudaMemcpyAsync(hG.data(), Gt, sizeof(double) * m * nc, cudaMemcpyDeviceToHost, st));
+    RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t jj = 0; jj < nc; ++jj)
+      for (int64_t i = 0; i < m; ++i) {
+        const double d = (i == j0 + jj ? 1.0 : 0.0) - hG[(size_t)(i + jj * m)];
+        acc += d * d;
+      }
+  }
+  *defect = std::sqrt(acc);
+  return RBGS_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+rbgs_status rbgs_embedding_check(const void* Z, int64_t n, int64_t m, int64_t ldz, int64_t mb, rbgs_sketch sketch,
+                                 int64_t k, uint64_t seed_theta, uint64_t seed_phi, const rbgs_opts* opts,
+                                 double* defect) {
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  if (!defect) return RBGS_EINVAL;
+  o.sync = 1;
+  o.timing = 0;
+  o.certify = 0;
+  const int64_t ldq = (n + 3) / 4 * 4;
+  const size_t es = o.prec == RBGS_P_FP64 ? 8 : 4;
+  // the library's own Q and R lie elsewhere: check Z's arguments against a disjoint stand-in
+  const uintptr_t qfake = (uintptr_t)Z + es * (size_t)(ldz * std::max<int64_t>(m, 1)) + 4096;
+  rbgs_status s = check_qr(Z, n, m, ldz, mb, sketch, k, (const void*)(qfake & ~(uintptr_t)255), ldq,
+                           (const double*)((qfake & ~(uintptr_t)255) + es * (size_t)(ldq * std::max<int64_t>(m, 1)) +
+                                           4096),
+                           m, o);
+  if (s) return s;
+  if (o.prec == RBGS_P_FP64)
+    return embedding_check_t<double>((const double*)Z, n, m, ldz, mb, sketch, k, seed_theta, seed_phi, o, defect);
+  return embedding_check_t<float>((const float*)Z, n, m, ldz, mb, sketch, k, seed_theta, seed_phi, o, defect);
+}
 
 rbgs_status rbgs_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch, int64_t k,
                     uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts* opts,
@@ -1156,13 +1240,6 @@ rbgs_status arnoldi_run(const rbgs_op& op, const void* B, int64_t ldb, int64_t m
                                mode, &op);
 }
 
-// Device buffers owned by one solver call.
-struct DevBuf {
-  void* p = nullptr;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-};
 
 // Restarted randomized block GMRES (method 0) or FOM (method 1).
 rbgs_status krylov_solve(int method, const rbgs_op* op, const double* B, int64_t ldb, double* X, int64_t ldx,

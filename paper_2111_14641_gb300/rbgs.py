@@ -112,6 +112,8 @@ def load(build_if_missing: bool = False):
     lib.rbgs_rayleigh_ritz.argtypes = [opp, vp, i64, i64, i64, i64, i32, ctypes.c_int, i64, u64, ctypes.POINTER(Opts),
                                        vp, i64, vp, vp, vp]
     lib.rbgs_qr_batched.argtypes = [ctypes.POINTER(Problem), i64, ctypes.c_int, ctypes.POINTER(Opts), i32]
+    lib.rbgs_embedding_check.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, u64, ctypes.POINTER(Opts),
+                                         vp]
     lib.rbgs_qr_host.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
                                  ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
     lib.rbgs_release_workspace.argtypes = []
@@ -119,7 +121,8 @@ def load(build_if_missing: bool = False):
     lib.rbgs_launch_count.restype = ctypes.c_int64
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
                  "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
-                 "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched", "rbgs_qr_host"):
+                 "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched", "rbgs_qr_host",
+                 "rbgs_embedding_check"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -203,6 +206,25 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
     stats = (QRStats(st.delta, st.delta_tilde, st.passes2, bool(st.certified), st.tall_ms, st.tall_bytes,
                      st.tall_launches, st.chol_rounds2) if sync else None)
     return Q, R, stats
+
+
+def embedding_check(Z: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed_theta: int = 0,
+                    seed_phi: int = 1, prec: str | None = None, ls_iters: int = 2, reorth: int = 0,
+                    fine: bool = False, stream=None) -> float:
+    """||I - (Theta Q_phi)^T (Theta Q_phi)||_F with Q_phi the RBGS factor of Z
+    under an independent sketch Phi (the a posteriori check of Sec. 4)."""
+    lib = load()
+    prec = _prec_of(Z, prec)
+    n, m = Z.shape
+    k = 2 * m if k is None else k
+    o = Opts()
+    lib.rbgs_opts_default(ctypes.byref(o))
+    o.prec, o.ls_iters, o.reorth, o.fine, o.stream = PREC[prec], ls_iters, reorth, int(fine), _stream_ptr(stream)
+    out = ctypes.c_double(0.0)
+    _check(lib.rbgs_embedding_check(Z.data_ptr(), n, m, _ld(Z, "Z"), mb, SKETCH[sketch], k, seed_theta, seed_phi,
+                                     ctypes.byref(o), ctypes.cast(ctypes.pointer(out), ctypes.c_void_p)),
+           "rbgs_embedding_check")
+    return float(out.value)
 
 
 def rbgs_qr_host(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,

@@ -130,3 +130,18 @@ def test_rayleigh_ritz_argument_checks_need_no_device(lib):
     assert lib.rbgs_rayleigh_ritz(ctypes.byref(big), fake, 65536, 64, 18, 1, 0, 0, 2048, 0, None, fake, 65536,
                                   *ptrs) == 1
     assert lib.rbgs_rayleigh_ritz(None, fake, 64, 2, 4, 1, 0, 0, 16, 0, None, fake, 64, *ptrs) == 1
+
+
+def test_embedding_check_argument_checks_need_no_device(lib):
+    """rbgs_embedding_check refuses a missing output and bad sizes first."""
+    import ctypes
+
+    from paper_2111_14641_gb300 import rbgs as rbmod
+
+    lib = rbmod.load()
+    fake = ctypes.c_void_p(1 << 20)
+    out = ctypes.c_double(0.0)
+    outp = ctypes.cast(ctypes.pointer(out), ctypes.c_void_p)
+    assert lib.rbgs_embedding_check(fake, 100, 8, 100, 4, 0, 16, 0, 1, None, None) == 1     # no output
+    assert lib.rbgs_embedding_check(fake, 100, 8, 100, 4, 0, 101, 0, 1, None, outp) == 1    # k > n
+    assert lib.rbgs_embedding_check(fake, 100, 8, 99, 4, 0, 16, 0, 1, None, outp) == 1      # ldz < n

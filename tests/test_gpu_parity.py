@@ -422,3 +422,24 @@ def test_c2_full_size_properties(rb):
     E = np.eye(m) - S.T @ S
     assert np.linalg.norm(E, 2) <= 1e-6
     assert np.linalg.norm(E) <= 2e-5
+
+
+# ------------------------------------------- the a posteriori Phi check --
+
+@pytest.mark.parametrize("prec,kind", [("fp64", "gauss"), ("fp64", "srht"), ("f16x3", "srht"), ("fp32", "gauss")])
+def test_embedding_check_matches_oracle(rb, prec, kind):
+    """||I - (Theta Q_phi)^T Theta Q_phi||_F with Q_phi the RBGS factor of Z
+    under an independent sketch Phi, against the oracle; Phi = Theta gives the
+    sketched orthogonality of RBGS itself."""
+    n, m, mb, k = 3000, 32, 8, 128
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Z = synth.svd_matrix(n, m, 1e2, 74)
+    if prec != "fp64":
+        Z = Z.astype(np.float32).astype(np.float64)
+    Zd = dev(Z, td)
+    got = rb.embedding_check(Zd, mb, kind, k, 5, 9, prec=prec, ls_iters=3, fine=prec != "fp64")
+    want = oracle.embedding_check(Z, mb, kind, k, 5, 9, ls="richardson", ls_iters=3)
+    tol = 1e-9 * want if prec == "fp64" else 1e-4
+    assert abs(got - want) <= tol and 0.05 < want < 10.0
+    same = rb.embedding_check(Zd, mb, kind, k, 5, 5, prec=prec, ls_iters=3, fine=prec != "fp64")
+    assert same < (1e-12 if prec == "fp64" else 1e-4)

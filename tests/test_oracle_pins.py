@@ -602,3 +602,39 @@ def test_ritz_select_conventions():
     np.testing.assert_allclose(vals2, [5.0, 3.0 + 2.0j], atol=1e-10)
     vals3, _, _ = oracle.ritz_select(mu, V, 2, "SR")
     np.testing.assert_allclose(vals3, [-1.0, 1.0], atol=1e-10)
+
+
+# ------------------------------------------- the a posteriori Phi check --
+
+@pytest.mark.parametrize("kind", ["gauss", "srht"])
+def test_embedding_check_equals_dense_brute_force(kind):
+    """||I - M^T M||_F with M = (Theta Z) R^{-1}, R the R factor of Phi Z, both
+    sketches built as dense matrices (no RBGS involved)."""
+    n, m, mp, k = 600, 12, 4, 80
+    Z = synth.svd_matrix(n, m, 1e2, 71)
+    got = oracle.embedding_check(Z, mp, kind, k, 5, 9)
+    T = oracle.theta_dense(kind, k, n, 5)
+    F = oracle.theta_dense(kind, k, n, 9)
+    Rf = np.linalg.qr(F @ Z)[1]
+    M = (T @ Z) @ np.linalg.inv(Rf)
+    want = np.linalg.norm(np.eye(m) - M.T @ M, "fro")
+    assert abs(got - want) <= 1e-10 * max(want, 1.0)
+    assert 0.05 < want < 10.0   # two independent k = 80 sketches of a 12-dimensional space
+
+
+def test_embedding_check_with_phi_equal_theta_is_sketched_orthogonality():
+    """Phi = Theta: Theta Q_phi is orthonormal by construction, the check
+    returns the sketched orthogonality of RBGS (FP64 rounding)."""
+    n, m, mp, k = 800, 16, 4, 90
+    Z = synth.svd_matrix(n, m, 1e3, 72)
+    assert oracle.embedding_check(Z, mp, "gauss", k, 3, 3) < 1e-12
+
+
+def test_embedding_check_shrinks_with_k():
+    """A larger sketch embeds the same space better: the defect falls roughly
+    like sqrt(m / k)."""
+    n, m, mp = 4000, 10, 5
+    Z = synth.svd_matrix(n, m, 1e2, 73)
+    small = np.mean([oracle.embedding_check(Z, mp, "gauss", 40, s, s + 100) for s in range(4)])
+    large = np.mean([oracle.embedding_check(Z, mp, "gauss", 1000, s, s + 100) for s in range(4)])
+    assert large < small / 2.5
