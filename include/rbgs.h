@@ -89,7 +89,11 @@ typedef struct {
   int32_t interblock;  /* steps 4-5: 0 or 5 = Alg. 5 (the sketch of Q'_i taken implicitly as
                           P_i - S R, one tall pass per block); 4 = Alg. 4 (RCholeskyQR on
                           the explicit sketch Theta Q'_i: the projection, a sketch, and an
-                          in-place scaling by R_ii^{-1}, two tall passes per block)      */
+                          in-place scaling by R_ii^{-1}, two tall passes per block);
+                          1 = single-vector RGS and 3 = vRCholeskyQR (Alg. 3): after the
+                          projection, the block's columns one at a time (RBGS with
+                          one-column blocks on Q'_i, explicit or implicit sketches; needs
+                          reorth 0 or 1; not for the Sec. 5 solvers)                    */
 } rbgs_opts;
 
 typedef struct {

@@ -618,6 +618,12 @@ static int solve_ls(int ls, int ls_iters, int64_t k, int64_t c, const double* S,
   return 0;
 }
 
+typedef struct or_stencil or_stencil;
+static int rbgs_core(const double* W, int64_t n, int64_t m, int64_t ldw, int64_t mp, int theta, int64_t k,
+                     uint64_t seed, int variant, int ls, int ls_iters, int ls_iters_first, int reorth,
+                     const or_stencil* op, double* Q, int64_t ldq, double* R, int64_t ldr, double* S_out,
+                     double* P_out, double* stats);
+
 /* ------------------------------------------------------------------------ */
 /* Steps 4-5 of Alg. 2 on the block Qp (n x mp, in place -> Q_i).            *
  * Outputs R_ii (mp x mp) and S_i = Theta Q_i (k x mp).                      *
@@ -626,7 +632,22 @@ static int interblock(int variant, int64_t n, int64_t mp, double* Qp, int64_t ld
                       int theta, int64_t k, uint64_t seed, double* Rii, int64_t ldr, double* Si, int64_t ldsi) {
   double* Sp = (double*)malloc(sizeof(double) * (size_t)(k * mp));
   int rc = 0;
-  if (variant == 5) {
+  if (variant == 1 || variant == 3) {
+    /* Column by column within the block: single-vector RGS (1: each new
+       column's sketch taken explicitly, as in Alg. 4) or vRCholeskyQR (3,
+       Alg. 3: the sketch taken implicitly, as in Alg. 5).  Both are RBGS with
+       one-column blocks on Q'_i itself (Householder least squares). */
+    double* Qc = (double*)malloc(sizeof(double) * (size_t)(n * mp));
+    double* Rc = (double*)malloc(sizeof(double) * (size_t)(mp * mp));
+    for (int64_t j = 0; j < mp; ++j)
+      for (int64_t i = 0; i < n; ++i) Qc[i + j * n] = Qp[i + j * ldq];
+    rc |= rbgs_core(Qc, n, mp, n, 1, theta, k, seed, variant == 1 ? 4 : 5, 0, 0, 0, 0, NULL, Qp, ldq, Rc, mp, NULL,
+                    NULL, NULL) ? 1 : 0;
+    for (int64_t j = 0; j < mp; ++j)
+      for (int64_t i = 0; i < mp; ++i) Rii[i + j * ldr] = Rc[i + j * mp];
+    free(Qc);
+    free(Rc);
+  } else if (variant == 5) {
     /* Alg. 5: S'_i is P_i - S_{1:i-1} R_{1:i-1,i}, given by the caller.    */
     for (int64_t j = 0; j < mp; ++j)
       for (int64_t i = 0; i < k; ++i) Sp[i + j * k] = Spp[i + j * lds];
@@ -672,10 +693,10 @@ static int interblock(int variant, int64_t n, int64_t mp, double* Qp, int64_t ld
  * the unit square, nx x ny interior points with spacing hx = 1/(nx+1),
  * hy = 1/(ny+1), zero Dirichlet boundary, central differences; point (x, y)
  * is row x + nx y.  (The synthetic operator of the Krylov experiments.)     */
-typedef struct {
+struct or_stencil {
   int64_t nx, ny;
   double bx, by;
-} or_stencil;
+};
 
 void or_stencil5_apply(const or_stencil* op, const double* X, int64_t ldx, int64_t ncols, double* Y, int64_t ldy) {
   const int64_t nx = op->nx, ny = op->ny;

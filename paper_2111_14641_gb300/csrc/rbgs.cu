@@ -203,6 +203,14 @@ struct DevBuf {
   }
 };
 
+// The status words of an inner factorization folded into the outer ones.
+__global__ void merge_flags_kernel(const int* inner, int* brk, int* tmo) {
+  if (threadIdx.x == 0) {
+    if (inner[0]) *brk = 1;
+    if (inner[3]) *tmo = 1;
+  }
+}
+
 // Device copies of W, Q and R for the host-buffer entry point, kept per device
 // and grown on demand (freed by rbgs_release_workspace), and its two copy streams.
 struct HostPathBuf {
@@ -362,6 +370,10 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     }
     TS *Rii = sm[5], *Riinv = sm[6], *R2ii = sm[7], *R2iinv = sm[8], *Ieye = sm[9];
     const bool alg4 = o.interblock == 4;
+    // single-vector RGS (1) and vRCholeskyQR (3, Alg. 3): after the projection, the
+    // block's own columns are orthonormalised one at a time, by RBGS with one-column
+    // blocks on Q'_i (explicit sketches for RGS, implicit for Alg. 3), in place
+    const bool percol = o.interblock == 1 || o.interblock == 3;
     int* brk = flags;          // breakdown
     int* active = flags + 1;   // second pass on/off for this block
     int* npass2 = flags + 2;   // number of second passes
@@ -445,7 +457,70 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       RBGS_CUDA_TRY(cudaStreamSynchronize(st));
       return RBGS_OK;
     };
-    if (alg4 && (s = set_eye(mb))) return s;
+    if ((alg4 || percol) && (s = set_eye(mb))) return s;
+    // the inner factorization's own workspace, side stream, status words and R
+    DevBuf inner_buf;
+    size_t inner_need = 0;
+    cudaStream_t inner_side = nullptr;
+    struct SideFree {
+      cudaStream_t* s;
+      ~SideFree() {
+        if (*s) cudaStreamDestroy(*s);
+      }
+    } inner_side_free{&inner_side};
+    int* inner_flags = nullptr;
+    double* Rinner = nullptr;
+    if (percol) {
+      rbgs_opts oq = o;
+      oq.reorth = 0;
+      oq.interblock = o.interblock == 1 ? 4 : 5;
+      QrCtx cq;
+      cq.need_out = &inner_need;
+      if ((s = qr_impl<T, TS>(W, n, mbf, ldq, 1, sketch, k, seed, Q, ldq, R, mbf, oq, nullptr, mode, nullptr, &cq)))
+        return s;
+      const size_t extra = 256 + 8 * (size_t)mbf * mbf + 256;
+      if (cudaMalloc(&inner_buf.p, inner_need + extra) != cudaSuccess) {
+        cudaGetLastError();
+        return RBGS_ENOMEM;
+      }
+      inner_flags = (int*)((char*)inner_buf.p + inner_need);
+      Rinner = (double*)((char*)inner_buf.p + inner_need + 256);
+      RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&inner_side, cudaStreamNonBlocking));
+    }
+    auto percol_pass = [&](int64_t c, const TS* Xc, const T* src, int64_t ldsrc, T* Qo, const TS* sraw, TS* Rd,
+                           TS* Sout, bool split_final) -> rbgs_status {
+      rbgs_status r;
+      if ((r = make_g(c, Xc, Ieye, Ieye, nullptr, nullptr))) return r;
+      if ((r = tall(c, c, src, ldsrc, Qo, nullptr, sraw, false))) return r;
+      rbgs_opts oq = o;
+      oq.reorth = 0;
+      oq.interblock = o.interblock == 1 ? 4 : 5;
+      oq.sync = 0;
+      oq.timing = 0;
+      oq.certify = 0;
+      oq.stream = st;
+      QrCtx cq;
+      cq.ws = inner_buf.p;
+      cq.ws_bytes = inner_need;
+      cq.side = inner_side;
+      cq.status_out = inner_flags;
+      if ((r = qr_impl<T, TS>(Qo, n, mb, ldq, 1, sketch, k, seed, Qo, ldq, Rinner, mb, oq, nullptr, mode, nullptr,
+                              &cq)))
+        return r;
+      merge_flags_kernel<<<1, 32, 0, st>>>(inner_flags, brk, tmo);
+      RBGS_LAUNCH_CHECK();
+      if (sizeof(TS) == 8) {
+        RBGS_CUDA_TRY(cudaMemcpyAsync(Rd, Rinner, 8 * (size_t)mb * mb, cudaMemcpyDeviceToDevice, st));
+      } else if ((r = cast_cols_t<double, float>(mb, mb, Rinner, mb, (float*)Rd, mb, st))) {
+        return r;
+      }
+      if ((r = sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sout, k, skscr, sk_bytes, st))) return r;
+      if (mode == 2 && split_final) {  // the pre-split copy of Q_i for the later blocks: an identity pass
+        if ((r = make_g(0, nullptr, Ieye, Ieye, nullptr, nullptr))) return r;
+        if ((r = tall(0, c, Qo, ldq, Qo, nullptr, Sout, true))) return r;
+      }
+      return RBGS_OK;
+    };
     // Steps 4-5 by Alg. 4 (RCholeskyQR on the explicit sketch) for the block
     // src - Q_{1:c} Xc written to Qo (column c of Q): the projection with
     // G = [-Xc; I], its sketch S'_i = Theta Q'_i, Cholesky QR of S'_i (one or two
@@ -495,7 +570,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     for (int64_t blk = 0; blk < p; ++blk) {
       const int64_t c = blk * mbf;
       mb = (int)std::min<int64_t>(mbf, m - c);  // this block's width
-      if (alg4 && mb != mbf && (s = set_eye(mb))) return s;  // the narrower last block
+      if ((alg4 || percol) && mb != mbf && (s = set_eye(mb))) return s;  // the narrower last block
       if (ctx && ctx->w_ready && op == nullptr) RBGS_CUDA_TRY(cudaStreamWaitEvent(st, ctx->w_ready[blk], 0));
       const int64_t wnext = blk + 1 < p ? std::min<int64_t>(mbf, m - c - mbf) : 0;
       const T* Wi = W + c * ldw;
@@ -570,6 +645,9 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       if (alg4) {
         if ((s = alg4_pass(c, Xc, Wi, ldwi, Qi, Pi, provisional, Rii, Riinv, Si, split1, nullptr))) return s;
         if ((s = make_g(c, Xc, Rii, Riinv, Rcol, nullptr))) return s;  // the R column (G is not used again)
+      } else if (percol) {
+        if ((s = percol_pass(c, Xc, Wi, ldwi, Qi, Pi, Rii, Si, split1))) return s;
+        if ((s = make_g(c, Xc, Rii, Rii, Rcol, nullptr))) return s;  // the R column only
       } else {
         if (provisional) s = cholqr1<TS>(k, mb, Spc, sm, partf, brk, nullptr, st, Rii, Riinv);
         else s = cholqr2<TS>(k, mb, Spc, Res, sm, partf, brk, nullptr, st, Rii, Riinv, need2, n2count);
@@ -594,6 +672,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         }
         if (alg4) {
           if ((s = alg4_pass(c, X2, Qi, ldq, Qi, Si, false, R2ii, R2iinv, Si, true, active))) return s;
+        } else if (percol) {  // (the second pass always runs: reorth 2 is refused with these variants)
+          if ((s = percol_pass(c, X2, Qi, ldq, Qi, Si, R2ii, Si, true))) return s;
         } else {
           RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
           s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Sp, k, partf, kPartElems, active, st);
@@ -725,7 +805,9 @@ rbgs_status check_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t m
   if (n < 1 || n >= ((int64_t)1 << 31) || m < 1 || mb < 1 || mb > 64) return RBGS_EINVAL;
   if (ldw < n || ldq < n || ldr < m || k < m) return RBGS_EINVAL;
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2) return RBGS_EINVAL;
-  if (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) return RBGS_EINVAL;
+  if (o.interblock != 0 && o.interblock != 1 && o.interblock != 3 && o.interblock != 4 && o.interblock != 5)
+    return RBGS_EINVAL;
+  if ((o.interblock == 1 || o.interblock == 3) && o.reorth == 2) return RBGS_EINVAL;
   if (sketch == RBGS_SK_SRHT) {
     int64_t np = 1;
     while (np < n) np <<= 1;

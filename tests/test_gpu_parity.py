@@ -171,6 +171,37 @@ def test_fp64_single_cholesky_round_when_well_conditioned(rb):
     assert st32.chol_rounds2 == m // mb
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f16x3", "tf32x3", "fp32"])
+@pytest.mark.parametrize("interblock", [1, 3])
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_rbgs_column_by_column_interblock_matches_oracle(rb, prec, interblock, reorth):
+    """Steps 4-5 one column at a time after the projection: single-vector RGS
+    (1, explicit sketches) or vRCholeskyQR (3, Alg. 3, implicit sketches),
+    against the oracle's; a ragged last block included."""
+    n, m, mb, kind, k = 3000, 44, 16, "srht", 200
+    cond = 1e4 if prec == "fp64" else 1e3
+    W = synth.svd_matrix(n, m, cond, 78)
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Qd, Rd, st = rb.rbgs_qr(dev(W, td), mb, kind, k, 5, prec=prec, ls_iters=3, reorth=reorth, interblock=interblock,
+                            fine=prec != "fp64")
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, 5, variant=interblock, ls="richardson", ls_iters=3, reorth=bool(reorth),
+                      ls_iters_first=1)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    fact = oracle.factorization_error(W, Q, R)
+    ortho = oracle.sketched_orthogonality(Q, kind, k, 5)[0]
+    if prec == "fp64":
+        tol = 1e-12 * cond
+        assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+        assert np.abs(Q - ref["Q"]).max() <= tol * np.abs(ref["Q"]).max()
+        assert fact < 1e-14 and ortho < 1e-12
+    else:
+        assert fact < 2e-6 and ortho < (1e-4 if reorth else 1e-3)
+        assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "f16x3", "tf32x3"])
 @pytest.mark.parametrize("reorth", [0, 1])
 def test_rbgs_alg4_matches_oracle(rb, prec, reorth):
@@ -278,6 +309,8 @@ def test_invalid_arguments(rb):
     W = dev(synth.gaussian(100, 8, 1))
     with pytest.raises(rb.RbgsError):
         rb.rbgs_qr(W, 65, "gauss", 16, 0, prec="fp64")    # mb > 64
+    with pytest.raises(rb.RbgsError):                       # the column-by-column variants need reorth 0 or 1
+        rb.rbgs_qr(W, 4, "gauss", 16, 0, prec="fp64", reorth=2, interblock=3)
     with pytest.raises(rb.RbgsError):
         rb.rbgs_qr(W, 4, "gauss", 101, 0, prec="fp64")    # k > n
     with pytest.raises(rb.RbgsError):
