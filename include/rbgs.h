@@ -187,6 +187,17 @@ RBGS_API rbgs_status rbgs_embedding_check(const void* Z, int64_t n, int64_t m, i
                                           rbgs_sketch sketch, int64_t k, uint64_t seed_theta, uint64_t seed_phi,
                                           const rbgs_opts* opts, double* defect);
 
+/* Cholesky QR post-processing (the remark after Alg. 2): with R' the
+ * Cholesky factor of Q^T Q, Q <- Q R'^{-1} and R <- R' R, in place, so that Q
+ * becomes l2-orthonormal and W = Q R still holds.  Q: n x m device array of
+ * the prec type (ldq); R: m x m device double (ldr).  Q^T Q is formed with
+ * FP64 products (n m^2 FMA on the FP64 pipe), R' by a blocked Cholesky with
+ * blocks of mb (<= 64) columns, and Q R'^{-1} by a forward sweep over those
+ * blocks on the tall-update kernels of prec.  RBGS_EBREAKDOWN if Q^T Q is
+ * not positive definite.  Synchronous (sync is ignored).                  */
+RBGS_API rbgs_status rbgs_cholqr_postprocess(int32_t prec, int64_t n, int64_t m, void* Q, int64_t ldq, double* R,
+                                             int64_t ldr, int64_t mb, void* stream, int32_t sync);
+
 /* Y = Theta X (Sec. 2.3), the sketch of steps 1 and 5 of Alg. 2.
  *  X device n x ncols (ldx), double if prec == RBGS_P_FP64 else float.
  *  Y device k x ncols (ldy), double.  FP64 sums in double; other precisions

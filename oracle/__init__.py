@@ -14,6 +14,8 @@ What each function follows (Balabanov & Grigori, arXiv 2111.14641):
   generator).  Each side implements that convention separately.
 * ``rbgs``: Alg. 2 with steps 4-5 from Alg. 4, 5 or 6 and step-2 solvers
   from Sec. 3.1 and its supplement (Householder, Richardson, CG).
+* ``cholqr_postprocess``: the Cholesky QR post-processing of the remark
+  after Alg. 2 (an l2-orthonormal Q).
 * ``embedding_check``: the a posteriori check of Theta with an independent
   sketch Phi (Sec. 4, the epsilon-embedding subsection).
 * ``rcholqr``: the closed form that RBGS reaches in exact arithmetic
@@ -280,6 +282,17 @@ def block_krylov(method: str, nx: int, ny: int, bx: float, by: float, B, X0, p: 
     if cyc < 0:
         raise np.linalg.LinAlgError(f"block Krylov solver failed ({cyc})")
     return X, int(cyc), relres
+
+
+def cholqr_postprocess(Q, R):
+    """The Cholesky QR post-processing of the remark after Alg. 2: R' the
+    upper Cholesky factor of Q^T Q, Q <- Q R'^{-1}, R <- R' R (numpy's
+    Cholesky and triangular solve as the library steps).  Returns (Q, R)."""
+    Q = _f64(Q)
+    R = _f64(R)
+    Rp = np.linalg.cholesky(Q.T @ Q).T
+    Qn = np.linalg.solve(Rp.T, Q.T).T
+    return np.asfortranarray(Qn), np.asfortranarray(Rp @ R)
 
 
 def embedding_check(Z, mp: int, kind: str, k: int, seed_theta: int, seed_phi: int, variant: int = 5,

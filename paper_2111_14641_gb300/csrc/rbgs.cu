@@ -1142,6 +1142,104 @@ rbgs_status rbgs_qr_host(const void* W, int64_t n, int64_t m, int64_t ldw, int64
   return RBGS_OK;
 }
 
+// Cholesky QR post-processing (the remark after Alg. 2): R' = chol(Q^T Q),
+// Q <- Q R'^{-1}, R <- R' R, so that Q becomes l2-orthonormal.  The Gram matrix
+// is formed with FP64 products, R' by a blocked Cholesky (blocks of mb), and
+// Q R'^{-1} by a forward sweep over column blocks on the tall kernels:
+// block j becomes [Q_new(:, 0:c) | Q_j] [-R'(0:c, j) R'_jj^{-1}; R'_jj^{-1}].
+rbgs_status rbgs_cholqr_postprocess(int32_t prec, int64_t n, int64_t m, void* Q, int64_t ldq, double* R, int64_t ldr,
+                                    int64_t mb, void* stream, int32_t sync) {
+  if (!Q || !R || n < 1 || m < 1 || ldq < n || ldr < m || mb < 1 || mb > 64) return RBGS_EINVAL;
+  if (prec < RBGS_P_FP64 || prec > RBGS_P_F16X3) return RBGS_EINVAL;
+  if ((prec == RBGS_P_TF32X3 || prec == RBGS_P_F16X3) && (((uintptr_t)Q & 15) || (ldq % 4))) return RBGS_EINVAL;
+  const size_t es = prec == RBGS_P_FP64 ? 8 : 4;
+  if (ranges_overlap(R, 8 * (size_t)(ldr * (m - 1) + m), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nb = (m + mb - 1) / mb;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t bmm = up(8 * (size_t)m * m), bt = up(8 * (size_t)mb * m), bd = up(8 * (size_t)mb * mb * nb),
+               bg = up(8 * (size_t)m * mb), bpart = up(8 * (size_t)kPartElems);
+  DevBuf buf;
+  if (cudaMalloc(&buf.p, 3 * bmm + bt + 2 * bd + bg + bpart + 1024) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  char* w = (char*)buf.p;
+  double* G = (double*)w;                     // Q^T Q, m x m
+  double* Rp = (double*)(w + bmm);            // R', m x m (upper)
+  double* Tmp = (double*)(w + 2 * bmm);       // R' R
+  double* Tb = (double*)(w + 3 * bmm);        // one block row of the Schur complement, mb x m (ld mb)
+  double* Dd = (double*)(w + 3 * bmm + bt);   // diagonal blocks R'_jj, mb x mb each
+  double* Di = (double*)(w + 3 * bmm + bt + bd);  // their inverses
+  double* Gb = (double*)(w + 3 * bmm + bt + 2 * bd);  // coefficients of one forward-sweep block
+  double* part = (double*)(w + 3 * bmm + bt + 2 * bd + bg);
+  int* flag = (int*)(w + 3 * bmm + bt + 2 * bd + bg + bpart);
+  RBGS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  RBGS_CUDA_TRY(cudaMemsetAsync(Rp, 0, 8 * (size_t)m * m, st));
+  rbgs_status s;
+  // G = Q^T Q in FP64
+  for (int64_t j0 = 0; j0 < m; j0 += 64) {
+    const int64_t nc = std::min<int64_t>(64, m - j0);
+    if (prec == RBGS_P_FP64)
+      s = small_gemm<double, double, double>(1, m, nc, n, 1.0, (const double*)Q, ldq, (const double*)Q + j0 * ldq, ldq,
+                                             0.0, G + j0 * m, m, part, kPartElems, nullptr, st);
+    else
+      s = small_gemm<float, double, double>(1, m, nc, n, 1.0, (const float*)Q, ldq, (const float*)Q + j0 * ldq, ldq,
+                                            0.0, G + j0 * m, m, part, kPartElems, nullptr, st);
+    if (s) return s;
+  }
+  // blocked Cholesky, row block by row block: T = G(c:c+w, c:m) - R'(0:c, c:c+w)^T R'(0:c, c:m);
+  // R'_jj = chol(T(:, 0:w)); R'(c:c+w, c+w:m) = R'_jj^{-T} T(:, w:)
+  for (int64_t jb = 0; jb < nb; ++jb) {
+    const int64_t c = jb * mb, wd = std::min<int64_t>(mb, m - c), rest = m - c;
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(Tb, 8 * (size_t)wd, G + c + c * m, 8 * (size_t)m, 8 * (size_t)wd, (size_t)rest,
+                                    cudaMemcpyDeviceToDevice, st));
+    if (c > 0) {
+      for (int64_t t0 = 0; t0 < rest; t0 += 64) {
+        const int64_t nt = std::min<int64_t>(64, rest - t0);
+        s = small_gemm<double, double, double>(1, wd, nt, c, -1.0, Rp + c * m, m, Rp + (c + t0) * m, m, 1.0,
+                                               Tb + t0 * wd, wd, part, kPartElems, nullptr, st);
+        if (s) return s;
+      }
+    }
+    double* Rjj = Dd + (size_t)jb * mb * mb;
+    double* Rjjinv = Di + (size_t)jb * mb * mb;
+    if ((s = chol_inv<double>((int)wd, Tb, Rjj, Rjjinv, 0.0, flag, nullptr, nullptr, nullptr, st))) return s;
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(Rp + c + c * m, 8 * (size_t)m, Rjj, 8 * (size_t)wd, 8 * (size_t)wd, (size_t)wd,
+                                    cudaMemcpyDeviceToDevice, st));
+    for (int64_t t0 = wd; t0 < rest; t0 += 64) {
+      const int64_t nt = std::min<int64_t>(64, rest - t0);
+      s = small_gemm<double, double, double>(1, wd, nt, wd, 1.0, Rjjinv, wd, Tb + t0 * wd, wd, 0.0,
+                                             Rp + c + (c + t0) * m, m, part, kPartElems, nullptr, st);
+      if (s) return s;
+    }
+  }
+  // Q <- Q R'^{-1}: the forward sweep, in place, block by block
+  for (int64_t jb = 0; jb < nb; ++jb) {
+    const int64_t c = jb * mb, wd = std::min<int64_t>(mb, m - c);
+    s = assemble_g<double, double>(c, (int)wd, Rp + c * m, m, Dd + (size_t)jb * mb * mb, Di + (size_t)jb * mb * mb, Gb,
+                                   c + wd, nullptr, 0, nullptr, st);
+    if (s) return s;
+    char* Qj = (char*)Q + es * (size_t)(c * ldq);
+    s = rbgs_tall_update(prec, n, c, wd, c > 0 ? Q : nullptr, ldq, Qj, ldq, Gb, c + wd, Qj, ldq, stream, 0);
+    if (s) return s;
+  }
+  // R <- R' R (both upper triangular)
+  for (int64_t t0 = 0; t0 < m; t0 += 64) {
+    const int64_t nt = std::min<int64_t>(64, m - t0);
+    s = small_gemm<double, double, double>(0, m, nt, m, 1.0, Rp, m, R + t0 * ldr, ldr, 0.0, Tmp + t0 * m, m, part,
+                                           kPartElems, nullptr, st);
+    if (s) return s;
+  }
+  RBGS_CUDA_TRY(cudaMemcpy2DAsync(R, 8 * (size_t)ldr, Tmp, 8 * (size_t)m, 8 * (size_t)m, (size_t)m,
+                                  cudaMemcpyDeviceToDevice, st));
+  int hf = 0;
+  RBGS_CUDA_TRY(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBGS_CUDA_TRY(cudaStreamSynchronize(st));  // the buffers are freed on return
+  (void)sync;
+  return hf ? RBGS_EBREAKDOWN : RBGS_OK;
+}
+
 rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,
                               int64_t ldx, int64_t ncols, double* Y, int64_t ldy, void* stream, int32_t sync) {
   if (!X || !Y || n < 1 || k < 1 || ncols < 0 || ldx < n || ldy < k) return RBGS_EINVAL;

@@ -114,6 +114,7 @@ def load(build_if_missing: bool = False):
     lib.rbgs_qr_batched.argtypes = [ctypes.POINTER(Problem), i64, ctypes.c_int, ctypes.POINTER(Opts), i32]
     lib.rbgs_embedding_check.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, u64, ctypes.POINTER(Opts),
                                          vp]
+    lib.rbgs_cholqr_postprocess.argtypes = [i32, i64, i64, vp, i64, vp, i64, i64, vp, i32]
     lib.rbgs_qr_host.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
                                  ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
     lib.rbgs_release_workspace.argtypes = []
@@ -122,7 +123,7 @@ def load(build_if_missing: bool = False):
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
                  "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
                  "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched", "rbgs_qr_host",
-                 "rbgs_embedding_check"):
+                 "rbgs_embedding_check", "rbgs_cholqr_postprocess"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -225,6 +226,17 @@ def embedding_check(Z: torch.Tensor, mb: int, sketch: str = "srht", k: int | Non
                                      ctypes.byref(o), ctypes.cast(ctypes.pointer(out), ctypes.c_void_p)),
            "rbgs_embedding_check")
     return float(out.value)
+
+
+def cholqr_postprocess(Q: torch.Tensor, R: torch.Tensor, mb: int = 64, prec: str | None = None, stream=None):
+    """In place: Q <- Q R'^{-1}, R <- R' R with R' = chol(Q^T Q) (the remark
+    after Alg. 2), making Q l2-orthonormal.  Returns (Q, R)."""
+    lib = load()
+    prec = _prec_of(Q, prec)
+    n, m = Q.shape
+    _check(lib.rbgs_cholqr_postprocess(PREC[prec], n, m, Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(), _ld(R, "R"), mb,
+                                        _stream_ptr(stream), 1), "rbgs_cholqr_postprocess")
+    return Q, R
 
 
 def rbgs_qr_host(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,

@@ -476,3 +476,36 @@ def test_embedding_check_matches_oracle(rb, prec, kind):
     assert abs(got - want) <= tol and 0.05 < want < 10.0
     same = rb.embedding_check(Zd, mb, kind, k, 5, 5, prec=prec, ls_iters=3, fine=prec != "fp64")
     assert same < (1e-12 if prec == "fp64" else 1e-4)
+
+
+# ------------------------------------------------ Cholesky QR post-processing --
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3", "tf32x3", "fp32"])
+@pytest.mark.parametrize("pmb", [64, 16, 48])
+def test_cholqr_postprocess_matches_oracle(rb, prec, pmb):
+    """The post-processing of an RBGS factorization on the GPU against the
+    oracle's on the same Q, R: an l2-orthonormal Q, W = QR kept, and for FP64
+    the thin Householder QR of W."""
+    n, m, mb, k = 5000, 100, 20, 240
+    cond = 1e4 if prec == "fp64" else 1e2
+    td = torch.float64 if prec == "fp64" else torch.float32
+    W = synth.svd_matrix(n, m, cond, 83)
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    Qd, Rd, _ = rb.rbgs_qr(dev(W, td), mb, "srht", k, 4, prec=prec, ls_iters=2, reorth=1, fine=prec != "fp64")
+    Q0, R0 = host(Qd), host(Rd)
+    rb.cholqr_postprocess(Qd, Rd, mb=pmb, prec=prec)
+    Q, R = host(Qd), host(Rd)
+    Qo, Ro = oracle.cholqr_postprocess(Q0, R0)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    orth = np.abs(Q.T @ Q - np.eye(m)).max()
+    fact = oracle.factorization_error(W, Q, R)
+    if prec == "fp64":
+        assert orth < 1e-13 and fact < 1e-14
+        np.testing.assert_allclose(R, Ro, atol=1e-12 * np.abs(Ro).max())
+        np.testing.assert_allclose(Q, Qo, atol=1e-10)
+        Rn = np.linalg.qr(W)[1]
+        np.testing.assert_allclose(R, np.sign(np.diag(Rn))[:, None] * Rn, atol=1e-10 * np.abs(Rn).max())
+    else:
+        assert orth < 2e-5 and fact < 5e-6
+        np.testing.assert_allclose(R, Ro, atol=1e-5 * np.abs(Ro).max())

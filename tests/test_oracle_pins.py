@@ -638,3 +638,31 @@ def test_embedding_check_shrinks_with_k():
     small = np.mean([oracle.embedding_check(Z, mp, "gauss", 40, s, s + 100) for s in range(4)])
     large = np.mean([oracle.embedding_check(Z, mp, "gauss", 1000, s, s + 100) for s in range(4)])
     assert large < small / 2.5
+
+
+# ------------------------------------------------ Cholesky QR post-processing --
+
+@pytest.mark.parametrize("kind", ["gauss", "srht"])
+def test_cholqr_postprocess_gives_householder_qr(kind):
+    """After the post-processing Q is l2-orthonormal and W = QR with a positive
+    diagonal, which makes (Q, R) the unique thin QR of W: numpy's Householder
+    QR up to the column signs."""
+    n, m, mp, k = 2000, 24, 6, 120
+    W = synth.svd_matrix(n, m, 1e4, 81)
+    out = oracle.rbgs(W, mp, kind, k, 2)
+    Q, R = oracle.cholqr_postprocess(out["Q"], out["R"])
+    assert np.abs(Q.T @ Q - np.eye(m)).max() < 1e-13
+    assert np.linalg.norm(W - Q @ R) / np.linalg.norm(W) < 1e-14
+    Qn, Rn = np.linalg.qr(W)
+    sg = np.sign(np.diag(Rn))
+    np.testing.assert_allclose(R, sg[:, None] * Rn, atol=1e-11 * np.abs(Rn).max())
+    np.testing.assert_allclose(Q, Qn * sg, atol=1e-8)
+
+
+def test_cholqr_postprocess_keeps_an_orthonormal_q():
+    """An l2-orthonormal Q (RBGS with Theta = I) gives R' = I."""
+    W = synth.svd_matrix(300, 12, 1e2, 82)
+    out = oracle.rbgs(W, 4, "identity", 300, 0)
+    Q, R = oracle.cholqr_postprocess(out["Q"], out["R"])
+    np.testing.assert_allclose(Q, out["Q"], atol=1e-13)
+    np.testing.assert_allclose(R, out["R"], atol=1e-12 * np.abs(out["R"]).max())
