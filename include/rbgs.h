@@ -94,6 +94,10 @@ typedef struct {
                           projection, the block's columns one at a time (RBGS with
                           one-column blocks on Q'_i, explicit or implicit sketches; needs
                           reorth 0 or 1; not for the Sec. 5 solvers)                    */
+  int32_t ls;          /* step 2 solver: 0 = Richardson (X <- X + S^T (P - S X), ls_iters
+                          steps from 0); 1 = conjugate gradients on the normal equations
+                          (S^T S) X = S^T P, ls_iters steps from 0, column by column
+                          (Sec. 3.1 and its supplement)                                  */
 } rbgs_opts;
 
 typedef struct {

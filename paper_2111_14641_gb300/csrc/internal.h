@@ -179,6 +179,15 @@ rbgs_status ritz_eig(int N, int mb, int mp, int which, const double* H, int64_t 
 // X[:, j] /= norms[j] (n x ncols, double)
 rbgs_status scale_cols(int64_t n, int64_t ncols, const double* norms, double* X, int64_t ldx, cudaStream_t st);
 
+// Conjugate gradients on the normal equations of step 2, column by column:
+// cg_init sets rr = ||r_j||^2 (r = S^T p); cg_step performs one step given
+// q = S^T S d (all c x mb with leading dimension ld; X with ldx).
+template <class TS>
+rbgs_status cg_init(int64_t c, int mb, const TS* Rr, int64_t ld, double* rr, int* done, cudaStream_t st);
+template <class TS>
+rbgs_status cg_step(int64_t c, int mb, TS* X, int64_t ldx, TS* Rr, TS* D, const TS* Qq, int64_t ld, double* rr,
+                    int* done, cudaStream_t st);
+
 // Elementwise C = A - B (k x mb) in TS.
 template <class TS>
 rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,

@@ -355,7 +355,14 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     TS* partf = cv.take<TS>(kPartElems);
     // look-ahead of step 2 on the side stream (second X buffer, the partial
     // residuals of the next block, the side stream's partial-sum scratch)
-    const bool look = p > 1 && op == nullptr && (o.reorth != 0 || l == 1);
+    const bool cg = o.ls == 1;  // step 2 by conjugate gradients
+    const bool look = p > 1 && op == nullptr && !cg && (o.reorth != 0 || l == 1);
+    TS* cgR = cg ? cv.take<TS>((size_t)m * mb) : nullptr;
+    TS* cgD = cg ? cv.take<TS>((size_t)m * mb) : nullptr;
+    TS* cgQ = cg ? cv.take<TS>((size_t)m * mb) : nullptr;
+    TS* cgT = cg ? cv.take<TS>((size_t)k * mb) : nullptr;
+    double* cgrr = cg ? cv.take<double>(64) : nullptr;
+    int* cgdone = cg ? cv.take<int>(64) : nullptr;
     TS* Xalt = look ? cv.take<TS>((size_t)m * mb) : nullptr;
     TS* Spo[2] = {look ? cv.take<TS>((size_t)k * mb) : nullptr, look ? cv.take<TS>((size_t)k * mb) : nullptr};
     TS* partf2 = look ? cv.take<TS>(kPartElems) : nullptr;
@@ -458,6 +465,25 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       return RBGS_OK;
     };
     if ((alg4 || percol) && (s = set_eye(mb))) return s;
+    // step 2: X (c x mb, ld m) from P (k x mb) by Richardson or by conjugate gradients, `its` steps
+    auto step2 = [&](int64_t c, const TS* Pb, TS* Xo, int its) -> rbgs_status {
+      if (!cg) return richardson<TS>(k, c, mb, S, Pb, Xo, m, Res, its, partf, nullptr, st);
+      rbgs_status r;
+      RBGS_CUDA_TRY(cudaMemset2DAsync(Xo, sizeof(TS) * m, 0, sizeof(TS) * c, mb, st));
+      if ((r = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Pb, k, 0.0, cgR, m, partf, kPartElems, nullptr, st)))
+        return r;
+      RBGS_CUDA_TRY(cudaMemcpy2DAsync(cgD, sizeof(TS) * m, cgR, sizeof(TS) * m, sizeof(TS) * c, mb,
+                                      cudaMemcpyDeviceToDevice, st));
+      if ((r = cg_init<TS>(c, mb, cgR, m, cgrr, cgdone, st))) return r;
+      for (int it = 0; it < its; ++it) {
+        if ((r = small_gemm<TS, TS, TS>(0, k, mb, c, 1.0, S, k, cgD, m, 0.0, cgT, k, partf, kPartElems, nullptr, st)))
+          return r;
+        if ((r = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, cgT, k, 0.0, cgQ, m, partf, kPartElems, nullptr, st)))
+          return r;
+        if ((r = cg_step<TS>(c, mb, Xo, m, cgR, cgD, cgQ, m, cgrr, cgdone, st))) return r;
+      }
+      return RBGS_OK;
+    };
     // the inner factorization's own workspace, side stream, status words and R
     DevBuf inner_buf;
     size_t inner_need = 0;
@@ -633,7 +659,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
                                    nullptr, st);
         if (s) return s;
       } else if (c > 0) {
-        if ((s = richardson<TS>(k, c, mb, S, Pi, X, m, Res, provisional ? 1 : l, partf, nullptr, st))) return s;
+        if ((s = step2(c, Pi, X, provisional ? 1 : l))) return s;
         RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Pi, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
         s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X, m, 1.0, Sp, k, partf, kPartElems, nullptr, st);
         if (s) return s;
@@ -660,10 +686,14 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       }
       // optional second projection pass
       if (o.reorth && c > 0) {
-        s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Si, k, 0.0, X2, m, partf, kPartElems, nullptr, st);
-        if (s) return s;
+        if (cg) {
+          if ((s = step2(c, Si, X2, l))) return s;
+        } else {
+          s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Si, k, 0.0, X2, m, partf, kPartElems, nullptr, st);
+          if (s) return s;
+        }
         if ((s = reorth_decide<TS>(c, mb, X2, m, o.reorth_tol, o.reorth, active, npass2, blk_on + blk, st))) return s;
-        for (int it = 1; it < l; ++it) {
+        for (int it = 1; it < l && !cg; ++it) {
           RBGS_CUDA_TRY(cudaMemcpyAsync(Res, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
           s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Res, k, partf, kPartElems, active, st);
           if (s) return s;
@@ -808,6 +838,7 @@ rbgs_status check_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t m
   if (o.interblock != 0 && o.interblock != 1 && o.interblock != 3 && o.interblock != 4 && o.interblock != 5)
     return RBGS_EINVAL;
   if ((o.interblock == 1 || o.interblock == 3) && o.reorth == 2) return RBGS_EINVAL;
+  if (o.ls != 0 && o.ls != 1) return RBGS_EINVAL;
   if (sketch == RBGS_SK_SRHT) {
     int64_t np = 1;
     while (np < n) np <<= 1;
@@ -1435,7 +1466,7 @@ rbgs_status krylov_solve(int method, const rbgs_op* op, const double* B, int64_t
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
-      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5))
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1))
     return RBGS_EINVAL;
   o.sync = 1;  // one synchronisation per cycle (breakdown and convergence are read on the host)
   o.timing = 0;
@@ -1540,7 +1571,7 @@ rbgs_status rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int6
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
-      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5))
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1))
     return RBGS_EINVAL;
   o.sync = 1;
   o.timing = 0;
@@ -1649,7 +1680,7 @@ rbgs_status rbgs_block_arnoldi(const rbgs_op* op, const void* B, int64_t ldb, in
   if (!B || !Q || !R || mb < 1 || mb > 64 || p < 1 || ldb < n || ldq < n || ldr < m) return RBGS_EINVAL;
   if ((s = check_sketch(sketch, n, k, m))) return s;
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
-      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5))
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1))
     return RBGS_EINVAL;
   const size_t es = o.prec == RBGS_P_FP64 ? 8 : 4;
   if (o.prec >= RBGS_P_TF32X3 && (((uintptr_t)B & 15) || ((uintptr_t)Q & 15) || (ldb % 4) || (ldq % 4)))

@@ -444,6 +444,83 @@ __global__ void round2_decide_kernel(int mb, const T* __restrict__ R1, const T* 
   }
 }
 
+// One conjugate-gradient step on the normal equations (S^T S) x_j = S^T p_j of
+// step 2, for every column j at once (one CTA per column): with q = S^T S d
+// given, alpha = rr / (d.q); x += alpha d; r -= alpha q; beta = rr' / rr;
+// d = r + beta d.  A column whose d.q <= 0 (or rr = 0) stops for good (done[j]).
+template <class TS>
+__global__ void __launch_bounds__(256) cg_step_kernel(int64_t c, TS* X, int64_t ldx, TS* Rr, TS* D, const TS* Qq,
+                                                      int64_t ld, double* rr, int* done) {
+  const int j = blockIdx.x;
+  __shared__ double red[256];
+  __shared__ double sh_alpha, sh_beta;
+  __shared__ int sh_go;
+  if (done[j]) return;
+  TS* x = X + (int64_t)j * ldx;
+  TS* r = Rr + (int64_t)j * ld;
+  TS* d = D + (int64_t)j * ld;
+  const TS* q = Qq + (int64_t)j * ld;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < c; i += blockDim.x) s += (double)d[i] * (double)q[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double dq = red[0];
+    sh_go = (dq > 0.0 && rr[j] > 0.0) ? 1 : 0;
+    sh_alpha = sh_go ? rr[j] / dq : 0.0;
+    if (!sh_go) done[j] = 1;
+  }
+  __syncthreads();
+  if (!sh_go) return;
+  const TS alpha = (TS)sh_alpha;
+  double s2 = 0.0;
+  for (int64_t i = threadIdx.x; i < c; i += blockDim.x) {
+    x[i] += alpha * d[i];
+    const TS ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s2 += (double)ri * (double)ri;
+  }
+  red[threadIdx.x] = s2;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sh_beta = rr[j] > 0.0 ? red[0] / rr[j] : 0.0;
+    rr[j] = red[0];
+  }
+  __syncthreads();
+  const TS beta = (TS)sh_beta;
+  for (int64_t i = threadIdx.x; i < c; i += blockDim.x) d[i] = r[i] + beta * d[i];
+}
+
+// rr[j] = ||r_j||^2 and done[j] = 0, one CTA per column.
+template <class TS>
+__global__ void __launch_bounds__(256) cg_init_kernel(int64_t c, const TS* Rr, int64_t ld, double* rr, int* done) {
+  const int j = blockIdx.x;
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < c; i += blockDim.x) {
+    const double v = (double)Rr[i + (int64_t)j * ld];
+    s += v * v;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    rr[j] = red[0];
+    done[j] = 0;
+  }
+}
+
 template <class TS>
 __global__ void sub_mat_kernel(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C,
                                int64_t ldc, const int* active) {
@@ -630,6 +707,26 @@ template rbgs_status round2_decide<double>(int, const double*, const double*, do
                                            int*, int*, cudaStream_t);
 template rbgs_status round2_decide<float>(int, const float*, const float*, float*, float*, double, const int*,
                                           int*, int*, cudaStream_t);
+
+template <class TS>
+rbgs_status cg_init(int64_t c, int mb, const TS* Rr, int64_t ld, double* rr, int* done, cudaStream_t st) {
+  cg_init_kernel<TS><<<mb, 256, 0, st>>>(c, Rr, ld, rr, done);
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
+template <class TS>
+rbgs_status cg_step(int64_t c, int mb, TS* X, int64_t ldx, TS* Rr, TS* D, const TS* Qq, int64_t ld, double* rr,
+                    int* done, cudaStream_t st) {
+  cg_step_kernel<TS><<<mb, 256, 0, st>>>(c, X, ldx, Rr, D, Qq, ld, rr, done);
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
+template rbgs_status cg_init<double>(int64_t, int, const double*, int64_t, double*, int*, cudaStream_t);
+template rbgs_status cg_init<float>(int64_t, int, const float*, int64_t, double*, int*, cudaStream_t);
+template rbgs_status cg_step<double>(int64_t, int, double*, int64_t, double*, double*, const double*, int64_t,
+                                     double*, int*, cudaStream_t);
+template rbgs_status cg_step<float>(int64_t, int, float*, int64_t, float*, float*, const float*, int64_t, double*,
+                                    int*, cudaStream_t);
 
 template <class TS>
 rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,

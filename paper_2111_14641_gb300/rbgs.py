@@ -37,7 +37,10 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("ls_iters", ctypes.c_int32), ("reorth", ctypes.c_int32),
                 ("certify", ctypes.c_int32), ("reorth_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("sync", ctypes.c_int32), ("timing", ctypes.c_int32), ("fine", ctypes.c_int32),
-                ("interblock", ctypes.c_int32)]
+                ("interblock", ctypes.c_int32), ("ls", ctypes.c_int32)]
+
+
+LS = {"richardson": 0, "cg": 1}
 
 
 class Problem(ctypes.Structure):
@@ -182,7 +185,7 @@ def _empty_cols(n: int, m: int, dtype, device) -> torch.Tensor:
 def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
             prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
             certify: bool = False, Q: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None,
-            sync: bool = True, timing: bool = False, fine: bool = False, interblock: int = 5):
+            sync: bool = True, timing: bool = False, fine: bool = False, interblock: int = 5, ls: str = "richardson"):
     """RBGS QR of W (n x m, column-major).  Returns (Q, R, QRStats | None).
     fine=True (FP32 / TF32X3 storage only) runs the sketch-space steps in FP64;
     interblock selects steps 4-5: 5 = Alg. 5 (implicit sketch), 4 = Alg. 4."""
@@ -200,6 +203,7 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
     o.reorth_tol, o.stream, o.sync, o.timing = reorth_tol, _stream_ptr(stream), int(sync), int(timing)
     o.fine = int(fine)
     o.interblock = int(interblock)
+    o.ls = LS[ls]
     st = Stats()
     code = lib.rbgs_qr(W.data_ptr(), n, m, _ld(W, "W"), mb, SKETCH[sketch], k, seed, Q.data_ptr(), _ld(Q, "Q"),
                        R.data_ptr(), _ld(R, "R"), ctypes.byref(o), ctypes.byref(st) if sync else None)

@@ -509,3 +509,35 @@ def test_cholqr_postprocess_matches_oracle(rb, prec, pmb):
     else:
         assert orth < 2e-5 and fact < 5e-6
         np.testing.assert_allclose(R, Ro, atol=1e-5 * np.abs(Ro).max())
+
+
+# ------------------------------------------------ step 2 by conjugate gradients --
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+@pytest.mark.parametrize("interblock", [5, 4])
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_rbgs_cg_step2_matches_oracle(rb, prec, interblock, reorth):
+    """Step 2 by l conjugate-gradient steps on the normal equations, column
+    by column (20 steps, the paper's first experiment), against the oracle."""
+    n, m, mb, kind, k = 3000, 48, 16, "gauss", 200
+    cond = 1e4 if prec == "fp64" else 1e3
+    W = synth.svd_matrix(n, m, cond, 79)
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Qd, Rd, st = rb.rbgs_qr(dev(W, td), mb, kind, k, 5, prec=prec, ls_iters=20, reorth=reorth, interblock=interblock,
+                            ls="cg", fine=prec != "fp64")
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, 5, variant=interblock, ls="cg", ls_iters=20, reorth=bool(reorth),
+                      ls_iters_first=1)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    fact = oracle.factorization_error(W, Q, R)
+    ortho = oracle.sketched_orthogonality(Q, kind, k, 5)[0]
+    if prec == "fp64":
+        tol = 1e-12 * cond
+        assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+        assert np.abs(Q - ref["Q"]).max() <= tol * np.abs(ref["Q"]).max()
+        assert fact < 1e-14 and ortho < 10 * ref["delta"] + 1e-13  # single pass: about u cond(W), like the oracle
+    else:
+        assert fact < 2e-6 and ortho < (1e-4 if reorth else 1e-3)
+        assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
