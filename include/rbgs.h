@@ -202,6 +202,24 @@ RBGS_API rbgs_status rbgs_embedding_check(const void* Z, int64_t n, int64_t m, i
 RBGS_API rbgs_status rbgs_cholqr_postprocess(int32_t prec, int64_t n, int64_t m, void* Q, int64_t ldq, double* R,
                                              int64_t ldr, int64_t mb, void* stream, int32_t sync);
 
+/* A factorization captured as a CUDA graph, for many factorizations of the
+ * same shape on the same buffers (new contents of W each time): create
+ * captures one rbgs_qr on W, Q, R (the pointers, sizes and options are fixed
+ * in the graph) after one ordinary run that fills the library's caches; the
+ * graph owns its workspace, side stream and status words.  launch replays
+ * it on stream (asynchronous; with sync, waits and returns the status as
+ * rbgs_qr would).  The sketch plans it uses stay cached until
+ * rbgs_release_workspace, which must not be called while a graph exists.
+ * Not for opts->interblock 1 or 3 (RBGS_EINVAL).  The paper has no
+ * counterpart: this removes the per-launch host cost of the ~30 launches per
+ * block when the blocks are small.                                          */
+typedef struct rbgs_graph rbgs_graph;
+RBGS_API rbgs_status rbgs_qr_graph_create(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb,
+                                          rbgs_sketch sketch, int64_t k, uint64_t seed, void* Q, int64_t ldq,
+                                          double* R, int64_t ldr, const rbgs_opts* opts, rbgs_graph** out);
+RBGS_API rbgs_status rbgs_qr_graph_launch(rbgs_graph* g, void* stream, int32_t sync);
+RBGS_API rbgs_status rbgs_qr_graph_destroy(rbgs_graph* g);
+
 /* Y = Theta X (Sec. 2.3), the sketch of steps 1 and 5 of Alg. 2.
  *  X device n x ncols (ldx), double if prec == RBGS_P_FP64 else float.
  *  Y device k x ncols (ldy), double.  FP64 sums in double; other precisions

@@ -203,6 +203,12 @@ struct DevBuf {
   }
 };
 
+// The w x w identity (ld w).
+template <class TS>
+__global__ void eye_kernel(int w, TS* I) {
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) I[e] = (e % w == e / w) ? (TS)1 : (TS)0;
+}
+
 // The status words of an inner factorization folded into the outer ones.
 __global__ void merge_flags_kernel(const int* inner, int* brk, int* tmo) {
   if (threadIdx.x == 0) {
@@ -458,10 +464,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     };
     // the identity (ld w), for the projection G = [-X; I] of Alg. 4
     auto set_eye = [&](int w) -> rbgs_status {
-      std::vector<TS> eye((size_t)w * w, (TS)0);
-      for (int j = 0; j < w; ++j) eye[(size_t)j * w + j] = (TS)1;
-      RBGS_CUDA_TRY(cudaMemcpyAsync(Ieye, eye.data(), sizeof(TS) * eye.size(), cudaMemcpyHostToDevice, st));
-      RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+      eye_kernel<TS><<<1, 256, 0, st>>>(w, Ieye);
+      RBGS_LAUNCH_CHECK();
       return RBGS_OK;
     };
     if ((alg4 || percol) && (s = set_eye(mb))) return s;
@@ -1269,6 +1273,116 @@ rbgs_status rbgs_cholqr_postprocess(int32_t prec, int64_t n, int64_t m, void* Q,
   RBGS_CUDA_TRY(cudaStreamSynchronize(st));  // the buffers are freed on return
   (void)sync;
   return hf ? RBGS_EBREAKDOWN : RBGS_OK;
+}
+
+}  // extern "C"
+
+// A captured factorization: the graph of one rbgs_qr on fixed W, Q, R with its
+// own workspace, side stream and status words, so that later library calls
+// (which may grow or free the shared workspace) do not touch its buffers.
+struct rbgs_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t side = nullptr;
+  void* ws = nullptr;
+  int* status = nullptr;
+};
+
+extern "C" {
+
+rbgs_status rbgs_qr_graph_destroy(rbgs_graph* g) {
+  if (!g) return RBGS_OK;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->side) {
+    cudaStreamSynchronize(g->side);
+    cudaStreamDestroy(g->side);
+  }
+  if (g->ws) cudaFree(g->ws);
+  if (g->status) cudaFree(g->status);
+  delete g;
+  return RBGS_OK;
+}
+
+rbgs_status rbgs_qr_graph_create(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch,
+                                 int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr,
+                                 const rbgs_opts* opts, rbgs_graph** out) {
+  if (!out) return RBGS_EINVAL;
+  *out = nullptr;
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  rbgs_status s = check_qr(W, n, m, ldw, mb, sketch, k, Q, ldq, R, ldr, o);
+  if (s) return s;
+  if (o.interblock == 1 || o.interblock == 3) return RBGS_EINVAL;  // they allocate inside the factorization
+  o.sync = 0;
+  o.timing = 0;
+  o.certify = 0;
+  rbgs_graph* g = new rbgs_graph();
+  struct Undo {
+    rbgs_graph** g;
+    ~Undo() {
+      if (*g) rbgs_qr_graph_destroy(*g);
+    }
+  } undo{&g};
+  size_t need = 0;
+  QrCtx cq;
+  cq.need_out = &need;
+  if ((s = qr_dispatch(W, n, m, ldw, mb, sketch, k, seed, Q, ldq, R, ldr, o, nullptr, &cq))) return s;
+  if (cudaMalloc(&g->ws, need) != cudaSuccess || cudaMalloc(&g->status, 8 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+  QrCtx c;
+  c.ws = g->ws;
+  c.ws_bytes = need;
+  c.side = g->side;
+  c.status_out = g->status;
+  // one run outside the capture builds what the library caches (sketch plans, the
+  // kernels' attributes), so that the capture holds stream work only
+  cudaStream_t cs = nullptr;
+  RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  struct StreamFree {
+    cudaStream_t s;
+    ~StreamFree() {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  } csf{cs};
+  o.stream = cs;
+  if ((s = qr_dispatch(W, n, m, ldw, mb, sketch, k, seed, Q, ldq, R, ldr, o, nullptr, &c))) return s;
+  RBGS_CUDA_TRY(cudaStreamSynchronize(cs));
+  RBGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  s = qr_dispatch(W, n, m, ldw, mb, sketch, k, seed, Q, ldq, R, ldr, o, nullptr, &c);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+  if (s) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ECUDA;
+  }
+  g->graph = graph;
+  RBGS_CUDA_TRY(cudaGraphInstantiate(&g->exec, g->graph, 0));
+  *out = g;
+  g = nullptr;  // owned by the caller now
+  return RBGS_OK;
+}
+
+rbgs_status rbgs_qr_graph_launch(rbgs_graph* g, void* stream, int32_t sync) {
+  if (!g || !g->exec) return RBGS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  RBGS_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+  if (!sync) return RBGS_OK;
+  int hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  RBGS_CUDA_TRY(cudaMemcpyAsync(hs, g->status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hs[3]) return RBGS_ETIMEOUT;
+  if (hs[0]) return RBGS_EBREAKDOWN;
+  return RBGS_OK;
 }
 
 rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,

@@ -118,6 +118,10 @@ def load(build_if_missing: bool = False):
     lib.rbgs_embedding_check.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, u64, ctypes.POINTER(Opts),
                                          vp]
     lib.rbgs_cholqr_postprocess.argtypes = [i32, i64, i64, vp, i64, vp, i64, i64, vp, i32]
+    lib.rbgs_qr_graph_create.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
+                                         ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]
+    lib.rbgs_qr_graph_launch.argtypes = [vp, vp, i32]
+    lib.rbgs_qr_graph_destroy.argtypes = [vp]
     lib.rbgs_qr_host.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
                                  ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
     lib.rbgs_release_workspace.argtypes = []
@@ -126,7 +130,8 @@ def load(build_if_missing: bool = False):
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
                  "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
                  "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched", "rbgs_qr_host",
-                 "rbgs_embedding_check", "rbgs_cholqr_postprocess"):
+                 "rbgs_embedding_check", "rbgs_cholqr_postprocess", "rbgs_qr_graph_create",
+                 "rbgs_qr_graph_launch", "rbgs_qr_graph_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -230,6 +235,47 @@ def embedding_check(Z: torch.Tensor, mb: int, sketch: str = "srht", k: int | Non
                                      ctypes.byref(o), ctypes.cast(ctypes.pointer(out), ctypes.c_void_p)),
            "rbgs_embedding_check")
     return float(out.value)
+
+
+class QRGraph:
+    """rbgs_qr captured once as a CUDA graph on fixed W, Q, R (column-major
+    CUDA tensors, kept alive by this object); launch() replays it on the
+    current contents of W."""
+
+    def __init__(self, W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
+                 prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
+                 fine: bool = False, interblock: int = 5, ls: str = "richardson"):
+        lib = load()
+        prec = _prec_of(W, prec)
+        n, m = W.shape
+        k = 2 * m if k is None else k
+        self.W = W
+        self.Q = _empty_cols(n, m, W.dtype, W.device)
+        self.R = torch.empty((m, m), dtype=torch.float64, device=W.device).t()
+        o = Opts()
+        lib.rbgs_opts_default(ctypes.byref(o))
+        o.prec, o.ls_iters, o.reorth, o.reorth_tol = PREC[prec], ls_iters, reorth, reorth_tol
+        o.fine, o.interblock, o.ls = int(fine), int(interblock), LS[ls]
+        h = ctypes.c_void_p()
+        _check(lib.rbgs_qr_graph_create(W.data_ptr(), n, m, _ld(W, "W"), mb, SKETCH[sketch], k, seed,
+                                        self.Q.data_ptr(), _ld(self.Q, "Q"), self.R.data_ptr(), _ld(self.R, "R"),
+                                        ctypes.byref(o), ctypes.byref(h)), "rbgs_qr_graph_create")
+        self._h = h
+
+    def launch(self, stream=None, sync: bool = True):
+        _check(load().rbgs_qr_graph_launch(self._h, _stream_ptr(stream), int(sync)), "rbgs_qr_graph_launch")
+        return self.Q, self.R
+
+    def destroy(self):
+        if self._h:
+            load().rbgs_qr_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def cholqr_postprocess(Q: torch.Tensor, R: torch.Tensor, mb: int = 64, prec: str | None = None, stream=None):

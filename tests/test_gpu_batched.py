@@ -104,3 +104,32 @@ def test_host_buffer_path_equals_device_path(rb, prec, pinned):
     Qd, Rd, std = rb.rbgs_qr(Wd, mb, "srht", k, 3, prec=prec, ls_iters=1, reorth=1, fine=prec != "fp64")
     assert torch.equal(Qh, Qd.cpu()) and torch.equal(Rh, Rd.cpu())
     assert st.passes2 == std.passes2 == (m + mb - 1) // mb - 1
+
+
+@pytest.mark.parametrize("prec,n,m,mb,kind,k,interblock", [("fp64", 10000, 100, 10, "gauss", 200, 5),
+                                                           ("f16x3", 20000, 128, 32, "srht", 256, 5),
+                                                           ("fp32", 8000, 60, 16, "srht", 160, 4)])
+def test_graph_replay_equals_direct_call(rb, prec, n, m, mb, kind, k, interblock):
+    """A captured factorization replays bit for bit the direct rbgs_qr, and a
+    replay after W changes factorizes the new contents (2 W: R doubles)."""
+    td = torch.float64 if prec == "fp64" else torch.float32
+    W = synth.svd_matrix(n, m, 1e3, 31)
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    Wd = dev(W, td)
+    kw = dict(prec=prec, ls_iters=2, reorth=1, fine=prec != "fp64", interblock=interblock)
+    g = rb.QRGraph(Wd, mb, kind, k, 6, **kw)
+    for _ in range(2):
+        Qg, Rg = g.launch()
+    Q1, R1, _ = rb.rbgs_qr(Wd, mb, kind, k, 6, **kw)
+    assert torch.equal(Qg, Q1) and torch.equal(Rg, R1)
+    Wd.mul_(2.0)
+    Qg2, Rg2 = g.launch()
+    assert torch.allclose(Rg2, 2.0 * R1, rtol=1e-12, atol=0) and torch.allclose(Qg2, Q1, rtol=1e-12, atol=1e-14)
+    g.destroy()
+
+
+def test_graph_refuses_the_column_by_column_variants(rb):
+    Wd = dev(synth.gaussian(2000, 16, 3))
+    with pytest.raises(rb.RbgsError):
+        rb.QRGraph(Wd, 4, "gauss", 32, 0, prec="fp64", interblock=3)
