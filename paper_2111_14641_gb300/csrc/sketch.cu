@@ -346,10 +346,11 @@ __global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
   auto item = [&](int64_t w, const float*& p, int64_t& row0, int& valid, uint32_t& bytes) {
     const int64_t col = w / T;
     const int t = (int)(w % T);
-    const int sidx = col < src.nc0 ? 0 : 1;
-    const int64_t lc = sidx ? col - src.nc0 : col;
+    const bool second = col >= src.nc0;
+    const int64_t lc = second ? col - src.nc0 : col;
     row0 = (int64_t)t * B;
-    p = src.x[sidx] + lc * src.ld[sidx] + row0;
+    // (a select, not src.x[index]: a runtime index would copy the parameter to local memory)
+    p = (second ? src.x[1] : src.x[0]) + lc * (second ? src.ld[1] : src.ld[0]) + row0;
     const int64_t v = n - row0;
     valid = v <= 0 ? 0 : (int)(v < B ? v : B);
     bytes = ((((uintptr_t)p) & 15) == 0) ? (uint32_t)((valid * 4) & ~15) : 0u;
@@ -472,13 +473,14 @@ __global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
 // 16-byte accesses free of bank conflicts.  Butterflies over float4 halves use
 // the packed FP32 add.
 constexpr int kB16 = 16384;
+constexpr int kB16Staged = 4096;  // up to this many sampled low indices are staged in shared memory
 
 __device__ __forceinline__ int b16_phys(int j) { return j ^ (((j >> 5) & 7) << 2); }
 
 __device__ __forceinline__ void b16_bfly(float& a0, float& a1, float& b0, float& b1) {
   const float2 a = make_float2(a0, a1), b = make_float2(b0, b1);
   const float2 s = __fadd2_rn(a, b);
-  const float2 d = __fadd2_rn(a, make_float2(-b0, -b1));
+  const float2 d = __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b in one packed instruction
   a0 = s.x;
   a1 = s.y;
   b0 = d.x;
@@ -524,6 +526,7 @@ __global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* bufs = reinterpret_cast<float*>(smem_raw);            // NB x B
   uint32_t* sgn = reinterpret_cast<uint32_t*>(bufs + NB * B);  // B / 32
+  int* lv_s = reinterpret_cast<int*>(sgn + B / 32);            // the L sampled low indices, when staged
   __shared__ __align__(8) uint64_t full[2];
   __shared__ int bad;
   const int tid = threadIdx.x;
@@ -534,14 +537,18 @@ __global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     bad = 0;
   }
+  const bool staged = L <= kB16Staged;  // uniform
+  if (staged)
+    for (int l = tid; l < L; l += blockDim.x) lv_s[l] = b16_phys(__ldg(lvals + l));
   __syncthreads();
   auto item = [&](int64_t w, const float*& p, int64_t& row0, int& valid, uint32_t& bytes) {
     const int64_t col = w / T;
     const int t = (int)(w % T);
-    const int sidx = col < src.nc0 ? 0 : 1;
-    const int64_t lc = sidx ? col - src.nc0 : col;
+    const bool second = col >= src.nc0;
+    const int64_t lc = second ? col - src.nc0 : col;
     row0 = (int64_t)t * B;
-    p = src.x[sidx] + lc * src.ld[sidx] + row0;
+    // (a select, not src.x[index]: a runtime index would copy the parameter to local memory)
+    p = (second ? src.x[1] : src.x[0]) + lc * (second ? src.ld[1] : src.ld[0]) + row0;
     const int64_t v = n - row0;
     valid = v <= 0 ? 0 : (int)(v < B ? v : B);
     bytes = ((((uintptr_t)p) & 15) == 0) ? (uint32_t)((valid * 4) & ~15) : 0u;
@@ -560,11 +567,12 @@ __global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
                    "l"(p), "r"(bytes), "r"(bar)
                    : "memory");
   };
-  int issued[2] = {0, 0}, consumed[2] = {0, 0};
+  // copies issued into / consumed from each buffer (scalars: no local memory)
+  int iss0 = 0, iss1 = 0, con0 = 0, con1 = 0;
   int64_t w = blockIdx.x;
   if (w < nitems) {
     if (tid == 0) issue(w, 0);
-    issued[0] = 1;
+    iss0 = 1;
   }
   // per-thread slot bases (float4 units) of the four passes
   const int t7 = tid & 7, t37 = (tid >> 3) & 7;
@@ -577,7 +585,8 @@ __global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
     const int64_t wn = w + gridDim.x;
     if (NB == 2 && wn < nitems) {
       if (tid == 0) issue(wn, b ^ 1);
-      issued[b ^ 1] += 1;
+      if (b) ++iss0;
+      else ++iss1;
     }
     const float* p;
     int64_t row0;
@@ -589,11 +598,13 @@ __global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
       const uint4 bits = srht_sign_bits(key, (uint32_t)((row0 >> 7) + tid));
       reinterpret_cast<uint4*>(sgn)[tid] = bits;
     }
-    if (!sk_mbar_wait(sk_smem_u32(&full[b]), (uint32_t)(consumed[b] & 1))) bad = 1;
-    consumed[b] += 1;
+    if (!sk_mbar_wait(sk_smem_u32(&full[b]), (uint32_t)((b ? con1 : con0) & 1))) bad = 1;
+    if (b) ++con1;
+    else ++con0;
     __syncthreads();
     if (bad) {
-      consumed[b] -= 1;
+      if (b) --con1;
+      else --con0;
       break;
     }
     float* buf = bufs + (size_t)b * B;
@@ -655,16 +666,23 @@ __global__ void __launch_bounds__(kSrhtThreads, NB == 1 ? 2 : 1)
     for (int q = 0; q < 8; ++q) buf4[slotD + 64 * q] = v[q];
     __syncthreads();
     float* zo = z + w * L;  // (col * T + t) * L
-    for (int l = tid; l < L; l += blockDim.x) zo[l] = buf[b16_phys(__ldg(lvals + l))];
+    if (staged) {
+#pragma unroll 4
+      for (int l = tid; l < L; l += blockDim.x) zo[l] = buf[lv_s[l]];
+    } else {
+      for (int l = tid; l < L; l += blockDim.x) zo[l] = buf[b16_phys(__ldg(lvals + l))];
+    }
     __syncthreads();  // buffer b may be refilled from here on
     if (NB == 1 && wn < nitems) {
       if (tid == 0) issue(wn, 0);
-      issued[0] += 1;
+      ++iss0;
     }
   }
   if (tid == 0) {
     for (int b = 0; b < 2; ++b)
-      if (issued[b] > consumed[b] && !sk_mbar_wait(sk_smem_u32(&full[b]), (uint32_t)((issued[b] - 1) & 1))) bad = 1;
+      if ((b ? iss1 : iss0) > (b ? con1 : con0) &&
+          !sk_mbar_wait(sk_smem_u32(&full[b]), (uint32_t)(((b ? iss1 : iss0) - 1) & 1)))
+        bad = 1;
     if (bad && err) atomicExch(err, 1);
   }
   __syncthreads();
@@ -910,8 +928,10 @@ rbgs_status sketch_apply2_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t see
     };
     if (plan->B == kB16) {
       auto k16 = nb == 1 ? srht_stage1_b16k<1> : srht_stage1_b16k<2>;
-      RBGS_CUDA_TRY(cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k16<<<grid, kSrhtThreads, smem, st>>>(sd, n, plan->T, key, plan->d_lvals, plan->L, zf, ncols, active, nullptr);
+      const size_t smem16 = smem + (plan->L <= kB16Staged ? sizeof(int) * (size_t)plan->L : 0);
+      RBGS_CUDA_TRY(cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16));
+      k16<<<grid, kSrhtThreads, smem16, st>>>(sd, n, plan->T, key, plan->d_lvals, plan->L, zf, ncols, active,
+                                              nullptr);
       RBGS_LAUNCH_CHECK();
       s = RBGS_OK;
     } else if (nb == 1) {
