@@ -126,6 +126,20 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+def aggregate_over_ranks(ms_local: float, flops: float, world: int, device):
+    """Replicas only: every rank factors its own copy of the workload.  The
+    step time is the slowest rank's (max over ranks) and the whole-job
+    throughput counts every rank's work: world * flops / max time (GFLOP/s)."""
+    import torch
+
+    ms_all = ms_local
+    if world > 1:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_all = float(t.item())
+    return ms_all, world * flops / (ms_all * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -310,13 +324,8 @@ def run_ours(args, cfg):
     launches = rb.launch_count() - l0
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_all = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_all = float(t.item())
     flops = algorithmic_flops(n, m, mb, k, cfg["sketch"], args.ls_iters, passes2)
-    value = world * flops / (ms_all * 1e-3) / 1e9
+    ms_all, value = aggregate_over_ranks(ms, flops, world, dev)
 
     # ---- roofline of the dominant kernel (tall update), from its own CUDA events
     peaks = {}
