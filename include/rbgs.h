@@ -93,7 +93,11 @@ typedef struct {
                           1 = single-vector RGS and 3 = vRCholeskyQR (Alg. 3): after the
                           projection, the block's columns one at a time (RBGS with
                           one-column blocks on Q'_i, explicit or implicit sketches; needs
-                          reorth 0 or 1; not for the Sec. 5 solvers)                    */
+                          reorth 0 or 1; not for the Sec. 5 solvers); 6 = Alg. 6: an l2
+                          QR Q'_i = Q* R' (Cholesky QR twice, FP64 Gram matrices over
+                          the n rows, four tall passes), then Alg. 4 on Q*, R_ii =
+                          R'' R' (breaks down where kappa_2(Q'_i) nears 1e8; not for
+                          the Sec. 5 solvers)                                            */
   int32_t ls;          /* step 2 solver: 0 = Richardson (X <- X + S^T (P - S X), ls_iters
                           steps from 0); 1 = conjugate gradients on the normal equations
                           (S^T S) X = S^T P, ls_iters steps from 0, column by column

@@ -204,6 +204,13 @@ struct DevBuf {
 };
 
 // The w x w identity (ld w).
+// b = a for an mb x mb matrix (ld mb), converting the element type
+template <class TI, class TO>
+__global__ void copy_sq_kernel(int mb, const TI* a, TO* b, const int* active) {
+  if (active && *active == 0) return;
+  for (int t = threadIdx.x; t < mb * mb; t += blockDim.x) b[t] = (TO)a[t];
+}
+
 template <class TS>
 __global__ void eye_kernel(int w, TS* I) {
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) I[e] = (e % w == e / w) ? (TS)1 : (TS)0;
@@ -372,6 +379,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     TS* Xalt = look ? cv.take<TS>((size_t)m * mb) : nullptr;
     TS* Spo[2] = {look ? cv.take<TS>((size_t)k * mb) : nullptr, look ? cv.take<TS>((size_t)k * mb) : nullptr};
     TS* partf2 = look ? cv.take<TS>(kPartElems) : nullptr;
+    double* l2s = o.interblock == 6 ? cv.take<double>((size_t)8 * 64 * 64) : nullptr;  // Alg. 6 scratch
     void* skscr = cv.take<char>(sk_bytes);
     void* skscr2 = cv.take<char>(sk_bytes);  // the side stream's sketches of the next blocks of W
     int* flags = cv.take<int>(64);
@@ -387,6 +395,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     // block's own columns are orthonormalised one at a time, by RBGS with one-column
     // blocks on Q'_i (explicit sketches for RGS, implicit for Alg. 3), in place
     const bool percol = o.interblock == 1 || o.interblock == 3;
+    // Alg. 6: an l2 QR of Q'_i (Cholesky QR twice with FP64 Gram matrices), then Alg. 4
+    const bool alg6 = o.interblock == 6;
     int* brk = flags;          // breakdown
     int* active = flags + 1;   // second pass on/off for this block
     int* npass2 = flags + 2;   // number of second passes
@@ -468,7 +478,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       RBGS_LAUNCH_CHECK();
       return RBGS_OK;
     };
-    if ((alg4 || percol) && (s = set_eye(mb))) return s;
+    if ((alg4 || percol || alg6) && (s = set_eye(mb))) return s;
     // step 2: X (c x mb, ld m) from P (k x mb) by Richardson or by conjugate gradients, `its` steps
     auto step2 = [&](int64_t c, const TS* Pb, TS* Xo, int its) -> rbgs_status {
       if (!cg) return richardson<TS>(k, c, mb, S, Pb, Xo, m, Res, its, partf, nullptr, st);
@@ -570,6 +580,51 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       return sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sout, k, skscr, sk_bytes, st, act);
     };
 
+    // Steps 4-5 by Alg. 6 for the block src - Q_{1:c} Xc written to Qo: the
+    // projection; an l2 QR Q'_i = Q* R' by Cholesky QR twice (FP64 Gram matrices
+    // over the n rows, in-place scaling on the tall kernels); Alg. 4 on Q*
+    // (sketch, Cholesky QR, scaling) giving R''; R_ii = R'' R' (into Rd, in TS);
+    // step 5, Sout = Theta Q_i.
+    auto alg6_pass = [&](int64_t c, const TS* Xc, const T* src, int64_t ldsrc, T* Qo, const TS* sraw, TS* Rd,
+                         TS* Sout, bool split_final, const int* act) -> rbgs_status {
+      rbgs_status r;
+      double *gram = l2s, *r1 = l2s + 4096, *r1i = l2s + 2 * 4096, *racc = l2s + 3 * 4096, *rtmp = l2s + 4 * 4096,
+             *rpp = l2s + 5 * 4096;
+      if ((r = make_g(c, Xc, Ieye, Ieye, nullptr, act))) return r;
+      if ((r = tall(c, c, src, ldsrc, Qo, act, sraw, false))) return r;
+      for (int round = 0; round < 2; ++round) {
+        if (fp64)
+          r = small_gemm<double, double, double>(1, mb, mb, n, 1.0, (const double*)Qo, ldq, (const double*)Qo, ldq,
+                                                 0.0, gram, mb, part, kPartElems, act, st);
+        else
+          r = small_gemm<float, double, double>(1, mb, mb, n, 1.0, (const float*)Qo, ldq, (const float*)Qo, ldq,
+                                                0.0, gram, mb, part, kPartElems, act, st);
+        if (r) return r;
+        // round 0 leaves R1 in racc; round 1 forms R' = R2 R1 in rtmp
+        if ((r = chol_inv<double>(mb, gram, round == 0 ? racc : r1, r1i, 0.0, brk, nullptr, nullptr, act, st)))
+          return r;
+        if (round == 1 && (r = tri_mul<double>(mb, r1, racc, rtmp, act, st))) return r;
+        // Qo <- Qo R_round^{-1} (the F16X3 path takes its column scales from the sketch of Qo)
+        if (tensor) r = assemble_g<double, double>(0, mb, nullptr, 0, r1i, r1i, Gd, mb, nullptr, 0, act, st);
+        else r = assemble_g<double, T>(0, mb, nullptr, 0, r1i, r1i, Gmat, mb, nullptr, 0, act, st);
+        if (r) return r;
+        if ((r = sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sp, k, skscr, sk_bytes, st, act))) return r;
+        if ((r = tall(0, c, Qo, ldq, Qo, act, Sp, false))) return r;
+      }
+      // Alg. 4 on Q*
+      if ((r = sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sp, k, skscr, sk_bytes, st, act))) return r;
+      if ((r = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, act, st, sm[10], sm[11], need2, n2count))) return r;
+      if ((r = make_g(0, nullptr, sm[10], sm[11], nullptr, act))) return r;
+      if ((r = tall(0, c, Qo, ldq, Qo, act, Sp, split_final))) return r;
+      // R_ii = R'' R' in FP64, stored in TS
+      copy_sq_kernel<TS, double><<<1, 256, 0, st>>>(mb, sm[10], rpp, act);
+      RBGS_LAUNCH_CHECK();
+      if ((r = tri_mul<double>(mb, rpp, rtmp, racc, act, st))) return r;
+      copy_sq_kernel<double, TS><<<1, 256, 0, st>>>(mb, racc, Rd, act);
+      RBGS_LAUNCH_CHECK();
+      return sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sout, k, skscr, sk_bytes, st, act);
+    };
+
     // Step 1 of block i + 1 (the sketch of W_{i+1}) depends on nothing in block
     // i, so it runs on a side stream while block i's sketch-space steps run
     // here (those keep few SMs busy); an event hands P_{i+1} over.
@@ -600,7 +655,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     for (int64_t blk = 0; blk < p; ++blk) {
       const int64_t c = blk * mbf;
       mb = (int)std::min<int64_t>(mbf, m - c);  // this block's width
-      if ((alg4 || percol) && mb != mbf && (s = set_eye(mb))) return s;  // the narrower last block
+      if ((alg4 || percol || alg6) && mb != mbf && (s = set_eye(mb))) return s;  // the narrower last block
       if (ctx && ctx->w_ready && op == nullptr) RBGS_CUDA_TRY(cudaStreamWaitEvent(st, ctx->w_ready[blk], 0));
       const int64_t wnext = blk + 1 < p ? std::min<int64_t>(mbf, m - c - mbf) : 0;
       const T* Wi = W + c * ldw;
@@ -678,6 +733,9 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       } else if (percol) {
         if ((s = percol_pass(c, Xc, Wi, ldwi, Qi, Pi, Rii, Si, split1))) return s;
         if ((s = make_g(c, Xc, Rii, Rii, Rcol, nullptr))) return s;  // the R column only
+      } else if (alg6) {
+        if ((s = alg6_pass(c, Xc, Wi, ldwi, Qi, Pi, Rii, Si, split1, nullptr))) return s;
+        if ((s = make_g(c, Xc, Rii, Rii, Rcol, nullptr))) return s;  // the R column only
       } else {
         if (provisional) s = cholqr1<TS>(k, mb, Spc, sm, partf, brk, nullptr, st, Rii, Riinv);
         else s = cholqr2<TS>(k, mb, Spc, Res, sm, partf, brk, nullptr, st, Rii, Riinv, need2, n2count);
@@ -708,6 +766,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
           if ((s = alg4_pass(c, X2, Qi, ldq, Qi, Si, false, R2ii, R2iinv, Si, true, active))) return s;
         } else if (percol) {  // (the second pass always runs: reorth 2 is refused with these variants)
           if ((s = percol_pass(c, X2, Qi, ldq, Qi, Si, R2ii, Si, true))) return s;
+        } else if (alg6) {
+          if ((s = alg6_pass(c, X2, Qi, ldq, Qi, Si, R2ii, Si, true, active))) return s;
         } else {
           RBGS_CUDA_TRY(cudaMemcpyAsync(Sp, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
           s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Sp, k, partf, kPartElems, active, st);
@@ -839,7 +899,8 @@ rbgs_status check_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t m
   if (n < 1 || n >= ((int64_t)1 << 31) || m < 1 || mb < 1 || mb > 64) return RBGS_EINVAL;
   if (ldw < n || ldq < n || ldr < m || k < m) return RBGS_EINVAL;
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2) return RBGS_EINVAL;
-  if (o.interblock != 0 && o.interblock != 1 && o.interblock != 3 && o.interblock != 4 && o.interblock != 5)
+  if (o.interblock != 0 && o.interblock != 1 && o.interblock != 3 && o.interblock != 4 && o.interblock != 5 &&
+      o.interblock != 6)
     return RBGS_EINVAL;
   if ((o.interblock == 1 || o.interblock == 3) && o.reorth == 2) return RBGS_EINVAL;
   if (o.ls != 0 && o.ls != 1) return RBGS_EINVAL;

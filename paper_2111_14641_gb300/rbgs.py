@@ -193,7 +193,8 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
             sync: bool = True, timing: bool = False, fine: bool = False, interblock: int = 5, ls: str = "richardson"):
     """RBGS QR of W (n x m, column-major).  Returns (Q, R, QRStats | None).
     fine=True (FP32 / TF32X3 storage only) runs the sketch-space steps in FP64;
-    interblock selects steps 4-5: 5 = Alg. 5 (implicit sketch), 4 = Alg. 4."""
+    interblock selects steps 4-5: 5 = Alg. 5 (implicit sketch), 4 = Alg. 4,
+    1 / 3 = column by column (RGS / Alg. 3), 6 = Alg. 6 (l2 QR, then Alg. 4)."""
     lib = load()
     prec = _prec_of(W, prec)
     n, m = W.shape

@@ -73,13 +73,14 @@ def test_argument_checks_need_no_device(lib):
     assert lib.rbgs_qr(fake, 1000, 128, 1000, 128, 0, 256, 0, other, 1000, rr, 128, None, None) == 1
     # W and Q overlap
     assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 16, 0, fake, 100, rr, 8, None, None) == 1
-    # steps 4-5 variant other than Alg. 4 or Alg. 5
+    # steps 4-5 variant other than 0, 1, 3, 4, 5 or 6
     from paper_2111_14641_gb300 import rbgs as rbmod
 
     o = rbmod.Opts()
     lib.rbgs_opts_default(ctypes.byref(o))
-    o.interblock = 6
-    assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 16, 0, other, 100, rr, 8, ctypes.byref(o), None) == 1
+    for bad in (2, 7, -1):
+        o.interblock = bad
+        assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 16, 0, other, 100, rr, 8, ctypes.byref(o), None) == 1
 
 
 def test_krylov_argument_checks_need_no_device(lib):

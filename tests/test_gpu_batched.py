@@ -108,7 +108,8 @@ def test_host_buffer_path_equals_device_path(rb, prec, pinned):
 
 @pytest.mark.parametrize("prec,n,m,mb,kind,k,interblock", [("fp64", 10000, 100, 10, "gauss", 200, 5),
                                                            ("f16x3", 20000, 128, 32, "srht", 256, 5),
-                                                           ("fp32", 8000, 60, 16, "srht", 160, 4)])
+                                                           ("fp32", 8000, 60, 16, "srht", 160, 4),
+                                                           ("fp64", 6000, 40, 8, "gauss", 80, 6)])
 def test_graph_replay_equals_direct_call(rb, prec, n, m, mb, kind, k, interblock):
     """A captured factorization replays bit for bit the direct rbgs_qr, and a
     replay after W changes factorizes the new contents (2 W: R doubles)."""

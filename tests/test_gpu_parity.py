@@ -234,6 +234,44 @@ def test_rbgs_alg4_matches_oracle(rb, prec, reorth):
         assert st.passes2 == m // mb - 1
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f16x3", "fp32"])
+@pytest.mark.parametrize("reorth,m", [(0, 48), (1, 48), (2, 48), (1, 45)])
+def test_rbgs_alg6_matches_oracle(rb, prec, reorth, m):
+    """Steps 4-5 by Alg. 6 (an l2 QR of Q'_i by Cholesky QR twice, then Alg. 4
+    on its orthonormal factor, R_ii = R'' R') against the oracle's Alg. 6
+    (Householder l2 QR with a positive diagonal: the same thin QR), ragged
+    last block included."""
+    n, mb, kind, k = 3000, 16, "srht", 200
+    cond = 1e4 if prec == "fp64" else 1e3
+    W = synth.svd_matrix(n, m, cond, 78)
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Qd, Rd, st = rb.rbgs_qr(dev(W, td), mb, kind, k, 5, prec=prec, ls_iters=3, reorth=reorth, interblock=6,
+                            certify=True, fine=prec != "fp64")
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, 5, variant=6, ls="richardson", ls_iters=3, reorth=bool(reorth),
+                      ls_iters_first=1 if reorth == 1 else 0)
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    fact = oracle.factorization_error(W, Q, R)
+    ortho = oracle.sketched_orthogonality(Q, kind, k, 5)[0]
+    if prec == "fp64":
+        if reorth != 2:
+            tol = 1e-13 * cond
+            assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+            assert np.abs(Q - ref["Q"]).max() <= tol * np.abs(ref["Q"]).max()
+        # the adaptive second pass is skipped where the block's coefficients on
+        # the basis are below reorth_tol (1e-8), which then bounds the defect
+        assert fact < 1e-14 and ortho < (1e-8 if reorth == 2 else 1e-12)
+        assert 0 <= st.passes2 <= (m + mb - 1) // mb - 1
+    else:
+        assert fact < 2e-6 and ortho < (1e-4 if reorth else 1e-3)
+        if reorth != 2:
+            assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
+    if reorth == 1:
+        assert st.passes2 == (m + mb - 1) // mb - 1
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3", "tf32x3"])
 @pytest.mark.parametrize("interblock", [5, 4])
 @pytest.mark.parametrize("m,mb,reorth", [(50, 16, 0), (60, 50, 1), (9, 4, 1)])
