@@ -101,7 +101,10 @@ typedef struct {
   int32_t ls;          /* step 2 solver: 0 = Richardson (X <- X + S^T (P - S X), ls_iters
                           steps from 0); 1 = conjugate gradients on the normal equations
                           (S^T S) X = S^T P, ls_iters steps from 0, column by column
-                          (Sec. 3.1 and its supplement)                                  */
+                          (Sec. 3.1 and its supplement); 2 = Householder least squares:
+                          a blocked Householder QR of S kept in compact WY form, one
+                          panel appended per block, X = R_S^{-1} (Q_S^T P)_{1:c}
+                          (ls_iters unused; not for the Sec. 5 solvers)                 */
 } rbgs_opts;
 
 typedef struct {

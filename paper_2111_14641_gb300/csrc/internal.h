@@ -131,6 +131,15 @@ template <class T>
 rbgs_status chol_inv(int mb, const T* G, T* R, T* Rinv, double shift, int* flag, const T* Rprev, const T* Rprev_inv,
                      const int* active, cudaStream_t st);
 
+// One panel of the blocked Householder QR of the sketch (step 2 by Householder
+// least squares): rows c..k-1 of B (k x w, ld ldb, holding Q_c^T S_i) factorised
+// in place; writes the explicit reflectors V (k x w, ld ldv), the panel's
+// compact-WY factor T and the inverse of its R (w x w each, ld ldm, zero below
+// the diagonal); *flag |= 1 on a zero or non-finite diagonal of R.  w <= 64.
+template <class TS>
+rbgs_status hh_panel(int64_t k, int64_t c, int w, TS* B, int64_t ldb, TS* V, int64_t ldv, TS* T, TS* Ri,
+                     int64_t ldm, int* flag, cudaStream_t st);
+
 // Out (k x mb, ldo) = A (k x mb, lda) * U (U upper mb x mb, ld mb).
 template <class TS>
 rbgs_status trmm_right_upper(int64_t k, int mb, const TS* A, int64_t lda, const TS* U, TS* Out, int64_t ldo,

@@ -369,7 +369,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     // look-ahead of step 2 on the side stream (second X buffer, the partial
     // residuals of the next block, the side stream's partial-sum scratch)
     const bool cg = o.ls == 1;  // step 2 by conjugate gradients
-    const bool look = p > 1 && op == nullptr && !cg && (o.reorth != 0 || l == 1);
+    const bool hh = o.ls == 2;  // step 2 by Householder least squares
+    const bool look = p > 1 && op == nullptr && !cg && !hh && (o.reorth != 0 || l == 1);
     TS* cgR = cg ? cv.take<TS>((size_t)m * mb) : nullptr;
     TS* cgD = cg ? cv.take<TS>((size_t)m * mb) : nullptr;
     TS* cgQ = cg ? cv.take<TS>((size_t)m * mb) : nullptr;
@@ -380,6 +381,15 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
     TS* Spo[2] = {look ? cv.take<TS>((size_t)k * mb) : nullptr, look ? cv.take<TS>((size_t)k * mb) : nullptr};
     TS* partf2 = look ? cv.take<TS>(kPartElems) : nullptr;
     double* l2s = o.interblock == 6 ? cv.take<double>((size_t)8 * 64 * 64) : nullptr;  // Alg. 6 scratch
+    // Householder least squares: S_{1:c} = Q_S [R_S; 0], Q_S = I - V T V^T (compact WY),
+    // kept with R_S^{-1}; scratch for Q_c^T S_i, Q_c^T P and two c x mb products
+    TS* hhV = hh ? cv.take<TS>((size_t)k * m) : nullptr;
+    TS* hhT = hh ? cv.take<TS>((size_t)m * m) : nullptr;
+    TS* hhRi = hh ? cv.take<TS>((size_t)m * m) : nullptr;
+    TS* hhB = hh ? cv.take<TS>((size_t)k * mb) : nullptr;
+    TS* hhY = hh ? cv.take<TS>((size_t)k * mb) : nullptr;
+    TS* hhW = hh ? cv.take<TS>((size_t)m * mb) : nullptr;
+    TS* hhW2 = hh ? cv.take<TS>((size_t)m * mb) : nullptr;
     void* skscr = cv.take<char>(sk_bytes);
     void* skscr2 = cv.take<char>(sk_bytes);  // the side stream's sketches of the next blocks of W
     int* flags = cv.take<int>(64);
@@ -479,8 +489,57 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       return RBGS_OK;
     };
     if ((alg4 || percol || alg6) && (s = set_eye(mb))) return s;
-    // step 2: X (c x mb, ld m) from P (k x mb) by Richardson or by conjugate gradients, `its` steps
+    // Y (k x mb, ld k) <- Q_c^T Y in its first `rows` rows, Q_c = I - V T V^T over
+    // the first c reflectors
+    auto hh_apply_qt = [&](int64_t c, TS* Y, int64_t rows) -> rbgs_status {
+      rbgs_status r;
+      if ((r = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, hhV, k, Y, k, 0.0, hhW, m, partf, kPartElems, nullptr, st)))
+        return r;
+      if ((r = small_gemm<TS, TS, TS>(1, c, mb, c, 1.0, hhT, m, hhW, m, 0.0, hhW2, m, partf, kPartElems, nullptr,
+                                      st)))
+        return r;
+      return small_gemm<TS, TS, TS>(0, rows, mb, c, -1.0, hhV, k, hhW2, m, 1.0, Y, k, partf, kPartElems, nullptr, st);
+    };
+    // Householder least squares: X = R_S^{-1} (Q_S^T P)_{1:c}
+    auto hh_solve = [&](int64_t c, const TS* Pb, TS* Xo) -> rbgs_status {
+      rbgs_status r;
+      RBGS_CUDA_TRY(cudaMemcpyAsync(hhY, Pb, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
+      if ((r = hh_apply_qt(c, hhY, c))) return r;
+      return small_gemm<TS, TS, TS>(0, c, mb, c, 1.0, hhRi, m, hhY, k, 0.0, Xo, m, partf, kPartElems, nullptr, st);
+    };
+    // append the final sketch S_i (columns c..c+mb-1) to the factorization:
+    // Q_c^T S_i, the panel's reflectors, then the off-diagonal blocks
+    // T_12 = -T_11 (V_1^T V_2) T_22 and (R_S^{-1})_12 = -R_11^{-1} R_12 R_22^{-1}
+    auto hh_extend = [&](int64_t c) -> rbgs_status {
+      rbgs_status r;
+      RBGS_CUDA_TRY(cudaMemcpyAsync(hhB, S + c * k, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
+      if (c > 0 && (r = hh_apply_qt(c, hhB, k))) return r;
+      if ((r = hh_panel<TS>(k, c, mb, hhB, k, hhV + c * k, k, hhT + c + c * m, hhRi + c + c * m, m, brk, st)))
+        return r;
+      if (c == 0) return RBGS_OK;
+      if ((r = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, hhV, k, hhV + c * k, k, 0.0, hhW, m, partf, kPartElems,
+                                      nullptr, st)))
+        return r;
+      if ((r = small_gemm<TS, TS, TS>(0, c, mb, c, 1.0, hhT, m, hhW, m, 0.0, hhW2, m, partf, kPartElems, nullptr,
+                                      st)))
+        return r;
+      if ((r = small_gemm<TS, TS, TS>(0, c, mb, mb, -1.0, hhW2, m, hhT + c + c * m, m, 0.0, hhT + c * m, m, partf,
+                                      kPartElems, nullptr, st)))
+        return r;
+      if ((r = small_gemm<TS, TS, TS>(0, c, mb, c, 1.0, hhRi, m, hhB, k, 0.0, hhW, m, partf, kPartElems, nullptr,
+                                      st)))
+        return r;
+      return small_gemm<TS, TS, TS>(0, c, mb, mb, -1.0, hhW, m, hhRi + c + c * m, m, 0.0, hhRi + c * m, m, partf,
+                                    kPartElems, nullptr, st);
+    };
+    if (hh) {
+      RBGS_CUDA_TRY(cudaMemsetAsync(hhT, 0, sizeof(TS) * m * m, st));
+      RBGS_CUDA_TRY(cudaMemsetAsync(hhRi, 0, sizeof(TS) * m * m, st));
+    }
+    // step 2: X (c x mb, ld m) from P (k x mb) by Richardson or by conjugate gradients
+    // (`its` steps), or by Householder least squares
     auto step2 = [&](int64_t c, const TS* Pb, TS* Xo, int its) -> rbgs_status {
+      if (hh) return hh_solve(c, Pb, Xo);
       if (!cg) return richardson<TS>(k, c, mb, S, Pb, Xo, m, Res, its, partf, nullptr, st);
       rbgs_status r;
       RBGS_CUDA_TRY(cudaMemset2DAsync(Xo, sizeof(TS) * m, 0, sizeof(TS) * c, mb, st));
@@ -748,14 +807,14 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       }
       // optional second projection pass
       if (o.reorth && c > 0) {
-        if (cg) {
+        if (cg || hh) {
           if ((s = step2(c, Si, X2, l))) return s;
         } else {
           s = small_gemm<TS, TS, TS>(1, c, mb, k, 1.0, S, k, Si, k, 0.0, X2, m, partf, kPartElems, nullptr, st);
           if (s) return s;
         }
         if ((s = reorth_decide<TS>(c, mb, X2, m, o.reorth_tol, o.reorth, active, npass2, blk_on + blk, st))) return s;
-        for (int it = 1; it < l && !cg; ++it) {
+        for (int it = 1; it < l && !cg && !hh; ++it) {
           RBGS_CUDA_TRY(cudaMemcpyAsync(Res, Si, sizeof(TS) * k * mb, cudaMemcpyDeviceToDevice, st));
           s = small_gemm<TS, TS, TS>(0, k, mb, c, -1.0, S, k, X2, m, 1.0, Res, k, partf, kPartElems, active, st);
           if (s) return s;
@@ -780,6 +839,8 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
         }
         if ((s = reorth_update_r<TS>(c, mb, X2, m, R2ii, Rcol, ldr, tmp, active, st))) return s;
       }
+      // S_i is final: append it to the Householder factorization of S
+      if (hh && blk + 1 < p && (s = hh_extend(c))) return s;
       if (ctx && ctx->q_done) RBGS_CUDA_TRY(cudaEventRecord(ctx->q_done[blk], st));
     }
     mb = mbf;
@@ -903,7 +964,7 @@ rbgs_status check_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t m
       o.interblock != 6)
     return RBGS_EINVAL;
   if ((o.interblock == 1 || o.interblock == 3) && o.reorth == 2) return RBGS_EINVAL;
-  if (o.ls != 0 && o.ls != 1) return RBGS_EINVAL;
+  if (o.ls != 0 && o.ls != 1 && o.ls != 2) return RBGS_EINVAL;
   if (sketch == RBGS_SK_SRHT) {
     int64_t np = 1;
     while (np < n) np <<= 1;

@@ -575,6 +575,144 @@ __global__ void fro_diff_kernel(int64_t rows, int64_t cols, const double* __rest
   }
 }
 
+
+// ------------------------------------------------- Householder least squares --
+// One panel of the Householder QR of the sketch S (the textbook least-squares
+// solver of step 2, Sec. 3.1), one CTA.  B (k x w, ld ldb) holds Q_c^T S_i, the
+// block's sketch after the c earlier reflectors; its rows c..k-1 (L = k - c)
+// are factorised in place (the LAPACK reflector convention:
+// H = I - tau v v^T, v(0) = 1, beta = -sign(alpha) ||x||).  Outputs:
+//   V  (k x w, ld ldv): the reflectors written out, zero above row c + t and 1 at it;
+//   T  (w x w, ld ldm): the panel's compact-WY factor, H_0 ... H_{w-1} = I - V T V^T
+//      (T(t, t) = tau_t, T(0:t, t) = -tau_t T(0:t, 0:t) V(:, 0:t)^T v_t);
+//   Ri (w x w, ld ldm): the inverse of the panel's R (upper, zero below).
+// A zero or non-finite diagonal of R sets *flag |= 1.
+// Dynamic shared memory: two 64 x 65 double arrays.
+template <class TS>
+__global__ void __launch_bounds__(512) hh_panel_kernel(int64_t k, int64_t c, int w, TS* B, int64_t ldb, TS* V,
+                                                       int64_t ldv, TS* T, TS* Ri, int64_t ldm, int* flag) {
+  extern __shared__ double hh_sm[];
+  double(*Rs)[65] = reinterpret_cast<double(*)[65]>(hh_sm);            // R, then R^{-1}
+  double(*G)[65] = reinterpret_cast<double(*)[65]>(hh_sm + 64 * 65);   // V^T V, then T
+  __shared__ double red[16];
+  __shared__ double wdot[64];
+  __shared__ double tau_s[64];
+  __shared__ double colv[64];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int64_t L = k - c;
+  TS* A = B + c;
+  for (int t = 0; t < w; ++t) {
+    TS* x = A + (int64_t)t * ldb;
+    double part = 0.0;
+    for (int64_t r = t + 1 + tid; r < L; r += blockDim.x) {
+      const double v = (double)x[r];
+      part += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    double sigma = 0.0;
+    for (int q = 0; q < nw; ++q) sigma += red[q];
+    const double alpha = (double)x[t];
+    double beta = alpha, tau = 0.0, scale = 0.0;
+    if (sigma > 0.0) {
+      const double nrm = sqrt(alpha * alpha + sigma);
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    for (int64_t r = t + 1 + tid; r < L; r += blockDim.x) x[r] = (TS)((double)x[r] * scale);
+    if (tid == 0) {
+      tau_s[t] = tau;
+      Rs[t][t] = beta;
+    }
+    __syncthreads();
+    // w_j = v^T A(t:, j) for the later columns of the panel
+    for (int j = t + 1 + warp; j < w; j += nw) {
+      const TS* a = A + (int64_t)j * ldb;
+      double d = 0.0;
+      for (int64_t r = t + 1 + lane; r < L; r += 32) d += (double)x[r] * (double)a[r];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) wdot[j] = d + (double)a[t];
+    }
+    __syncthreads();
+    const int ncol = w - t - 1;
+    const int64_t nrow = L - t;
+    for (int64_t idx = tid; idx < nrow * ncol; idx += blockDim.x) {
+      const int64_t r = t + idx % nrow;
+      const int j = t + 1 + (int)(idx / nrow);
+      const double v = r == t ? 1.0 : (double)x[r];
+      TS* a = A + r + (int64_t)j * ldb;
+      *a = (TS)((double)*a - tau * v * wdot[j]);
+    }
+    __syncthreads();
+  }
+  // R above the diagonal: row t is final once reflector t has been applied
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    const int i = idx % w, j = idx / w;
+    if (i < j) Rs[i][j] = (double)A[i + (int64_t)j * ldb];
+    else if (i > j) Rs[i][j] = 0.0;
+  }
+  // the reflectors written out
+  for (int64_t idx = tid; idx < k * w; idx += blockDim.x) {
+    const int64_t r = idx % k;
+    const int t = (int)(idx / k);
+    const int64_t rr = r - c;
+    V[r + (int64_t)t * ldv] = rr < t ? (TS)0 : rr == t ? (TS)1 : A[rr + (int64_t)t * ldb];
+  }
+  // G(a, b) = v_a^T v_b, a < b (v_b is zero above row b and 1 at it)
+  for (int idx = warp; idx < w * w; idx += nw) {
+    const int a = idx % w, b = idx / w;
+    if (a >= b) continue;
+    double d = 0.0;
+    for (int64_t r = b + 1 + lane; r < L; r += 32) d += (double)A[r + (int64_t)a * ldb] * (double)A[r + (int64_t)b * ldb];
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) G[a][b] = d + (double)A[b + (int64_t)a * ldb];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int t = 0; t < w; ++t) {
+      const double d = Rs[t][t];
+      if (!(d != 0.0) || !isfinite(d)) *flag |= 1;
+    }
+  }
+  // T, column by column, in place of G (column t of G is read before it is overwritten)
+  for (int t = 0; t < w; ++t) {
+    if (tid < t) {
+      double acc = 0.0;
+      for (int q = tid; q < t; ++q) acc += G[tid][q] * G[q][t];  // G(tid, q), q < t, already holds T
+      colv[tid] = -tau_s[t] * acc;
+    }
+    __syncthreads();
+    if (tid < t) G[tid][t] = colv[tid];
+    if (tid == t) G[t][t] = tau_s[t];
+    __syncthreads();
+  }
+  // R^{-1} in place, column by column: Ri(i, j) = -(sum_{q = i+1..j} R(i, q) Ri(q, j)) / R(i, i)
+  // with the columns < j already inverted; column j is computed into colv first
+  for (int j = 0; j < w; ++j) {
+    if (tid <= j) {
+      const double rjj = 1.0 / Rs[j][j];
+      double acc = 0.0;
+      if (tid < j) {
+        // y_i = sum_{q = i..j-1} Ri(i, q) R(q, j), then Ri(i, j) = -y_i / R(j, j)
+        for (int q = tid; q < j; ++q) acc += Rs[tid][q] * Rs[q][j];
+        colv[tid] = -acc * rjj;
+      } else {
+        colv[tid] = rjj;
+      }
+    }
+    __syncthreads();
+    if (tid <= j) Rs[tid][j] = colv[tid];
+    __syncthreads();
+  }
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    const int i = idx % w, j = idx / w;
+    T[i + (int64_t)j * ldm] = i <= j ? (TS)G[i][j] : (TS)0;
+    Ri[i + (int64_t)j * ldm] = i <= j ? (TS)Rs[i][j] : (TS)0;
+  }
+}
+
 }  // namespace
 
 template <class TA, class TO, class TACC>
@@ -754,5 +892,20 @@ rbgs_status fro_norm_diff(int64_t rows, int64_t cols, const double* A, int64_t l
   RBGS_LAUNCH_CHECK();
   return RBGS_OK;
 }
+
+template <class TS>
+rbgs_status hh_panel(int64_t k, int64_t c, int w, TS* B, int64_t ldb, TS* V, int64_t ldv, TS* T, TS* Ri,
+                     int64_t ldm, int* flag, cudaStream_t st) {
+  if (w < 1 || w > 64 || k - c < w) return RBGS_EINVAL;
+  const int smem = (int)(2 * 64 * 65 * sizeof(double));
+  RBGS_CUDA_TRY(cudaFuncSetAttribute(hh_panel_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  hh_panel_kernel<TS><<<1, 512, smem, st>>>(k, c, w, B, ldb, V, ldv, T, Ri, ldm, flag);
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
+template rbgs_status hh_panel<double>(int64_t, int64_t, int, double*, int64_t, double*, int64_t, double*, double*,
+                                      int64_t, int*, cudaStream_t);
+template rbgs_status hh_panel<float>(int64_t, int64_t, int, float*, int64_t, float*, int64_t, float*, float*,
+                                     int64_t, int*, cudaStream_t);
 
 }  // namespace rbgs

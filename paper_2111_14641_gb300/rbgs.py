@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("interblock", ctypes.c_int32), ("ls", ctypes.c_int32)]
 
 
-LS = {"richardson": 0, "cg": 1}
+LS = {"richardson": 0, "cg": 1, "householder": 2}
 
 
 class Problem(ctypes.Structure):

@@ -81,6 +81,11 @@ def test_argument_checks_need_no_device(lib):
     for bad in (2, 7, -1):
         o.interblock = bad
         assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 16, 0, other, 100, rr, 8, ctypes.byref(o), None) == 1
+    # step-2 solver other than Richardson, CG or Householder
+    o.interblock = 5
+    for bad in (3, -1):
+        o.ls = bad
+        assert lib.rbgs_qr(fake, 100, 8, 100, 4, 0, 16, 0, other, 100, rr, 8, ctypes.byref(o), None) == 1
 
 
 def test_krylov_argument_checks_need_no_device(lib):

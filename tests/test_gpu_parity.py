@@ -551,6 +551,52 @@ def test_cholqr_postprocess_matches_oracle(rb, prec, pmb):
 
 # ------------------------------------------------ step 2 by conjugate gradients --
 
+@pytest.mark.parametrize("prec,fine", [("fp64", False), ("f16x3", True), ("fp32", False)])
+@pytest.mark.parametrize("interblock", [5, 4, 6])
+@pytest.mark.parametrize("reorth,m", [(0, 48), (1, 48), (1, 45)])
+def test_rbgs_householder_step2_matches_oracle(rb, prec, fine, interblock, reorth, m):
+    """Step 2 by Householder least squares (the textbook solver of Sec. 3.1):
+    the blocked Householder QR of S in compact WY form, one panel per block,
+    against the oracle's column-by-column Householder solver.  Both give the
+    exact least-squares solution up to rounding; fp32 with fine=False runs the
+    factorization in FP32."""
+    n, mb, kind, k = 3000, 16, "gauss", 200
+    cond = 1e4 if prec == "fp64" else 1e3
+    W = synth.svd_matrix(n, m, cond, 80)
+    if prec != "fp64":
+        W = W.astype(np.float32).astype(np.float64)
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Qd, Rd, st = rb.rbgs_qr(dev(W, td), mb, kind, k, 5, prec=prec, reorth=reorth, interblock=interblock,
+                            ls="householder", fine=fine)
+    Q, R = host(Qd), host(Rd)
+    ref = oracle.rbgs(W, mb, kind, k, 5, variant=interblock, ls="householder", reorth=bool(reorth))
+    assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+    fact = oracle.factorization_error(W, Q, R)
+    ortho = oracle.sketched_orthogonality(Q, kind, k, 5)[0]
+    if prec == "fp64":
+        tol = 1e-13 * cond
+        assert np.abs(R - ref["R"]).max() <= tol * np.abs(ref["R"]).max()
+        assert np.abs(Q - ref["Q"]).max() <= tol * np.abs(ref["Q"]).max()
+        assert fact < 1e-14 and ortho < 10 * ref["delta"] + 1e-13
+    else:
+        assert fact < 2e-6 and ortho < (1e-4 if reorth else 1e-3)
+        assert np.abs(R - ref["R"]).max() <= 1e-5 * cond * np.abs(ref["R"]).max()
+    if reorth:
+        assert st.passes2 == (m + mb - 1) // mb - 1
+
+
+def test_rbgs_householder_step2_column_by_column(rb):
+    """The column-by-column inter-block variant runs its inner factorization
+    with the same solver."""
+    n, m, mb, kind, k = 2000, 24, 8, "gauss", 96
+    W = synth.svd_matrix(n, m, 1e3, 81)
+    Qd, Rd, _ = rb.rbgs_qr(dev(W), mb, kind, k, 5, prec="fp64", reorth=1, interblock=3, ls="householder")
+    ref = oracle.rbgs(W, mb, kind, k, 5, variant=3, ls="householder", reorth=True)
+    R = host(Rd)
+    assert np.abs(R - ref["R"]).max() <= 1e-10 * np.abs(ref["R"]).max()
+    assert oracle.factorization_error(W, host(Qd), R) < 1e-14
+
+
 @pytest.mark.parametrize("prec", ["fp64", "f16x3"])
 @pytest.mark.parametrize("interblock", [5, 4])
 @pytest.mark.parametrize("reorth", [0, 1])
