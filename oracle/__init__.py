@@ -41,7 +41,7 @@ _SRC = _HERE / "rbgs_oracle.c"
 _BUILD = _HERE / "_build"
 _LIB = _BUILD / "liborbgs.so"
 
-THETA = {"gauss": 0, "rademacher": 1, "srht": 2, "identity": 3}
+THETA = {"gauss": 0, "rademacher": 1, "srht": 2, "identity": 3, "sparse": 4}
 LS = {"householder": 0, "richardson": 1, "cg": 2}
 
 _lib = None
@@ -78,6 +78,8 @@ def _load():
         lib.or_srht_padded.argtypes = [i64]
         lib.or_srht_padded.restype = i64
         lib.or_fwht.argtypes = [dp, i64]
+        lib.or_sparse_column.argtypes = [u64, i64, i64, dp, dp]
+        lib.or_sparse_column.restype = ctypes.c_int
         lib.or_householder_qr.argtypes = [i64, i64, dp, i64, dp]
         lib.or_qr_r.argtypes = [i64, i64, dp, i64, dp, i64]
         lib.or_qr_r.restype = ctypes.c_int
@@ -148,6 +150,21 @@ def srht_samples(seed: int, n: int, k: int) -> np.ndarray:
 def srht_signs(seed: int, n: int) -> np.ndarray:
     lib = _load()
     return np.array([lib.or_srht_sign(int(seed), j) for j in range(int(n))])
+
+
+def sparse_columns(seed: int, k: int, j0: int, count: int):
+    """Rows (count x z, int64) and signs (count x z, +-1.0) of the nonzeros of
+    columns j0 .. j0 + count - 1 of the sparse-sign Theta, z = min(8, k)."""
+    lib = _load()
+    z = min(8, int(k))
+    rows = np.zeros((count, z), dtype=np.int64)
+    signs = np.zeros((count, z), dtype=np.float64)
+    r8 = np.zeros(8, dtype=np.int64)
+    s8 = np.zeros(8, dtype=np.float64)
+    for t in range(count):
+        lib.or_sparse_column(int(seed), int(k), int(j0) + t, _ptr(r8), _ptr(s8))
+        rows[t], signs[t] = r8[:z], s8[:z]
+    return rows, signs
 
 
 def theta_dense(kind: str, k: int, n: int, seed: int) -> np.ndarray:

@@ -14,7 +14,9 @@
  * problems"), with no blocking or fusion beyond what a step states:
  *
  *   Sec. 2.3  sketching matrices (Rademacher, SRHT with zero padding); the
- *             Gaussian sketch is the i.i.d. N(0,1/k) matrix.
+ *             Gaussian sketch is the i.i.d. N(0,1/k) matrix, and the
+ *             sparse-sign sketch the block sparse JL transform (neither is in
+ *             the paper).
  *   Alg. 2    RBGS: sketch W_i, sketched least squares for R_{1:i-1,i},
  *             projection Q'_i = W_i - Q_{1:i-1} R_{1:i-1,i}, sketched QR of
  *             the block (steps 4-5), optional certification (step 6).
@@ -44,6 +46,7 @@
 #define OR_THETA_RADEMACHER 1
 #define OR_THETA_SRHT 2
 #define OR_THETA_IDENTITY 3
+#define OR_THETA_SPARSE 4
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11).
@@ -91,7 +94,14 @@ static void philox_call(uint64_t seed, uint32_t a, uint32_t b, uint32_t purpose,
  *  SRHT       theta_{r,j} = D_j * (-1)^{popcount(s_r & j)} / sqrt(k), D_j the
  *             sign bit (j & 31) of word (j>>5)&3 of block (j>>7, 0, 2, 0),
  *             s_0 < ... < s_{k-1} the sampled rows of the n' x n' Sylvester
- *             Hadamard matrix, n' = 2^ceil(log2 n).                        */
+ *             Hadamard matrix, n' = 2^ceil(log2 n).
+ *  Sparse     sign (not in the paper): the block construction of the sparse
+ *             Johnson-Lindenstrauss transform (Kane and Nelson, J. ACM 2014).
+ *             With z = min(8, k), the rows split into z segments
+ *             [floor(s k / z), floor((s+1) k / z)); column j has exactly one
+ *             nonzero in each segment s, +-1/sqrt(z), at offset
+ *             (x >> 1) mod (segment size), negative when bit 0 of x is set,
+ *             x = word s&3 of the block with counter (j_lo, s>>2, 4, j_hi). */
 static double gauss_pair(uint64_t seed, int64_t j, int64_t rpair, int which) {
   uint32_t x[4];
   philox_call(seed, (uint32_t)(j & 0xffffffff), (uint32_t)rpair, 0u, (uint32_t)(j >> 32), x);
@@ -124,6 +134,21 @@ double or_srht_sign(uint64_t seed, int64_t j) {
   philox_call(seed, (uint32_t)(j >> 7), 0u, 2u, 0u, x);
   uint32_t bit = (x[(j >> 5) & 3] >> (j & 31)) & 1u;
   return bit ? -1.0 : 1.0;
+}
+
+/* The z nonzeros of column j of the sparse-sign Theta: rows[s] (segment s)
+ * and signs[s] = +-1.  Returns z = min(8, k).                               */
+int or_sparse_column(uint64_t seed, int64_t k, int64_t j, int64_t* rows, double* signs) {
+  int z = k < 8 ? (int)k : 8;
+  for (int s = 0; s < z; ++s) {
+    uint32_t x[4];
+    philox_call(seed, (uint32_t)(j & 0xffffffff), (uint32_t)(s >> 2), 4u, (uint32_t)(j >> 32), x);
+    uint32_t w = x[s & 3];
+    int64_t lo = (int64_t)s * k / z, hi = (int64_t)(s + 1) * k / z;
+    rows[s] = lo + (int64_t)((w >> 1) % (uint32_t)(hi - lo));
+    signs[s] = (w & 1u) ? -1.0 : 1.0;
+  }
+  return z;
 }
 
 static int cmp_i64(const void* a, const void* b) {
@@ -181,8 +206,16 @@ int or_theta_dense(int type, int64_t k, int64_t n, uint64_t seed, double* T) {
       if (type == OR_THETA_GAUSS) v = or_theta_gauss_entry(seed, k, r, j);
       else if (type == OR_THETA_RADEMACHER) v = or_theta_rademacher_entry(seed, k, r, j);
       else if (type == OR_THETA_SRHT) v = or_theta_srht_entry(seed, k, n, samples, r, j);
+      else if (type == OR_THETA_SPARSE) v = 0.0;
       else v = (r == j) ? 1.0 : 0.0;
       T[r + j * k] = v;
+    }
+  if (type == OR_THETA_SPARSE)
+    for (int64_t j = 0; j < n; ++j) {
+      int64_t rows[8];
+      double signs[8];
+      int z = or_sparse_column(seed, k, j, rows, signs);
+      for (int s = 0; s < z; ++s) T[rows[s] + j * k] = signs[s] / sqrt((double)z);
     }
   free(samples);
   return 0;
@@ -212,6 +245,23 @@ static void* theta_dense_worker(void* arg) {
       double t = (J->type == OR_THETA_GAUSS) ? or_theta_gauss_entry(J->seed, J->k, r, j)
                                              : or_theta_rademacher_entry(J->seed, J->k, r, j);
       for (int64_t c = 0; c < J->ncols; ++c) J->Y[r + c * J->ldy] += t * J->X[j + c * J->ldx];
+    }
+  }
+  return NULL;
+}
+
+/* Sparse sign: each worker owns a range of columns of X and scatters every
+ * row x_j into the z rows of column j of Theta.                             */
+static void* theta_sparse_worker(void* arg) {
+  theta_job* J = (theta_job*)arg;
+  int64_t rows[8];
+  double signs[8];
+  for (int64_t c = J->lo; c < J->hi; ++c) {
+    for (int64_t r = 0; r < J->k; ++r) J->Y[r + c * J->ldy] = 0.0;
+    for (int64_t j = 0; j < J->n; ++j) {
+      int z = or_sparse_column(J->seed, J->k, j, rows, signs);
+      double v = J->X[j + c * J->ldx] / sqrt((double)z);
+      for (int s = 0; s < z; ++s) J->Y[rows[s] + c * J->ldy] += signs[s] * v;
     }
   }
   return NULL;
@@ -266,7 +316,7 @@ int or_theta_apply(int type, int64_t k, int64_t n, uint64_t seed, const double* 
     if (or_srht_samples(seed, or_srht_padded(n), k, samples)) { free(samples); return -1; }
   }
   int nt = g_threads;
-  int64_t total = (type == OR_THETA_SRHT) ? ncols : k;
+  int64_t total = (type == OR_THETA_SRHT || type == OR_THETA_SPARSE) ? ncols : k;
   if (nt > total) nt = (int)(total > 0 ? total : 1);
   pthread_t th[256];
   theta_job jobs[256];
@@ -284,7 +334,9 @@ int or_theta_apply(int type, int64_t k, int64_t n, uint64_t seed, const double* 
       J->lo = total * t / nt;
       J->hi = total * (t + 1) / nt;
     }
-    void* (*fn)(void*) = (type == OR_THETA_SRHT) ? theta_srht_worker : theta_dense_worker;
+    void* (*fn)(void*) = (type == OR_THETA_SRHT)     ? theta_srht_worker
+                         : (type == OR_THETA_SPARSE) ? theta_sparse_worker
+                                                     : theta_dense_worker;
     if (nt == 1) fn(J);
     else pthread_create(&th[t], NULL, fn, J);
   }

@@ -15,7 +15,9 @@ import oracle  # noqa: E402
 def main():
     # Sketching matrices of Sec. 2.3 (SRHT with zero padding, Rademacher) and the
     # Gaussian N(0, 1/k) sketch, under the Philox4x32-10 entry convention.
-    for kind, k, n, seed in [("srht", 5, 12, 3), ("rademacher", 6, 9, 4), ("gauss", 4, 7, 5)]:
+    # The sparse-sign sketch is the block construction of the sparse JL transform.
+    for kind, k, n, seed in [("srht", 5, 12, 3), ("rademacher", 6, 9, 4), ("gauss", 4, 7, 5),
+                             ("sparse", 19, 6, 6)]:
         T = oracle.theta_dense(kind, k, n, seed)
         path = os.path.join(HERE, f"theta_{kind}_k{k}_n{n}_seed{seed}.txt")
         with open(path, "w") as f:

@@ -134,7 +134,79 @@ def test_rademacher_theta_distribution():
     np.testing.assert_allclose(oracle.theta_apply("gauss", 40, 5, Xg), Tg @ Xg, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("kind", ["gauss", "rademacher", "srht"])
+def _segments(k):
+    z = min(8, k)
+    return z, [(s * k // z, (s + 1) * k // z) for s in range(z)]
+
+
+@pytest.mark.parametrize("k", [1, 5, 8, 19, 200, 2001])
+def test_sparse_sign_theta_structure(k):
+    """The block construction of the sparse JL transform (Kane and Nelson
+    2014): z = min(8, k) row segments, exactly one nonzero +-1/sqrt(z) per
+    segment and column, so every column has unit norm.  k <= 8 leaves one row
+    per segment: a dense +-1/sqrt(k) sign matrix."""
+    n = 300
+    z, seg = _segments(k)
+    T = oracle.theta_dense("sparse", k, n, 11)
+    for s, (lo, hi) in enumerate(seg):
+        block = T[lo:hi]
+        assert np.all((block != 0).sum(axis=0) == 1)
+    assert set(np.unique(np.abs(T[T != 0]) * np.sqrt(z)).round(14)) == {1.0}
+    np.testing.assert_allclose(np.linalg.norm(T, axis=0), 1.0, rtol=0, atol=1e-15)
+    if k <= 8:
+        assert np.all(T != 0)
+    # columns beyond 2^32 take the high counter word: they differ from their low twins
+    r_lo, s_lo = oracle.sparse_columns(11, k, 5, 3)
+    r_hi, s_hi = oracle.sparse_columns(11, k, 5 + (1 << 32), 3)
+    if k > 8:
+        assert not (np.array_equal(r_lo, r_hi) and np.array_equal(s_lo, s_hi))
+    for (lo, hi), col in zip(seg, r_hi.T):
+        assert np.all((col >= lo) & (col < hi))
+
+
+def test_sparse_sign_theta_distribution():
+    """Within each segment the nonzero's row is uniform and its sign is a fair
+    coin, independently over columns (chi-square and binomial bounds at about
+    five standard deviations)."""
+    k, n = 200, 20000
+    z, seg = _segments(k)
+    rows, signs = oracle.sparse_columns(3, k, 0, n)
+    for s, (lo, hi) in enumerate(seg):
+        size = hi - lo
+        cnt = np.bincount(rows[:, s] - lo, minlength=size)
+        expect = n / size
+        chi2 = ((cnt - expect) ** 2 / expect).sum()
+        assert chi2 < (size - 1) + 5 * np.sqrt(2 * (size - 1))
+    neg = (signs < 0).mean()
+    assert abs(neg - 0.5) < 5 * 0.5 / np.sqrt(signs.size)
+    off = rows - np.array([lo for lo, _ in seg])[None, :]
+    assert abs(np.corrcoef(off[:-1].ravel(), off[1:].ravel())[0, 1]) < 0.02
+    # E[Theta^T Theta] = I: the off-diagonal inner products of distinct columns average to 0
+    T = oracle.theta_dense("sparse", k, 2000, 3)
+    G = T.T @ T
+    off_diag = G[~np.eye(2000, dtype=bool)]
+    assert abs(off_diag.mean()) < 5 * off_diag.std() / np.sqrt(off_diag.size)
+
+
+def test_sparse_sign_columns_follow_the_written_definition():
+    """The nonzeros restated from the raw Philox blocks (word s & 3 of the
+    block with counter (j_lo, s >> 2, 4, j_hi)), for low and high column
+    indices; the raw generator is pinned by the cuRAND known answers."""
+    seed, k = (9 << 33) + 5, 2001
+    z, seg = _segments(k)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for j0 in (0, 777, (3 << 32) + 11):
+        rows, signs = oracle.sparse_columns(seed, k, j0, 4)
+        for t in range(4):
+            j = j0 + t
+            for s, (lo, hi) in enumerate(seg):
+                x = oracle.philox([j & 0xFFFFFFFF, s >> 2, 4, j >> 32], key)
+                w = int(x[s & 3])
+                assert rows[t, s] == lo + (w >> 1) % (hi - lo)
+                assert signs[t, s] == (-1.0 if w & 1 else 1.0)
+
+
+@pytest.mark.parametrize("kind", ["gauss", "rademacher", "srht", "sparse"])
 def test_subspace_embedding(kind):
     """Def. 2.1: with k large against d, Theta is an eps-embedding of a fixed
     d-dimensional subspace with eps < 1/2; by Cor. 2.4 the sketch then keeps
@@ -221,7 +293,7 @@ def test_rbgs_identity_sketch_is_householder_qr(variant):
     np.testing.assert_allclose(out["R"], s[:, None] * Rn, atol=1e-12)
 
 
-@pytest.mark.parametrize("kind", ["gauss", "rademacher", "srht"])
+@pytest.mark.parametrize("kind", ["gauss", "rademacher", "srht", "sparse"])
 @pytest.mark.parametrize("variant", [1, 3, 4, 5, 6])
 def test_rbgs_reaches_closed_form(kind, variant):
     """In exact arithmetic R = R(Theta W) with a positive diagonal and
@@ -361,6 +433,7 @@ def test_bad_arguments_rejected():
     ("theta_srht_k5_n12_seed3.txt", "srht", 5, 12, 3),
     ("theta_rademacher_k6_n9_seed4.txt", "rademacher", 6, 9, 4),
     ("theta_gauss_k4_n7_seed5.txt", "gauss", 4, 7, 5),
+    ("theta_sparse_k19_n6_seed6.txt", "sparse", 19, 6, 6),
 ])
 def test_theta_golden(fname, kind, k, n, seed):
     """Stored Theta entries (tests/golden, written by make_golden.py from the
