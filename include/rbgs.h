@@ -50,11 +50,16 @@ typedef enum {
 } rbgs_status;
 
 /* Sketching matrices Theta (k x n).  Sec. 2.3 uses Rademacher and SRHT; the
- * Gaussian N(0, 1/k) matrix is the classical oblivious embedding.  Theta is
+ * Gaussian N(0, 1/k) matrix is the classical oblivious embedding, and the
+ * sparse sign matrix is the block construction of the sparse JL transform
+ * (Kane and Nelson 2014): z = min(8, k) row segments, one nonzero
+ * +-1/sqrt(z) per segment and column (neither is in the paper).  Theta is
  * never stored: its entries are regenerated from a Philox4x32-10 counter
- * generator keyed by `seed` (layout in the library's DESIGN notes; the CPU
- * oracle implements the same definition independently).                   */
-typedef enum { RBGS_SK_GAUSS = 0, RBGS_SK_RADEMACHER = 1, RBGS_SK_SRHT = 2 } rbgs_sketch;
+ * generator keyed by (seed_lo, seed_hi), counter word 2 naming the stream
+ * (0 Gaussian, 1 Rademacher, 2 SRHT signs, 3 SRHT row sampling, 4 sparse
+ * sign); the CPU oracle implements the same definitions independently.
+ * Every kind needs k <= n, SRHT k <= 2^ceil(log2 n).                       */
+typedef enum { RBGS_SK_GAUSS = 0, RBGS_SK_RADEMACHER = 1, RBGS_SK_SRHT = 2, RBGS_SK_SPARSE = 3 } rbgs_sketch;
 
 /* Arithmetic of the tall (n-row) operations: the projection of step 3 fused
  * with R_ii^{-1}, and the sketches.
@@ -342,6 +347,16 @@ RBGS_API rbgs_status rbgs_rayleigh_ritz(const rbgs_op* op, const double* B0, int
 /* Philox4x32-10 blocks on the device: out[4i..4i+3] = philox(ctr[4i..4i+3],
  * key = (seed_lo, seed_hi)) for i < count (device pointers).              */
 RBGS_API rbgs_status rbgs_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t count, void* stream, int32_t sync);
+
+/* The nonzeros of columns j0 .. j0 + count - 1 of the sparse-sign Theta, on
+ * the host (the generator the sketch kernels evaluate, exposed so that the
+ * definition can be checked without a device): rows[t z + s] is the row of
+ * the nonzero of column j0 + t in segment s, neg[...] = 1 where it is
+ * -1/sqrt(z), z = min(8, k).  rows and neg are caller-owned host arrays of
+ * count * z entries.  RBGS_EINVAL on a null pointer, k < 1, j0 < 0 or
+ * count < 0.                                                                */
+RBGS_API rbgs_status rbgs_sparse_sign_columns(uint64_t seed, int64_t k, int64_t j0, int64_t count, int64_t* rows,
+                                              int32_t* neg);
 
 /* Number of kernels this library has launched in the process so far (all
  * devices, all entry points); a counter for profiling and accounting.     */

@@ -7,9 +7,9 @@ kernels, include/rbgs.h); this package is its Python binding.
 from .rbgs import (NOALLOC_MAX_K, PREC, SKETCH, Op, QRGraph, QRStats, RbgsError, block_arnoldi, block_fom,
                    block_gmres, cholqr_postprocess, colmajor, embedding_check, launch_count, load, op_apply, philox,
                    rayleigh_ritz, rbgs_qr, rbgs_qr_batched, rbgs_qr_host, release_workspace, sketch_apply,
-                   stencil_op, tall_update, tall_update_noalloc, version)
+                   sparse_sign_columns, stencil_op, tall_update, tall_update_noalloc, version)
 
 __all__ = ["NOALLOC_MAX_K", "PREC", "SKETCH", "Op", "QRGraph", "QRStats", "RbgsError", "block_arnoldi", "block_fom",
            "block_gmres", "cholqr_postprocess", "colmajor", "embedding_check", "launch_count", "load", "op_apply", "philox",
            "rayleigh_ritz", "rbgs_qr", "rbgs_qr_batched", "rbgs_qr_host", "release_workspace",
-           "sketch_apply", "stencil_op", "tall_update", "tall_update_noalloc", "version"]
+           "sketch_apply", "sparse_sign_columns", "stencil_op", "tall_update", "tall_update_noalloc", "version"]

@@ -38,7 +38,13 @@ __host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
 }
 
 // Stream purposes carried in counter word 2.
-enum : uint32_t { kPurposeGauss = 0, kPurposeRademacher = 1, kPurposeSrhtSign = 2, kPurposeSrhtSample = 3 };
+enum : uint32_t {
+  kPurposeGauss = 0,
+  kPurposeRademacher = 1,
+  kPurposeSrhtSign = 2,
+  kPurposeSrhtSample = 3,
+  kPurposeSparse = 4
+};
 
 // Gaussian pair for column j, row pair rp of Theta (Box-Muller on 53-bit
 // uniforms in (0,1)); z0 serves row 2 rp, z1 row 2 rp + 1.
@@ -61,6 +67,31 @@ __device__ __forceinline__ uint4 rademacher_bits(uint2 key, int64_t j, uint32_t 
 // 128 SRHT diagonal sign bits for padded rows [128 g, 128 g + 128).
 __device__ __forceinline__ uint4 srht_sign_bits(uint2 key, uint32_t g) {
   return philox10(make_uint4(g, 0u, kPurposeSrhtSign, 0u), key);
+}
+
+// Sparse sign, the block construction of the sparse Johnson-Lindenstrauss
+// transform (Kane and Nelson 2014): with z = min(8, k) the rows split into z
+// segments [floor(s k / z), floor((s + 1) k / z)); column j has one nonzero
+// +-1/sqrt(z) in each, at offset (x >> 1) mod (segment size), negative when
+// bit 0 of x is set, x = word s & 3 of the block with counter
+// (j_lo, s >> 2, 4, j_hi).  Fills rows[s], neg[s] for s < z; returns z.
+__host__ __device__ __forceinline__ int sparse_zeta(int64_t k) { return k < 8 ? (int)k : 8; }
+__host__ __device__ __forceinline__ int sparse_column(uint2 key, int64_t j, int64_t k, int64_t (&rows)[8],
+                                                      bool (&neg)[8]) {
+  const int z = sparse_zeta(k);
+  uint4 x = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    if (s < z) {
+      if ((s & 3) == 0)
+        x = philox10(make_uint4((uint32_t)j, (uint32_t)(s >> 2), kPurposeSparse, (uint32_t)(j >> 32)), key);
+      const uint32_t v = (s & 3) == 0 ? x.x : ((s & 3) == 1 ? x.y : ((s & 3) == 2 ? x.z : x.w));
+      const int64_t lo = (int64_t)s * k / z, hi = (int64_t)(s + 1) * k / z;
+      rows[s] = lo + (int64_t)((v >> 1) % (uint32_t)(hi - lo));
+      neg[s] = (v & 1u) != 0u;
+    }
+  }
+  return z;
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint4& v, int w) {

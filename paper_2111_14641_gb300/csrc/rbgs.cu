@@ -969,7 +969,7 @@ rbgs_status check_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t m
     int64_t np = 1;
     while (np < n) np <<= 1;
     if (k > np) return RBGS_EINVAL;
-  } else if (sketch == RBGS_SK_GAUSS || sketch == RBGS_SK_RADEMACHER) {
+  } else if (sketch == RBGS_SK_GAUSS || sketch == RBGS_SK_RADEMACHER || sketch == RBGS_SK_SPARSE) {
     if (k > n) return RBGS_EINVAL;
   } else {
     return RBGS_EINVAL;
@@ -1515,7 +1515,7 @@ rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t
     int64_t np = 1;
     while (np < n) np <<= 1;
     if (k > np) return RBGS_EINVAL;
-  } else if (sketch != RBGS_SK_GAUSS && sketch != RBGS_SK_RADEMACHER) {
+  } else if (sketch != RBGS_SK_GAUSS && sketch != RBGS_SK_RADEMACHER && sketch != RBGS_SK_SPARSE) {
     return RBGS_EINVAL;
   }
   const bool fp64 = prec == RBGS_P_FP64;
@@ -1629,6 +1629,22 @@ rbgs_status rbgs_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64
   return RBGS_OK;
 }
 
+rbgs_status rbgs_sparse_sign_columns(uint64_t seed, int64_t k, int64_t j0, int64_t count, int64_t* rows,
+                                     int32_t* neg) {
+  if (!rows || !neg || k < 1 || j0 < 0 || count < 0) return RBGS_EINVAL;
+  const uint2 key = seed_key(seed);
+  for (int64_t t = 0; t < count; ++t) {
+    int64_t r[8];
+    bool g[8];
+    const int z = sparse_column(key, j0 + t, k, r, g);
+    for (int s = 0; s < z; ++s) {
+      rows[t * z + s] = r[s];
+      neg[t * z + s] = g[s] ? 1 : 0;
+    }
+  }
+  return RBGS_OK;
+}
+
 rbgs_status rbgs_release_workspace(void) {
   int dev = 0;
   RBGS_CUDA_TRY(cudaGetDevice(&dev));
@@ -1667,7 +1683,8 @@ rbgs_status check_sketch(rbgs_sketch sketch, int64_t n, int64_t k, int64_t m) {
     while (np < n) np <<= 1;
     return k > np ? RBGS_EINVAL : RBGS_OK;
   }
-  if (sketch == RBGS_SK_GAUSS || sketch == RBGS_SK_RADEMACHER) return k > n ? RBGS_EINVAL : RBGS_OK;
+  if (sketch == RBGS_SK_GAUSS || sketch == RBGS_SK_RADEMACHER || sketch == RBGS_SK_SPARSE)
+    return k > n ? RBGS_EINVAL : RBGS_OK;
   return RBGS_EINVAL;
 }
 

@@ -799,6 +799,25 @@ __global__ void __launch_bounds__(kDenseThreads) dense_sketch_part(const TX* __r
         th[2 * rpl][jl] = (TC)(z0 * scale);
         th[2 * rpl + 1][jl] = (TC)(z1 * scale);
       }
+    } else if (KIND == RBGS_SK_SPARSE) {
+      // 64 rows x 32 columns of Theta: each column's z nonzeros, kept where
+      // they fall into this CTA's rows
+      if (tid < kDenseJ) {
+        const int64_t j = jj0 + tid;
+        for (int rl = 0; rl < kDenseRows; ++rl) th[rl][tid] = (TC)0;
+        if (j < j1) {
+          int64_t rows[8];
+          bool neg[8];
+          const int z = sparse_column(key, j, k, rows, neg);
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            if (s < z) {
+              const int64_t rl = rows[s] - r0;
+              if (rl >= 0 && rl < kDenseRows) th[rl][tid] = neg[s] ? (TC)(-scale) : (TC)scale;
+            }
+          }
+        }
+      }
     } else {
       if (tid < kDenseJ) {
         const int64_t j = jj0 + tid;
@@ -999,8 +1018,8 @@ rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed
     return sketch_apply2_t<TX, TY>(kind, k, n, seed, X, ldx, ncols, Y, ldy, X, ldx, 0, Y, ldy, scratch,
                                    scratch_bytes, st, active);
   const uint2 key = seed_key(seed);
-  const double dscale = 1.0 / std::sqrt((double)k);
-  if (kind != RBGS_SK_GAUSS && kind != RBGS_SK_RADEMACHER) return RBGS_EINVAL;
+  const double dscale = 1.0 / std::sqrt((double)(kind == RBGS_SK_SPARSE ? sparse_zeta(k) : k));
+  if (kind != RBGS_SK_GAUSS && kind != RBGS_SK_RADEMACHER && kind != RBGS_SK_SPARSE) return RBGS_EINVAL;
   const int nsplit = dense_nsplit(k, n);
   const int64_t rows_per_split = ((n + nsplit - 1) / nsplit + kDenseJ - 1) / kDenseJ * kDenseJ;
   TC* part = reinterpret_cast<TC*>(scratch);
@@ -1012,6 +1031,9 @@ rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed
     if (kind == RBGS_SK_GAUSS)
       dense_sketch_part<RBGS_SK_GAUSS, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
                                                                               dscale, rows_per_split, part, active);
+    else if (kind == RBGS_SK_SPARSE)
+      dense_sketch_part<RBGS_SK_SPARSE, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
+                                                                               dscale, rows_per_split, part, active);
     else
       dense_sketch_part<RBGS_SK_RADEMACHER, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
                                                                                    dscale, rows_per_split, part,

@@ -18,7 +18,7 @@ from . import build as _build
 
 _HDR = Path(__file__).resolve().parent.parent / "include" / "rbgs.h"
 
-SKETCH = {"gauss": 0, "rademacher": 1, "srht": 2}
+SKETCH = {"gauss": 0, "rademacher": 1, "srht": 2, "sparse": 3}
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "f16x3": 3}
 # Largest c + mb that rbgs_tall_update_noalloc accepts (its fixed scratch).
 NOALLOC_MAX_K = int(re.search(r"#define RBGS_NOALLOC_MAX_K (\d+)", _HDR.read_text()).group(1))
@@ -125,13 +125,14 @@ def load(build_if_missing: bool = False):
     lib.rbgs_qr_host.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
                                  ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
     lib.rbgs_release_workspace.argtypes = []
+    lib.rbgs_sparse_sign_columns.argtypes = [u64, i64, i64, i64, vp, vp]
     lib.rbgs_version.restype = ctypes.c_char_p
     lib.rbgs_launch_count.restype = ctypes.c_int64
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
                  "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
                  "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched", "rbgs_qr_host",
                  "rbgs_embedding_check", "rbgs_cholqr_postprocess", "rbgs_qr_graph_create",
-                 "rbgs_qr_graph_launch", "rbgs_qr_graph_destroy"):
+                 "rbgs_qr_graph_launch", "rbgs_qr_graph_destroy", "rbgs_sparse_sign_columns"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -501,6 +502,21 @@ def rayleigh_ritz(op: Op, B0: torch.Tensor, p: int = 10, n_iter: int = 1, which:
                                   ctypes.cast(rs, ctypes.c_void_p)), "rbgs_rayleigh_ritz")
     vals = [complex(re[j], im[j]) for j in range(mb)]
     return vals, X, [float(v) for v in rs]
+
+
+def sparse_sign_columns(seed: int, k: int, j0: int, count: int):
+    """Rows (count x z) and negative flags of the nonzeros of columns j0 ..
+    j0 + count - 1 of the sparse-sign Theta, z = min(8, k), as numpy arrays
+    (the generator the sketch kernels evaluate, run on the host)."""
+    import numpy as np
+
+    lib = load()
+    z = min(8, int(k))
+    rows = np.zeros((count, z), dtype=np.int64)
+    neg = np.zeros((count, z), dtype=np.int32)
+    _check(lib.rbgs_sparse_sign_columns(int(seed), int(k), int(j0), int(count), rows.ctypes.data, neg.ctypes.data),
+           "rbgs_sparse_sign_columns")
+    return rows, neg
 
 
 def philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:

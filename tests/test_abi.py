@@ -151,3 +151,22 @@ def test_embedding_check_argument_checks_need_no_device(lib):
     assert lib.rbgs_embedding_check(fake, 100, 8, 100, 4, 0, 16, 0, 1, None, None) == 1     # no output
     assert lib.rbgs_embedding_check(fake, 100, 8, 100, 4, 0, 101, 0, 1, None, outp) == 1    # k > n
     assert lib.rbgs_embedding_check(fake, 100, 8, 99, 4, 0, 16, 0, 1, None, outp) == 1      # ldz < n
+
+
+@pytest.mark.parametrize("seed,k", [(0, 1), (6, 5), (11, 8), ((9 << 33) + 5, 2001), (3, 200)])
+def test_sparse_sign_generator_matches_the_oracle(lib, seed, k):
+    """The sparse-sign Theta the sketch kernels evaluate (run here on the host
+    through the C ABI) has the oracle's nonzeros exactly, columns beyond 2^32
+    included; the two sides implement the definition independently."""
+    import numpy as np
+
+    import oracle
+    from paper_2111_14641_gb300 import rbgs as rbmod
+
+    for j0, count in ((0, 300), ((5 << 32) + 7, 40)):
+        rows, neg = rbmod.sparse_sign_columns(seed, k, j0, count)
+        r_ref, s_ref = oracle.sparse_columns(seed, k, j0, count)
+        assert np.array_equal(rows, r_ref)
+        assert np.array_equal(neg == 1, s_ref < 0)
+    with pytest.raises(rbmod.RbgsError):
+        rbmod.sparse_sign_columns(seed, 0, 0, 1)
