@@ -659,7 +659,7 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
           r = small_gemm<float, double, double>(1, mb, mb, n, 1.0, (const float*)Qo, ldq, (const float*)Qo, ldq,
                                                 0.0, gram, mb, part, kPartElems, act, st);
         if (r) return r;
-        // round 0 leaves R1 in racc; round 1 forms R' = R2 R1 in rtmp
+        // the first Cholesky round leaves R1 in racc; the second forms R' = R2 R1 in rtmp
         if ((r = chol_inv<double>(mb, gram, round == 0 ? racc : r1, r1i, 0.0, brk, nullptr, nullptr, act, st)))
           return r;
         if (round == 1 && (r = tri_mul<double>(mb, r1, racc, rtmp, act, st))) return r;
