@@ -16,6 +16,14 @@ prescribed structure.  Recipes:
   N(0,1), and every 8th column j (j = 8, 16, ...) is replaced by column
   j - 1 - (r mod j), r a seeded integer, plus Gaussian noise of relative size
   1e-7 (a numerically rank-deficient matrix in FP32).
+* ``gaussian_random_field``: the log-coefficient g of the random diffusion
+  problems, a ~ exp(g): a stationary Gaussian field on the (N+2) x (N+2) grid
+  nodes of the unit square (spacing h = 1/(N+1)), zero mean, variance ``var``,
+  squared-exponential covariance var * exp(-|x - y|^2 / (2 corr^2)), drawn by
+  the spectral method on a periodic grid of twice the size (so the wrap-around
+  does not correlate opposite sides) from numpy's PCG64 with the given seed.
+* ``unet_params``: He-normal initial weights and zero biases of the small
+  U-Net preconditioner (3 x 3 kernels; the layer widths c, c, 2c, 2c, c, 1).
 
 CPU draws use numpy's PCG64; device draws (large sizes) use torch's generator
 on the given device, so the two do not produce the same numbers: a test that
@@ -121,3 +129,33 @@ def near_duplicate_matrix_torch(n: int, m: int, seed: int, device="cuda", dtype=
         scale = float(torch.linalg.norm(W[:, src])) / n ** 0.5
         W[:, j] = W[:, src] + 1e-7 * scale * torch.randn(n, device=device, generator=g, dtype=dtype)
     return W
+
+
+def gaussian_random_field(N: int, seed: int, corr: float = 0.05, var: float = 1.0) -> np.ndarray:
+    """(N+2) x (N+2) node values of a zero-mean stationary Gaussian field with
+    covariance var * exp(-r^2 / (2 corr^2)) on the unit square."""
+    h = 1.0 / (N + 1)
+    M = 2 * (N + 2)
+    f = np.fft.fftfreq(M, d=h)  # cycles per unit length
+    kx, ky = np.meshgrid(f, f, indexing="ij")
+    # spectral density of the squared-exponential covariance (2-D Fourier transform)
+    dens = var * 2.0 * np.pi * corr ** 2 * np.exp(-2.0 * np.pi ** 2 * corr ** 2 * (kx ** 2 + ky ** 2))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xi = rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))
+    L = M * h  # period of the embedding grid
+    g = np.fft.ifft2(xi * np.sqrt(dens / L ** 2)) * M * M
+    return np.ascontiguousarray(g.real[: N + 2, : N + 2])
+
+
+def unet_params(c: int, seed: int) -> dict:
+    """Initial weights of the U-Net preconditioner: w (C_out, C_in, 3, 3) He
+    normal (std sqrt(2 / (9 C_in))), b zero.  Layers: e1 1->c, e2 c->c, m1
+    c->2c, m2 2c->2c, o1 3c->c, o2 c->1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shapes = {"e1": (c, 1), "e2": (c, c), "m1": (2 * c, c), "m2": (2 * c, 2 * c), "o1": (c, 3 * c), "o2": (1, c)}
+    out = {}
+    for name, (co, ci) in shapes.items():
+        out[name + ".w"] = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (9 * ci))
+        out[name + ".b"] = np.zeros(co)
+    return out
+
