@@ -199,13 +199,15 @@ def test_adam_first_step_moves_by_the_learning_rate():
     np.testing.assert_allclose(P["w"] - w0, -1e-2 * np.sign(g["w"]), rtol=1e-12, atol=0)
 
 
-def test_residual_loss_gradients_match_finite_differences():
-    """The residual-norm pair loss differentiates through the operator."""
+@pytest.mark.parametrize("loss", ["residual", "correction"])
+def test_pair_loss_gradients_match_finite_differences(loss):
+    """Both pair losses; the residual-norm one differentiates through the operator."""
     N = 8
     a = np.exp(synth.gaussian_random_field(N, 31))
     params = synth.unet_params(2, 32)
     r = synth.gaussian(N * N, 1, 33)[:, 0]
-    val, g = L.pair_loss_and_grad(params, a, r)
+    e = L.correction_targets(a, r)[:, 0]
+    val, g = L.pair_loss_and_grad(params, a, r, e, loss=loss)
     rng = np.random.default_rng(6)
     eps = 1e-6
     for name in ("e1.w", "m2.w", "o1.b", "o2.w"):
@@ -214,7 +216,8 @@ def test_residual_loss_gradients_match_finite_differences():
             Pm = {k2: v.copy() for k2, v in params.items()}
             Pp[name].reshape(-1)[idx] += eps
             Pm[name].reshape(-1)[idx] -= eps
-            fd = (L.pair_loss_and_grad(Pp, a, r)[0] - L.pair_loss_and_grad(Pm, a, r)[0]) / (2 * eps)
+            fd = (L.pair_loss_and_grad(Pp, a, r, e, loss=loss)[0] - L.pair_loss_and_grad(Pm, a, r, e, loss=loss)[0]) \
+                / (2 * eps)
             an = g[name].reshape(-1)[idx]
             assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * val), (name, idx, fd, an)
 
