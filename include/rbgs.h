@@ -261,9 +261,15 @@ RBGS_API rbgs_status rbgs_tall_update(int32_t prec, int64_t n, int64_t c, int64_
  * about 4.03 MiB) is a fixed __device__ array inside the library, present on
  * every device that loads it until the process exits.  The first call on a
  * device looks up that array's device address (with the device current);
- * make that first call before any stream capture on the device.  All calls
- * share the array: calls whose GPU work overlaps (unordered streams, or host
- * threads calling at once) race on it and give wrong results.            */
+ * make that first call before any stream capture on the device.  The address
+ * is kept until rbgs_release_workspace() on that device, which a caller must
+ * call after cudaDeviceReset before the next call.  All calls share the
+ * array: calls whose GPU work overlaps (unordered streams, or host threads
+ * calling at once) race on it and give wrong results.
+ * Status: with sync != 0 a bounded device wait that expired in the TF32X3
+ * kernel returns RBGS_ETIMEOUT; with sync == 0 the call returns after
+ * enqueueing and that timeout is not reported (the next call clears its
+ * flag), so callers that need it pass sync = 1.                           */
 #define RBGS_NOALLOC_MAX_K 8192
 RBGS_API rbgs_status rbgs_tall_update_noalloc(int32_t prec, int64_t n, int64_t c, int64_t mb, const void* Qprev,
                                      int64_t ldq, const void* X, int64_t ldx, const double* G, int64_t ldg,
@@ -362,7 +368,9 @@ RBGS_API rbgs_status rbgs_sparse_sign_columns(uint64_t seed, int64_t k, int64_t 
  * devices, all entry points); a counter for profiling and accounting.     */
 RBGS_API int64_t rbgs_launch_count(void);
 
-/* Release the cached device workspace of the current device.             */
+/* Release the cached device workspace of the current device, the cached
+ * SRHT plans and the looked-up address of the no-allocation entry point's
+ * scratch array (call it after cudaDeviceReset before any further call). */
 RBGS_API rbgs_status rbgs_release_workspace(void);
 
 /* Library version string (static storage).                               */

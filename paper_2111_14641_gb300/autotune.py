@@ -27,6 +27,17 @@ FP32_VARIANTS = ("f16x3", "tf32x3", "fp32")
 STREAM_COUNTS = (1, 4, 8, 16)
 
 
+def _failed(out) -> bool:
+    """True when a run's per-problem statuses (the third item of what the
+    batched entry point returns) hold a nonzero code: RBGS_EBREAKDOWN or
+    RBGS_ETIMEOUT are reported there rather than raised."""
+    try:
+        statuses = out[2]
+    except (TypeError, IndexError):
+        return False
+    return any(int(s) != 0 for s in statuses)
+
+
 def shape_class(n: int, m: int, mb: int) -> tuple:
     """(2^floor(log2 n), m, m_p): problems of one class share a configuration."""
     return (1 << (max(int(n), 1).bit_length() - 1), int(m), int(mb))
@@ -51,6 +62,7 @@ class BatchTuner:
         self.device_name = device_name
         self.cache: dict = {}
         self.trials: dict = {}  # key -> {(prec, nstreams): best seconds}, for inspection
+        self.rejected: dict = {}  # key -> [(prec, nstreams)] whose sampled problems reported a failure
         if cache_file and os.path.exists(cache_file):
             with open(cache_file) as f:
                 self.cache = json.load(f)
@@ -72,19 +84,29 @@ class BatchTuner:
         for prec in variants:
             for ns in self.streams:
                 try:
-                    run(probe, prec, ns)  # warm-up: sketch plans, kernel attributes, workspaces
+                    out = run(probe, prec, ns)  # warm-up: sketch plans, kernel attributes, workspaces
                 except RuntimeError:
                     # a variant the problems cannot take (the tensor-core
                     # variants need leading dimensions that are multiples of 4)
                     continue
+                if _failed(out):
+                    # a breakdown or a timeout on a sampled problem: a variant
+                    # that stops early would otherwise time fastest
+                    self.rejected.setdefault(key, []).append((prec, ns))
+                    continue
                 best = float("inf")
+                ok = True
                 for _ in range(self.reps):
                     t0 = self.timer()
-                    run(probe, prec, ns)
+                    out = run(probe, prec, ns)
                     best = min(best, self.timer() - t0)
+                    ok = ok and not _failed(out)
+                if not ok:
+                    self.rejected.setdefault(key, []).append((prec, ns))
+                    continue
                 results[(prec, ns)] = best
         if not results:
-            raise RuntimeError("no candidate configuration runs on these problems")
+            raise RuntimeError("no candidate configuration runs on these problems without a breakdown")
         prec, ns = min(results, key=lambda c: (results[c], self.variants.index(c[0]) if c[0] in self.variants else 0,
                                                c[1]))
         self.trials[key] = results

@@ -202,6 +202,10 @@ template <class TS>
 rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,
                     const int* active, cudaStream_t st);
 
+// Forgets the no-allocation entry point's looked-up scratch address on device
+// dev (noalloc.cu); the next call there looks it up again.
+void noalloc_forget_device(int dev);
+
 // Frobenius norms for step 6.
 rbgs_status fro_identity_defect(int64_t m, const double* G, int64_t ldg, double* out, cudaStream_t st);
 rbgs_status fro_norm_diff(int64_t rows, int64_t cols, const double* A, int64_t lda, const double* B, int64_t ldb,

@@ -11,7 +11,9 @@
 // Scratch: one file-scope __device__ array of kNoallocBytes (about 4.03 MiB),
 // present on every device that loads this library until the process exits.
 // It holds
-//   [0, 256)    int error flag of the tensor-core kernel (cleared by every call);
+//   [0, 256)    int error flag of the tensor-core kernel (cleared by every call;
+//               read back only with sync != 0, so with sync == 0 a timeout of
+//               the bounded device waits is not reported);
 //   [256, ...)  the FP32 copy of G (FP32 path) or its TF32 hi/lo split in the
 //               tensor-core operand layout (TF32X3 path); every entry that a
 //               kernel reads, padding included, is rewritten by each call.
@@ -73,6 +75,17 @@ __global__ void noalloc_g_to_f32(int64_t K, int64_t mb, const double* __restrict
 }
 
 }  // namespace
+
+namespace rbgs {
+// Forgets the looked-up address of the scratch array on device dev, so that
+// the next call looks it up again.  rbgs_release_workspace calls this: after
+// cudaDeviceReset the old context's address is stale.
+void noalloc_forget_device(int dev) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  g_noalloc_ptr[dev] = nullptr;
+}
+}  // namespace rbgs
 
 using namespace rbgs;
 

@@ -1660,6 +1660,7 @@ rbgs_status rbgs_release_workspace(void) {
   }
   host_path_release();
   srht_plans_release();
+  noalloc_forget_device(dev);
   return RBGS_OK;
 }
 

@@ -107,3 +107,35 @@ def test_refused_variants_are_skipped():
     with pytest.raises(RuntimeError):
         at.rbgs_qr_batched_auto(Ws, 4, 32, 0, tuner=at.BatchTuner(streams=(4,), timer=clock), batched=fake_all,
                                 sync=lambda: None)
+
+
+def test_variant_with_failing_statuses_is_rejected_even_when_fastest():
+    """rbgs_qr_batched reports breakdowns (4) and timeouts (6) as per-problem
+    statuses instead of raising.  A variant that breaks down stops early and
+    would time fastest; the tuner must not cache it."""
+    clock = FakeClock()
+    calls = []
+    cost = {"f16x3": 0.1, "tf32x3": 1.0, "fp32": 2.0}
+
+    def fake(Ws, mbs, ks, seeds, sketch, prec, ls_iters, reorth, fine, interblock, nstreams):
+        calls.append((len(Ws), prec, nstreams))
+        clock.t += cost[prec]
+        st = [4 if prec == "f16x3" and i == 1 else 0 for i in range(len(Ws))]
+        return ([None] * len(Ws), [None] * len(Ws), st, [0] * len(Ws))
+
+    tuner = at.BatchTuner(streams=(1,), sample=3, reps=2, timer=clock)
+    Ws = [np.zeros((5000, 64), dtype=np.float32) for _ in range(4)]
+    _, _, st, _, cfg = at.rbgs_qr_batched_auto(Ws, 16, 128, 0, tuner=tuner, batched=fake, sync=lambda: None)
+    assert cfg == [("tf32x3", 1)] * 4 and st == [0] * 4
+    key = next(iter(tuner.cache))
+    assert ("f16x3", 1) in tuner.rejected[key] and ("f16x3", 1) not in tuner.trials[key]
+    # a timeout on every candidate leaves nothing to choose from
+    fake_to = make_fake(clock, lambda p, ns, c: 1.0, [])
+
+    def timing_out(*a, **kw):
+        q, r, s, p2 = fake_to(*a, **kw)
+        return q, r, [6] * len(s), p2
+
+    with pytest.raises(RuntimeError):
+        at.rbgs_qr_batched_auto(Ws, 16, 128, 0, tuner=at.BatchTuner(streams=(1,), timer=clock), batched=timing_out,
+                                sync=lambda: None)
