@@ -15,6 +15,13 @@ sketch-space steps (least squares, block Cholesky QR, R) run in FP64
 (--fine 0 runs them in FP32; the line reports the other choice as a variant).  Step 2 takes one Richardson iteration per pass; every block
 after the first takes a second projection pass (--reorth 1).
 
+`value` is GFLOP/s of the method's own work per factorization (the cost model
+of Sec. 3: step 3's products, the triangular solve and the sketches of W and
+Q); the Richardson products and the second pass are reported apart under
+`reorth_overhead`.  `roofline` is the dominant kernel (the tall update)
+against the measured HBM copy bandwidth; `step_roofline` is the whole step's
+minimum HBM bytes at that bandwidth over the measured step time.
+
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
 """
@@ -47,25 +54,52 @@ TALL_KERNEL = {"f16x3": "tall_h3_kernel", "tf32x3": "tall_tc_kernel"}
 TALL_SOURCE = {"f16x3": "tall_h3.cu", "tf32x3": "tall_tc.cu"}
 
 
-def algorithmic_flops(n, m, mb, k, sketch, ls_iters, reorth_blocks):
-    """Work the method must do: step 3 + the triangular solve (n m^2 over all
-    blocks), the sketches of W and Q (SRHT: n' log2 n' additions per column;
-    dense: 2 k n per column), and the sketch-space least squares
-    (Richardson: 2 l k m (m - m_p)); a second pass on a block repeats its
-    projection, sketch and least squares."""
-    p = m // mb
+def sketch_flops_per_col(n, k, sketch):
+    """SRHT: n' log2 n' additions per column (n' = 2^ceil(log2 n)); a dense
+    Gaussian or Rademacher sketch: 2 k n per column."""
     npad = 1 << max(0, math.ceil(math.log2(n)))
-    per_col_sketch = npad * math.log2(npad) if sketch == "srht" else 2.0 * k * n
-    tall = float(n) * m * m
-    sk = 2.0 * m * per_col_sketch
-    ls = 2.0 * ls_iters * k * m * (m - mb)
-    f = tall + sk + ls
+    return npad * math.log2(npad) if sketch == "srht" else 2.0 * k * n
+
+
+def algorithmic_flops(n, m, mb, k, sketch):
+    """Work the method must do in one factorization (the cost model of the
+    discussion after Alg. 2, Sec. 3): step 3's tall products,
+    sum_i 2 n (i-1) m_p m_p = n m (m - m_p), the triangular solve with R_ii,
+    n m m_p, and the sketches of W and Q (step 1 and step 5), 2 m columns.
+    The sketch-space steps (least squares and block QR, O(k m^2)) are not
+    counted, nor anything a second pass repeats."""
+    return float(n) * m * (m - mb) + float(n) * m * mb + 2.0 * m * sketch_flops_per_col(n, k, sketch)
+
+
+def overhead_flops(n, m, mb, k, sketch, ls_iters, reorth_blocks):
+    """Work done beyond the method's count: the Richardson products of step 2
+    (2 l k m (m - m_p)), and for each block that takes the second projection
+    pass (an extension for the orthogonality targets) its projection,
+    triangular update, sketch and least squares once more."""
+    psk = sketch_flops_per_col(n, k, sketch)
+    f = 2.0 * ls_iters * k * m * (m - mb)
     if reorth_blocks:
-        # block i (c = (i-1) mb) costs 2 n c mb + n mb^2 in the tall product
-        c_avg = (m - mb) / 2.0 + mb / 2.0
-        f += reorth_blocks * (2.0 * n * c_avg * mb + n * mb * mb + mb * per_col_sketch
-                              + 4.0 * ls_iters * k * c_avg * mb)
+        c_avg = (m - mb) / 2.0 + mb / 2.0  # mean c over the blocks that take it
+        f += reorth_blocks * (2.0 * n * c_avg * mb + n * mb * mb + mb * psk + 4.0 * ls_iters * k * c_avg * mb)
     return f
+
+
+def algorithmic_bytes(n, m, mb, elem):
+    """Minimum HBM traffic of one factorization: step 3 reads the basis
+    Q_{1:i-1} for every block (elem n m_p p (p - 1) / 2 bytes), and W is read
+    and Q written once (2 n m elem)."""
+    p = m // mb
+    return elem * (float(n) * mb * p * (p - 1) / 2.0 + 2.0 * n * m)
+
+
+def two_pass_bytes(n, m, mb, elem, reorth_blocks):
+    """The same with the second projection pass on reorth_blocks blocks: each
+    reads the basis and its own block again and writes it (the tall kernel's
+    bytes, 4 n (c + 2 m_p) per launch in FP32)."""
+    p = m // mb
+    c_avg = (m - mb) / 2.0 + mb / 2.0
+    return algorithmic_bytes(n, m, mb, elem) + reorth_blocks * elem * float(n) * (c_avg + 2 * mb) * (
+        1.0 if p > 1 else 0.0)
 
 
 class ClockSampler:
@@ -238,7 +272,7 @@ def cpu_baseline(cfg, ls_iters, reorth):
     out = oracle.rbgs(W, cfg["mb"], cfg["sketch"], cfg["k"], cfg["seed_theta"], variant=5, ls="richardson",
                       ls_iters=ls_iters, reorth=bool(reorth), ls_iters_first=1)
     dt = time.perf_counter() - t0
-    flops = algorithmic_flops(ns, ms, cfg["mb"], cfg["k"], cfg["sketch"], ls_iters, out["passes2"])
+    flops = algorithmic_flops(ns, ms, cfg["mb"], cfg["k"], cfg["sketch"])
     del W
     return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle RBGS (Alg. 2, Alg. 5, Richardson l={ls_iters}, reorth={int(bool(reorth))}) on "
@@ -324,8 +358,9 @@ def run_ours(args, cfg):
     launches = rb.launch_count() - l0
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    flops = algorithmic_flops(n, m, mb, k, cfg["sketch"], args.ls_iters, passes2)
+    flops = algorithmic_flops(n, m, mb, k, cfg["sketch"])
     ms_all, value = aggregate_over_ranks(ms, flops, world, dev)
+    extra = overhead_flops(n, m, mb, k, cfg["sketch"], args.ls_iters, passes2)
 
     # ---- roofline of the dominant kernel (tall update), from its own CUDA events
     peaks = {}
@@ -345,6 +380,19 @@ def run_ours(args, cfg):
                 "kernel": TALL_KERNEL.get(prec, "tall_simt_kernel"),
                 "peak_source": peak_src, "launch_ms_avg": tall_ms / max(tall_launches, 1),
                 "bytes_per_launch_avg": tall_bytes / max(tall_launches, 1)}
+
+    # ---- the whole step against the HBM roofline: the minimum bytes of one
+    # factorization (the basis read once per block, W read and Q written once)
+    # at the measured copy bandwidth, over the measured step time; and the
+    # same with the second pass's bytes
+    elem = 8 if prec == "fp64" else 4
+    b1 = algorithmic_bytes(n, m, mb, elem)
+    b2 = two_pass_bytes(n, m, mb, elem, passes2)
+    step_roofline = {"bound": "hbm", "bytes_single_pass": b1, "bytes_two_pass": b2, "peak_gbs": peak,
+                     "roofline_ms_single_pass": b1 / (peak * 1e9) * 1e3,
+                     "roofline_ms_two_pass": b2 / (peak * 1e9) * 1e3, "ms_per_step": ms_all,
+                     "frac": b1 / (peak * 1e9) * 1e3 / ms_all, "frac_two_pass": b2 / (peak * 1e9) * 1e3 / ms_all,
+                     "peak_source": peak_src}
 
     # ---- end to end: the host-buffer entry point (rbgs_qr_host) on pinned host
     # W, Q, R; its copies of W up and of Q, R down are inside the timed region
@@ -391,8 +439,13 @@ def run_ours(args, cfg):
                        "reorth_tol": args.reorth_tol, "passes2": passes2,
                        "l2": "inputs larger than L2 (W and Q are GBs; no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
-            "algorithmic_gflop_per_step": flops / 1e9}
+            "roofline": roofline, "step_roofline": step_roofline, "clocks": clocks, "gpu_launches": launches,
+            "e2e": e2e, "algorithmic_gflop_per_step": flops / 1e9,
+            "reorth_overhead": {"gflop_per_step": extra / 1e9, "passes2": passes2,
+                                "value_counting_it": world * (flops + extra) / (ms_all * 1e-3) / 1e9,
+                                "note": "step-2 Richardson products, and the second projection pass (projection, "
+                                        "triangular update, sketch, least squares) on passes2 blocks: work done to "
+                                        "meet the orthogonality target, not counted in value"}}
 
     if rank == 0 and not args.no_quality:
         line["quality"] = quality(rb, W if args.no_e2e else _refill(W, cfg, dev, dtype), Q, R, cfg)
@@ -442,8 +495,8 @@ def sketch_space_variant(rb, W, Q, R, cfg, args, prec, fine, flops_ref):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     out = {"ms_per_step": ms, "steps": steps, "sketch_space": "fp64" if fine else "fp32",
-           "value": algorithmic_flops(cfg["n"], cfg["m"], cfg["mb"], cfg["k"], cfg["sketch"], args.ls_iters,
-                                      st.passes2) / (ms * 1e-3) / 1e9, "unit": "GFLOP/s"}
+           "value": algorithmic_flops(cfg["n"], cfg["m"], cfg["mb"], cfg["k"], cfg["sketch"]) / (ms * 1e-3) / 1e9,
+           "unit": "GFLOP/s", "passes2": st.passes2}
     if not args.no_quality:
         out["quality"] = quality(rb, W, Q, R, cfg)
     return out
@@ -570,7 +623,7 @@ def fp64_compare(rb, cfg, args, dev):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
-    flops = algorithmic_flops(n, m, mb, k, cfg["sketch"], args.ls_iters, st.passes2)
+    flops = algorithmic_flops(n, m, mb, k, cfg["sketch"])
     q = quality(rb, W64, Q64, R64, cfg) if not args.no_quality else None
     del W64, Q64, R64
     torch.cuda.empty_cache()
