@@ -297,6 +297,126 @@ def unet_backward(params: dict, cache: dict, gy):
     return g, gx
 
 
+# ------------------------------------------------- the L-level U-Net --
+# The same network with L levels of widths c_0 .. c_{L-1} (level l at 1/2^l of
+# the resolution; N divisible by 2^(L-1)):
+#   encoder, l = 0 .. L-1:  a = relu(conv_enc{l}a(x_l)), s_l = relu(conv_enc{l}b(a)),
+#                           x_0 = the input (1 channel), x_{l+1} = avgpool2(s_l)
+#   decoder, l = L-2 .. 0:  d_l = relu(conv_dec{l}([upsample2(d_{l+1}); s_l])),
+#                           d_{L-1} = s_{L-1}
+#   output:                 y = conv_out(d_0)  (c_0 -> 1, linear)
+# With L = 2 and widths (c, 2c) it is the two-level network above
+# (enc0a = e1, enc0b = e2, enc1a = m1, enc1b = m2, dec0 = o1, out = o2).
+# bf16=True rounds every convolution's operands (its input activations or
+# gradients, and its weights) to bfloat16 after rounding them to FP32, the
+# points where a network that stores activations in bfloat16 and computes in
+# FP32 rounds; the sums stay in FP64.
+
+
+def unet_layers(widths) -> list:
+    """[(name, C_in, C_out, relu)] of the L-level network, in evaluation order."""
+    L = len(widths)
+    out = []
+    for l in range(L):
+        out.append((f"enc{l}a", 1 if l == 0 else widths[l - 1], widths[l], True))
+        out.append((f"enc{l}b", widths[l], widths[l], True))
+    for l in range(L - 2, -1, -1):
+        out.append((f"dec{l}", widths[l + 1] + widths[l], widths[l], True))
+    out.append(("out", widths[0], 1, False))
+    return out
+
+
+def round_bf16(x) -> np.ndarray:
+    """x rounded to FP32, then to bfloat16 (round to nearest, ties to even),
+    returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(f.shape)
+
+
+def _conv_fwd(x, w, b, bf16):
+    if bf16:
+        return conv3x3(round_bf16(x), round_bf16(w), b)
+    return conv3x3(x, w, b)
+
+
+def _conv_bwd(x, w, gz, bf16):
+    """conv3x3_backward with the operands of the two backward products
+    rounded as the forward ones: x and gz for the weights, w and gz for x."""
+    if bf16:
+        gx, gw, _ = conv3x3_backward(round_bf16(x), round_bf16(w), round_bf16(gz))
+        return gx, gw, gz.sum(axis=(1, 2))
+    return conv3x3_backward(x, w, gz)
+
+
+def unet_forward_levels(params: dict, x, widths, bf16: bool = False):
+    """y = U-Net(x) of the L-level network, x (1, N, N); returns (y, cache)."""
+    L = len(widths)
+    P = params
+    cache = {"x": x}
+    skips = []
+    h = x
+    for l in range(L):
+        if l > 0:
+            h = avgpool2(skips[-1])
+            cache[f"pool{l}"] = h
+        cache[f"in_enc{l}a"] = h
+        z = _conv_fwd(h, P[f"enc{l}a.w"], P[f"enc{l}a.b"], bf16)
+        a = np.maximum(z, 0.0)
+        if bf16:
+            a = round_bf16(a)
+        cache[f"z_enc{l}a"], cache[f"in_enc{l}b"] = z, a
+        z = _conv_fwd(a, P[f"enc{l}b.w"], P[f"enc{l}b.b"], bf16)
+        s_l = np.maximum(z, 0.0)
+        if bf16:
+            s_l = round_bf16(s_l)
+        cache[f"z_enc{l}b"] = z
+        skips.append(s_l)
+    d = skips[L - 1]
+    for l in range(L - 2, -1, -1):
+        cat = np.concatenate([upsample2(d), skips[l]], axis=0)
+        cache[f"in_dec{l}"] = cat
+        z = _conv_fwd(cat, P[f"dec{l}.w"], P[f"dec{l}.b"], bf16)
+        d = np.maximum(z, 0.0)
+        if bf16:
+            d = round_bf16(d)
+        cache[f"z_dec{l}"] = z
+    cache["in_out"] = d
+    y = _conv_fwd(d, P["out.w"], P["out.b"], bf16)
+    return y, cache
+
+
+def unet_backward_levels(params: dict, cache: dict, gy, widths, bf16: bool = False):
+    """Gradients of sum(gy * y) of the L-level network with respect to every
+    parameter and to x."""
+    L = len(widths)
+    P, C = params, cache
+    g = {}
+    gd, g["out.w"], g["out.b"] = _conv_bwd(C["in_out"], P["out.w"], gy, bf16)
+    gskip = [None] * L
+    for l in range(0, L - 1):
+        gz = gd * (C[f"z_dec{l}"] > 0)
+        gcat, g[f"dec{l}.w"], g[f"dec{l}.b"] = _conv_bwd(C[f"in_dec{l}"], P[f"dec{l}.w"], gz, bf16)
+        cu = widths[l + 1]
+        gskip[l] = gcat[cu:].copy()
+        gd = upsample2_backward(gcat[:cu])
+    gs = gd  # gradient of s_{L-1}
+    gx = None
+    for l in range(L - 1, -1, -1):
+        if l < L - 1:
+            gs = gskip[l] + gs_from_pool
+        gz = gs * (C[f"z_enc{l}b"] > 0)
+        ga, g[f"enc{l}b.w"], g[f"enc{l}b.b"] = _conv_bwd(C[f"in_enc{l}b"], P[f"enc{l}b.w"], gz, bf16)
+        gz = ga * (C[f"z_enc{l}a"] > 0)
+        gh, g[f"enc{l}a.w"], g[f"enc{l}a.b"] = _conv_bwd(C[f"in_enc{l}a"], P[f"enc{l}a.w"], gz, bf16)
+        if l > 0:
+            gs_from_pool = avgpool2_backward(gh)
+        else:
+            gx = gh
+    return g, gx
+
+
 def precondition(params: dict, R) -> np.ndarray:
     """Z = M(R), column by column: s = ||r|| / sqrt(n) (zero columns give zero),
     z = s (h^2 / 8) vec(U-Net(r / s as an N x N image)), an approximation of

@@ -23,7 +23,21 @@ prescribed structure.  Recipes:
   the spectral method on a periodic grid of twice the size (so the wrap-around
   does not correlate opposite sides) from numpy's PCG64 with the given seed.
 * ``unet_params``: He-normal initial weights and zero biases of the small
-  U-Net preconditioner (3 x 3 kernels; the layer widths c, c, 2c, 2c, c, 1).
+  U-Net preconditioner (3 x 3 kernels; the layer widths c, c, 2c, 2c, c, 1);
+  ``unet_params_levels`` the same for the L-level network of widths
+  c_0 .. c_{L-1}.
+
+* ``hadamard_svd_matrix`` / ``hadamard_svd_matrix_torch``: the full-size
+  mixed-precision workload, W = 2^-s (Omega diag(sigma) H_L)[:, :m] with
+  Omega (n x L) random signs, sigma L FP32 values log-spaced from 1 to
+  1/cond, H_L the Sylvester-Hadamard matrix of order L = 2^ceil(log2 m) and
+  2^-s a power of two that brings the largest singular value near 1.  Omega
+  / sqrt(n) is orthonormal up to sqrt(L/n) and H_L / sqrt(L) is orthogonal,
+  so this is the U diag(sigma) V^T recipe with cond(W) about cond.  Every
+  partial sum of the product is an integer multiple of the smallest sigma's
+  ulp below 2^53, so the FP64 product is exact in any summation order: the
+  CPU and the device build the same W bit for bit, and the oracle can be
+  run on exactly the matrix the device factors.
 
 CPU draws use numpy's PCG64; device draws (large sizes) use torch's generator
 on the given device, so the two do not produce the same numbers: a test that
@@ -158,4 +172,104 @@ def unet_params(c: int, seed: int) -> dict:
         out[name + ".w"] = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (9 * ci))
         out[name + ".b"] = np.zeros(co)
     return out
+
+
+def unet_params_levels(widths, seed: int) -> dict:
+    """Initial weights of the L-level U-Net (layer list of
+    oracle.learned.unet_layers, written out here): w (C_out, C_in, 3, 3) He
+    normal, std sqrt(2 / (9 C_in)), b zero."""
+    L = len(widths)
+    shapes = []
+    for l in range(L):
+        shapes.append((f"enc{l}a", widths[l], 1 if l == 0 else widths[l - 1]))
+        shapes.append((f"enc{l}b", widths[l], widths[l]))
+    for l in range(L - 2, -1, -1):
+        shapes.append((f"dec{l}", widths[l], widths[l + 1] + widths[l]))
+    shapes.append(("out", 1, widths[0]))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for name, co, ci in shapes:
+        out[name + ".w"] = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (9 * ci))
+        out[name + ".b"] = np.zeros(co)
+    return out
+
+
+def _hadamard_cols(L: int, m: int) -> np.ndarray:
+    """The first m columns of the unnormalised Sylvester-Hadamard matrix of
+    order L (entries (-1)^popcount(l & j))."""
+    l = np.arange(L)[:, None]
+    j = np.arange(m)[None, :]
+    v = l & j
+    par = np.zeros_like(v)
+    while np.any(v):
+        par ^= v & 1
+        v >>= 1
+    return 1.0 - 2.0 * par
+
+
+def _hadamard_plan(n: int, m: int, cond: float):
+    L = 1 << max(0, (m - 1).bit_length())
+    sig = np.logspace(0.0, -np.log10(cond), L).astype(np.float32).astype(np.float64)
+    # exactness: all sigma are multiples of the smallest one's FP32 ulp, and
+    # sum(sigma) / ulp must stay below 2^53 (then every partial sum is exact)
+    ulp = 2.0 ** (np.floor(np.log2(sig.min())) - 23)
+    assert sig.sum() / ulp < 2.0 ** 53, "the product would not be exact in FP64"
+    s = int(np.ceil(np.log2(np.sqrt(float(n) * L))))
+    return L, sig, 2.0 ** (-s)
+
+
+def _sign_words(n: int, L: int, seed: int) -> np.ndarray:
+    """n L sign bits from numpy's Philox generator (platform independent),
+    64 per word: bit (i L + l) gives Omega[i, l] = -1 where set."""
+    bg = np.random.Philox(seed)
+    return bg.random_raw((n * L + 63) // 64).astype(np.uint64)
+
+
+def _signs_rows(words: np.ndarray, r0: int, r1: int, L: int) -> np.ndarray:
+    """Omega[r0:r1] as a float64 array of +-1 (L a multiple of 64 or the rows
+    packed contiguously)."""
+    b0, b1 = r0 * L, r1 * L
+    w0, w1 = b0 // 64, (b1 + 63) // 64
+    bits = np.unpackbits(words[w0:w1].view(np.uint8), bitorder="little")[b0 - 64 * w0: b1 - 64 * w0]
+    return 1.0 - 2.0 * bits.reshape(r1 - r0, L).astype(np.float64)
+
+
+def hadamard_svd_matrix(n: int, m: int, cond: float, seed: int, chunk: int = 65536) -> np.ndarray:
+    """n x m FP32 matrix (Fortran order) of the exact recipe, on the CPU."""
+    L, sig, scale = _hadamard_plan(n, m, cond)
+    Hs = _hadamard_cols(L, m) * (sig * scale)[:, None]  # diag(sigma) H 2^-s: exact (powers of two, +-1)
+    words = _sign_words(n, L, seed)
+    W = np.empty((n, m), dtype=np.float32, order="F")
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        W[r0:r1] = (_signs_rows(words, r0, r1, L) @ Hs).astype(np.float32)
+    return W
+
+
+def hadamard_svd_matrix_torch(n: int, m: int, cond: float, seed: int, device="cuda", dtype=None,
+                              chunk: int = 131072):
+    """The same matrix built on ``device`` (the signs are unpacked on the CPU,
+    the exact FP64 product runs on the device); column-major (n x m) with a
+    leading dimension of n.  dtype float32 (default) or float64 (the FP32
+    values widened)."""
+    import torch
+
+    dtype = dtype or torch.float32
+    L, sig, scale = _hadamard_plan(n, m, cond)
+    Hs = torch.from_numpy(_hadamard_cols(L, m) * (sig * scale)[:, None]).to(device)
+    words = _sign_words(n, L, seed)
+    Wt = torch.empty((m, n), dtype=dtype, device=device)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        Om = torch.from_numpy(_signs_rows(words, r0, r1, L)).to(device)
+        Wt[:, r0:r1] = (Om @ Hs).to(torch.float32).to(dtype).t()
+        del Om
+    return Wt.t()
+
+
+def bit_checksum(W32) -> int:
+    """Sum of the FP32 bit patterns of W as signed 32-bit integers (an exact
+    fingerprint that the CPU and the device compute alike)."""
+    a = np.asarray(W32, dtype=np.float32)
+    return int(a.view(np.int32).astype(np.int64).sum())
 

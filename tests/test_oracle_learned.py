@@ -263,3 +263,125 @@ def test_trained_network_beats_plain_block_gmres_on_an_unseen_field():
     assert hist_net[-1] <= 1e-8
     assert cyc_net < cyc_plain and hist_plain[cyc_net] > 1e-8
     assert rec["fallbacks"] < cyc_net
+
+
+# ----------------------------------------------------- the L-level U-Net --
+
+
+def test_two_level_network_is_the_l_level_network_with_two_levels():
+    """unet_forward_levels with widths (c, 2c) is the two-level network of the
+    pins above, layer for layer (enc0a = e1, enc0b = e2, enc1a = m1,
+    enc1b = m2, dec0 = o1, out = o2), forward and backward."""
+    c, N = 3, 8
+    p2 = synth.unet_params(c, 5)
+    names = {"e1": "enc0a", "e2": "enc0b", "m1": "enc1a", "m2": "enc1b", "o1": "dec0", "o2": "out"}
+    pl = {names[k.split(".")[0]] + "." + k.split(".")[1]: v for k, v in p2.items()}
+    x = np.random.default_rng(1).standard_normal((1, N, N))
+    y2, c2 = L.unet_forward(p2, x)
+    yl, cl = L.unet_forward_levels(pl, x, (c, 2 * c))
+    np.testing.assert_allclose(yl, y2, rtol=1e-13, atol=1e-13)
+    gy = np.random.default_rng(2).standard_normal(y2.shape)
+    g2, gx2 = L.unet_backward(p2, c2, gy)
+    gl, gxl = L.unet_backward_levels(pl, cl, gy, (c, 2 * c))
+    np.testing.assert_allclose(gxl, gx2, rtol=1e-12, atol=1e-12)
+    for k, v in g2.items():
+        np.testing.assert_allclose(gl[names[k.split(".")[0]] + "." + k.split(".")[1]], v, rtol=1e-12, atol=1e-12)
+
+
+def test_layer_list_of_the_four_level_network():
+    """Widths (16, 32, 64, 64): twelve convolutions, concatenations of the
+    upsampled level and the skip, a linear single-channel output."""
+    lay = L.unet_layers((16, 32, 64, 64))
+    assert [x[0] for x in lay] == ["enc0a", "enc0b", "enc1a", "enc1b", "enc2a", "enc2b", "enc3a", "enc3b", "dec2",
+                                   "dec1", "dec0", "out"]
+    assert [(x[1], x[2]) for x in lay] == [(1, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (64, 64),
+                                           (64, 64), (128, 64), (96, 32), (48, 16), (16, 1)]
+    assert [x[3] for x in lay] == [True] * 11 + [False]
+    P = synth.unet_params_levels((16, 32, 64, 64), 3)
+    assert set(P) == {f"{n}.{t}" for n, _, _, _ in lay for t in "wb"}
+    for n, ci, co, _ in lay:
+        assert P[n + ".w"].shape == (co, ci, 3, 3) and P[n + ".b"].shape == (co,)
+
+
+def test_l_level_gradients_match_finite_differences():
+    """Four levels on a 16 x 16 image (levels 16, 8, 4, 2): the backward pass
+    equals central differences of sum(gy * y) for sampled weights, biases and
+    inputs."""
+    widths = (4, 6, 8, 8)
+    N = 16
+    P = synth.unet_params_levels(widths, 9)
+    rng = np.random.default_rng(4)
+    for k in P:
+        if k.endswith(".b"):
+            P[k] = 0.1 * rng.standard_normal(P[k].shape)
+    x = rng.standard_normal((1, N, N))
+    y, cache = L.unet_forward_levels(P, x, widths)
+    gy = rng.standard_normal(y.shape)
+    g, gx = L.unet_backward_levels(P, cache, gy, widths)
+
+    def f(PP, xx):
+        return float(np.sum(gy * L.unet_forward_levels(PP, xx, widths)[0]))
+
+    eps = 1e-5
+    for name in ("enc0a.w", "enc2b.w", "enc3a.b", "dec1.w", "dec0.b", "out.w"):
+        for _ in range(2):
+            idx = tuple(rng.integers(0, s) for s in P[name].shape)
+            Pp = {k: v.copy() for k, v in P.items()}
+            Pm = {k: v.copy() for k, v in P.items()}
+            Pp[name][idx] += eps
+            Pm[name][idx] -= eps
+            fd = (f(Pp, x) - f(Pm, x)) / (2 * eps)
+            assert abs(fd - g[name][idx]) <= 1e-5 * (abs(fd) + abs(g[name][idx])) + 1e-6, name
+    for _ in range(3):
+        idx = (0,) + tuple(rng.integers(0, N, size=2))
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += eps
+        xm[idx] -= eps
+        fd = (f(P, xp) - f(P, xm)) / (2 * eps)
+        assert abs(fd - gx[idx]) <= 1e-5 * (abs(fd) + 1e-3)
+
+
+def test_bf16_gradients_stay_within_their_rounding_of_the_fp64_gradients():
+    """With bf16 the backward products take rounded operands.  The gradients of
+    a randomly initialised ReLU network are sensitive: perturbing the weights
+    by 2^-9 relative noise alone moves some layers' gradients by 5-16%, and
+    the bf16 roundings move them by up to about 30%.  The check is that they
+    stay of that size (an error in a rounding point or a dropped term gives
+    O(1))."""
+    widths = (4, 6, 8, 8)
+    N = 16
+    P = synth.unet_params_levels(widths, 9)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((1, N, N))
+    gy = rng.standard_normal((1, N, N))
+    g64, gx64 = L.unet_backward_levels(P, L.unet_forward_levels(P, x, widths)[1], gy, widths)
+    g16, gx16 = L.unet_backward_levels(P, L.unet_forward_levels(P, x, widths, bf16=True)[1], gy, widths, bf16=True)
+    for k in g64:
+        rel = np.linalg.norm(g16[k] - g64[k]) / (np.linalg.norm(g64[k]) + 1e-30)
+        assert rel < 0.5, (k, rel)
+    assert 1e-4 < np.linalg.norm(gx16 - gx64) / np.linalg.norm(gx64) < 0.5
+
+
+def test_bfloat16_rounding_is_round_to_nearest_even():
+    """round_bf16 against torch's float32 -> bfloat16 conversion (round to
+    nearest, ties to even) on random values and on the ties themselves."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-6, 6, 10000),
+                        1.0 + np.array([2 ** -8, 3 * 2 ** -8, 2 ** -9, 3 * 2 ** -9, -2 ** -8])])
+    want = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(L.round_bf16(x), want)
+    assert L.round_bf16(1.0 + 2 ** -8) == 1.0 and L.round_bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6
+
+
+def test_bf16_network_stays_within_its_rounding_of_the_fp64_network():
+    """The bf16 forward differs from the FP64 one by the operand roundings:
+    a few 2^-8 relative, far above the FP64 level and far below O(1)."""
+    widths = (8, 16, 16)
+    N = 16
+    P = synth.unet_params_levels(widths, 2)
+    x = np.random.default_rng(6).standard_normal((1, N, N))
+    y64 = L.unet_forward_levels(P, x, widths)[0]
+    y16 = L.unet_forward_levels(P, x, widths, bf16=True)[0]
+    rel = np.linalg.norm(y16 - y64) / np.linalg.norm(y64)
+    assert 1e-4 < rel < 0.05
