@@ -7,7 +7,9 @@ resident in HBM, through the C ABI of librbgs.
 
 Default workload (mixed precision): n = 1,000,000 rows, m = 1000 columns,
 block size m_p = 50, SRHT sketch k = 2000, W in FP32 with singular values
-log-spaced from 1 to 1e-6 (W = U diag(sigma) V^T from seeded N(0,1) factors).
+log-spaced from 1 to 1e-6 (W = U diag(sigma) V^T with U random signs scaled by
+a power of two and V Sylvester-Hadamard, a product that is exact in FP64, so
+the CPU oracle can be given the very matrix the GPU factors).
 W and Q are stored in FP32; the tall products run on the tcgen05 tensor cores
 with FP16 hi/lo split operands (three products, about 2^-22 relative; the
 basis is kept pre-split in the workspace), the sketches in FP32; the
@@ -43,7 +45,9 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # name: (n, m, mb, sketch, k, cond, seed_W, seed_theta, description)
     "c2": dict(n=1_000_000, m=1000, mb=50, sketch="srht", k=2000, cond=1e6, seed_w=7, seed_theta=1,
-               desc="RBGS QR n=1e6 m=1000 mb=50 SRHT k=2000, W fp32 cond 1e6 (log-spaced sigma)"),
+               recipe="hadamard",
+               desc="RBGS QR n=1e6 m=1000 mb=50 SRHT k=2000, W fp32 cond 1e6 (log-spaced sigma; "
+                    "W = 2^-15 (signs x diag(sigma) x Hadamard), exact on CPU and GPU)"),
     "c1": dict(n=10_000, m=100, mb=10, sketch="gauss", k=200, cond=1e8, seed_w=7, seed_theta=1,
                desc="RBGS QR n=1e4 m=100 mb=10 Gaussian k=200, W fp64 cond 1e8"),
 }
@@ -185,7 +189,11 @@ def make_w(cfg, device, dtype):
     import torch
     import synth
 
-    W = synth.svd_matrix_torch(cfg["n"], cfg["m"], cfg["cond"], cfg["seed_w"], device=device, dtype=dtype)
+    if cfg.get("recipe") == "hadamard":
+        W = synth.hadamard_svd_matrix_torch(cfg["n"], cfg["m"], cfg["cond"], cfg["seed_w"], device=device,
+                                            dtype=dtype)
+    else:
+        W = synth.svd_matrix_torch(cfg["n"], cfg["m"], cfg["cond"], cfg["seed_w"], device=device, dtype=dtype)
     torch.cuda.synchronize()
     return W
 
@@ -253,7 +261,7 @@ def tall_traffic(prec, bytes_per_launch):
     return None
 
 
-def cpu_baseline(cfg, ls_iters, reorth):
+def cpu_baseline(cfg, ls_iters, reorth, one_core=False):
     """The CPU oracle (plain FP64 C, all host cores) on a bounded sample of the
     workload: a CPU_SAMPLE_ROWS x CPU_SAMPLE_COLS matrix of the same recipe
     (same m_p, k, sketch and conditioning), i.e. the first blocks of a
@@ -267,18 +275,51 @@ def cpu_baseline(cfg, ls_iters, reorth):
     oracle.set_threads(cores)
     ns = min(cfg["n"], CPU_SAMPLE_ROWS)
     ms = min(cfg["m"], CPU_SAMPLE_COLS)
-    W = synth.svd_matrix(ns, ms, cfg["cond"], cfg["seed_w"])
+    if cfg.get("recipe") == "hadamard":
+        W = synth.hadamard_svd_matrix(ns, ms, cfg["cond"], cfg["seed_w"]).astype(np.float64)
+    else:
+        W = synth.svd_matrix(ns, ms, cfg["cond"], cfg["seed_w"])
     t0 = time.perf_counter()
     out = oracle.rbgs(W, cfg["mb"], cfg["sketch"], cfg["k"], cfg["seed_theta"], variant=5, ls="richardson",
                       ls_iters=ls_iters, reorth=bool(reorth), ls_iters_first=1)
     dt = time.perf_counter() - t0
     flops = algorithmic_flops(ns, ms, cfg["mb"], cfg["k"], cfg["sketch"])
+    res = {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+           "sample": f"oracle RBGS (Alg. 2, Alg. 5, Richardson l={ls_iters}, reorth={int(bool(reorth))}) on "
+                     f"n={ns} rows x m={ms} (m_p={cfg['mb']}, {cfg['sketch']} k={cfg['k']}, same recipe), "
+                     f"{dt:.1f} s", "seconds": dt, "delta": float(out["delta"]), "cpu": cpu_model()}
+    if one_core:
+        # the same sample's first quarter of the rows on one thread
+        n1 = max(cfg["mb"], ns // 4)
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.rbgs(np.asfortranarray(W[:n1]), cfg["mb"], cfg["sketch"], min(cfg["k"], n1), cfg["seed_theta"],
+                    variant=5, ls="richardson", ls_iters=ls_iters, reorth=bool(reorth), ls_iters_first=1)
+        d1 = time.perf_counter() - t0
+        oracle.set_threads(cores)
+        res["one_core"] = {"value": algorithmic_flops(n1, ms, cfg["mb"], min(cfg["k"], n1), cfg["sketch"]) / d1 / 1e9,
+                           "unit": "GFLOP/s", "sample": f"n={n1} rows x m={ms}, 1 thread, {d1:.1f} s"}
     del W
-    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"oracle RBGS (Alg. 2, Alg. 5, Richardson l={ls_iters}, reorth={int(bool(reorth))}) on "
-                      f"n={ns} rows x m={ms} (m_p={cfg['mb']}, {cfg['sketch']} k={cfg['k']}, same recipe), "
-                      f"{dt:.1f} s", "seconds": dt, "delta": float(out["delta"]),
-            "_np": np.__version__}
+    return res
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo; on Arm the part is named by
+    the implementer and part fields, given as they are)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+    except OSError:
+        return "unknown"
+    for ln in txt.splitlines():
+        if ln.lower().startswith(("model name", "cpu model")):
+            return ln.split(":", 1)[1].strip()
+    impl = [ln.split(":", 1)[1].strip() for ln in txt.splitlines() if ln.startswith("CPU implementer")]
+    part = [ln.split(":", 1)[1].strip() for ln in txt.splitlines() if ln.startswith("CPU part")]
+    if impl and part:
+        name = " (Neoverse V2)" if impl[0].lower() == "0x41" and part[0].lower() == "0xd4f" else ""
+        return f"Arm implementer {impl[0]} part {part[0]}{name}"
+    return "unknown"
 
 
 def run_reference(args, cfg):
@@ -464,8 +505,8 @@ def run_ours(args, cfg):
         line["batched_c3"] = batched_c3(rb, dev, prec if prec != "fp64" else "f16x3")
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(cfg, args.ls_iters, args.reorth)
-        line["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+        cb = cpu_baseline(cfg, args.ls_iters, args.reorth, one_core=True)
+        line["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample", "cpu", "one_core")}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -502,64 +543,151 @@ def sketch_space_variant(rb, W, Q, R, cfg, args, prec, fine, flops_ref):
     return out
 
 
+def stencil_eigs_smallest(nx, ny, bx, by, count):
+    """The count smallest eigenvalues of the 5-point convection-diffusion
+    operator in closed form: with h = 1/(nx+1) (= 1/(ny+1)) and cell Peclet
+    numbers P = b h / 2 < 1, lambda_jl = (2/h^2) [2 - sqrt(1 - Px^2) cos(j pi h)
+    - sqrt(1 - Py^2) cos(l pi h)] (real: the operator is similar to a
+    symmetric one by a diagonal scaling)."""
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+    px, py = bx * hx / 2.0, by * hy / 2.0
+    jm = int(math.ceil(math.sqrt(count))) + 4
+    lam = []
+    for j in range(1, jm + 1):
+        for l in range(1, jm + 1):
+            lam.append(2.0 * (1.0 - math.sqrt(1 - px * px) * math.cos(j * math.pi * hx)) / hx ** 2 +
+                       2.0 * (1.0 - math.sqrt(1 - py * py) * math.cos(l * math.pi * hy)) / hy ** 2)
+    return sorted(lam)[:count]
+
+
+def eigvec_condition_log10(nx, ny, bx, by):
+    """log10 of the condition number of the diagonal scaling D that makes the
+    operator symmetric (D^-1 A D), ((1+P)/(1-P))^(n/2) per direction: a bound
+    for the eigenvector matrix's condition, i.e. how far rounding can move the
+    eigenvalues of this non-normal operator."""
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+    px, py = bx * hx / 2.0, by * hy / 2.0
+    return (nx / 2.0) * math.log10((1 + px) / (1 - px)) + (ny / 2.0) * math.log10((1 + py) / (1 - py))
+
+
+def ritz_smallest(rb, nx, ny, bx, by, mb, p, iters, prec, fine, dev, nev=20, tol=None):
+    """Alg. 8 with which = smallest real part on the stencil operator, restarted
+    one iteration at a time from the previous X (the restart block of step 4),
+    stopping after `iters` iterations or when every one of the nev smallest
+    values has a residual estimate below tol |mu|.  Returns the nev smallest
+    Ritz values with their estimates and their errors against the closed-form
+    spectrum."""
+    import torch
+
+    n = nx * ny
+    op = rb.stencil_op(nx, ny, bx, by)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    B = torch.randn((mb, n), generator=g, device=dev, dtype=torch.float64).t()
+    k = 4 * p * mb
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = 0
+    for it in range(iters):
+        vals, X, res = rb.rayleigh_ritz(op, B, p=p, n_iter=1, which="SR", sketch="srht", k=k, seed=1, prec=prec,
+                                        ls_iters=1, reorth=1, fine=fine)
+        B = X
+        done = it + 1
+        order = sorted(range(mb), key=lambda j: vals[j].real)[:nev]
+        if tol is not None and all(res[j] <= tol * abs(vals[j]) for j in order):
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    exact = stencil_eigs_smallest(nx, ny, bx, by, nev)
+    order = sorted(range(mb), key=lambda j: vals[j].real)[:nev]
+    got = [vals[j] for j in order]
+    rel = [abs(v - e) / abs(e) for v, e in zip(got, exact)]
+    return {"grid": [nx, ny], "b": [bx, by], "block": mb, "blocks_per_iteration": p, "k": k, "prec": prec,
+            "iterations": done, "s_per_iteration": dt / done,
+            "ritz_values": [[v.real, v.imag] for v in got], "exact": exact,
+            "rel_error": rel, "max_rel_error": max(rel),
+            "rel_resid_estimate": [res[j] / abs(vals[j]) for j in order],
+            "log10_eigvec_condition_bound": eigvec_condition_log10(nx, ny, bx, by)}
+
+
 def krylov_c4(rb, dev, prec):
     """Restarted randomized block GMRES (Sec. 5.2) on the 2-D convection-
     diffusion operator: 1024 x 1024 interior points, b = (100, 50), 8 right
-    sides N(0,1), 40 blocks per cycle, SRHT with k = 4 x 320.  Unpreconditioned
-    restarted GMRES converges slowly on this operator, so the line reports the
-    time per cycle and the residuals after a fixed number of cycles, for the
-    mixed basis and for the FP64 path (same cycles, same residual history)."""
+    sides N(0,1), 40 blocks per cycle, SRHT with k = 4 x 320.  The mixed basis
+    and the FP64 path run the same number of cycles, one call per cycle
+    (restarted from the previous X), so the line carries both residual
+    histories.  Unpreconditioned restarted GMRES converges slowly on this
+    operator: the line reports the time per cycle and the history.
+
+    Then Alg. 8 for the 20 smallest-real-part eigenvalues (block of 24, 10
+    blocks per iteration, restarted) on the same operator, with each Ritz
+    value's error against the closed-form spectrum; and the same on a 64 x 64
+    grid with b = (10, 5), where the eigenproblem is well conditioned enough
+    for the Ritz values to converge to the closed form."""
     import torch
 
     nx = ny = 1024
     n, mb, restart = nx * ny, 8, 40
     p, k = restart + 1, 4 * restart * mb
+    cycles = 5
     op = rb.stencil_op(nx, ny, 100.0, 50.0)
     g = torch.Generator(device=dev)
     g.manual_seed(3)
     B = torch.randn((mb, n), generator=g, device=dev, dtype=torch.float64).t()
     out = {"workload": "block GMRES(40 blocks), 5-point convection-diffusion 1024^2, b=(100,50), 8 RHS, SRHT k=1280",
            "n": n, "rhs": mb, "blocks_per_cycle": restart}
-    for label, pr, fine, cycles in (("mixed", prec, True, 5), ("fp64", "fp64", False, 1)):
+    for label, pr, fine in (("mixed", prec, True), ("fp64", "fp64", False)):
         rb.block_gmres(op, B, None, p=p, rtol=0.0, max_cycles=1, sketch="srht", k=k, seed=1, prec=pr, ls_iters=1,
                        reorth=1, fine=fine)  # warm-up cycle
         X = torch.zeros((mb, n), device=dev, dtype=torch.float64).t()
         torch.cuda.synchronize()
+        hist = []
         t0 = time.perf_counter()
-        X, cyc, rel = rb.block_gmres(op, B, X, p=p, rtol=0.0, max_cycles=cycles, sketch="srht", k=k, seed=1,
-                                     prec=pr, ls_iters=1, reorth=1, fine=fine)
+        for _ in range(cycles):
+            X, cyc, rel = rb.block_gmres(op, B, X, p=p, rtol=0.0, max_cycles=1, sketch="srht", k=k, seed=1,
+                                         prec=pr, ls_iters=1, reorth=1, fine=fine)
+            hist.append(max(rel))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        out[label] = {"prec": pr, "sketch_space": "fp64", "cycles": cyc, "s_per_cycle": dt / max(cyc, 1),
-                      "relres_max": max(rel)}
+        out[label] = {"prec": pr, "sketch_space": "fp64", "cycles": cycles, "s_per_cycle": dt / cycles,
+                      "relres_max_history": hist, "relres_max": hist[-1]}
     out["fp64_over_mixed_time_per_cycle"] = out["fp64"]["s_per_cycle"] / out["mixed"]["s_per_cycle"]
-    # Alg. 8 on the same operator: the 8 Ritz pairs of largest real part, restarted from B
-    rr = {"workload": "randomized Rayleigh-Ritz (Alg. 8), 8 vectors, 40 blocks per iteration, largest real part, "
-                      "same operator and sketch"}
-    for label, pr, fine, iters in (("mixed", prec, True, 3), ("fp64", "fp64", False, 1)):
-        rb.rayleigh_ritz(op, B, p=restart, n_iter=1, which="LR", sketch="srht", k=k, seed=1, prec=pr, ls_iters=1,
-                         reorth=1, fine=fine)  # warm-up iteration
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        vals, _, res = rb.rayleigh_ritz(op, B, p=restart, n_iter=iters, which="LR", sketch="srht", k=k, seed=1,
-                                        prec=pr, ls_iters=1, reorth=1, fine=fine)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        rr[label] = {"prec": pr, "iterations": iters, "s_per_iteration": dt / iters,
-                     "leading_ritz_value": [vals[0].real, vals[0].imag], "leading_resid_estimate": res[0]}
+    out["note"] = ("1e-8 is not reached without a preconditioner (the paper's GMRES experiment uses ILU(0)); "
+                   f"residual after {cycles} cycles of 40 blocks reported for both paths")
+    rr = {"workload": "randomized Rayleigh-Ritz (Alg. 8), 20 smallest-real-part values, block 24, 10 blocks per "
+                      "iteration, SRHT k = 4 x 240, restarted"}
+    rr["mixed"] = ritz_smallest(rb, 1024, 1024, 100.0, 50.0, 24, 11, 6, prec, True, dev)
+    rr["fp64"] = ritz_smallest(rb, 1024, 1024, 100.0, 50.0, 24, 11, 2, "fp64", False, dev)
     rr["fp64_over_mixed_time_per_iteration"] = rr["fp64"]["s_per_iteration"] / rr["mixed"]["s_per_iteration"]
+    rr["note"] = ("at 1024^2 the eigenvector matrix of this non-normal operator has condition up to "
+                  f"1e{rr['mixed']['log10_eigvec_condition_bound']:.0f}, and the 20 smallest eigenvalues are "
+                  "3.5e-6 of the spectral range apart, so restarted Ritz values approach them slowly")
+    rr["converged_64x64_b10_5"] = ritz_smallest(rb, 64, 64, 10.0, 5.0, 24, 11, 150, prec, True, dev, tol=1e-8)
     out["rayleigh_ritz"] = rr
     return out
 
 
-def batched_c3(rb, dev, prec, count=32):
+def batched_c3(rb, dev, prec, count=32, sample=8):
     """Many independent factorizations in one call (rbgs_qr_batched): the first
     `count` problems of the 256-problem workload (n ~ U[2e4, 2e5], m in
-    {64..256}, m_p in {16, 32}, Gaussian k = 2m, near-duplicate columns),
-    timed on 1 and on 8 internal streams, for the mixed path and the FP64
-    path.  Quality is sampled on two problems: ||W - QR|| / ||W|| and cond(Q).
-    The near-duplicates sit at the FP32 rounding level, outside the stability
-    hypothesis u_crs cond(W) < 1 for FP32 storage; the FP64 path keeps it."""
+    {64..256}, m_p in {16, 32}, Gaussian k = 2m, near-duplicate columns).
+
+    The near-duplicates are perturbed at the FP32 rounding level, so in FP32
+    storage W is numerically rank deficient (the regime of the paper's first
+    experiment).  With Alg. 5 the sketch of Q'_i is taken implicitly,
+    P_i - S R, and misses the rounding noise that FP32 storage leaves in the
+    computed Q'_i: R_ii^{-1} then amplifies that noise and Q loses its
+    conditioning.  Alg. 4 sketches the computed Q'_i explicitly, so R_ii
+    normalises what was stored and cond(Q) stays O(1) (Sec. 3.2; the paper's
+    experiments take the explicit variant).  The mixed path therefore runs
+    Alg. 4 (and Alg. 5 is shown beside it); the FP64 path runs Alg. 5.
+
+    Each configuration is timed on 8 internal streams (the mixed Alg. 4 also
+    on 1); quality on `sample` problems: ||W - QR|| / ||W||, cond(Q),
+    Delta = ||I - S^T S||_F and Delta~ = ||P - S R||_F / ||P||_F with S =
+    Theta Q and P = Theta W (step 6 of Alg. 2, Theta applied in FP64).
+    problems_per_s_at_quality counts the batch only when every sampled problem
+    has cond(Q) <= 10 and ||W - QR|| / ||W|| <= 1e-5."""
     import torch
     import synth
 
@@ -567,14 +695,16 @@ def batched_c3(rb, dev, prec, count=32):
     out = {"workload": f"{count} problems of the 256-problem batch: n~U[2e4,2e5], m in {{64..256}}, "
                        "m_p in {16,32}, Gaussian k=2m, every 8th column a 1e-7-perturbed duplicate",
            "problems": count}
-    for label, pr, dt in (("mixed", prec, torch.float32), ("fp64", "fp64", torch.float64)):
+    runs = (("mixed_alg4", prec, torch.float32, 4, (1, 8)), ("mixed_alg5", prec, torch.float32, 5, (8,)),
+            ("fp64", "fp64", torch.float64, 5, (8,)))
+    for label, pr, dt, ib, stream_counts in runs:
         Ws = [synth.near_duplicate_matrix_torch(n, m, 11 + i, device=dev, dtype=dt) for i, (n, m, _) in enumerate(specs)]
         mbs = [mp for _, _, mp in specs]
         ks = [2 * m for _, m, _ in specs]
         seeds = [7 + i for i in range(count)]
-        kw = dict(ls_iters=1, reorth=1, fine=pr != "fp64")
-        res = {"prec": pr}
-        for ns in (1, 8):
+        kw = dict(ls_iters=1, reorth=1, fine=pr != "fp64", interblock=ib)
+        res = {"prec": pr, "interblock": ib}
+        for ns in stream_counts:
             rb.rbgs_qr_batched(Ws[:2], mbs[:2], ks[:2], seeds[:2], "gauss", prec=pr, nstreams=ns, **kw)  # warm-up
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -584,12 +714,22 @@ def batched_c3(rb, dev, prec, count=32):
             res[f"streams_{ns}"] = {"s": dts, "problems_per_s": count / dts,
                                     "statuses_ok": sum(1 for x in status if x == 0)}
         qual = []
-        for i in range(2):
-            Q = Qs[i].double()
-            fe = float(torch.linalg.norm(Ws[i].double() - Q @ Rs[i]) / torch.linalg.norm(Ws[i].double()))
+        for i in range(min(sample, count)):
+            Q, W = Qs[i].double(), Ws[i].double()
+            fe = float(torch.linalg.norm(W - Q @ Rs[i]) / torch.linalg.norm(W))
             sv = torch.linalg.svdvals(Q)
-            qual.append({"rel_factorization_error": fe, "cond_Q": float(sv[0] / sv[-1])})
+            S = rb.sketch_apply(rb.colmajor(Q), "gauss", ks[i], seeds[i], prec="fp64")
+            P = rb.sketch_apply(rb.colmajor(W), "gauss", ks[i], seeds[i], prec="fp64")
+            m = Q.shape[1]
+            delta = float(torch.linalg.norm(torch.eye(m, device=dev, dtype=torch.float64) - S.t() @ S))
+            delta_t = float(torch.linalg.norm(P - S @ Rs[i]) / torch.linalg.norm(P))
+            qual.append({"n": W.shape[0], "m": m, "mb": mbs[i], "rel_factorization_error": fe,
+                         "cond_Q": float(sv[0] / sv[-1]), "delta": delta, "delta_tilde": delta_t,
+                         "certified": delta <= 0.1 and delta_t <= 0.1})
         res["quality_sample"] = qual
+        ok = all(q["cond_Q"] <= 10.0 and q["rel_factorization_error"] <= 1e-5 for q in qual)
+        res["quality_holds"] = ok
+        res["problems_per_s_at_quality"] = res["streams_8"]["problems_per_s"] if ok else None
         out[label] = res
         del Ws, Qs, Rs
         torch.cuda.empty_cache()
