@@ -110,6 +110,13 @@ typedef struct {
                           a blocked Householder QR of S kept in compact WY form, one
                           panel appended per block, X = R_S^{-1} (Q_S^T P)_{1:c}
                           (ls_iters unused; not for the Sec. 5 solvers)                 */
+  int32_t trsm;        /* with interblock 4: 1 = Q_i = Q'_i R_ii^{-1} by a row-wise triangular
+                          solve (forward substitution, backward stable whatever cond(R_ii))
+                          instead of the product with the explicit inverse (the remark
+                          after Alg. 4), whose error grows with cond(R_ii): needed when a
+                          block is numerically rank deficient in the storage precision
+                          (near-duplicate columns); 0 = the explicit inverse (default).
+                          RBGS_EINVAL with another interblock                            */
 } rbgs_opts;
 
 typedef struct {
@@ -234,8 +241,10 @@ RBGS_API rbgs_status rbgs_qr_graph_destroy(rbgs_graph* g);
 
 /* Y = Theta X (Sec. 2.3), the sketch of steps 1 and 5 of Alg. 2.
  *  X device n x ncols (ldx), double if prec == RBGS_P_FP64 else float.
- *  Y device k x ncols (ldy), double.  FP64 sums in double; other precisions
- *  sum in float.  stream: cudaStream_t.  Synchronous only if sync != 0.    */
+ *  Y device k x ncols (ldy), double.  The Gaussian, Rademacher and sparse
+ *  sketches sum in double for every prec; the SRHT sums in double for FP64
+ *  and in float otherwise.  stream: cudaStream_t.  Synchronous only if
+ *  sync != 0.                                                              */
 RBGS_API rbgs_status rbgs_sketch_apply(rbgs_sketch sketch, int64_t k, int64_t n, uint64_t seed, int32_t prec, const void* X,
                               int64_t ldx, int64_t ncols, double* Y, int64_t ldy, void* stream, int32_t sync);
 
@@ -278,18 +287,39 @@ RBGS_API rbgs_status rbgs_tall_update_noalloc(int32_t prec, int64_t n, int64_t c
 /* ------------------------------------------------------------------------
  * Randomized block Krylov methods (Sec. 5).
  *
- * Operator: the 5-point convection-diffusion operator
- *   A u = -(u_xx + u_yy) + bx u_x + by u_y
- * on nx x ny interior points of the unit square (spacing 1/(nx+1) and
- * 1/(ny+1)), zero Dirichlet boundary, central differences.  Point (x, y) is
- * row x + nx y, so n = nx ny.                                              */
-typedef enum { RBGS_OP_STENCIL5 = 0 } rbgs_op_kind;
+ * Operators on nx x ny interior points of the unit square (spacing
+ * hx = 1/(nx+1), hy = 1/(ny+1)), zero Dirichlet boundary; point (x, y) is row
+ * x + nx y, so n = nx ny.
+ *  RBGS_OP_STENCIL5   the 5-point convection-diffusion operator
+ *                     A u = -(u_xx + u_yy) + bx u_x + by u_y, central differences.
+ *  RBGS_OP_DIFFUSION  -div(a grad u) by the cell-centred five-point scheme:
+ *                     (A u)_P = sum over the four faces f of P of
+ *                     a_f (u_P - u_neighbour) / h^2 (h = hx across x faces,
+ *                     hy across y faces), with face coefficients coef
+ *                     (device, double): first the x faces, (nx+1) x (ny+2)
+ *                     values, face (i, j) between nodes (i, j) and (i+1, j) at
+ *                     i + (nx+1) j; then the y faces, (nx+2) x (ny+1) values,
+ *                     face (i, j) between (i, j) and (i, j+1) at i + (nx+2) j
+ *                     (nodes 0-based over the (nx+2) x (ny+2) grid with the
+ *                     boundary; interior node (i, j) is point (i-1, j-1)).
+ *                     rbgs_diffusion_faces fills coef with the harmonic means
+ *                     of node values of a.  bx, by are unused.  Not in the
+ *                     paper: the problem class of the learned preconditioner. */
+typedef enum { RBGS_OP_STENCIL5 = 0, RBGS_OP_DIFFUSION = 1 } rbgs_op_kind;
 typedef struct {
   int32_t kind;      /* rbgs_op_kind                                                   */
   int32_t reserved;
   int64_t nx, ny;    /* interior points                                                */
-  double bx, by;     /* convection velocity                                            */
+  double bx, by;     /* convection velocity (RBGS_OP_STENCIL5)                        */
+  const double* coef; /* face coefficients (RBGS_OP_DIFFUSION; device, caller-owned)  */
 } rbgs_op;
+
+/* coef (layout of RBGS_OP_DIFFUSION) = harmonic means 2 a_P a_Q / (a_P + a_Q)
+ * of the node values a (device, (nx+2) x (ny+2), node (i, j) at
+ * i + (nx+2) j, all > 0) of the two nodes of each face.  RBGS_EINVAL on a
+ * null pointer or nx, ny < 1.                                               */
+RBGS_API rbgs_status rbgs_diffusion_faces(int64_t nx, int64_t ny, const double* a, double* coef, void* stream,
+                                          int32_t sync);
 
 /* Y = A X for ncols columns (device, column-major).  X and Y are double if
  * prec == RBGS_P_FP64, else float.  X and Y must not overlap.               */
@@ -349,6 +379,107 @@ RBGS_API rbgs_status rbgs_rayleigh_ritz(const rbgs_op* op, const double* B0, int
                                         int64_t n_iter, int32_t which, rbgs_sketch sketch, int64_t k, uint64_t seed,
                                         const rbgs_opts* opts, double* X, int64_t ldx, double* ritz_re,
                                         double* ritz_im, double* resid_est);
+
+/* ------------------------------------------------------------------------
+ * The learned right preconditioner (not in the paper, which preconditions
+ * its block GMRES with ILU(0)): a U-Net M on the residual columns of a
+ * diffusion problem on an N x N grid (n = N^2), used inside randomized block
+ * flexible GMRES (the flexible variant of Saad 1993 on the paper's Alg. 7 and
+ * Sec. 5.2), trained by the entry points below.
+ *
+ * Network with L = levels (2..6) levels of width[l] channels (multiples of 8,
+ * 8..64); level l works at N / 2^l (N divisible by 2^(L-1)):
+ *   encoder l = 0..L-1:  a_l = relu(conv(x_l)),  s_l = relu(conv(a_l)),
+ *                        x_0 = the input image, x_{l+1} = avgpool2(s_l)
+ *   decoder l = L-2..0:  d_l = relu(conv([upsample2(d_{l+1}); s_l])),  d_{L-1} = s_{L-1}
+ *   output:              y = conv(d_0)  (width[0] -> 1 channel, linear)
+ * 3 x 3 convolutions with zero padding (cross-correlation), 2 x 2 average
+ * pooling, nearest-neighbour upsampling.  Activations are stored in
+ * bfloat16; every convolution multiplies bfloat16 operands (its input and
+ * weights) with FP32 accumulation; y, gradients and parameters are FP32.
+ * Parameters: one FP32 device vector of rbgs_unet_num_params() values, layer
+ * after layer in evaluation order (enc0a, enc0b, enc1a, enc1b, ...,
+ * dec{L-2}, ..., dec0, out), each as w[tap][ci][co] then b[co], tap = 3 ox +
+ * oy with ox, oy in {0, 1, 2} the offset + 1 along the image's fast (x) and
+ * slow (y) index.  Images: image b of a batch is column b of an n x batch
+ * column-major FP32 array with leading dimension n (pixel (x, y) at x + N y).
+ * The library keeps the activations of the last forward call with save != 0
+ * (for rbgs_unet_backward) and its other buffers in cached device workspace
+ * (freed by rbgs_release_workspace).                                        */
+typedef struct {
+  int32_t levels;
+  int32_t width[6];
+} rbgs_unet;
+
+/* Number of parameters of the network, or -1 if its shape is invalid.      */
+RBGS_API int64_t rbgs_unet_num_params(const rbgs_unet* net);
+
+/* y = U-Net(x) for batch images of N x N (x, y device FP32, n x batch with
+ * leading dimension n).  save != 0 keeps the activations for the next
+ * rbgs_unet_backward call.  RBGS_EINVAL on an invalid shape or pointer.     */
+RBGS_API rbgs_status rbgs_unet_forward(const rbgs_unet* net, const float* params, int64_t N, int64_t batch,
+                                       const float* x, float* y, int32_t save, void* stream, int32_t sync);
+
+/* grads (device FP32, the parameter layout, overwritten) = d sum(gy * y) /
+ * d params for the last forward call made with save != 0 on this device,
+ * which must have had the same network, N, batch and x (x is read again).
+ * RBGS_EINVAL if no such forward was saved.                                */
+RBGS_API rbgs_status rbgs_unet_backward(const rbgs_unet* net, const float* params, int64_t N, int64_t batch,
+                                        const float* x, const float* gy, float* grads, void* stream, int32_t sync);
+
+/* The training loss of a batch of (x, y) with x the scaled residual image and
+ * y = U-Net(x): L = 1/2 mean over images and pixels of (B_f y - x)^2 with
+ * B_f = A_f h^2 / 8, A_f the RBGS_OP_DIFFUSION operator of image b's field
+ * f = field[b] (face coefficients at coef + f coef_stride, device double;
+ * nx = ny = N, h = 1/(N+1)), so that U-Net(x) learns B_f^{-1} x measured in
+ * the residual norm.  *loss (device double) receives L and gy (device FP32,
+ * n x batch, ld n) its gradient dL/dy = B_f (B_f y - x) / (n batch) (B_f is
+ * symmetric).  field: device int32, batch values.                          */
+RBGS_API rbgs_status rbgs_unet_residual_loss(int64_t N, int64_t batch, const double* coef, int64_t coef_stride,
+                                             const int32_t* field, const float* x, const float* y, float* gy,
+                                             double* loss, void* stream, int32_t sync);
+
+/* One Adam update (Kingma and Ba 2015) of count FP32 parameters in place:
+ * m and v (device FP32, zero before the first step) are the moment
+ * estimates, t >= 1 the step number for the bias correction.               */
+RBGS_API rbgs_status rbgs_adam_step(int64_t count, float* params, const float* grads, float* m, float* v, int64_t t,
+                                    double lr, double beta1, double beta2, double eps, void* stream, int32_t sync);
+
+/* The network's input scaling: X (device FP32, n x ncols, ldx) = the columns
+ * of Q (prec type, ldq) scaled to unit root mean square, x = q / s with
+ * s = ||q|| / sqrt(n) (zero columns stay zero): the images the preconditioner
+ * feeds the network, for making training inputs from Krylov basis vectors. */
+RBGS_API rbgs_status rbgs_unet_scale_inputs(int64_t n, int64_t ncols, int32_t prec, const void* Q, int64_t ldq,
+                                            float* X, int64_t ldx, void* stream, int32_t sync);
+
+/* The preconditioner applied to ncols (<= 64) columns: Z = M(Q) with, per
+ * column, s = ||q|| / sqrt(n) and z = s (h^2 / 8) U-Net(q / s) (zero where
+ * q = 0), h = 1/(N+1); positively homogeneous, M(alpha q) = alpha M(q).
+ * Q, Z: device arrays of the prec type (double for RBGS_P_FP64, float
+ * otherwise), n x ncols with leading dimensions ldq, ldz >= n.            */
+RBGS_API rbgs_status rbgs_unet_precondition(const rbgs_unet* net, const float* params, int64_t N, int32_t prec,
+                                            const void* Q, int64_t ldq, int64_t ncols, void* Z, int64_t ldz,
+                                            void* stream, int32_t sync);
+
+/* Restarted randomized block flexible GMRES for A X = B with the U-Net as a
+ * right preconditioner that may differ from cycle to cycle (Saad 1993 on the
+ * paper's Alg. 7 and Sec. 5.2): each cycle runs the RBGS Arnoldi process on
+ * r = B - A X with W_1 = r and W_{j+1} = A Z_j, Z_j = M(Q_j), so that
+ * A Z_{1:p-1} = Q H with H = R(:, mb:); z = argmin || H z - R(:, 0:mb) ||
+ * (the sketched residual), X += Z z.  Plain block GMRES is the fallback and
+ * the true residual decides: a cycle run with M is kept only when it brings
+ * max_j ||r_j|| / ||b_j|| to at most accept (0 < accept <= 1) times its value
+ * before the cycle; otherwise the cycle is repeated from the same X with
+ * M = I (net == NULL runs plain block GMRES throughout).  op must be
+ * RBGS_OP_DIFFUSION (or RBGS_OP_STENCIL5) with nx = ny = N.  *fallbacks
+ * (host, may be NULL) receives the number of cycles that fell back.  Other
+ * arguments, stopping and errors as rbgs_block_gmres; the workspace holds Z
+ * (n x (p-1) mb in the basis type) besides the basis.  Synchronous.       */
+RBGS_API rbgs_status rbgs_block_fgmres(const rbgs_op* op, const rbgs_unet* net, const float* params,
+                                       const double* B, int64_t ldb, double* X, int64_t ldx, int64_t mb, int64_t p,
+                                       double rtol, int64_t max_cycles, double accept, rbgs_sketch sketch, int64_t k,
+                                       uint64_t seed, const rbgs_opts* opts, int64_t* cycles, double* relres,
+                                       int64_t* fallbacks);
 
 /* Philox4x32-10 blocks on the device: out[4i..4i+3] = philox(ctr[4i..4i+3],
  * key = (seed_lo, seed_hi)) for i < count (device pointers).              */

@@ -417,6 +417,30 @@ def unet_backward_levels(params: dict, cache: dict, gy, widths, bf16: bool = Fal
     return g, gx
 
 
+def precondition_levels(params: dict, R, widths, bf16: bool = False) -> np.ndarray:
+    """precondition() with the L-level network: z = s (h^2 / 8) U-Net(r / s)
+    per column, s = ||r|| / sqrt(n) (zero columns give zero).  With bf16 the
+    scaled input r / s is rounded to FP32 first, as a network with FP32 inputs
+    receives it."""
+    R = np.asarray(R, dtype=np.float64)
+    one = R.ndim == 1
+    R = R.reshape(R.shape[0], -1)
+    n = R.shape[0]
+    N = int(round(np.sqrt(n)))
+    hh8 = (1.0 / (N + 1)) ** 2 / 8.0
+    Z = np.zeros_like(R)
+    for j in range(R.shape[1]):
+        s = np.linalg.norm(R[:, j]) / np.sqrt(n)
+        if s == 0.0:
+            continue
+        x = (R[:, j] / s).reshape(1, N, N, order="F")
+        if bf16:
+            x = x.astype(np.float32).astype(np.float64)
+        y, _ = unet_forward_levels(params, x, widths, bf16=bf16)
+        Z[:, j] = s * hh8 * y[0].reshape(-1, order="F")
+    return Z[:, 0] if one else Z
+
+
 def precondition(params: dict, R) -> np.ndarray:
     """Z = M(R), column by column: s = ||r|| / sqrt(n) (zero columns give zero),
     z = s (h^2 / 8) vec(U-Net(r / s as an N x N image)), an approximation of

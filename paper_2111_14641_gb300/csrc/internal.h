@@ -202,6 +202,22 @@ template <class TS>
 rbgs_status sub_mat(int64_t k, int64_t mb, const TS* A, int64_t lda, const TS* B, int64_t ldb, TS* C, int64_t ldc,
                     const int* active, cudaStream_t st);
 
+// Q <- Q R^{-1} by a row-wise forward substitution (tall_simt.cu).
+template <class T, class TS>
+rbgs_status trsm_rows(int64_t n, int mb, T* Q, int64_t ldq, const TS* R, const int* active, cudaStream_t st);
+
+// Face coefficients of RBGS_OP_DIFFUSION from node values (krylov.cu).
+rbgs_status diffusion_faces(int64_t nx, int64_t ny, const double* a, double* fc, cudaStream_t st);
+
+// The U-Net preconditioner (unet.cu): Z (n x ncols, ldz) = M(Q) column by
+// column, M(q) = s (h^2 / 8) U-Net(q / s), s = ||q|| / sqrt(n), h = 1 / (N + 1).
+template <class T>
+rbgs_status unet_precondition(const rbgs_unet& net, const float* params, int N, int ncols, const T* Q, int64_t ldq,
+                              T* Z, int64_t ldz, cudaStream_t st);
+bool unet_valid(const rbgs_unet* net, int64_t N);
+// Frees the U-Net buffers of device dev (rbgs_release_workspace).
+void unet_release(int dev);
+
 // Forgets the no-allocation entry point's looked-up scratch address on device
 // dev (noalloc.cu); the next call there looks it up again.
 void noalloc_forget_device(int dev);

@@ -13,12 +13,31 @@
 namespace rbgs {
 namespace {
 
-// Y = A X: A = -Laplace + b . grad on nx x ny interior points of the unit
-// square (spacing 1/(nx+1), 1/(ny+1)), zero Dirichlet boundary, central
-// differences; point (x, y) is row x + nx y.  One thread per point and column.
+// (A x)_i at point i = (ix, iy) from its value c and its four neighbours
+// (zero outside).  fc == null: A = -Laplace + b . grad, central differences
+// (cx = 1/hx^2, cy = 1/hy^2, ax = bx / (2 hx), ay = by / (2 hy)).  fc != null:
+// -div(a grad) with the face coefficients of RBGS_OP_DIFFUSION: x faces
+// (nx+1) x (ny+2) then y faces (nx+2) x (ny+1); interior point (ix, iy) is
+// node (ix+1, iy+1), its east face is x face (ix+1, iy+1), its west face
+// (ix, iy+1), its north face y face (ix+1, iy+1), its south face (ix+1, iy).
+__device__ __forceinline__ double op_point(int64_t nx, int64_t ny, double cx, double cy, double ax, double ay,
+                                           const double* __restrict__ fc, int64_t ix, int64_t iy, double c, double w,
+                                           double e, double s, double no) {
+  if (!fc) return cx * (2.0 * c - w - e) + cy * (2.0 * c - s - no) + ax * (e - w) + ay * (no - s);
+  const double* fx = fc;
+  const double* fy = fc + (nx + 1) * (ny + 2);
+  const double ae = fx[(ix + 1) + (nx + 1) * (iy + 1)], aw = fx[ix + (nx + 1) * (iy + 1)];
+  const double an = fy[(ix + 1) + (nx + 2) * (iy + 1)], as = fy[(ix + 1) + (nx + 2) * iy];
+  return cx * (ae * (c - e) + aw * (c - w)) + cy * (an * (c - no) + as * (c - s));
+}
+
+// Y = A X on nx x ny interior points of the unit square (spacing 1/(nx+1),
+// 1/(ny+1)), zero Dirichlet boundary; point (x, y) is row x + nx y.  One
+// thread per point and column.
 template <class TI, class TO>
 __global__ void stencil5_kernel(int64_t nx, int64_t ny, double cx, double cy, double ax, double ay,
-                                const TI* __restrict__ X, int64_t ldx, TO* __restrict__ Y, int64_t ldy) {
+                                const double* __restrict__ fc, const TI* __restrict__ X, int64_t ldx,
+                                TO* __restrict__ Y, int64_t ldy) {
   const int64_t n = nx * ny;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -30,13 +49,35 @@ __global__ void stencil5_kernel(int64_t nx, int64_t ny, double cx, double cy, do
   const double e = ix + 1 < nx ? (double)x[i + 1] : 0.0;
   const double s = iy > 0 ? (double)x[i - nx] : 0.0;
   const double no = iy + 1 < ny ? (double)x[i + nx] : 0.0;
-  Y[i + col * ldy] = (TO)(cx * (2.0 * c - w - e) + cy * (2.0 * c - s - no) + ax * (e - w) + ay * (no - s));
+  Y[i + col * ldy] = (TO)op_point(nx, ny, cx, cy, ax, ay, fc, ix, iy, c, w, e, s, no);
+}
+
+// Face coefficients of -div(a grad) (layout of RBGS_OP_DIFFUSION): harmonic
+// means of the node values a ((nx+2) x (ny+2)).
+__global__ void diffusion_faces_kernel(int64_t nx, int64_t ny, const double* __restrict__ a,
+                                       double* __restrict__ fc) {
+  const int64_t nfx = (nx + 1) * (ny + 2), nfy = (nx + 2) * (ny + 1);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nfx + nfy) return;
+  double p, q;
+  if (t < nfx) {
+    const int64_t i = t % (nx + 1), j = t / (nx + 1);
+    p = a[i + (nx + 2) * j];
+    q = a[i + 1 + (nx + 2) * j];
+  } else {
+    const int64_t u = t - nfx;
+    const int64_t i = u % (nx + 2), j = u / (nx + 2);
+    p = a[i + (nx + 2) * j];
+    q = a[i + (nx + 2) * (j + 1)];
+  }
+  fc[t] = 2.0 * p * q / (p + q);
 }
 
 // r = B - A X (FP64), and the partial sums of ||r_j||^2 per block of rows.
 __global__ void residual_kernel(int64_t nx, int64_t ny, double cx, double cy, double ax, double ay,
-                                const double* __restrict__ B, int64_t ldb, const double* __restrict__ X, int64_t ldx,
-                                double* __restrict__ r, int64_t ldr, double* __restrict__ part) {
+                                const double* __restrict__ fc, const double* __restrict__ B, int64_t ldb,
+                                const double* __restrict__ X, int64_t ldx, double* __restrict__ r, int64_t ldr,
+                                double* __restrict__ part) {
   __shared__ double red[8];
   const int64_t n = nx * ny;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -50,7 +91,7 @@ __global__ void residual_kernel(int64_t nx, int64_t ny, double cx, double cy, do
     const double e = ix + 1 < nx ? x[i + 1] : 0.0;
     const double s = iy > 0 ? x[i - nx] : 0.0;
     const double no = iy + 1 < ny ? x[i + nx] : 0.0;
-    const double ax_i = cx * (2.0 * c - w - e) + cy * (2.0 * c - s - no) + ax * (e - w) + ay * (no - s);
+    const double ax_i = op_point(nx, ny, cx, cy, ax, ay, fc, ix, iy, c, w, e, s, no);
     v = B[i + col * ldb] - ax_i;
     r[i + col * ldr] = v;
   }
@@ -192,9 +233,12 @@ void stencil_coeffs(const rbgs_op& op, double& cx, double& cy, double& ax, doubl
   const double hx = 1.0 / (double)(op.nx + 1), hy = 1.0 / (double)(op.ny + 1);
   cx = 1.0 / (hx * hx);
   cy = 1.0 / (hy * hy);
-  ax = op.bx / (2.0 * hx);
-  ay = op.by / (2.0 * hy);
+  const bool diff = op.kind == RBGS_OP_DIFFUSION;
+  ax = diff ? 0.0 : op.bx / (2.0 * hx);
+  ay = diff ? 0.0 : op.by / (2.0 * hy);
 }
+
+const double* op_faces(const rbgs_op& op) { return op.kind == RBGS_OP_DIFFUSION ? op.coef : nullptr; }
 
 }  // namespace
 
@@ -206,7 +250,7 @@ rbgs_status stencil_apply_t(const rbgs_op& op, const TI* X, int64_t ldx, int64_t
   double cx, cy, ax, ay;
   stencil_coeffs(op, cx, cy, ax, ay);
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)ncols);
-  stencil5_kernel<TI, TO><<<grid, 256, 0, st>>>(op.nx, op.ny, cx, cy, ax, ay, X, ldx, Y, ldy);
+  stencil5_kernel<TI, TO><<<grid, 256, 0, st>>>(op.nx, op.ny, cx, cy, ax, ay, op_faces(op), X, ldx, Y, ldy);
   RBGS_LAUNCH_CHECK();
   return RBGS_OK;
 }
@@ -223,8 +267,8 @@ rbgs_status residual_t(const rbgs_op& op, const double* B, int64_t ldb, const do
   double cx, cy, ax, ay;
   stencil_coeffs(op, cx, cy, ax, ay);
   const unsigned nb = (unsigned)((n + 255) / 256);
-  residual_kernel<<<dim3(nb, (unsigned)ncols), 256, 0, st>>>(op.nx, op.ny, cx, cy, ax, ay, B, ldb, X, ldx, r, ldr,
-                                                              part);
+  residual_kernel<<<dim3(nb, (unsigned)ncols), 256, 0, st>>>(op.nx, op.ny, cx, cy, ax, ay, op_faces(op), B, ldb, X,
+                                                              ldx, r, ldr, part);
   RBGS_LAUNCH_CHECK();
   colnorm_finish_kernel<<<(unsigned)ncols, 32, 0, st>>>(ncols, (int)nb, part, norms);
   RBGS_LAUNCH_CHECK();
@@ -266,6 +310,13 @@ rbgs_status add_cols_t(int64_t n, int64_t ncols, const TD* D, int64_t ldd, doubl
 }
 template rbgs_status add_cols_t<float>(int64_t, int64_t, const float*, int64_t, double*, int64_t, cudaStream_t);
 template rbgs_status add_cols_t<double>(int64_t, int64_t, const double*, int64_t, double*, int64_t, cudaStream_t);
+
+rbgs_status diffusion_faces(int64_t nx, int64_t ny, const double* a, double* fc, cudaStream_t st) {
+  const int64_t tot = (nx + 1) * (ny + 2) + (nx + 2) * (ny + 1);
+  diffusion_faces_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(nx, ny, a, fc);
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
 
 rbgs_status banded_ls(int M, int N, int bw, double* H, int ldh, double* F, int ldf, int nrhs, double* Z, int ldz,
                       int* flag, cudaStream_t st) {

@@ -309,6 +309,13 @@ struct QrCtx {
   // q_done[i] is recorded once column block i of Q and of R is final
   const cudaEvent_t* w_ready = nullptr;
   const cudaEvent_t* q_done = nullptr;
+  // flexible Arnoldi (with op): block i > 1 is W_i = A Z_{i-1} with Z_{i-1} =
+  // flex(Q_{i-1}) written to zbuf + (i-2) mb ldz (elements of the basis type)
+  rbgs_status (*flex)(void* fctx, const void* Qprev, int64_t ldq, int mb, void* Z, int64_t ldz,
+                      cudaStream_t st) = nullptr;
+  void* flex_ctx = nullptr;
+  void* zbuf = nullptr;
+  int64_t ldz = 0;
 };
 
 // T: storage of W and Q; TS: storage/arithmetic of the sketch space.
@@ -634,6 +641,15 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       if (one_round) r = cholqr1<TS>(k, mb, Sp, sm, partf, brk, act, st, Rd, Rdinv);
       else r = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, act, st, Rd, Rdinv, need2, n2count);
       if (r) return r;
+      if (o.trsm) {  // Q_i = Q'_i R_ii^{-1} by forward substitution, row by row
+        if ((r = trsm_rows<T, TS>(n, mb, Qo, ldq, Rd, act, st))) return r;
+        if ((r = sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sout, k, skscr, sk_bytes, st, act))) return r;
+        if (mode == 2 && split_final) {  // the pre-split copy of Q_i: an identity pass
+          if ((r = make_g(0, nullptr, Ieye, Ieye, nullptr, act))) return r;
+          if ((r = tall(0, c, Qo, ldq, Qo, act, Sout, true))) return r;
+        }
+        return RBGS_OK;
+      }
       if ((r = make_g(0, nullptr, Rd, Rdinv, nullptr, act))) return r;
       if ((r = tall(0, c, Qo, ldq, Qo, act, Sp, split_final))) return r;
       return sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sout, k, skscr, sk_bytes, st, act);
@@ -724,7 +740,13 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       TS* Si = S + c * k;
       double* Rcol = R + c * ldr;
       if (op && blk > 0) {  // Alg. 7, step 2: W_i = A Q_{i-1}, then its sketch (step 1 of the block)
-        if ((s = stencil_apply_t<T, T>(*op, Qi - mbf * ldq, ldq, mb, Qi, ldq, st))) return s;
+        if (ctx && ctx->flex) {  // flexible: W_i = A M(Q_{i-1})
+          T* Zs = (T*)ctx->zbuf + (blk - 1) * mbf * ctx->ldz;
+          if ((s = ctx->flex(ctx->flex_ctx, Qi - mbf * ldq, ldq, mb, Zs, ctx->ldz, st))) return s;
+          if ((s = stencil_apply_t<T, T>(*op, Zs, ctx->ldz, mb, Qi, ldq, st))) return s;
+        } else if ((s = stencil_apply_t<T, T>(*op, Qi - mbf * ldq, ldq, mb, Qi, ldq, st))) {
+          return s;
+        }
         Wi = Qi;
         ldwi = ldq;
         if ((s = sketch_apply_t<T, TS>(sketch, k, n, seed, Wi, ldwi, mb, Pi, k, skscr, sk_bytes, st))) return s;
@@ -964,6 +986,7 @@ rbgs_status check_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t m
       o.interblock != 6)
     return RBGS_EINVAL;
   if ((o.interblock == 1 || o.interblock == 3) && o.reorth == 2) return RBGS_EINVAL;
+  if (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)) return RBGS_EINVAL;
   if (o.ls != 0 && o.ls != 1 && o.ls != 2) return RBGS_EINVAL;
   if (sketch == RBGS_SK_SRHT) {
     int64_t np = 1;
@@ -1660,6 +1683,7 @@ rbgs_status rbgs_release_workspace(void) {
   }
   host_path_release();
   srht_plans_release();
+  unet_release(dev);
   noalloc_forget_device(dev);
   return RBGS_OK;
 }
@@ -1671,9 +1695,11 @@ rbgs_status rbgs_release_workspace(void) {
 namespace {
 
 rbgs_status check_op(const rbgs_op* op) {
-  if (!op || op->kind != RBGS_OP_STENCIL5 || op->nx < 1 || op->ny < 1) return RBGS_EINVAL;
+  if (!op || (op->kind != RBGS_OP_STENCIL5 && op->kind != RBGS_OP_DIFFUSION) || op->nx < 1 || op->ny < 1)
+    return RBGS_EINVAL;
   if (op->nx * op->ny >= ((int64_t)1 << 31)) return RBGS_EINVAL;
-  if (!std::isfinite(op->bx) || !std::isfinite(op->by)) return RBGS_EINVAL;
+  if (op->kind == RBGS_OP_STENCIL5 && (!std::isfinite(op->bx) || !std::isfinite(op->by))) return RBGS_EINVAL;
+  if (op->kind == RBGS_OP_DIFFUSION && !op->coef) return RBGS_EINVAL;
   return RBGS_OK;
 }
 
@@ -1692,17 +1718,182 @@ rbgs_status check_sketch(rbgs_sketch sketch, int64_t n, int64_t k, int64_t m) {
 // Alg. 7 on (W = B, Q): dispatch by precision (the arguments are checked).
 rbgs_status arnoldi_run(const rbgs_op& op, const void* B, int64_t ldb, int64_t mb, int64_t p, rbgs_sketch sketch,
                         int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr, const rbgs_opts& o,
-                        rbgs_stats* stats) {
+                        rbgs_stats* stats, const QrCtx* ctx = nullptr) {
   const int64_t n = op.nx * op.ny, m = p * mb;
   if (o.prec == RBGS_P_FP64)
     return qr_impl<double, double>((const double*)B, n, m, ldb, (int)mb, sketch, k, seed, (double*)Q, ldq, R, ldr, o,
-                                   stats, 0, &op);
+                                   stats, 0, &op, ctx);
   const int mode = o.prec == RBGS_P_TF32X3 ? 1 : (o.prec == RBGS_P_F16X3 ? 2 : 0);
   if (o.fine)
     return qr_impl<float, double>((const float*)B, n, m, ldb, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o,
-                                  stats, mode, &op);
+                                  stats, mode, &op, ctx);
   return qr_impl<float, float>((const float*)B, n, m, ldb, (int)mb, sketch, k, seed, (float*)Q, ldq, R, ldr, o, stats,
-                               mode, &op);
+                               mode, &op, ctx);
+}
+
+// The U-Net preconditioner as the flexible Arnoldi's hook.
+struct FlexNet {
+  const rbgs_unet* net;
+  const float* params;
+  int N;
+  bool f64;
+};
+rbgs_status flex_unet(void* fctx, const void* Q, int64_t ldq, int mb, void* Z, int64_t ldz, cudaStream_t st) {
+  const FlexNet* f = (const FlexNet*)fctx;
+  if (f->f64)
+    return unet_precondition<double>(*f->net, f->params, f->N, mb, (const double*)Q, ldq, (double*)Z, ldz, st);
+  return unet_precondition<float>(*f->net, f->params, f->N, mb, (const float*)Q, ldq, (float*)Z, ldz, st);
+}
+
+// Restarted randomized block flexible GMRES with the U-Net preconditioner and
+// plain block GMRES as the fallback (rbgs_block_fgmres).
+rbgs_status fgmres_solve(const rbgs_op* op, const rbgs_unet* net, const float* params, const double* B, int64_t ldb,
+                         double* X, int64_t ldx, int64_t mb, int64_t p, double rtol, int64_t max_cycles,
+                         double accept, rbgs_sketch sketch, int64_t k, uint64_t seed, const rbgs_opts* opts,
+                         int64_t* cycles, double* relres, int64_t* fallbacks) {
+  rbgs_status s;
+  if ((s = check_op(op))) return s;
+  const int64_t n = op->nx * op->ny, m = p * mb, nk = m - mb;
+  if (!B || !X || !relres || mb < 1 || mb > 64 || p < 2 || ldb < n || ldx < n || max_cycles < 0 || !(rtol >= 0.0) ||
+      !(accept > 0.0 && accept <= 1.0))
+    return RBGS_EINVAL;
+  if (net && (!params || op->nx != op->ny || !unet_valid(net, op->nx))) return RBGS_EINVAL;
+  if ((s = check_sketch(sketch, n, k, m))) return s;
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1) ||
+      (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)))
+    return RBGS_EINVAL;
+  o.sync = 1;
+  o.timing = 0;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const bool f64 = o.prec == RBGS_P_FP64;
+  const size_t es = f64 ? 8 : 4;
+  const size_t part_elems = residual_part_elems(n, mb);
+  const size_t bytes_q = es * (size_t)n * (size_t)m, bytes_z = es * (size_t)n * (size_t)nk,
+               bytes_r = 8 * (size_t)n * (size_t)mb, bytes_d = es * (size_t)n * (size_t)mb;
+  const size_t small = 8 * ((size_t)m * m + (size_t)m * nk + (size_t)m * mb + (size_t)nk * mb + 2 * mb + part_elems) +
+                       4 * ((size_t)nk * mb) + 1024;
+  DevBuf buf;
+  if (cudaMalloc(&buf.p, bytes_q + bytes_z + 2 * bytes_r + bytes_d + small + 8192) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  char* w = (char*)buf.p;
+  auto take = [&](size_t b) {
+    char* r = w;
+    w += (b + 255) & ~(size_t)255;
+    return (void*)r;
+  };
+  void* Qb = take(bytes_q);
+  void* Zb = take(bytes_z);
+  double* r = (double*)take(bytes_r);
+  double* Xt = (double*)take(bytes_r);
+  void* D = take(bytes_d);
+  double* Rm = (double*)take(8 * (size_t)m * m);
+  double* Hb = (double*)take(8 * (size_t)m * nk);
+  double* Fb = (double*)take(8 * (size_t)m * mb);
+  double* Zc = (double*)take(8 * (size_t)nk * mb);
+  float* Zf = (float*)take(4 * (size_t)nk * mb);
+  double* norms = (double*)take(8 * (size_t)mb);
+  double* bnorm = (double*)take(8 * (size_t)mb);
+  double* part = (double*)take(8 * part_elems);
+  int* flag = (int*)take(256);
+  RBGS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  std::vector<double> hb((size_t)mb), hn((size_t)mb);
+  if ((s = colnorms_t(n, mb, B, ldb, part, bnorm, st))) return s;
+  RBGS_CUDA_TRY(cudaMemcpyAsync(hb.data(), bnorm, 8 * mb, cudaMemcpyDeviceToHost, st));
+  RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  for (auto& v : hb)
+    if (!(v > 0.0)) v = 1.0;
+  FlexNet fn{net, params, (int)op->nx, f64};
+  QrCtx fctx;
+  fctx.flex = flex_unet;
+  fctx.flex_ctx = &fn;
+  fctx.zbuf = Zb;
+  fctx.ldz = n;
+  // relative residuals of r (norms on the device) into rel[] and their maximum
+  auto rel_of = [&](std::vector<double>& rel, double& worst) -> rbgs_status {
+    RBGS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, 8 * mb, cudaMemcpyDeviceToHost, st));
+    RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+    worst = 0.0;
+    for (int64_t j = 0; j < mb; ++j) {
+      rel[(size_t)j] = hn[(size_t)j] / hb[(size_t)j];
+      worst = std::max(worst, rel[(size_t)j]);
+    }
+    return RBGS_OK;
+  };
+  // one cycle from r into Xt = X + (Z or Q) z; with_net selects the flexible basis
+  auto cycle = [&](bool with_net) -> rbgs_status {
+    rbgs_status e;
+    if (f64) e = cast_cols_t<double, double>(n, mb, r, n, (double*)Qb, n, st);
+    else e = cast_cols_t<double, float>(n, mb, r, n, (float*)Qb, n, st);
+    if (e) return e;
+    if ((e = arnoldi_run(*op, Qb, n, mb, p, sketch, k, seed, Qb, n, Rm, m, o, nullptr, with_net ? &fctx : nullptr)))
+      return e;
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(Hb, 8 * m, Rm + mb * m, 8 * m, 8 * m, nk, cudaMemcpyDeviceToDevice, st));
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(Fb, 8 * m, Rm, 8 * m, 8 * m, mb, cudaMemcpyDeviceToDevice, st));
+    if ((e = banded_ls((int)m, (int)nk, (int)mb, Hb, (int)m, Fb, (int)m, (int)mb, Zc, (int)nk, flag, st))) return e;
+    const void* Vb = with_net ? Zb : Qb;  // the correction lives in range(Z) (flexible) or range(Q)
+    const int64_t c = nk - mb;
+    if (f64) {
+      e = tall_update_simt<double>(n, c, mb, (const double*)Vb, n, (const double*)Vb + c * n, n, Zc, nk, (double*)D, n,
+                                   nullptr, st);
+    } else {
+      if ((e = cast_cols_t<double, float>(nk, mb, Zc, nk, Zf, nk, st))) return e;
+      e = tall_update_simt<float>(n, c, mb, (const float*)Vb, n, (const float*)Vb + c * n, n, Zf, nk, (float*)D, n,
+                                  nullptr, st);
+    }
+    if (e) return e;
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(Xt, 8 * n, X, 8 * ldx, 8 * n, mb, cudaMemcpyDeviceToDevice, st));
+    if (f64) e = add_cols_t<double>(n, mb, (const double*)D, n, Xt, n, st);
+    else e = add_cols_t<float>(n, mb, (const float*)D, n, Xt, n, st);
+    if (e) return e;
+    int hflag = 0;
+    RBGS_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+    return hflag ? RBGS_EBREAKDOWN : RBGS_OK;
+  };
+  std::vector<double> rel((size_t)mb), rel_t((size_t)mb);
+  int64_t cyc = 0, fb = 0;
+  double worst = 0.0;
+  if ((s = residual_t(*op, B, ldb, X, ldx, mb, r, n, part, norms, st))) return s;
+  if ((s = rel_of(rel, worst))) return s;
+  for (;;) {
+    if (!(worst > rtol) || cyc >= max_cycles) {
+      for (int64_t j = 0; j < mb; ++j) relres[j] = rel[(size_t)j];
+      if (cycles) *cycles = cyc;
+      if (fallbacks) *fallbacks = fb;
+      return worst <= rtol ? RBGS_OK : RBGS_ENOCONV;
+    }
+    bool plain = net == nullptr;
+    double worst_t = 0.0;
+    if (!plain) {
+      s = cycle(true);
+      if (s && s != RBGS_EBREAKDOWN) return s;
+      if (!s) {
+        if ((s = residual_t(*op, B, ldb, Xt, n, mb, r, n, part, norms, st))) return s;
+        if ((s = rel_of(rel_t, worst_t))) return s;
+      }
+      if (s == RBGS_EBREAKDOWN || !(worst_t <= accept * worst)) {  // fall back from the same X (r is recomputed)
+        plain = true;
+        ++fb;
+        RBGS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+        if ((s = residual_t(*op, B, ldb, X, ldx, mb, r, n, part, norms, st))) return s;
+      }
+    }
+    if (plain) {
+      if ((s = cycle(false))) return s;
+      if ((s = residual_t(*op, B, ldb, Xt, n, mb, r, n, part, norms, st))) return s;
+      if ((s = rel_of(rel_t, worst_t))) return s;
+    }
+    RBGS_CUDA_TRY(cudaMemcpy2DAsync(X, 8 * ldx, Xt, 8 * n, 8 * n, mb, cudaMemcpyDeviceToDevice, st));
+    rel = rel_t;
+    worst = worst_t;
+    ++cyc;
+  }
 }
 
 
@@ -1720,7 +1911,8 @@ rbgs_status krylov_solve(int method, const rbgs_op* op, const double* B, int64_t
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
-      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1))
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1) ||
+      (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)))
     return RBGS_EINVAL;
   o.sync = 1;  // one synchronisation per cycle (breakdown and convergence are read on the host)
   o.timing = 0;
@@ -1825,7 +2017,8 @@ rbgs_status rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int6
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
-      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1))
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1) ||
+      (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)))
     return RBGS_EINVAL;
   o.sync = 1;
   o.timing = 0;
@@ -1922,6 +2115,15 @@ rbgs_status rbgs_op_apply(const rbgs_op* op, int32_t prec, const void* X, int64_
   return RBGS_OK;
 }
 
+rbgs_status rbgs_diffusion_faces(int64_t nx, int64_t ny, const double* a, double* coef, void* stream, int32_t sync) {
+  if (!a || !coef || nx < 1 || ny < 1 || (nx + 2) * (ny + 2) >= ((int64_t)1 << 31)) return RBGS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  rbgs_status s = diffusion_faces(nx, ny, a, coef, st);
+  if (s) return s;
+  if (sync) RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  return RBGS_OK;
+}
+
 rbgs_status rbgs_block_arnoldi(const rbgs_op* op, const void* B, int64_t ldb, int64_t mb, int64_t p,
                                rbgs_sketch sketch, int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R,
                                int64_t ldr, const rbgs_opts* opts, rbgs_stats* stats) {
@@ -1934,7 +2136,8 @@ rbgs_status rbgs_block_arnoldi(const rbgs_op* op, const void* B, int64_t ldb, in
   if (!B || !Q || !R || mb < 1 || mb > 64 || p < 1 || ldb < n || ldq < n || ldr < m) return RBGS_EINVAL;
   if ((s = check_sketch(sketch, n, k, m))) return s;
   if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
-      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1))
+      (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1) ||
+      (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)))
     return RBGS_EINVAL;
   const size_t es = o.prec == RBGS_P_FP64 ? 8 : 4;
   if (o.prec >= RBGS_P_TF32X3 && (((uintptr_t)B & 15) || ((uintptr_t)Q & 15) || (ldb % 4) || (ldq % 4)))
@@ -1950,6 +2153,14 @@ rbgs_status rbgs_block_gmres(const rbgs_op* op, const double* B, int64_t ldb, do
                              int64_t p, double rtol, int64_t max_cycles, rbgs_sketch sketch, int64_t k,
                              uint64_t seed, const rbgs_opts* opts, int64_t* cycles, double* relres) {
   return krylov_solve(0, op, B, ldb, X, ldx, mb, p, rtol, max_cycles, sketch, k, seed, opts, cycles, relres);
+}
+
+rbgs_status rbgs_block_fgmres(const rbgs_op* op, const rbgs_unet* net, const float* params, const double* B,
+                              int64_t ldb, double* X, int64_t ldx, int64_t mb, int64_t p, double rtol,
+                              int64_t max_cycles, double accept, rbgs_sketch sketch, int64_t k, uint64_t seed,
+                              const rbgs_opts* opts, int64_t* cycles, double* relres, int64_t* fallbacks) {
+  return fgmres_solve(op, net, params, B, ldb, X, ldx, mb, p, rtol, max_cycles, accept, sketch, k, seed, opts, cycles,
+                      relres, fallbacks);
 }
 
 rbgs_status rbgs_block_fom(const rbgs_op* op, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t mb,

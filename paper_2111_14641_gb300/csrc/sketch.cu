@@ -18,6 +18,8 @@
 #include <unordered_set>
 #include <vector>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -893,8 +895,9 @@ size_t sketch_scratch_bytes(rbgs_sketch kind, int64_t k, int64_t n, int64_t ncol
     const int64_t L = std::min<int64_t>(B, k);
     return es * (size_t)(ncols * T * L);
   }
+  // the dense sketches accumulate in FP64 whenever the sketch space is FP64
   const int64_t c = std::min<int64_t>(ncols, kDenseCols);
-  return es * (size_t)(dense_nsplit(k, n) * c * k);
+  return 8 * (size_t)(dense_nsplit(k, n) * c * k);
 }
 
 template <class TX, class TY>
@@ -1012,7 +1015,13 @@ template <class TX, class TY>
 rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed, const TX* X, int64_t ldx,
                            int64_t ncols, TY* Y, int64_t ldy, void* scratch, size_t scratch_bytes, cudaStream_t st,
                            const int* active) {
-  using TC = TX;  // arithmetic follows the input precision
+  // The dense sketches (Gaussian, Rademacher, sparse sign) accumulate in the
+  // precision of the sketch space TY: FP32 data sketched into an FP64 sketch
+  // space are summed in FP64 (steps 1 and 5 at the fine precision, as the
+  // paper's precision split has them).  A block that is numerically rank
+  // deficient in FP32 needs this: its projected part is of the size of the
+  // FP32 rounding, and an FP32 sum would not resolve it.
+  using TC = typename std::conditional<sizeof(TY) == 8, double, TX>::type;
   if (ncols == 0 || k == 0) return RBGS_OK;
   if (kind == RBGS_SK_SRHT)
     return sketch_apply2_t<TX, TY>(kind, k, n, seed, X, ldx, ncols, Y, ldy, X, ldx, 0, Y, ldy, scratch,

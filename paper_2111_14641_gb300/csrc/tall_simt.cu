@@ -82,7 +82,56 @@ __global__ void __launch_bounds__(NT) tall_simt_kernel(int64_t n, int64_t c, int
   }
 }
 
+// Q (n x mb, ldq) <- Q R^{-1} row by row by forward substitution with the
+// upper-triangular R (mb x mb, ld mb, type TS): one thread per row, R in
+// shared memory (ld 64), the substitution in FP64 whatever the storage type T
+// (the result is rounded to T once).  Each row's solve is backward stable,
+// (q + dq) R = q' with |dq| <= u |q| |R| elementwise, whatever the condition
+// of R, unlike the product with an explicit inverse, whose error grows with
+// cond(R).  The FP64 arithmetic matters for FP32 storage: a substitution in
+// FP32 is backward stable in FP32 too, but its forward error u_32 cond(R) in
+// a numerically rank-deficient block leaves the block's columns dependent in
+// a way the second projection pass cannot undo.
+template <class T, class TS>
+__global__ void __launch_bounds__(128) trsm_rows_kernel(int64_t n, int mb, T* __restrict__ Q, int64_t ldq,
+                                                        const TS* __restrict__ R, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ double Rs[64 * 64];
+  for (int t = threadIdx.x; t < mb * mb; t += blockDim.x) Rs[(t % mb) + 64 * (t / mb)] = (double)R[t];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // in place, column sweep: x_j = v_j / r_jj, then v_l -= x_j r_jl for l > j
+  double v[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) v[j] = j < mb ? (double)Q[i + (int64_t)j * ldq] : 0.0;
+#pragma unroll
+  for (int j = 0; j < 64; ++j) {
+    if (j < mb) {
+      v[j] /= Rs[j + 64 * j];
+#pragma unroll
+      for (int l = j + 1; l < 64; ++l) v[l] -= v[j] * Rs[j + 64 * l];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 64; ++j)
+    if (j < mb) Q[i + (int64_t)j * ldq] = (T)v[j];
+}
+
 }  // namespace
+
+template <class T, class TS>
+rbgs_status trsm_rows(int64_t n, int mb, T* Q, int64_t ldq, const TS* R, const int* active, cudaStream_t st) {
+  if (mb < 1 || mb > 64) return RBGS_EINVAL;
+  if (n == 0) return RBGS_OK;
+  trsm_rows_kernel<T, TS><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, mb, Q, ldq, R, active);
+  RBGS_LAUNCH_CHECK();
+  return RBGS_OK;
+}
+template rbgs_status trsm_rows<double, double>(int64_t, int, double*, int64_t, const double*, const int*,
+                                               cudaStream_t);
+template rbgs_status trsm_rows<float, double>(int64_t, int, float*, int64_t, const double*, const int*, cudaStream_t);
+template rbgs_status trsm_rows<float, float>(int64_t, int, float*, int64_t, const float*, const int*, cudaStream_t);
 
 template <class T>
 rbgs_status tall_update_simt(int64_t n, int64_t c, int64_t mb, const T* A1, int64_t lda1, const T* A2, int64_t lda2,

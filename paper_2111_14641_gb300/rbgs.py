@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("ls_iters", ctypes.c_int32), ("reorth", ctypes.c_int32),
                 ("certify", ctypes.c_int32), ("reorth_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("sync", ctypes.c_int32), ("timing", ctypes.c_int32), ("fine", ctypes.c_int32),
-                ("interblock", ctypes.c_int32), ("ls", ctypes.c_int32)]
+                ("interblock", ctypes.c_int32), ("ls", ctypes.c_int32), ("trsm", ctypes.c_int32)]
 
 
 LS = {"richardson": 0, "cg": 1, "householder": 2}
@@ -51,13 +51,45 @@ class Problem(ctypes.Structure):
 
 
 class Op(ctypes.Structure):
-    """rbgs_op: the 5-point convection-diffusion operator on nx x ny interior points."""
+    """rbgs_op: the 5-point convection-diffusion operator (kind 0) or
+    -div(a grad) with face coefficients (kind 1) on nx x ny interior points."""
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nx", ctypes.c_int64),
-                ("ny", ctypes.c_int64), ("bx", ctypes.c_double), ("by", ctypes.c_double)]
+                ("ny", ctypes.c_int64), ("bx", ctypes.c_double), ("by", ctypes.c_double),
+                ("coef", ctypes.c_void_p)]
+
+
+class UNet(ctypes.Structure):
+    """rbgs_unet: the levels and per-level widths of the U-Net preconditioner."""
+    _fields_ = [("levels", ctypes.c_int32), ("width", ctypes.c_int32 * 6)]
+
+
+def unet_shape(widths) -> UNet:
+    w = (ctypes.c_int32 * 6)(*([int(x) for x in widths] + [0] * (6 - len(widths))))
+    return UNet(len(widths), w)
 
 
 def stencil_op(nx: int, ny: int, bx: float, by: float) -> Op:
-    return Op(0, 0, nx, ny, bx, by)
+    return Op(0, 0, nx, ny, bx, by, None)
+
+
+def diffusion_faces(a: torch.Tensor, stream=None) -> torch.Tensor:
+    """Face coefficients (harmonic means) of -div(a grad) from the node values
+    a, a float64 CUDA tensor of (nx+2) x (ny+2) nodes with node (i, j) at
+    i + (nx+2) j (a[j, i] of a row-major (ny+2, nx+2) tensor)."""
+    lib = load()
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise ValueError("a must be a contiguous float64 tensor")
+    ny, nx = a.shape[0] - 2, a.shape[1] - 2
+    fc = torch.empty((nx + 1) * (ny + 2) + (nx + 2) * (ny + 1), dtype=torch.float64, device=a.device)
+    _check(lib.rbgs_diffusion_faces(nx, ny, a.data_ptr(), fc.data_ptr(), _stream_ptr(stream), 1),
+           "rbgs_diffusion_faces")
+    return fc
+
+
+def diffusion_op(nx: int, ny: int, coef: torch.Tensor) -> Op:
+    """rbgs_op of -div(a grad u) with the face coefficients coef (kept alive
+    by the caller for as long as the operator is used)."""
+    return Op(1, 0, nx, ny, 0.0, 0.0, coef.data_ptr())
 
 
 class Stats(ctypes.Structure):
@@ -107,6 +139,20 @@ def load(build_if_missing: bool = False):
     lib.rbgs_philox.argtypes = [u64, vp, vp, i64, vp, i32]
     opp = ctypes.POINTER(Op)
     lib.rbgs_op_apply.argtypes = [opp, i32, vp, i64, i64, vp, i64, vp, i32]
+    lib.rbgs_diffusion_faces.argtypes = [i64, i64, vp, vp, vp, i32]
+    unp = ctypes.POINTER(UNet)
+    lib.rbgs_unet_num_params.argtypes = [unp]
+    lib.rbgs_unet_num_params.restype = i64
+    lib.rbgs_unet_forward.argtypes = [unp, vp, i64, i64, vp, vp, i32, vp, i32]
+    lib.rbgs_unet_backward.argtypes = [unp, vp, i64, i64, vp, vp, vp, vp, i32]
+    lib.rbgs_unet_residual_loss.argtypes = [i64, i64, vp, i64, vp, vp, vp, vp, vp, vp, i32]
+    lib.rbgs_adam_step.argtypes = [i64, vp, vp, vp, vp, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, vp, i32]
+    lib.rbgs_unet_precondition.argtypes = [unp, vp, i64, i32, vp, i64, i64, vp, i64, vp, i32]
+    lib.rbgs_unet_scale_inputs.argtypes = [i64, i64, i32, vp, i64, vp, i64, vp, i32]
+    lib.rbgs_block_fgmres.argtypes = [opp, unp, vp, vp, i64, vp, i64, i64, i64, ctypes.c_double, i64,
+                                      ctypes.c_double, ctypes.c_int, i64, u64, ctypes.POINTER(Opts),
+                                      ctypes.POINTER(ctypes.c_int64), vp, ctypes.POINTER(ctypes.c_int64)]
     lib.rbgs_block_arnoldi.argtypes = [opp, vp, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
                                        ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
     for fn in ("rbgs_block_gmres", "rbgs_block_fom"):
@@ -191,11 +237,14 @@ def _empty_cols(n: int, m: int, dtype, device) -> torch.Tensor:
 def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
             prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
             certify: bool = False, Q: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None,
-            sync: bool = True, timing: bool = False, fine: bool = False, interblock: int = 5, ls: str = "richardson"):
+            sync: bool = True, timing: bool = False, fine: bool = False, interblock: int = 5, ls: str = "richardson",
+            trsm: bool = False):
     """RBGS QR of W (n x m, column-major).  Returns (Q, R, QRStats | None).
     fine=True (FP32 / TF32X3 storage only) runs the sketch-space steps in FP64;
     interblock selects steps 4-5: 5 = Alg. 5 (implicit sketch), 4 = Alg. 4,
-    1 / 3 = column by column (RGS / Alg. 3), 6 = Alg. 6 (l2 QR, then Alg. 4)."""
+    1 / 3 = column by column (RGS / Alg. 3), 6 = Alg. 6 (l2 QR, then Alg. 4);
+    trsm=True (interblock 4) scales by R_ii^{-1} with a row-wise triangular
+    solve instead of the explicit inverse."""
     lib = load()
     prec = _prec_of(W, prec)
     n, m = W.shape
@@ -211,6 +260,7 @@ def rbgs_qr(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None
     o.fine = int(fine)
     o.interblock = int(interblock)
     o.ls = LS[ls]
+    o.trsm = int(bool(trsm))
     st = Stats()
     code = lib.rbgs_qr(W.data_ptr(), n, m, _ld(W, "W"), mb, SKETCH[sketch], k, seed, Q.data_ptr(), _ld(Q, "Q"),
                        R.data_ptr(), _ld(R, "R"), ctypes.byref(o), ctypes.byref(st) if sync else None)
@@ -320,7 +370,8 @@ def rbgs_qr_host(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None =
 
 def rbgs_qr_batched(Ws: list, mbs, ks, seeds, sketch: str = "gauss", prec: str | None = None, ls_iters: int = 2,
                     reorth: int = 0, reorth_tol: float = 1e-8, fine: bool = False, interblock: int = 5,
-                    nstreams: int = 8, Qs: list | None = None, Rs: list | None = None, stream=None):
+                    nstreams: int = 8, Qs: list | None = None, Rs: list | None = None, stream=None,
+                    trsm: bool = False):
     """Independent RBGS factorizations of the column-major matrices Ws (one
     mb, k and seed per problem, or one value for all) on nstreams internal
     streams.  Returns (Qs, Rs, statuses, passes2)."""
@@ -341,6 +392,7 @@ def rbgs_qr_batched(Ws: list, mbs, ks, seeds, sketch: str = "gauss", prec: str |
     lib.rbgs_opts_default(ctypes.byref(o))
     o.prec, o.ls_iters, o.reorth, o.reorth_tol = PREC[prec], ls_iters, reorth, reorth_tol
     o.fine, o.interblock, o.stream = int(fine), int(interblock), _stream_ptr(stream)
+    o.trsm = int(bool(trsm))
     code = lib.rbgs_qr_batched(probs, cnt, SKETCH[sketch], ctypes.byref(o), int(nstreams))
     if code not in (0, 4, 6):  # per-problem breakdowns and timeouts are reported in the statuses
         _check(code, "rbgs_qr_batched")
@@ -540,3 +592,119 @@ def launch_count() -> int:
 
 def version() -> str:
     return load().rbgs_version().decode()
+
+
+# ------------------------------------------------- the learned preconditioner --
+
+def _images(t: torch.Tensor, n: int, name: str):
+    """n x batch FP32 CUDA tensor with leading dimension n (image b = column b)."""
+    if t.dtype != torch.float32 or t.shape[0] != n or (t.shape[1] > 1 and t.stride(1) != n) or t.stride(0) != 1:
+        raise ValueError(f"{name} must be a float32 n x batch tensor with leading dimension n")
+    return t.shape[1]
+
+
+def unet_num_params(widths) -> int:
+    n = load().rbgs_unet_num_params(ctypes.byref(unet_shape(widths)))
+    if n < 0:
+        raise ValueError("invalid U-Net shape")
+    return int(n)
+
+
+def unet_forward(widths, params: torch.Tensor, N: int, x: torch.Tensor, save: bool = False, stream=None,
+                 sync: bool = True) -> torch.Tensor:
+    """y = U-Net(x) for the columns of x (N^2 x batch, float32)."""
+    lib = load()
+    b = _images(x, N * N, "x")
+    y = torch.empty((b, N * N), dtype=torch.float32, device=x.device).t()
+    _check(lib.rbgs_unet_forward(ctypes.byref(unet_shape(widths)), params.data_ptr(), N, b, x.data_ptr(),
+                                 y.data_ptr(), int(save), _stream_ptr(stream), int(sync)), "rbgs_unet_forward")
+    return y
+
+
+def unet_backward(widths, params: torch.Tensor, N: int, x: torch.Tensor, gy: torch.Tensor,
+                  grads: torch.Tensor | None = None, stream=None, sync: bool = True) -> torch.Tensor:
+    """d sum(gy * y) / d params of the last forward with save=True."""
+    lib = load()
+    b = _images(x, N * N, "x")
+    _images(gy, N * N, "gy")
+    if grads is None:
+        grads = torch.empty(params.numel(), dtype=torch.float32, device=params.device)
+    _check(lib.rbgs_unet_backward(ctypes.byref(unet_shape(widths)), params.data_ptr(), N, b, x.data_ptr(),
+                                  gy.data_ptr(), grads.data_ptr(), _stream_ptr(stream), int(sync)),
+           "rbgs_unet_backward")
+    return grads
+
+
+def unet_residual_loss(N: int, coef: torch.Tensor, field: torch.Tensor, x: torch.Tensor, y: torch.Tensor,
+                       gy: torch.Tensor | None = None, loss: torch.Tensor | None = None, stream=None,
+                       sync: bool = True):
+    """(loss (device float64 scalar tensor), gy) of the residual-norm loss;
+    coef: (fields, stride) float64 face coefficients, field: int32 per image."""
+    lib = load()
+    b = _images(x, N * N, "x")
+    if gy is None:
+        gy = torch.empty((b, N * N), dtype=torch.float32, device=x.device).t()
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+    _check(lib.rbgs_unet_residual_loss(N, b, coef.data_ptr(), coef.stride(0), field.data_ptr(), x.data_ptr(),
+                                       y.data_ptr(), gy.data_ptr(), loss.data_ptr(), _stream_ptr(stream), int(sync)),
+           "rbgs_unet_residual_loss")
+    return loss, gy
+
+
+def adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: torch.Tensor, t: int, lr: float = 1e-3,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None, sync: bool = True):
+    lib = load()
+    _check(lib.rbgs_adam_step(params.numel(), params.data_ptr(), grads.data_ptr(), m.data_ptr(), v.data_ptr(), int(t),
+                              lr, beta1, beta2, eps, _stream_ptr(stream), int(sync)), "rbgs_adam_step")
+
+
+def unet_scale_inputs(Q: torch.Tensor, X: torch.Tensor | None = None, prec: str | None = None, stream=None,
+                      sync: bool = True) -> torch.Tensor:
+    """X = Q's columns scaled to unit root mean square (float32, ld n)."""
+    lib = load()
+    prec = _prec_of(Q, prec)
+    n, c = Q.shape
+    if X is None:
+        X = torch.empty((c, n), dtype=torch.float32, device=Q.device).t()
+    _check(lib.rbgs_unet_scale_inputs(n, c, PREC[prec], Q.data_ptr(), _ld(Q, "Q"), X.data_ptr(), _ld(X, "X"),
+                                      _stream_ptr(stream), int(sync)), "rbgs_unet_scale_inputs")
+    return X
+
+
+def unet_precondition(widths, params: torch.Tensor, N: int, Q: torch.Tensor, prec: str | None = None,
+                      stream=None) -> torch.Tensor:
+    """Z = M(Q) (float64 or float32 columns of N^2 rows)."""
+    lib = load()
+    prec = _prec_of(Q, prec)
+    n, c = Q.shape
+    Z = torch.empty((c, n), dtype=Q.dtype, device=Q.device).t()
+    _check(lib.rbgs_unet_precondition(ctypes.byref(unet_shape(widths)), params.data_ptr(), N, PREC[prec],
+                                      Q.data_ptr(), _ld(Q, "Q"), c, Z.data_ptr(), n, _stream_ptr(stream), 1),
+           "rbgs_unet_precondition")
+    return Z
+
+
+def block_fgmres(op: Op, widths, params: torch.Tensor | None, B: torch.Tensor, X: torch.Tensor | None = None,
+                 p: int = 10, rtol: float = 1e-8, max_cycles: int = 100, accept: float = 0.9, sketch: str = "srht",
+                 k: int | None = None, seed: int = 0, prec: str = "fp64", ls_iters: int = 2, reorth: int = 0,
+                 reorth_tol: float = 1e-8, fine: bool = False, stream=None):
+    """Restarted randomized block flexible GMRES with the U-Net preconditioner
+    (widths=None: plain block GMRES).  Returns (X, cycles, relres, fallbacks)."""
+    lib = load()
+    n, mb = B.shape
+    if X is None:
+        X = torch.zeros((mb, n), dtype=torch.float64, device=B.device).t()
+    k = 2 * p * mb if k is None else k
+    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream)
+    cyc, fb = ctypes.c_int64(0), ctypes.c_int64(0)
+    rel = (ctypes.c_double * mb)()
+    net = ctypes.byref(unet_shape(widths)) if widths is not None else None
+    code = lib.rbgs_block_fgmres(ctypes.byref(op), net, params.data_ptr() if params is not None else None,
+                                 B.data_ptr(), _ld(B, "B"), X.data_ptr(), _ld(X, "X"), mb, p, rtol, max_cycles,
+                                 accept, SKETCH[sketch], k, seed, ctypes.byref(o), ctypes.byref(cyc),
+                                 ctypes.cast(rel, ctypes.c_void_p), ctypes.byref(fb))
+    if code not in (0, 7):
+        _check(code, "rbgs_block_fgmres")
+    return X, int(cyc.value), [float(r) for r in rel], int(fb.value)
+

@@ -161,6 +161,26 @@ def gaussian_random_field(N: int, seed: int, corr: float = 0.05, var: float = 1.
     return np.ascontiguousarray(g.real[: N + 2, : N + 2])
 
 
+def gaussian_random_field_torch(N: int, seed: int, corr: float = 0.05, var: float = 1.0, device="cuda"):
+    """gaussian_random_field drawn with torch on ``device`` (same spectral
+    recipe, torch's generator: not the same numbers as the CPU version).
+    Returns an (N+2) x (N+2) float64 tensor indexed [i, j], i along x."""
+    import torch
+
+    h = 1.0 / (N + 1)
+    M = 2 * (N + 2)
+    f = torch.fft.fftfreq(M, d=h, dtype=torch.float64, device=device)
+    kx, ky = torch.meshgrid(f, f, indexing="ij")
+    dens = var * 2.0 * np.pi * corr ** 2 * torch.exp(-2.0 * np.pi ** 2 * corr ** 2 * (kx ** 2 + ky ** 2))
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    xi = torch.complex(torch.randn((M, M), generator=g, device=device, dtype=torch.float64),
+                       torch.randn((M, M), generator=g, device=device, dtype=torch.float64))
+    L = M * h
+    out = torch.fft.ifft2(xi * torch.sqrt(dens / L ** 2)) * M * M
+    return out.real[: N + 2, : N + 2].contiguous()
+
+
 def unet_params(c: int, seed: int) -> dict:
     """Initial weights of the U-Net preconditioner: w (C_out, C_in, 3, 3) He
     normal (std sqrt(2 / (9 C_in))), b zero.  Layers: e1 1->c, e2 c->c, m1
@@ -191,6 +211,43 @@ def unet_params_levels(widths, seed: int) -> dict:
     for name, co, ci in shapes:
         out[name + ".w"] = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (9 * ci))
         out[name + ".b"] = np.zeros(co)
+    return out
+
+
+def unet_flat_params(params: dict, widths) -> np.ndarray:
+    """The dict of unet_params_levels in the library's parameter layout: layer
+    after layer (enc0a, enc0b, ..., enc{L-1}b, dec{L-2}, ..., dec0, out),
+    w[o, c, s, t] stored as w[3 s + t][c][o], then b[o]; float32."""
+    L = len(widths)
+    names = [f"enc{l}{h}" for l in range(L) for h in "ab"] + [f"dec{l}" for l in range(L - 2, -1, -1)] + ["out"]
+    parts = []
+    for nm in names:
+        w = params[nm + ".w"]
+        co, ci = w.shape[:2]
+        parts.append(np.transpose(w, (2, 3, 1, 0)).reshape(9 * ci * co))
+        parts.append(params[nm + ".b"])
+    return np.concatenate(parts).astype(np.float32)
+
+
+def unet_dict_params(flat, widths) -> dict:
+    """The inverse of unet_flat_params (float64 arrays)."""
+    flat = np.asarray(flat, dtype=np.float64)
+    L = len(widths)
+    shapes = []
+    for l in range(L):
+        shapes.append((f"enc{l}a", widths[l], 1 if l == 0 else widths[l - 1]))
+        shapes.append((f"enc{l}b", widths[l], widths[l]))
+    for l in range(L - 2, -1, -1):
+        shapes.append((f"dec{l}", widths[l], widths[l + 1] + widths[l]))
+    shapes.append(("out", 1, widths[0]))
+    out, off = {}, 0
+    for nm, co, ci in shapes:
+        w = flat[off:off + 9 * ci * co].reshape(3, 3, ci, co)
+        out[nm + ".w"] = np.ascontiguousarray(np.transpose(w, (3, 2, 0, 1)))
+        off += 9 * ci * co
+        out[nm + ".b"] = flat[off:off + co].copy()
+        off += co
+    assert off == flat.size
     return out
 
 
