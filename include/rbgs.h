@@ -90,7 +90,9 @@ typedef struct {
   int32_t timing;      /* 1: time the tall-update launches with CUDA events (needs sync) */
   int32_t fine;        /* FP32 / TF32X3 / F16X3: 1 = the sketch-space steps (P and S stored,
                           step-2 least squares, block Cholesky QR, R) in FP64 (the
-                          paper's u_fine); 0 = in FP32                                  */
+                          paper's u_fine); 2 = the same, with the sketch-space products
+                          in double-FP32 arithmetic on the FP32 pipe (about 2^-44
+                          relative; GB300's FP64 pipe is narrow); 0 = in FP32         */
   int32_t interblock;  /* steps 4-5: 0 or 5 = Alg. 5 (the sketch of Q'_i taken implicitly as
                           P_i - S R, one tall pass per block); 4 = Alg. 4 (RCholeskyQR on
                           the explicit sketch Theta Q'_i: the projection, a sketch, and an
@@ -237,6 +239,20 @@ RBGS_API rbgs_status rbgs_qr_graph_create(const void* W, int64_t n, int64_t m, i
                                           rbgs_sketch sketch, int64_t k, uint64_t seed, void* Q, int64_t ldq,
                                           double* R, int64_t ldr, const rbgs_opts* opts, rbgs_graph** out);
 RBGS_API rbgs_status rbgs_qr_graph_launch(rbgs_graph* g, void* stream, int32_t sync);
+
+/* A batch of independent factorizations (as rbgs_qr_batched) captured as one
+ * CUDA graph: every problem on one of min(nstreams, count, 32) slot streams
+ * with its own workspace and side stream, forked from and joined back to the
+ * launching stream, so that rbgs_qr_graph_launch replays the whole batch
+ * with a single graph launch (the pointers, sizes and options fixed; new
+ * contents of each W each time).  The graph owns the slot streams,
+ * workspaces and status words; probs (caller-owned) must stay valid while the
+ * graph exists: a launch with sync writes each problem's status and passes2
+ * there and returns the first problem's error.  Not for opts->interblock 1
+ * or 3.  The paper has no batched form: this removes the host cost of
+ * launching every kernel of every problem when the problems are small.     */
+RBGS_API rbgs_status rbgs_qr_batched_graph_create(rbgs_problem* probs, int64_t count, rbgs_sketch sketch,
+                                                  const rbgs_opts* opts, int32_t nstreams, rbgs_graph** out);
 RBGS_API rbgs_status rbgs_qr_graph_destroy(rbgs_graph* g);
 
 /* Y = Theta X (Sec. 2.3), the sketch of steps 1 and 5 of Alg. 2.
@@ -409,6 +425,9 @@ RBGS_API rbgs_status rbgs_rayleigh_ritz(const rbgs_op* op, const double* B0, int
 typedef struct {
   int32_t levels;
   int32_t width[6];
+  int32_t flags;     /* bit 0: every convolution on the SIMT kernels (by default the
+                        levels whose rows are multiples of 128 pixels and whose channel
+                        counts are multiples of 16 use the tcgen05 tensor cores)      */
 } rbgs_unet;
 
 /* Number of parameters of the network, or -1 if its shape is invalid.      */
@@ -416,7 +435,8 @@ RBGS_API int64_t rbgs_unet_num_params(const rbgs_unet* net);
 
 /* y = U-Net(x) for batch images of N x N (x, y device FP32, n x batch with
  * leading dimension n).  save != 0 keeps the activations for the next
- * rbgs_unet_backward call.  RBGS_EINVAL on an invalid shape or pointer.     */
+ * rbgs_unet_backward call.  RBGS_EINVAL on an invalid shape or pointer;
+ * with sync, RBGS_ETIMEOUT if a bounded wait of a tensor-core kernel expired. */
 RBGS_API rbgs_status rbgs_unet_forward(const rbgs_unet* net, const float* params, int64_t N, int64_t batch,
                                        const float* x, float* y, int32_t save, void* stream, int32_t sync);
 

@@ -121,6 +121,16 @@ template <class TA, class TO, class TACC>
 rbgs_status small_gemm(int trans, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t lda,
                        const TA* B, int64_t ldb, double beta, TO* out, int64_t ldo, TACC* part, int64_t part_elems,
                        const int* active, cudaStream_t st);
+// While an instance is alive on this host thread, the FP64 small products
+// and the FP64 sums of the dense sketches of FP32 data run in double-FP32
+// arithmetic on the FP32 pipe (about 2^-44 relative): the mixed-precision
+// path's FP64 sketch space with opts.fine = 2.  The FP64 path never sets it.
+extern thread_local int g_df_products;
+struct DfProducts {
+  explicit DfProducts(bool on);
+  ~DfProducts();
+  int prev;
+};
 
 // Cholesky G (+ shift * trace(G) I) = R^T R (upper R, positive diagonal) of an
 // mb x mb matrix and R^{-1}, in the arithmetic of T; sets *flag |= 1 on a
@@ -208,6 +218,18 @@ rbgs_status trsm_rows(int64_t n, int mb, T* Q, int64_t ldq, const TS* R, const i
 
 // Face coefficients of RBGS_OP_DIFFUSION from node values (krylov.cu).
 rbgs_status diffusion_faces(int64_t nx, int64_t ny, const double* a, double* fc, cudaStream_t st);
+
+// The tensor-core 3 x 3 convolution (unet_tc.cu): out = conv3x3(in) with
+// bfloat16 NHWC input (ld_in, channel offset off_in), weights packed by
+// conv_tc_pack (flip: the backward convolution's flipped, transposed weights
+// of a layer with cin and cout exchanged), bias and relu optional, output
+// bfloat16 (out_bf16) or FP32.
+bool conv_tc_supported(int N, int cin, int cout, int64_t ld_in, int off_in, int64_t ld_out, int off_out);
+size_t conv_tc_pack_bytes(int cin, int cout);
+rbgs_status conv_tc_pack(int cin, int cout, const float* w, int flip, void* packed, cudaStream_t st);
+rbgs_status conv_tc(int N, int batch, int cin, int cout, const void* in, int64_t ld_in, int off_in, const void* packed,
+                    const float* bias, int relu, void* out, int out_bf16, int64_t ld_out, int off_out, int* err,
+                    cudaStream_t st);
 
 // The U-Net preconditioner (unet.cu): Z (n x ncols, ldz) = M(Q) column by
 // column, M(q) = s (h^2 / 8) U-Net(q / s), s = ||q|| / sqrt(n), h = 1 / (N + 1).

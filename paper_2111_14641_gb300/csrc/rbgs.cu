@@ -328,6 +328,9 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
   // mode 0: SIMT tall product; 1: TF32X3 tensor cores; 2: F16X3 tensor cores with the pre-split basis
   const bool tensor = mode != 0;
   cudaStream_t st = (cudaStream_t)o.stream;
+  // fine == 2: the FP64 sketch space of FP32 storage takes its products in
+  // double-FP32 arithmetic (small_gemm's df kernel) instead of on the FP64 pipe
+  DfProducts df_guard(sizeof(T) == 4 && sizeof(TS) == 8 && o.fine == 2);
   // m need not be a multiple of mb: the last of the p blocks takes the
   // m - (p - 1) mb remaining columns.  Inside the block loop mb is the width of
   // the current block (every helper below reads it); mbf is the full width.
@@ -1001,7 +1004,7 @@ rbgs_status check_qr(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t m
   if (ranges_overlap(W, es * (size_t)(ldw * (m - 1) + n), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
   if (ranges_overlap(R, 8 * (size_t)(ldr * (m - 1) + m), Q, es * (size_t)(ldq * (m - 1) + n))) return RBGS_EINVAL;
   if (o.prec == RBGS_P_FP64) return RBGS_OK;
-  if (o.fine < 0 || o.fine > 1) return RBGS_EINVAL;
+  if (o.fine < 0 || o.fine > 2) return RBGS_EINVAL;
   // tensor-core paths: TMA needs 16-byte aligned bases and leading dimensions
   if ((o.prec == RBGS_P_TF32X3 || o.prec == RBGS_P_F16X3) &&
       (((uintptr_t)W & 15) || ((uintptr_t)Q & 15) || (ldw % 4) || (ldq % 4)))
@@ -1431,6 +1434,13 @@ struct rbgs_graph {
   cudaStream_t side = nullptr;
   void* ws = nullptr;
   int* status = nullptr;
+  // a captured batch (rbgs_qr_batched_graph_create): one stream, side stream,
+  // workspace and done event per slot, 8 status words per problem
+  std::vector<cudaStream_t> streams, sides;
+  std::vector<void*> wss;
+  std::vector<cudaEvent_t> events;
+  int64_t count = 0;
+  rbgs_problem* probs = nullptr;  // the caller's array, for the per-problem statuses
 };
 
 extern "C" {
@@ -1445,6 +1455,20 @@ rbgs_status rbgs_qr_graph_destroy(rbgs_graph* g) {
   }
   if (g->ws) cudaFree(g->ws);
   if (g->status) cudaFree(g->status);
+  for (auto x : g->streams)
+    if (x) {
+      cudaStreamSynchronize(x);
+      cudaStreamDestroy(x);
+    }
+  for (auto x : g->sides)
+    if (x) {
+      cudaStreamSynchronize(x);
+      cudaStreamDestroy(x);
+    }
+  for (auto x : g->wss)
+    if (x) cudaFree(x);
+  for (auto x : g->events)
+    if (x) cudaEventDestroy(x);
   delete g;
   return RBGS_OK;
 }
@@ -1517,11 +1541,134 @@ rbgs_status rbgs_qr_graph_create(const void* W, int64_t n, int64_t m, int64_t ld
   return RBGS_OK;
 }
 
+rbgs_status rbgs_qr_batched_graph_create(rbgs_problem* probs, int64_t count, rbgs_sketch sketch, const rbgs_opts* opts,
+                                         int32_t nstreams, rbgs_graph** out) {
+  if (!out || !probs || count < 1 || nstreams < 1) return RBGS_EINVAL;
+  *out = nullptr;
+  rbgs_opts o;
+  if (opts) o = *opts;
+  else rbgs_opts_default(&o);
+  if (o.interblock == 1 || o.interblock == 3) return RBGS_EINVAL;  // they allocate inside the factorization
+  for (int64_t i = 0; i < count; ++i) {
+    const rbgs_problem& q = probs[i];
+    rbgs_status s = check_qr(q.W, q.n, q.m, q.ldw, q.mb, sketch, q.k, q.Q, q.ldq, q.R, q.ldr, o);
+    if (s) return s;
+  }
+  o.sync = 0;
+  o.timing = 0;
+  o.certify = 0;
+  const int ns = (int)std::min<int64_t>(std::min<int64_t>(nstreams, count), 32);
+  rbgs_graph* g = new rbgs_graph();
+  struct Undo {
+    rbgs_graph** g;
+    ~Undo() {
+      if (*g) rbgs_qr_graph_destroy(*g);
+    }
+  } undo{&g};
+  g->count = count;
+  g->probs = probs;
+  std::vector<size_t> need((size_t)ns, 0);
+  rbgs_status s;
+  for (int64_t i = 0; i < count; ++i) {
+    const rbgs_problem& q = probs[i];
+    size_t nd = 0;
+    QrCtx c;
+    c.need_out = &nd;
+    if ((s = qr_dispatch(q.W, q.n, q.m, q.ldw, q.mb, sketch, q.k, q.seed, q.Q, q.ldq, q.R, q.ldr, o, nullptr, &c)))
+      return s;
+    need[(size_t)(i % ns)] = std::max(need[(size_t)(i % ns)], nd);
+  }
+  g->streams.assign((size_t)ns, nullptr);
+  g->sides.assign((size_t)ns, nullptr);
+  g->wss.assign((size_t)ns, nullptr);
+  g->events.assign((size_t)ns + 1, nullptr);
+  for (int j = 0; j < ns; ++j) {
+    RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&g->streams[(size_t)j], cudaStreamNonBlocking));
+    RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&g->sides[(size_t)j], cudaStreamNonBlocking));
+    if (cudaMalloc(&g->wss[(size_t)j], need[(size_t)j]) != cudaSuccess) {
+      cudaGetLastError();
+      return RBGS_ENOMEM;
+    }
+  }
+  for (auto& e : g->events) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  if (cudaMalloc(&g->status, sizeof(int) * 8 * (size_t)count) != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ENOMEM;
+  }
+  cudaStream_t cs = nullptr;
+  RBGS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  struct StreamFree {
+    cudaStream_t s;
+    ~StreamFree() {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  } csf{cs};
+  // the batch from cs: fork to the slot streams, every problem on its slot, join
+  auto enqueue = [&]() -> rbgs_status {
+    RBGS_CUDA_TRY(cudaEventRecord(g->events[(size_t)ns], cs));
+    for (auto x : g->streams) RBGS_CUDA_TRY(cudaStreamWaitEvent(x, g->events[(size_t)ns], 0));
+    for (int64_t i = 0; i < count; ++i) {
+      const rbgs_problem& q = probs[i];
+      const size_t j = (size_t)(i % ns);
+      QrCtx c;
+      c.ws = g->wss[j];
+      c.ws_bytes = need[j];
+      c.side = g->sides[j];
+      c.status_out = g->status + 8 * i;
+      rbgs_opts oi = o;
+      oi.stream = g->streams[j];
+      rbgs_status r = qr_dispatch(q.W, q.n, q.m, q.ldw, q.mb, sketch, q.k, q.seed, q.Q, q.ldq, q.R, q.ldr, oi,
+                                  nullptr, &c);
+      if (r) return r;
+    }
+    for (int j = 0; j < ns; ++j) {
+      RBGS_CUDA_TRY(cudaEventRecord(g->events[(size_t)j], g->streams[(size_t)j]));
+      RBGS_CUDA_TRY(cudaStreamWaitEvent(cs, g->events[(size_t)j], 0));
+    }
+    return RBGS_OK;
+  };
+  // one run outside the capture fills the library's caches (sketch plans, kernel attributes)
+  if ((s = enqueue())) return s;
+  RBGS_CUDA_TRY(cudaStreamSynchronize(cs));
+  RBGS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  s = enqueue();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+  if (s) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return RBGS_ECUDA;
+  }
+  g->graph = graph;
+  RBGS_CUDA_TRY(cudaGraphInstantiate(&g->exec, g->graph, 0));
+  *out = g;
+  g = nullptr;
+  return RBGS_OK;
+}
+
 rbgs_status rbgs_qr_graph_launch(rbgs_graph* g, void* stream, int32_t sync) {
   if (!g || !g->exec) return RBGS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   RBGS_CUDA_TRY(cudaGraphLaunch(g->exec, st));
   if (!sync) return RBGS_OK;
+  if (g->count > 0) {  // a batch: every problem's status words
+    std::vector<int> hs((size_t)g->count * 8);
+    RBGS_CUDA_TRY(cudaMemcpyAsync(hs.data(), g->status, sizeof(int) * hs.size(), cudaMemcpyDeviceToHost, st));
+    RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+    rbgs_status first = RBGS_OK;
+    for (int64_t i = 0; i < g->count; ++i) {
+      const int* f = hs.data() + 8 * i;
+      const rbgs_status si = f[3] ? RBGS_ETIMEOUT : (f[0] ? RBGS_EBREAKDOWN : RBGS_OK);
+      g->probs[i].status = si;
+      g->probs[i].passes2 = f[2];
+      if (si && !first) first = si;
+    }
+    return first;
+  }
   int hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   RBGS_CUDA_TRY(cudaMemcpyAsync(hs, g->status, sizeof(hs), cudaMemcpyDeviceToHost, st));
   RBGS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1762,7 +1909,7 @@ rbgs_status fgmres_solve(const rbgs_op* op, const rbgs_unet* net, const float* p
   rbgs_opts o;
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
-  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 2 ||
       (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1) ||
       (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)))
     return RBGS_EINVAL;
@@ -1910,7 +2057,7 @@ rbgs_status krylov_solve(int method, const rbgs_op* op, const double* B, int64_t
   rbgs_opts o;
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
-  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 2 ||
       (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1) ||
       (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)))
     return RBGS_EINVAL;
@@ -2016,7 +2163,7 @@ rbgs_status rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int6
   rbgs_opts o;
   if (opts) o = *opts;
   else rbgs_opts_default(&o);
-  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 2 ||
       (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1) ||
       (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)))
     return RBGS_EINVAL;
@@ -2135,7 +2282,7 @@ rbgs_status rbgs_block_arnoldi(const rbgs_op* op, const void* B, int64_t ldb, in
   const int64_t n = op->nx * op->ny, m = p * mb;
   if (!B || !Q || !R || mb < 1 || mb > 64 || p < 1 || ldb < n || ldq < n || ldr < m) return RBGS_EINVAL;
   if ((s = check_sketch(sketch, n, k, m))) return s;
-  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 1 ||
+  if (o.prec < RBGS_P_FP64 || o.prec > RBGS_P_F16X3 || o.reorth < 0 || o.reorth > 2 || o.fine < 0 || o.fine > 2 ||
       (o.interblock != 0 && o.interblock != 4 && o.interblock != 5) || (o.ls != 0 && o.ls != 1) ||
       (o.trsm != 0 && (o.trsm != 1 || o.interblock != 4)))
     return RBGS_EINVAL;

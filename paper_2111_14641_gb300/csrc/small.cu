@@ -100,6 +100,106 @@ __global__ void __launch_bounds__(256) small_gemm_part(int trans, int64_t M, int
   }
 }
 
+// The same product for FP64 data with double-FP32 ("double-float")
+// arithmetic on the FP32 pipe: each operand is split once, a = a_hi + a_lo
+// with a_hi = fl32(a) and a_lo = fl32(a - a_hi) (48 significant bits), each
+// product a_hi b_hi is formed exactly with its FMA error term, the cross
+// terms a_hi b_lo + a_lo b_hi are added into that error, and the running sum
+// is a double-float (s_hi, s_lo) kept by TwoSum (Knuth; Dekker 1971).  The
+// relative error of the result is a few units of 2^-44, far below the FP32
+// storage of the tall data, at about six times the FP64 pipe's rate on
+// GB300.  The mixed-precision path uses it for its FP64 sketch space; the
+// FP64 path keeps the FP64 kernel.
+__global__ void __launch_bounds__(256) small_gemm_part_df(int trans, int64_t M, int N, int64_t K, int64_t kper,
+                                                          const double* __restrict__ A, int64_t lda,
+                                                          const double* __restrict__ B, int64_t ldb,
+                                                          double* __restrict__ part, const int* active) {
+  if (active && *active == 0) return;
+  __shared__ float2 As[SG_K][SG_T + 1];
+  __shared__ float2 Bs[SG_K][SG_N + 1];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int jw = 8 * warp;
+  const bool busy = jw < N;
+  const int64_t i0 = (int64_t)blockIdx.x * SG_T;
+  const int split = blockIdx.y;
+  const int64_t kb = (int64_t)split * kper;
+  const int64_t ke = min(K, kb + kper);
+  constexpr int PER = (SG_K * SG_T) / 256;
+  double ra[PER], rb[PER];
+  auto load = [&](int64_t l0) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      int il, ll;
+      if (trans) { ll = e % SG_K; il = e / SG_K; }
+      else { il = e % SG_T; ll = e / SG_T; }
+      const int64_t gi = i0 + il, gl = l0 + ll;
+      ra[q] = (gi < M && gl < ke) ? (trans ? A[gl + gi * lda] : A[gi + gl * lda]) : 0.0;
+      const int lb = e % SG_K, j = e / SG_K;
+      const int64_t gb = l0 + lb;
+      rb[q] = (gb < ke && j < N) ? B[gb + (int64_t)j * ldb] : 0.0;
+    }
+  };
+  auto split2 = [](double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  };
+  float hi[2][8], lo[2][8];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) hi[i][q] = lo[i][q] = 0.f;
+  if (kb < ke) load(kb);
+  for (int64_t l0 = kb; l0 < ke; l0 += SG_K) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      int il, ll;
+      if (trans) { ll = e % SG_K; il = e / SG_K; }
+      else { il = e % SG_T; ll = e / SG_T; }
+      As[ll][il] = split2(ra[q]);
+      Bs[e % SG_K][e / SG_K] = split2(rb[q]);
+    }
+    __syncthreads();
+    if (l0 + SG_K < ke) load(l0 + SG_K);
+    if (busy) {
+#pragma unroll
+      for (int ll = 0; ll < SG_K; ++ll) {
+        const float2 a0 = As[ll][lane], a1 = As[ll][lane + 32];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float2 b = Bs[ll][jw + q];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const float2 a = r ? a1 : a0;
+            const float p = a.x * b.x;
+            float e = fmaf(a.x, b.x, -p);
+            e = fmaf(a.x, b.y, e);
+            e = fmaf(a.y, b.x, e);
+            const float sacc = hi[r][q] + p;
+            const float bp = sacc - hi[r][q];
+            const float err = (hi[r][q] - (sacc - bp)) + (p - bp);
+            hi[r][q] = sacc;
+            lo[r][q] += err + e;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (busy) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t gi = i0 + lane + 32 * i;
+        const int j = jw + q;
+        if (gi < M && j < N) part[((int64_t)split * N + j) * M + gi] = (double)hi[i][q] + (double)lo[i][q];
+      }
+  }
+}
+
 template <class TACC, class TO>
 __global__ void small_gemm_reduce(int64_t M, int N, int ks, const TACC* __restrict__ part, double alpha,
                                   double beta, TO* out, int64_t ldo, const int* active) {
@@ -715,6 +815,11 @@ __global__ void __launch_bounds__(512) hh_panel_kernel(int64_t k, int64_t c, int
 
 }  // namespace
 
+thread_local int g_df_products = 0;
+
+DfProducts::DfProducts(bool on) : prev(g_df_products) { g_df_products = on ? 1 : 0; }
+DfProducts::~DfProducts() { g_df_products = prev; }
+
 template <class TA, class TO, class TACC>
 rbgs_status small_gemm(int trans, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t lda,
                        const TA* B, int64_t ldb, double beta, TO* out, int64_t ldo, TACC* part, int64_t part_elems,
@@ -731,7 +836,15 @@ rbgs_status small_gemm(int trans, int64_t M, int64_t N, int64_t K, double alpha,
   kper = std::max<int64_t>(SG_K, (kper + SG_K - 1) / SG_K * SG_K);
   ks = std::max<int64_t>(1, (K + kper - 1) / kper);
   dim3 grid((unsigned)mt, (unsigned)ks);
-  small_gemm_part<TA, TACC><<<grid, 256, 0, st>>>(trans, M, (int)N, K, kper, A, lda, B, ldb, part, active);
+  if constexpr (sizeof(TA) == 8 && sizeof(TACC) == 8) {
+    if (g_df_products)
+      small_gemm_part_df<<<grid, 256, 0, st>>>(trans, M, (int)N, K, kper, (const double*)A, lda, (const double*)B, ldb,
+                                               (double*)part, active);
+    else
+      small_gemm_part<TA, TACC><<<grid, 256, 0, st>>>(trans, M, (int)N, K, kper, A, lda, B, ldb, part, active);
+  } else {
+    small_gemm_part<TA, TACC><<<grid, 256, 0, st>>>(trans, M, (int)N, K, kper, A, lda, B, ldb, part, active);
+  }
   RBGS_LAUNCH_CHECK();
   const int64_t tot = M * N;
   small_gemm_reduce<TACC, TO><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, (int)N, (int)ks, part, alpha, beta,

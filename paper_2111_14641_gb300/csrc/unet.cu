@@ -25,9 +25,14 @@
 // w[tap][ci][co] (tap = 3 ox + oy, ox / oy in {0, 1, 2} the offset + 1 along
 // ix / iy) followed by b[co].
 //
-// The convolutions here are direct SIMT kernels (FP32 FMA on bfloat16
-// operands): each CTA computes an 8 x 64-pixel tile for 16 output channels,
-// staging 8 input channels at a time in shared memory.
+// Convolutions run on the tensor cores (unet_tc.cu: tcgen05 with bfloat16
+// operands and FP32 accumulators) at the levels whose rows are multiples of
+// 128 pixels and whose channel counts are multiples of 16, for the forward
+// pass and the backward convolution of the input gradient; elsewhere (the
+// one-channel input and output layers, the small levels) and for the weight
+// gradients they run as direct SIMT kernels (FP32 FMA on bfloat16 operands:
+// each CTA computes an 8 x 64-pixel tile for 16 output channels, staging 8
+// input channels at a time in shared memory).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -248,13 +253,15 @@ __global__ void bias_grad_kernel(int64_t npix, int Cout, const float* __restrict
 // act: bfloat16 with its own ld and channel offset).
 __global__ void relu_mask_kernel(int64_t npix, int C, const float* __restrict__ g, int64_t ld_g,
                                  const __nv_bfloat16* __restrict__ act, int64_t ld_a, int off_a,
-                                 float* __restrict__ gz) {
+                                 float* __restrict__ gz, __nv_bfloat16* __restrict__ gzb) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npix * C) return;
   const int64_t p = t / C;
   const int c = (int)(t % C);
   const float a = __bfloat162float(act[p * ld_a + off_a + c]);
-  gz[p * C + c] = a > 0.f ? g[p * ld_g + c] : 0.f;
+  const float v = a > 0.f ? g[p * ld_g + c] : 0.f;
+  gz[p * C + c] = v;
+  if (gzb) gzb[p * C + c] = __float2bfloat16_rn(v);  // the operand of a tensor-core backward convolution
 }
 
 // x_{l+1} = avgpool2(s_l): out (batch, N/2 x N/2, C, ld C) from in (N x N, ld_in, off_in).
@@ -468,7 +475,7 @@ int64_t num_params(const rbgs_unet& net) {
 }
 
 bool net_ok(const rbgs_unet* net) {
-  if (!net || net->levels < 2 || net->levels > 6) return false;
+  if (!net || net->levels < 2 || net->levels > 6 || net->flags < 0 || net->flags > 1) return false;
   for (int l = 0; l < net->levels; ++l)
     if (net->width[l] < 8 || net->width[l] > 64 || net->width[l] % 8) return false;
   return true;
@@ -483,6 +490,10 @@ struct Plan {
   __nv_bfloat16* SB = nullptr;              // s_{L-1}
   __nv_bfloat16* wbf = nullptr;             // bfloat16 weights
   __nv_bfloat16* wd = nullptr;              // backward weights of one layer (largest)
+  unsigned char* wpk = nullptr;             // tensor-core packed weights, per layer at w_off bytes * 2
+  unsigned char* wdpk = nullptr;            // tensor-core packed backward weights of one layer
+  std::vector<__nv_bfloat16*> GB;           // per level: bfloat16 copy of the masked gradient
+  int* tc_err = nullptr;                    // bounded-wait flag of the tensor-core kernels
   // gradients (FP32)
   std::vector<float*> G1, G2, G3;  // per level: three buffers of npix * cmax_l
   size_t bytes = 0;
@@ -533,10 +544,18 @@ size_t plan_layout(const rbgs_unet& net, int N, int batch, bool grads, char* bas
     }
   }
   P->wbf = (__nv_bfloat16*)take(2 * num_params(net));
+  P->wpk = (unsigned char*)take(2 * num_params(net));
+  P->tc_err = (int*)take(256);
+  P->GB.assign(L, nullptr);
   if (grads) {
     int64_t wmax = 0;
     for (const auto& ly : layers_of(net)) wmax = std::max<int64_t>(wmax, 9LL * ly.cin * ly.cout);
     P->wd = (__nv_bfloat16*)take(2 * wmax);
+    P->wdpk = (unsigned char*)take(2 * wmax);
+    for (int l = 0; l < L; ++l) {
+      int cmax = net.width[l];
+      P->GB[l] = (__nv_bfloat16*)take(2 * P->npix[l] * cmax);
+    }
   }
   P->bytes = off;
   return off;
@@ -659,6 +678,26 @@ rbgs_status wgrad(int N, int batch, int Cin, int Cout, const TIn* in, int64_t ld
   return RBGS_OK;
 }
 
+template <class T>
+constexpr int is_bf16() {
+  return sizeof(T) == 2 ? 1 : 0;
+}
+
+// A forward convolution from bfloat16 activations: on the tensor cores where
+// the level and channel counts allow it (rows of a multiple of 128 pixels,
+// channels in multiples of 16; rbgs_unet.flags bit 0 turns them off), else the
+// SIMT kernel.
+template <class TOut>
+rbgs_status conv_fwd(const rbgs_unet& net, Plan& P, int N, int B, int cin, int cout, const __nv_bfloat16* in,
+                     int64_t ld_in, int off_in, const Layer& ly, const float* params, int relu, TOut* out,
+                     int64_t ld_out, int off_out, cudaStream_t st) {
+  if (!(net.flags & 1) && conv_tc_supported(N, cin, cout, ld_in, off_in, ld_out, off_out))
+    return conv_tc(N, B, cin, cout, in, ld_in, off_in, P.wpk + 2 * ly.w_off, params + ly.b_off, relu, out,
+                   is_bf16<TOut>(), ld_out, off_out, P.tc_err, st);
+  return conv<__nv_bfloat16, TOut>(N, B, cin, cout, in, ld_in, off_in, P.wbf + ly.w_off, params + ly.b_off, relu,
+                                   out, ld_out, off_out, st);
+}
+
 // The forward pass into the buffers of nb; y (FP32) column b at y + b ldy.
 rbgs_status forward(NetBuf& nb, const float* params, const float* x, int64_t ldx, float* y, int64_t ldy,
                     cudaStream_t st) {
@@ -670,6 +709,12 @@ rbgs_status forward(NetBuf& nb, const float* params, const float* x, int64_t ldx
   to_bf16_kernel<<<blocks_for(np), 256, 0, st>>>(np, params, P.wbf);
   RBGS_LAUNCH_CHECK();
   rbgs_status s;
+  RBGS_CUDA_TRY(cudaMemsetAsync(P.tc_err, 0, sizeof(int), st));
+  if (!(net.flags & 1)) {  // the tensor-core operand layout of every layer that can use it
+    for (const auto& ly : lay)
+      if (ly.cin % 16 == 0 && ly.cout % 16 == 0 && ly.cout <= 128)
+        if ((s = conv_tc_pack(ly.cin, ly.cout, params + ly.w_off, 0, P.wpk + 2 * ly.w_off, st))) return s;
+  }
   int li = 0;
   // the network input x is FP32 with one channel: image b at x + b ldx, i.e.
   // pixel-major with ld 1 only when ldx == N^2; otherwise copy it first
@@ -686,17 +731,14 @@ rbgs_status forward(NetBuf& nb, const float* params, const float* x, int64_t ldx
       avgpool_kernel<<<blocks_for((int64_t)B * Nl * Nl * cp), 256, 0, st>>>(
           Nl * 2, B, cp, P.CAT[l - 1], c + cp, c, P.X[l]);
       RBGS_LAUNCH_CHECK();
-      s = conv<__nv_bfloat16, __nv_bfloat16>(Nl, B, cp, c, P.X[l], cp, 0, P.wbf + la.w_off, params + la.b_off, 1,
-                                             P.A[l], c, 0, st);
+      s = conv_fwd<__nv_bfloat16>(net, P, Nl, B, cp, c, P.X[l], cp, 0, la, params, 1, P.A[l], c, 0, st);
     }
     if (s) return s;
     if (l < L - 1) {
       const int cn = net.width[l + 1];
-      s = conv<__nv_bfloat16, __nv_bfloat16>(Nl, B, c, c, P.A[l], c, 0, P.wbf + lb.w_off, params + lb.b_off, 1,
-                                             P.CAT[l], cn + c, cn, st);
+      s = conv_fwd<__nv_bfloat16>(net, P, Nl, B, c, c, P.A[l], c, 0, lb, params, 1, P.CAT[l], cn + c, cn, st);
     } else {
-      s = conv<__nv_bfloat16, __nv_bfloat16>(Nl, B, c, c, P.A[l], c, 0, P.wbf + lb.w_off, params + lb.b_off, 1, P.SB,
-                                             c, 0, st);
+      s = conv_fwd<__nv_bfloat16>(net, P, Nl, B, c, c, P.A[l], c, 0, lb, params, 1, P.SB, c, 0, st);
     }
     if (s) return s;
   }
@@ -706,8 +748,7 @@ rbgs_status forward(NetBuf& nb, const float* params, const float* x, int64_t ldx
     const __nv_bfloat16* prev = l == L - 2 ? P.SB : P.D[l + 1];
     upsample_kernel<<<blocks_for((int64_t)B * Nl * Nl * cn), 256, 0, st>>>(Nl, B, cn, prev, P.CAT[l], cn + c);
     RBGS_LAUNCH_CHECK();
-    s = conv<__nv_bfloat16, __nv_bfloat16>(Nl, B, cn + c, c, P.CAT[l], cn + c, 0, P.wbf + ld.w_off,
-                                           params + ld.b_off, 1, P.D[l], c, 0, st);
+    s = conv_fwd<__nv_bfloat16>(net, P, Nl, B, cn + c, c, P.CAT[l], cn + c, 0, ld, params, 1, P.D[l], c, 0, st);
     if (s) return s;
   }
   const Layer& lo = lay[li++];
@@ -723,6 +764,18 @@ rbgs_status dgrad(int N, int batch, int Cin, int Cout, const float* w, __nv_bflo
   return conv<float, float>(N, batch, Cout, Cin, gz, Cout, 0, wd, nullptr, 0, gx, Cin, 0, st);
 }
 
+// The backward convolution gx = conv(gz, flipped transposed w): on the tensor
+// cores from the bfloat16 copy gzb of gz where possible, else SIMT from gz.
+rbgs_status dgrad_any(const rbgs_unet& net, Plan& P, int N, int batch, int Cin, int Cout, const float* w,
+                      const float* gz, const __nv_bfloat16* gzb, float* gx, cudaStream_t st) {
+  if (!(net.flags & 1) && gzb && conv_tc_supported(N, Cout, Cin, Cout, 0, Cin, 0)) {
+    rbgs_status s = conv_tc_pack(Cout, Cin, w, 1, P.wdpk, st);
+    if (s) return s;
+    return conv_tc(N, batch, Cout, Cin, gzb, Cout, 0, P.wdpk, nullptr, 0, gx, 0, Cin, 0, P.tc_err, st);
+  }
+  return dgrad(N, batch, Cin, Cout, w, P.wd, gz, gx, st);
+}
+
 // The backward pass of the last forward saved in nb: grads (FP32, the
 // parameter layout) = d sum(gy * y) / d params.
 rbgs_status backward(NetBuf& nb, const float* params, const float* gy, float* grads, const float* x,
@@ -733,6 +786,7 @@ rbgs_status backward(NetBuf& nb, const float* params, const float* gy, float* gr
   const auto lay = layers_of(net);
   rbgs_status s;
   RBGS_CUDA_TRY(cudaMemsetAsync(grads, 0, sizeof(float) * num_params(net), st));
+  RBGS_CUDA_TRY(cudaMemsetAsync(P.tc_err, 0, sizeof(int), st));
   int li = (int)lay.size() - 1;
   // output layer: z = y (linear); input D_0
   {
@@ -747,13 +801,13 @@ rbgs_status backward(NetBuf& nb, const float* params, const float* gy, float* gr
     const Layer& ld = lay[li--];
     const int Nl = N >> l, c = net.width[l], cn = net.width[l + 1];
     const int64_t npx = P.npix[l];
-    relu_mask_kernel<<<blocks_for(npx * c), 256, 0, st>>>(npx, c, P.G1[l], c, P.D[l], c, 0, P.G2[l]);
+    relu_mask_kernel<<<blocks_for(npx * c), 256, 0, st>>>(npx, c, P.G1[l], c, P.D[l], c, 0, P.G2[l], P.GB[l]);
     RBGS_LAUNCH_CHECK();
     if ((s = wgrad<__nv_bfloat16>(Nl, B, cn + c, c, P.CAT[l], cn + c, 0, P.G2[l], grads + ld.w_off,
                                   grads + ld.b_off, st)))
       return s;
     // G3[l] = g(CAT_l): channels [0, cn) go to the upsampled d_{l+1}, [cn, cn + c) to s_l
-    if ((s = dgrad(Nl, B, cn + c, c, params + ld.w_off, P.wd, P.G2[l], P.G3[l], st))) return s;
+    if ((s = dgrad_any(net, P, Nl, B, cn + c, c, params + ld.w_off, P.G2[l], P.GB[l], P.G3[l], st))) return s;
     upsample_bwd_kernel<<<blocks_for(P.npix[l + 1] * cn), 256, 0, st>>>(Nl, B, cn, P.G3[l], cn + c, 0, P.G1[l + 1]);
     RBGS_LAUNCH_CHECK();
   }
@@ -772,12 +826,12 @@ rbgs_status backward(NetBuf& nb, const float* params, const float* gy, float* gr
     const __nv_bfloat16* s_act = l < L - 1 ? P.CAT[l] : P.SB;
     const int64_t s_ld = l < L - 1 ? net.width[l + 1] + c : c;
     const int s_off = l < L - 1 ? net.width[l + 1] : 0;
-    relu_mask_kernel<<<blocks_for(npx * c), 256, 0, st>>>(npx, c, P.G1[l], c, s_act, s_ld, s_off, P.G2[l]);
+    relu_mask_kernel<<<blocks_for(npx * c), 256, 0, st>>>(npx, c, P.G1[l], c, s_act, s_ld, s_off, P.G2[l], P.GB[l]);
     RBGS_LAUNCH_CHECK();
     if ((s = wgrad<__nv_bfloat16>(Nl, B, c, c, P.A[l], c, 0, P.G2[l], grads + lb.w_off, grads + lb.b_off, st)))
       return s;
-    if ((s = dgrad(Nl, B, c, c, params + lb.w_off, P.wd, P.G2[l], P.G3[l], st))) return s;  // g(A_l)
-    relu_mask_kernel<<<blocks_for(npx * c), 256, 0, st>>>(npx, c, P.G3[l], c, P.A[l], c, 0, P.G1[l]);
+    if ((s = dgrad_any(net, P, Nl, B, c, c, params + lb.w_off, P.G2[l], P.GB[l], P.G3[l], st))) return s;  // g(A_l)
+    relu_mask_kernel<<<blocks_for(npx * c), 256, 0, st>>>(npx, c, P.G3[l], c, P.A[l], c, 0, P.G1[l], P.GB[l]);
     RBGS_LAUNCH_CHECK();
     if (l == 0) {
       if ((s = wgrad<float>(Nl, B, 1, c, x, 1, 0, P.G1[0], grads + la.w_off, grads + la.b_off, st))) return s;
@@ -785,10 +839,20 @@ rbgs_status backward(NetBuf& nb, const float* params, const float* gy, float* gr
       const int cp = net.width[l - 1];
       if ((s = wgrad<__nv_bfloat16>(Nl, B, cp, c, P.X[l], cp, 0, P.G1[l], grads + la.w_off, grads + la.b_off, st)))
         return s;
-      if ((s = dgrad(Nl, B, cp, c, params + la.w_off, P.wd, P.G1[l], P.G2[l], st))) return s;  // g(x_l) in G2[l]
+      if ((s = dgrad_any(net, P, Nl, B, cp, c, params + la.w_off, P.G1[l], P.GB[l], P.G2[l], st))) return s;
     }
   }
   return RBGS_OK;
+}
+
+// With sync: wait, and report an expired bounded wait of the tensor-core
+// kernels (their flag) as RBGS_ETIMEOUT.
+rbgs_status finish(NetBuf& nb, cudaStream_t st, int sync) {
+  if (!sync) return RBGS_OK;
+  int herr = 0;
+  RBGS_CUDA_TRY(cudaMemcpyAsync(&herr, nb.plan.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBGS_CUDA_TRY(cudaStreamSynchronize(st));
+  return herr ? RBGS_ETIMEOUT : RBGS_OK;
 }
 
 }  // namespace
@@ -868,8 +932,7 @@ rbgs_status rbgs_unet_forward(const rbgs_unet* net, const float* params, int64_t
   if ((s = net_buffer(save ? 0 : 1, *net, (int)N, (int)batch, save != 0, &nb))) return s;
   if ((s = forward(*nb, params, x, N * N, y, N * N, st))) return s;
   nb->saved = save != 0;
-  if (sync) RBGS_CUDA_TRY(cudaStreamSynchronize(st));
-  return RBGS_OK;
+  return finish(*nb, st, sync);
 }
 
 rbgs_status rbgs_unet_backward(const rbgs_unet* net, const float* params, int64_t N, int64_t batch, const float* x,
@@ -891,8 +954,7 @@ rbgs_status rbgs_unet_backward(const rbgs_unet* net, const float* params, int64_
   cudaStream_t st = (cudaStream_t)stream;
   rbgs_status s = backward(*nb, params, gy, grads, x, st);
   if (s) return s;
-  if (sync) RBGS_CUDA_TRY(cudaStreamSynchronize(st));
-  return RBGS_OK;
+  return finish(*nb, st, sync);
 }
 
 rbgs_status rbgs_unet_residual_loss(int64_t N, int64_t batch, const double* coef, int64_t coef_stride,

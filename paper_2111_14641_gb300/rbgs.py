@@ -59,13 +59,14 @@ class Op(ctypes.Structure):
 
 
 class UNet(ctypes.Structure):
-    """rbgs_unet: the levels and per-level widths of the U-Net preconditioner."""
-    _fields_ = [("levels", ctypes.c_int32), ("width", ctypes.c_int32 * 6)]
+    """rbgs_unet: the levels and per-level widths of the U-Net preconditioner;
+    flags bit 0 keeps every convolution on the SIMT kernels."""
+    _fields_ = [("levels", ctypes.c_int32), ("width", ctypes.c_int32 * 6), ("flags", ctypes.c_int32)]
 
 
-def unet_shape(widths) -> UNet:
+def unet_shape(widths, simt: bool = False) -> UNet:
     w = (ctypes.c_int32 * 6)(*([int(x) for x in widths] + [0] * (6 - len(widths))))
-    return UNet(len(widths), w)
+    return UNet(len(widths), w, 1 if simt else 0)
 
 
 def stencil_op(nx: int, ny: int, bx: float, by: float) -> Op:
@@ -167,6 +168,8 @@ def load(build_if_missing: bool = False):
     lib.rbgs_qr_graph_create.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
                                          ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]
     lib.rbgs_qr_graph_launch.argtypes = [vp, vp, i32]
+    lib.rbgs_qr_batched_graph_create.argtypes = [ctypes.POINTER(Problem), i64, ctypes.c_int, ctypes.POINTER(Opts),
+                                                 i32, ctypes.POINTER(ctypes.c_void_p)]
     lib.rbgs_qr_graph_destroy.argtypes = [vp]
     lib.rbgs_qr_host.argtypes = [vp, i64, i64, i64, i64, ctypes.c_int, i64, u64, vp, i64, vp, i64,
                                  ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
@@ -317,6 +320,57 @@ class QRGraph:
     def launch(self, stream=None, sync: bool = True):
         _check(load().rbgs_qr_graph_launch(self._h, _stream_ptr(stream), int(sync)), "rbgs_qr_graph_launch")
         return self.Q, self.R
+
+    def destroy(self):
+        if self._h:
+            load().rbgs_qr_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class BatchedQRGraph:
+    """rbgs_qr_batched captured once as one CUDA graph on fixed W, Q, R of every
+    problem (column-major CUDA tensors, kept alive by this object); launch()
+    replays the whole batch with one graph launch and returns (Qs, Rs,
+    statuses, passes2)."""
+
+    def __init__(self, Ws: list, mbs, ks, seeds, sketch: str = "gauss", prec: str | None = None, ls_iters: int = 2,
+                 reorth: int = 0, reorth_tol: float = 1e-8, fine: bool = False, interblock: int = 5,
+                 nstreams: int = 8, trsm: bool = False):
+        lib = load()
+        cnt = len(Ws)
+        pick = (lambda v, i: v[i] if isinstance(v, (list, tuple)) else v)
+        prec = _prec_of(Ws[0], prec)
+        self.Ws = list(Ws)
+        self.Qs = [_empty_cols(W.shape[0], W.shape[1], W.dtype, W.device) for W in Ws]
+        self.Rs = [torch.empty((W.shape[1], W.shape[1]), dtype=torch.float64, device=W.device).t() for W in Ws]
+        self.probs = (Problem * cnt)()
+        for i, W in enumerate(Ws):
+            n, m = W.shape
+            self.probs[i] = Problem(W.data_ptr(), n, m, _ld(W, "W"), int(pick(mbs, i)), int(pick(ks, i)),
+                                    int(pick(seeds, i)), self.Qs[i].data_ptr(), _ld(self.Qs[i], "Q"),
+                                    self.Rs[i].data_ptr(), _ld(self.Rs[i], "R"), 0, 0)
+        o = Opts()
+        lib.rbgs_opts_default(ctypes.byref(o))
+        o.prec, o.ls_iters, o.reorth, o.reorth_tol = PREC[prec], ls_iters, reorth, reorth_tol
+        o.fine, o.interblock, o.trsm = int(fine), int(interblock), int(bool(trsm))
+        h = ctypes.c_void_p()
+        _check(lib.rbgs_qr_batched_graph_create(self.probs, cnt, SKETCH[sketch], ctypes.byref(o), int(nstreams),
+                                                ctypes.byref(h)), "rbgs_qr_batched_graph_create")
+        self._h = h
+        self.count = cnt
+
+    def launch(self, stream=None, sync: bool = True):
+        code = load().rbgs_qr_graph_launch(self._h, _stream_ptr(stream), int(sync))
+        if code not in (0, 4, 6):
+            _check(code, "rbgs_qr_graph_launch")
+        return (self.Qs, self.Rs, [int(self.probs[i].status) for i in range(self.count)],
+                [int(self.probs[i].passes2) for i in range(self.count)])
 
     def destroy(self):
         if self._h:
@@ -611,25 +665,25 @@ def unet_num_params(widths) -> int:
 
 
 def unet_forward(widths, params: torch.Tensor, N: int, x: torch.Tensor, save: bool = False, stream=None,
-                 sync: bool = True) -> torch.Tensor:
+                 sync: bool = True, simt: bool = False) -> torch.Tensor:
     """y = U-Net(x) for the columns of x (N^2 x batch, float32)."""
     lib = load()
     b = _images(x, N * N, "x")
     y = torch.empty((b, N * N), dtype=torch.float32, device=x.device).t()
-    _check(lib.rbgs_unet_forward(ctypes.byref(unet_shape(widths)), params.data_ptr(), N, b, x.data_ptr(),
+    _check(lib.rbgs_unet_forward(ctypes.byref(unet_shape(widths, simt)), params.data_ptr(), N, b, x.data_ptr(),
                                  y.data_ptr(), int(save), _stream_ptr(stream), int(sync)), "rbgs_unet_forward")
     return y
 
 
 def unet_backward(widths, params: torch.Tensor, N: int, x: torch.Tensor, gy: torch.Tensor,
-                  grads: torch.Tensor | None = None, stream=None, sync: bool = True) -> torch.Tensor:
+                  grads: torch.Tensor | None = None, stream=None, sync: bool = True, simt: bool = False) -> torch.Tensor:
     """d sum(gy * y) / d params of the last forward with save=True."""
     lib = load()
     b = _images(x, N * N, "x")
     _images(gy, N * N, "gy")
     if grads is None:
         grads = torch.empty(params.numel(), dtype=torch.float32, device=params.device)
-    _check(lib.rbgs_unet_backward(ctypes.byref(unet_shape(widths)), params.data_ptr(), N, b, x.data_ptr(),
+    _check(lib.rbgs_unet_backward(ctypes.byref(unet_shape(widths, simt)), params.data_ptr(), N, b, x.data_ptr(),
                                   gy.data_ptr(), grads.data_ptr(), _stream_ptr(stream), int(sync)),
            "rbgs_unet_backward")
     return grads

@@ -134,3 +134,31 @@ def test_graph_refuses_the_column_by_column_variants(rb):
     Wd = dev(synth.gaussian(2000, 16, 3))
     with pytest.raises(rb.RbgsError):
         rb.QRGraph(Wd, 4, "gauss", 32, 0, prec="fp64", interblock=3)
+
+
+@pytest.mark.parametrize("prec,interblock,trsm", [("fp64", 5, False), ("f16x3", 5, False), ("f16x3", 4, True)])
+@pytest.mark.parametrize("nstreams", [1, 4])
+def test_batched_graph_replays_the_batch(rb, prec, interblock, trsm, nstreams):
+    """The batch captured as one CUDA graph: a replay gives the batched call's
+    results bit for bit, and a replay after new contents of every W gives the
+    factorization of the new matrices (again equal to the batched call)."""
+    td = torch.float64 if prec == "fp64" else torch.float32
+    Wd = [dev(synth.svd_matrix(n, m, 1e3, 60 + i), td) for i, (n, m, _) in enumerate(SHAPES)]
+    mbs = [mb for _, _, mb in SHAPES]
+    ks = [2 * m for _, m, _ in SHAPES]
+    seeds = [300 + i for i in range(len(SHAPES))]
+    kw = dict(ls_iters=1, reorth=1, fine=2 if prec != "fp64" else 0, interblock=interblock, trsm=trsm)
+    g = rb.BatchedQRGraph(Wd, mbs, ks, seeds, "gauss", prec=prec, nstreams=nstreams, **kw)
+    for round_ in range(2):
+        if round_:
+            for i, (n, m, _) in enumerate(SHAPES):
+                Wd[i].copy_(dev(synth.svd_matrix(n, m, 1e2, 90 + i), td))
+        Qg, Rg, st, p2 = g.launch()
+        Qs = [q.clone() for q in Qg]
+        Rs = [r.clone() for r in Rg]
+        assert st == [0] * len(SHAPES)
+        Qb, Rb, stb, _ = rb.rbgs_qr_batched(Wd, mbs, ks, seeds, "gauss", prec=prec, nstreams=nstreams, **kw)
+        assert stb == [0] * len(SHAPES)
+        for i in range(len(SHAPES)):
+            assert torch.equal(Qs[i], Qb[i]) and torch.equal(Rs[i], Rb[i]), (round_, i)
+    g.destroy()

@@ -156,6 +156,53 @@ def test_unet_backward_matches_oracle(rb):
     assert worst16 <= 0.5 * worst64
 
 
+@pytest.mark.parametrize("N,batch", [(128, 2), (256, 1)])
+def test_tensor_core_forward_matches_simt_and_oracle(rb, N, batch):
+    """At N >= 128 the levels with 128-pixel rows run their convolutions on the
+    tcgen05 tensor cores (bfloat16 operands, FP32 accumulators in tensor
+    memory): against the SIMT kernels (the same roundings, another summation
+    order) and, at N = 128, against the oracle's bf16 network."""
+    P, flat, X = _net_case(N, batch, 12)
+    pd = torch.from_numpy(flat).cuda()
+    xd = cols(X, torch.float32)
+    Ytc = rb.unet_forward(WIDTHS, pd, N, xd).double().cpu().numpy()
+    Ysi = rb.unet_forward(WIDTHS, pd, N, xd, simt=True).double().cpu().numpy()
+    for b in range(batch):
+        e = relnorm(Ytc[:, b], Ysi[:, b])
+        print(f"[unet tc fwd] N {N} image {b}: tensor cores vs SIMT {e:.2e}")
+        assert e <= 1e-2
+    if N == 128:
+        ref16 = L.unet_forward_levels(P, _img(X[:, 0], N), WIDTHS, bf16=True)[0].reshape(-1, order="F")
+        ref64 = L.unet_forward_levels(P, _img(X[:, 0], N), WIDTHS)[0].reshape(-1, order="F")
+        e16, e64 = relnorm(Ytc[:, 0], ref16), relnorm(Ytc[:, 0], ref64)
+        print(f"[unet tc fwd] N {N}: vs bf16 oracle {e16:.2e}, vs fp64 oracle {e64:.2e}")
+        assert e16 <= 1e-2 and e16 <= 0.5 * e64
+
+
+def test_tensor_core_backward_matches_simt_and_oracle(rb):
+    """Parameter gradients with the tensor-core forward and backward
+    convolutions (levels of 128 and more pixels per row) against the SIMT
+    path, and against the oracle's bf16 backward, per layer."""
+    N, batch = 128, 1
+    P, flat, X = _net_case(N, batch, 13)
+    gy = np.random.default_rng(4).standard_normal((N * N, batch)).astype(np.float32)
+    pd = torch.from_numpy(flat).cuda()
+    xd, gyd = cols(X, torch.float32), cols(gy, torch.float32)
+    rb.unet_forward(WIDTHS, pd, N, xd, save=True)
+    Gtc = synth.unet_dict_params(rb.unet_backward(WIDTHS, pd, N, xd, gyd).cpu().numpy(), WIDTHS)
+    rb.unet_forward(WIDTHS, pd, N, xd, save=True, simt=True)
+    Gsi = synth.unet_dict_params(rb.unet_backward(WIDTHS, pd, N, xd, gyd, simt=True).cpu().numpy(), WIDTHS)
+    x = _img(X[:, 0], N)
+    g16, _ = L.unet_backward_levels(P, L.unet_forward_levels(P, x, WIDTHS, bf16=True)[1],
+                                    _img(gy[:, 0].astype(np.float64), N), WIDTHS, bf16=True)
+    worst_si = worst_or = 0.0
+    for k in P:
+        es, eo = relnorm(Gtc[k], Gsi[k]), relnorm(Gtc[k], g16[k])
+        worst_si, worst_or = max(worst_si, es), max(worst_or, eo)
+        assert es <= 0.05 and eo <= 0.05, (k, es, eo)
+    print(f"[unet tc bwd] worst layer: vs SIMT {worst_si:.2e}, vs bf16 oracle {worst_or:.2e}")
+
+
 def test_backward_needs_a_saved_forward(rb):
     N = 16
     flat = synth.unet_flat_params(synth.unet_params_levels(WIDTHS, 1), WIDTHS)

@@ -311,8 +311,8 @@ def test_rbgs_alg4_triangular_solve_matches_oracle(rb, prec, reorth):
         assert_factor_parity(Q, R, ref["Q"], ref["R"], U32, label=f"alg4 trsm {prec} reorth {reorth}")
 
 
-@pytest.mark.parametrize("prec", ["f16x3", "fp64"])
-def test_triangular_solve_keeps_near_duplicate_columns_well_conditioned(rb, prec):
+@pytest.mark.parametrize("prec,fine", [("f16x3", 1), ("f16x3", 2), ("fp64", 0)])
+def test_triangular_solve_keeps_near_duplicate_columns_well_conditioned(rb, prec, fine):
     """Columns that nearly repeat earlier ones at the FP32 rounding level (the
     many-small-problems workload) make a block's R_ii about as ill-conditioned
     as 1/u_32.  With the explicit inverse the mixed path loses W = QR and
@@ -327,7 +327,7 @@ def test_triangular_solve_keeps_near_duplicate_columns_well_conditioned(rb, prec
     out = {}
     for trsm in (True, False):
         Q, R, st = rb.rbgs_qr(W, mb, "gauss", 2 * m, 7, prec=prec, ls_iters=1, reorth=1, interblock=4, trsm=trsm,
-                              fine=prec != "fp64")
+                              fine=fine)
         Qh, Rh = host(Q), host(R)
         sv = np.linalg.svd(Qh, compute_uv=False)
         out[trsm] = (oracle.factorization_error(Wh, Qh, Rh), sv[0] / sv[-1])
@@ -575,14 +575,15 @@ def test_rbgs_f16x3_matches_oracle(rb, n, m, mb, kind, k, reorth, fine):
 # ------------------------------------- several 128-row tiles per CTA --
 
 @pytest.mark.parametrize("prec", ["f16x3", "tf32x3"])
-@pytest.mark.parametrize("fine", [True, False])
+@pytest.mark.parametrize("fine", [True, False, 2])
 @pytest.mark.parametrize("reorth", [0, 1])
 def test_rbgs_tensor_core_tile_walk_matches_oracle(rb, prec, fine, reorth):
     """n = 65,536 rows: 512 tiles of 128 rows over 152 persistent CTAs, so every
     CTA walks three or four tiles and its copy/MMA rings wrap across tiles;
     m = 300 with m_p = 50 gives up to four 64-column basis chunks per tile
     (and block starts that do not fall on chunk boundaries).  Element-wise
-    parity of Q and R with the oracle's Alg. 2 / Alg. 5 in FP64."""
+    parity of Q and R with the oracle's Alg. 2 / Alg. 5 in FP64.  fine = 2
+    takes the FP64 sketch space's products in double-FP32 arithmetic."""
     n, m, mb, kind, k = 65536, 300, 50, "srht", 600
     cond = 1e3
     oracle.set_threads(os.cpu_count() or 1)
@@ -693,7 +694,8 @@ def test_c2_full_size_fp64_matches_oracle(rb, c2_golden, c2_matrix):
     torch.cuda.empty_cache()
 
 
-def test_c2_full_size_mixed_matches_oracle(rb, c2_golden, c2_matrix):
+@pytest.mark.parametrize("fine", [1, 2])
+def test_c2_full_size_mixed_matches_oracle(rb, c2_golden, c2_matrix, fine):
     """The mixed path at the full size in the launch configuration bench.py
     times (F16X3 tall products, FP64 sketch space, one Richardson iteration,
     second pass on every block) against the same stored oracle run: sampled
@@ -704,13 +706,13 @@ def test_c2_full_size_mixed_matches_oracle(rb, c2_golden, c2_matrix):
     g = c2_golden
     W = c2_matrix
     Q, R, st = rb.rbgs_qr(W, g["mb"], g["sketch"], g["k"], g["seed_theta"], prec="f16x3", ls_iters=1, reorth=1,
-                          fine=True)
+                          fine=fine)
     assert st.passes2 == g["m"] // g["mb"] - 1
     Rh = R.cpu().numpy()
     assert np.allclose(np.tril(Rh, -1), 0.0) and np.all(np.diag(Rh) > 0)
-    _compare_c2(Q, R, g, U32, "c2 f16x3")
+    _compare_c2(Q, R, g, U32, f"c2 f16x3 fine {fine}")
     fact, d_fro, d_two = _c2_quality(W, Q, R, g)
-    print(f"[quality] c2 f16x3: ||W-QR||/||W|| {fact:.3e}, Delta_F {d_fro:.3e}, Delta_2 {d_two:.3e}")
+    print(f"[quality] c2 f16x3 fine {fine}: ||W-QR||/||W|| {fact:.3e}, Delta_F {d_fro:.3e}, Delta_2 {d_two:.3e}")
     assert fact <= 1e-6
     assert d_two <= 1e-6
     assert d_fro <= 2e-5
