@@ -508,7 +508,7 @@ def run_ours(args, cfg):
     if rank == 0 and world == 1 and not args.no_batched:
         line["batched_c3"] = batched_c3(rb, dev, prec if prec != "fp64" else "f16x3")
     if rank == 0 and world == 1 and not args.no_learned:
-        line["learned_c5"] = learned_c5(rb, dev, C5_FULL if args.c5_full else C5_DEFAULT)
+        line["learned_c5"] = learned_c5(rb, dev, C5_FULL if args.c5_full else C5_SHORT if args.c5_short else C5_DEFAULT)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(cfg, args.ls_iters, args.reorth, one_core=True)
@@ -576,7 +576,7 @@ def eigvec_condition_log10(nx, ny, bx, by):
     return (nx / 2.0) * math.log10((1 + px) / (1 - px)) + (ny / 2.0) * math.log10((1 + py) / (1 - py))
 
 
-def ritz_smallest(rb, nx, ny, bx, by, mb, p, iters, prec, fine, dev, nev=20, tol=None):
+def ritz_smallest(rb, nx, ny, bx, by, mb, p, iters, prec, fine, dev, nev=20, tol=None, interblock=4, trsm=True):
     """Alg. 8 with which = smallest real part on the stencil operator, restarted
     one iteration at a time from the previous X (the restart block of step 4),
     stopping after `iters` iterations or when every one of the nev smallest
@@ -596,7 +596,7 @@ def ritz_smallest(rb, nx, ny, bx, by, mb, p, iters, prec, fine, dev, nev=20, tol
     done = 0
     for it in range(iters):
         vals, X, res = rb.rayleigh_ritz(op, B, p=p, n_iter=1, which="SR", sketch="srht", k=k, seed=1, prec=prec,
-                                        ls_iters=1, reorth=1, fine=fine)
+                                        ls_iters=1, reorth=1, fine=fine, interblock=interblock, trsm=trsm)
         B = X
         done = it + 1
         order = sorted(range(mb), key=lambda j: vals[j].real)[:nev]
@@ -609,6 +609,7 @@ def ritz_smallest(rb, nx, ny, bx, by, mb, p, iters, prec, fine, dev, nev=20, tol
     got = [vals[j] for j in order]
     rel = [abs(v - e) / abs(e) for v, e in zip(got, exact)]
     return {"grid": [nx, ny], "b": [bx, by], "block": mb, "blocks_per_iteration": p, "k": k, "prec": prec,
+            "interblock": interblock, "trsm": trsm,
             "iterations": done, "s_per_iteration": dt / done,
             "ritz_values": [[v.real, v.imag] for v in got], "exact": exact,
             "rel_error": rel, "max_rel_error": max(rel),
@@ -629,7 +630,11 @@ def krylov_c4(rb, dev, prec):
     blocks per iteration, restarted) on the same operator, with each Ritz
     value's error against the closed-form spectrum; and the same on a 64 x 64
     grid with b = (10, 5), where the eigenproblem is well conditioned enough
-    for the Ritz values to converge to the closed form."""
+    for the Ritz values to converge to the closed form.  Alg. 8 runs the
+    Arnoldi steps with Alg. 4 and the row-wise triangular solve: once Ritz
+    vectors converge, the restart block spans a nearly invariant subspace, the
+    next Krylov block is numerically rank deficient, and the explicit
+    R_ii^{-1} of Alg. 5 then loses the basis."""
     import torch
 
     nx = ny = 1024
@@ -675,7 +680,8 @@ def krylov_c4(rb, dev, prec):
     rr["note"] = ("at 1024^2 the eigenvector matrix of this non-normal operator has condition up to "
                   f"1e{eigvec_condition_log10(1024, 1024, 100.0, 50.0):.0f}, and the 20 smallest eigenvalues are "
                   "3.5e-6 of the spectral range apart, so restarted Ritz values approach them slowly")
-    rr["converged_64x64_b10_5"] = guarded(rb, 64, 64, 10.0, 5.0, 24, 11, 150, prec, FINE_MIXED, dev, tol=1e-8)
+    rr["converged_64x64_b10_5"] = guarded(rb, 64, 64, 10.0, 5.0, 24, 11, 60, prec, FINE_MIXED, dev, tol=1e-8)
+    rr["converged_64x64_b10_5_fp64"] = guarded(rb, 64, 64, 10.0, 5.0, 24, 11, 60, "fp64", 0, dev, tol=1e-10)
     out["rayleigh_ritz"] = rr
     return out
 
@@ -771,6 +777,8 @@ def batched_c3(rb, dev, prec, count=32, sample=8):
 C5_FULL = dict(N=512, mb=4, widths=(16, 32, 64, 64), train_fields=200, pairs_per_field=100, steps=12000,
                test_fields=50, p=40, kfac=4, max_cycles=200, batch=16, lr=1e-3, basis="f16x3")
 C5_DEFAULT = dict(C5_FULL, train_fields=24, steps=2500, test_fields=3, max_cycles=60)
+# a few training steps and one short solve: the kernels at the configured sizes, for profiler captures
+C5_SHORT = dict(C5_FULL, train_fields=1, pairs_per_field=8, steps=20, test_fields=1, max_cycles=2)
 
 
 def learned_c5(rb, dev, cfg):
@@ -819,10 +827,11 @@ def learned_c5(rb, dev, cfg):
     xab, fab, xc, fc = [], [], [], []
     nblk = (ppf + mb - 1) // mb + 1
     kw = dict(sketch="srht", seed=1, prec=basis, ls_iters=1, reorth=1, fine=FINE_MIXED)
+    bdt = torch.float64 if basis == "fp64" else torch.float32  # the Arnoldi basis's storage type
     for f in range(F):
         coef[f] = field(5000 + f)
         op = rb.diffusion_op(N, N, coef[f])
-        B = torch.randn((mb, n), generator=g, device=dev, dtype=torch.float32).t()
+        B = torch.randn((mb, n), generator=g, device=dev, dtype=bdt).t()
         Q, _ = rb.block_arnoldi(op, B, p=nblk, k=2 * nblk * mb, **kw)
         xab.append(rb.unet_scale_inputs(Q[:, :ppf]))
         fab += [f] * ppf
@@ -832,7 +841,7 @@ def learned_c5(rb, dev, cfg):
         for target in (5, 20):
             X, _, _, _ = rb.block_fgmres(op, None, None, B64, X, p=20, rtol=0.0, max_cycles=target - done, k=160, **kw)
             done = target
-            R = rb.colmajor((B64 - rb.op_apply(op, X)).float())
+            R = rb.colmajor((B64 - rb.op_apply(op, X)).to(bdt))
             Q, _ = rb.block_arnoldi(op, R, p=20, k=160, **kw)
             xab.append(rb.unet_scale_inputs(Q))
             fab += [f] * Q.shape[1]
@@ -980,6 +989,9 @@ def main(argv=None):
     ap.add_argument("--c5-full", action="store_true",
                     help="learned preconditioner at the configured sizes (200 training fields x 100 pairs, "
                          "50 unseen fields; tens of minutes) instead of the reduced default")
+    ap.add_argument("--c5-short", action="store_true",
+                    help="learned preconditioner with one training field, 20 steps and a 2-cycle solve (the "
+                         "kernels at the configured sizes, for profiler captures)")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (smaller cases for profiler captures; recorded in config.workload)")
     args = ap.parse_args(argv)

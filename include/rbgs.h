@@ -92,7 +92,8 @@ typedef struct {
                           step-2 least squares, block Cholesky QR, R) in FP64 (the
                           paper's u_fine); 2 = the same, with the sketch-space products
                           in double-FP32 arithmetic on the FP32 pipe (about 2^-44
-                          relative; GB300's FP64 pipe is narrow); 0 = in FP32         */
+                          relative; GB300's FP64 pipe is narrow); the dense sketches
+                          still sum in FP64; 0 = in FP32                              */
   int32_t interblock;  /* steps 4-5: 0 or 5 = Alg. 5 (the sketch of Q'_i taken implicitly as
                           P_i - S R, one tall pass per block); 4 = Alg. 4 (RCholeskyQR on
                           the explicit sketch Theta Q'_i: the projection, a sketch, and an

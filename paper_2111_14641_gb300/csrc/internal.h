@@ -122,9 +122,9 @@ rbgs_status small_gemm(int trans, int64_t M, int64_t N, int64_t K, double alpha,
                        const TA* B, int64_t ldb, double beta, TO* out, int64_t ldo, TACC* part, int64_t part_elems,
                        const int* active, cudaStream_t st);
 // While an instance is alive on this host thread, the FP64 small products
-// and the FP64 sums of the dense sketches of FP32 data run in double-FP32
-// arithmetic on the FP32 pipe (about 2^-44 relative): the mixed-precision
-// path's FP64 sketch space with opts.fine = 2.  The FP64 path never sets it.
+// run in double-FP32 arithmetic on the FP32 pipe (about 2^-44 relative): the
+// mixed-precision path's FP64 sketch space with opts.fine = 2.  The dense
+// sketches keep their FP64 sums.  The FP64 path never sets it.
 extern thread_local int g_df_products;
 struct DfProducts {
   explicit DfProducts(bool on);

@@ -863,115 +863,6 @@ __global__ void __launch_bounds__(kDenseThreads) dense_sketch_part(const TX* __r
     }
 }
 
-// The same dense sketch of FP32 data with double-FP32 sums: every Theta entry
-// (computed in FP64 as above) is split once as t = t_hi + t_lo (two floats),
-// each product t_hi x is formed exactly with its FMA error term, t_lo x is
-// added into that error, and the running sum (s_hi, s_lo) is kept by TwoSum.
-// About 2^-44 relative, for FP64 sketches of FP32 data at FP32-pipe rates.
-template <int KIND>
-__global__ void __launch_bounds__(kDenseThreads) dense_sketch_part_df(const float* __restrict__ X, int64_t ldx,
-                                                                      int64_t n, int ncols, int64_t k, uint2 key,
-                                                                      double scale, int64_t rows_per_split,
-                                                                      double* __restrict__ part, const int* active) {
-  if (active && *active == 0) return;
-  __shared__ float2 th[kDenseRows][kDenseJ + 1];
-  __shared__ float xs[kDenseJ][kDenseCols + 1];
-  const int tid = threadIdx.x;
-  const int64_t r0 = (int64_t)blockIdx.x * kDenseRows;
-  const int split = blockIdx.y;
-  const int64_t j0 = (int64_t)split * rows_per_split;
-  const int64_t j1 = min(n, j0 + rows_per_split);
-  const int tr = tid & 15, tc = tid >> 4;
-  auto split2 = [](double v) {
-    const float hi = (float)v;
-    return make_float2(hi, (float)(v - (double)hi));
-  };
-  float hi[4][4], lo[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) hi[i][q] = lo[i][q] = 0.f;
-  for (int64_t jj0 = j0; jj0 < j1; jj0 += kDenseJ) {
-    if (KIND == RBGS_SK_GAUSS) {
-      for (int p = tid; p < (kDenseRows / 2) * kDenseJ; p += kDenseThreads) {
-        const int rpl = p & 31, jl = p >> 5;
-        const int64_t j = jj0 + jl;
-        const int64_t rr = r0 + 2 * rpl;
-        double z0 = 0.0, z1 = 0.0;
-        if (j < j1 && rr < k) gauss_pair(key, j, (uint32_t)(rr >> 1), z0, z1);
-        th[2 * rpl][jl] = split2(z0 * scale);
-        th[2 * rpl + 1][jl] = split2(z1 * scale);
-      }
-    } else if (KIND == RBGS_SK_SPARSE) {
-      if (tid < kDenseJ) {
-        const int64_t j = jj0 + tid;
-        for (int rl = 0; rl < kDenseRows; ++rl) th[rl][tid] = make_float2(0.f, 0.f);
-        if (j < j1) {
-          int64_t rows[8];
-          bool neg[8];
-          const int z = sparse_column(key, j, k, rows, neg);
-#pragma unroll
-          for (int s = 0; s < 8; ++s) {
-            if (s < z) {
-              const int64_t rl = rows[s] - r0;
-              if (rl >= 0 && rl < kDenseRows) th[rl][tid] = split2(neg[s] ? -scale : scale);
-            }
-          }
-        }
-      }
-    } else {
-      if (tid < kDenseJ) {
-        const int64_t j = jj0 + tid;
-        uint4 bits = make_uint4(0, 0, 0, 0);
-        if (j < j1) bits = rademacher_bits(key, j, (uint32_t)(r0 >> 7));
-        const int off = (int)(r0 & 127);
-        for (int rl = 0; rl < kDenseRows; ++rl) {
-          const int rb = off + rl;
-          const uint32_t b = (word_of(bits, rb >> 5) >> (rb & 31)) & 1u;
-          th[rl][tid] = (j < j1) ? split2(b ? -scale : scale) : make_float2(0.f, 0.f);
-        }
-      }
-    }
-    for (int e = tid; e < kDenseJ * kDenseCols; e += kDenseThreads) {
-      const int jl = e % kDenseJ, c = e / kDenseJ;
-      const int64_t j = jj0 + jl;
-      xs[jl][c] = (c < ncols && j < j1) ? X[j + (int64_t)c * ldx] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int jl = 0; jl < kDenseJ; ++jl) {
-      float2 a[4];
-      float b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = th[tr + 16 * i][jl];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = xs[jl][tc + 16 * q];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float pr = a[i].x * b[q];
-          float e = fmaf(a[i].x, b[q], -pr);
-          e = fmaf(a[i].y, b[q], e);
-          const float s = hi[i][q] + pr;
-          const float bp = s - hi[i][q];
-          const float err = (hi[i][q] - (s - bp)) + (pr - bp);
-          hi[i][q] = s;
-          lo[i][q] += err + e;
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t r = r0 + tr + 16 * i;
-      const int c = tc + 16 * q;
-      if (r < k && c < ncols) part[((int64_t)split * ncols + c) * k + r] = (double)hi[i][q] + (double)lo[i][q];
-    }
-}
-
 template <class TC, class TY>
 __global__ void dense_sketch_reduce(const TC* __restrict__ part, int nsplit, int64_t k, int ncols,
                                     TY* __restrict__ Y, int64_t ldy, const int* active) {
@@ -1146,27 +1037,6 @@ rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed
     const size_t need = sizeof(TC) * (size_t)nsplit * nc * (size_t)k;
     if (scratch_bytes < need) return RBGS_EINVAL;
     dim3 grid((unsigned)((k + kDenseRows - 1) / kDenseRows), (unsigned)nsplit);
-    if constexpr (sizeof(TX) == 4 && sizeof(TC) == 8) {
-      if (g_df_products) {
-        const float* Xc = reinterpret_cast<const float*>(X + c0 * ldx);
-        double* pd = reinterpret_cast<double*>(part);
-        if (kind == RBGS_SK_GAUSS)
-          dense_sketch_part_df<RBGS_SK_GAUSS><<<grid, kDenseThreads, 0, st>>>(Xc, ldx, n, nc, k, key, dscale,
-                                                                              rows_per_split, pd, active);
-        else if (kind == RBGS_SK_SPARSE)
-          dense_sketch_part_df<RBGS_SK_SPARSE><<<grid, kDenseThreads, 0, st>>>(Xc, ldx, n, nc, k, key, dscale,
-                                                                               rows_per_split, pd, active);
-        else
-          dense_sketch_part_df<RBGS_SK_RADEMACHER><<<grid, kDenseThreads, 0, st>>>(Xc, ldx, n, nc, k, key, dscale,
-                                                                                   rows_per_split, pd, active);
-        RBGS_LAUNCH_CHECK();
-        const int64_t tot = k * nc;
-        dense_sketch_reduce<TC, TY><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nsplit, k, nc, Y + c0 * ldy,
-                                                                                   ldy, active);
-        RBGS_LAUNCH_CHECK();
-        continue;
-      }
-    }
     if (kind == RBGS_SK_GAUSS)
       dense_sketch_part<RBGS_SK_GAUSS, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
                                                                               dscale, rows_per_split, part, active);

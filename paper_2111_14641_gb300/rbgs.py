@@ -515,17 +515,19 @@ def op_apply(op: Op, X: torch.Tensor, prec: str | None = None, stream=None) -> t
     return Y
 
 
-def _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream):
+def _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream, interblock=5, trsm=False):
     o = Opts()
     load().rbgs_opts_default(ctypes.byref(o))
     o.prec, o.ls_iters, o.reorth, o.reorth_tol = PREC[prec], ls_iters, reorth, reorth_tol
     o.stream, o.fine = _stream_ptr(stream), int(fine)
+    o.interblock, o.trsm = int(interblock), int(bool(trsm))
     return o
 
 
 def block_arnoldi(op: Op, B: torch.Tensor, p: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
                   prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
-                  fine: bool = False, Q: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None):
+                  fine: bool = False, Q: torch.Tensor | None = None, R: torch.Tensor | None = None, stream=None,
+                  interblock: int = 5, trsm: bool = False):
     """Alg. 7: returns (Q, R) with A Q[:, :(p-1) mb] = Q R[:, mb:]."""
     lib = load()
     prec = _prec_of(B, prec)
@@ -536,7 +538,7 @@ def block_arnoldi(op: Op, B: torch.Tensor, p: int, sketch: str = "srht", k: int 
         Q = torch.empty((m, n), dtype=B.dtype, device=B.device).t()
     if R is None:
         R = torch.empty((m, m), dtype=torch.float64, device=B.device).t()
-    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream)
+    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream, interblock, trsm)
     st = Stats()
     _check(lib.rbgs_block_arnoldi(ctypes.byref(op), B.data_ptr(), _ld(B, "B"), mb, p, SKETCH[sketch], k, seed,
                                   Q.data_ptr(), _ld(Q, "Q"), R.data_ptr(), _ld(R, "R"), ctypes.byref(o),
@@ -546,7 +548,7 @@ def block_arnoldi(op: Op, B: torch.Tensor, p: int, sketch: str = "srht", k: int 
 
 def _block_solve(fn: str, op: Op, B: torch.Tensor, X: torch.Tensor | None, p: int, rtol: float, max_cycles: int,
                  sketch: str, k: int | None, seed: int, prec: str, ls_iters: int, reorth: int, reorth_tol: float,
-                 fine: bool, stream, raise_on_noconv: bool):
+                 fine: bool, stream, raise_on_noconv: bool, interblock: int = 5, trsm: bool = False):
     lib = load()
     n, mb = B.shape
     if B.dtype != torch.float64:
@@ -554,7 +556,7 @@ def _block_solve(fn: str, op: Op, B: torch.Tensor, X: torch.Tensor | None, p: in
     if X is None:
         X = torch.zeros((mb, n), dtype=torch.float64, device=B.device).t()
     k = 2 * p * mb if k is None else k
-    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream)
+    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream, interblock, trsm)
     cyc = ctypes.c_int64(0)
     rel = (ctypes.c_double * mb)()
     code = getattr(lib, fn)(ctypes.byref(op), B.data_ptr(), _ld(B, "B"), X.data_ptr(), _ld(X, "X"), mb, p,
@@ -569,19 +571,21 @@ def _block_solve(fn: str, op: Op, B: torch.Tensor, X: torch.Tensor | None, p: in
 def block_gmres(op: Op, B: torch.Tensor, X: torch.Tensor | None = None, p: int = 10, rtol: float = 1e-8,
                 max_cycles: int = 100, sketch: str = "srht", k: int | None = None, seed: int = 0,
                 prec: str = "fp64", ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
-                fine: bool = False, stream=None, raise_on_noconv: bool = False):
+                fine: bool = False, stream=None, raise_on_noconv: bool = False, interblock: int = 5,
+                trsm: bool = False):
     """Restarted randomized block GMRES (Sec. 5.2): returns (X, cycles, relres)."""
     return _block_solve("rbgs_block_gmres", op, B, X, p, rtol, max_cycles, sketch, k, seed, prec, ls_iters, reorth,
-                        reorth_tol, fine, stream, raise_on_noconv)
+                        reorth_tol, fine, stream, raise_on_noconv, interblock, trsm)
 
 
 def block_fom(op: Op, B: torch.Tensor, X: torch.Tensor | None = None, p: int = 10, rtol: float = 1e-8,
               max_cycles: int = 100, sketch: str = "srht", k: int | None = None, seed: int = 0,
               prec: str = "fp64", ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
-              fine: bool = False, stream=None, raise_on_noconv: bool = False):
+              fine: bool = False, stream=None, raise_on_noconv: bool = False, interblock: int = 5,
+              trsm: bool = False):
     """Restarted randomized block FOM (Sec. 5.3): returns (X, cycles, relres)."""
     return _block_solve("rbgs_block_fom", op, B, X, p, rtol, max_cycles, sketch, k, seed, prec, ls_iters, reorth,
-                        reorth_tol, fine, stream, raise_on_noconv)
+                        reorth_tol, fine, stream, raise_on_noconv, interblock, trsm)
 
 
 RITZ_WHICH = {"LR": 0, "SR": 1}
@@ -589,7 +593,8 @@ RITZ_WHICH = {"LR": 0, "SR": 1}
 
 def rayleigh_ritz(op: Op, B0: torch.Tensor, p: int = 10, n_iter: int = 1, which: str = "LR", sketch: str = "srht",
                   k: int | None = None, seed: int = 0, prec: str = "fp64", ls_iters: int = 2, reorth: int = 0,
-                  reorth_tol: float = 1e-8, fine: bool = False, X: torch.Tensor | None = None, stream=None):
+                  reorth_tol: float = 1e-8, fine: bool = False, X: torch.Tensor | None = None, stream=None,
+                  interblock: int = 5, trsm: bool = False):
     """Randomized Rayleigh-Ritz with restarting (Alg. 8, Sec. 5.4).  B0: n x mb
     float64 on the device.  Returns (values (complex, mb), X (n x mb float64,
     unit columns), resid (mb estimates ||H_(p,1:p-1) y||))."""
@@ -600,7 +605,7 @@ def rayleigh_ritz(op: Op, B0: torch.Tensor, p: int = 10, n_iter: int = 1, which:
     if X is None:
         X = torch.empty((mb, n), dtype=torch.float64, device=B0.device).t()
     k = 2 * p * mb if k is None else k
-    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream)
+    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream, interblock, trsm)
     re, im, rs = (ctypes.c_double * mb)(), (ctypes.c_double * mb)(), (ctypes.c_double * mb)()
     _check(lib.rbgs_rayleigh_ritz(ctypes.byref(op), B0.data_ptr(), _ld(B0, "B0"), mb, p, n_iter, RITZ_WHICH[which],
                                   SKETCH[sketch], k, seed, ctypes.byref(o), X.data_ptr(), _ld(X, "X"),
@@ -742,7 +747,8 @@ def unet_precondition(widths, params: torch.Tensor, N: int, Q: torch.Tensor, pre
 def block_fgmres(op: Op, widths, params: torch.Tensor | None, B: torch.Tensor, X: torch.Tensor | None = None,
                  p: int = 10, rtol: float = 1e-8, max_cycles: int = 100, accept: float = 0.9, sketch: str = "srht",
                  k: int | None = None, seed: int = 0, prec: str = "fp64", ls_iters: int = 2, reorth: int = 0,
-                 reorth_tol: float = 1e-8, fine: bool = False, stream=None):
+                 reorth_tol: float = 1e-8, fine: bool = False, stream=None, interblock: int = 5,
+                 trsm: bool = False):
     """Restarted randomized block flexible GMRES with the U-Net preconditioner
     (widths=None: plain block GMRES).  Returns (X, cycles, relres, fallbacks)."""
     lib = load()
@@ -750,7 +756,7 @@ def block_fgmres(op: Op, widths, params: torch.Tensor | None, B: torch.Tensor, X
     if X is None:
         X = torch.zeros((mb, n), dtype=torch.float64, device=B.device).t()
     k = 2 * p * mb if k is None else k
-    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream)
+    o = _krylov_opts(prec, ls_iters, reorth, reorth_tol, fine, stream, interblock, trsm)
     cyc, fb = ctypes.c_int64(0), ctypes.c_int64(0)
     rel = (ctypes.c_double * mb)()
     net = ctypes.byref(unet_shape(widths)) if widths is not None else None
