@@ -789,13 +789,16 @@ def learned_c5(rb, dev, cfg):
     Training inputs (the vectors M sees inside flexible GMRES, scaled to unit
     RMS by the library): per training field, (A) pairs_per_field columns of
     the Arnoldi basis of a plain randomized block Arnoldi run from a seeded
-    N(0,1) block; (B) the Arnoldi bases at the residuals of plain block GMRES
-    after 5 and 20 cycles (smoother: what is left once the high frequencies
-    are gone); (C) x = A e for smooth fields e (Gaussian random fields with
-    correlation lengths 0.02 .. 1.5), the smooth residuals a good network must
-    also invert.  Training: Adam on the residual-norm loss, `steps` batches of
-    `batch` pairs drawn at random, half from (A, B) and half from (C), all on
-    the GPU by the library's forward, backward, loss and Adam kernels.
+    N(0,1) block; (S) pairs_per_field residuals r_k = b - A x_k of plain
+    randomized block GMRES (restart 20 blocks) at cycles 0, 1, 2, 4, 8, 14,
+    20 and 30 of solves with b = A x*, x* smooth Gaussian random fields
+    (correlation lengths 0.02 .. 0.8): the (residual, correction) pairs
+    (r_k, x* - x_k) of the plain solver, whose later residuals are dominated
+    by the low modes the plain solver cannot remove.  Training: Adam on the
+    residual-norm loss ||B (y - B^{-1} x)|| (the correction enters through
+    B^{-1} x, so it needs no solve), `steps` batches of `batch` pairs drawn
+    at random, half from (A) and half from (S), all on the GPU by the
+    library's forward, backward, loss and Adam kernels.
     Evaluation on unseen fields: randomized block flexible GMRES with the
     network (plain GMRES as the fallback, accept 0.9) to relative residual
     1e-8 against plain randomized block GMRES with the same restart (p
@@ -828,36 +831,48 @@ def learned_c5(rb, dev, cfg):
     nblk = (ppf + mb - 1) // mb + 1
     kw = dict(sketch="srht", seed=1, prec=basis, ls_iters=1, reorth=1, fine=FINE_MIXED)
     bdt = torch.float64 if basis == "fp64" else torch.float32  # the Arnoldi basis's storage type
+    stops = (0, 1, 2, 4, 8, 14, 20, 30)  # plain-solver cycles whose residuals are kept
+    corrs = (0.02, 0.05, 0.1, 0.2, 0.4, 0.8)
     for f in range(F):
         coef[f] = field(5000 + f)
         op = rb.diffusion_op(N, N, coef[f])
+        # (A) the Arnoldi basis of a plain run from an N(0,1) block
         B = torch.randn((mb, n), generator=g, device=dev, dtype=bdt).t()
         Q, _ = rb.block_arnoldi(op, B, p=nblk, k=2 * nblk * mb, **kw)
         xab.append(rb.unet_scale_inputs(Q[:, :ppf]))
         fab += [f] * ppf
-        B64 = torch.randn((mb, n), generator=g, device=dev, dtype=torch.float64).t()
-        X = torch.zeros((mb, n), dtype=torch.float64, device=dev).t()
-        done = 0
-        for target in (5, 20):
-            X, _, _, _ = rb.block_fgmres(op, None, None, B64, X, p=20, rtol=0.0, max_cycles=target - done, k=160, **kw)
-            done = target
-            R = rb.colmajor((B64 - rb.op_apply(op, X)).to(bdt))
-            Q, _ = rb.block_arnoldi(op, R, p=20, k=160, **kw)
-            xab.append(rb.unet_scale_inputs(Q))
-            fab += [f] * Q.shape[1]
-        for corr in (0.02, 0.05, 0.1, 0.2, 0.4, 0.8, 1.5):
-            for rep in range(12):
-                e = synth.gaussian_random_field_torch(N, 777 + 100 * f + rep, corr=corr, device=dev)
-                x = rb.op_apply(op, e[1:-1, 1:-1].t().contiguous().reshape(n, 1))
-                xc.append(rb.unet_scale_inputs(x))
-                fc.append(f)
+        # (S) residuals along plain solves: x* smooth, b = A x*, r_k = b - A x_k
+        kept = 0
+        rep = 0
+        while kept < ppf:
+            cols = []
+            for jj in range(mb):
+                e = synth.gaussian_random_field_torch(N, 31000 + 100 * f + 10 * rep + jj,
+                                                      corr=corrs[(rep * mb + jj + f) % len(corrs)], device=dev)
+                cols.append(e[1:-1, 1:-1].t().contiguous().reshape(n))
+            b = rb.colmajor(rb.op_apply(op, rb.colmajor(torch.stack(cols, 1).double())))
+            X = torch.zeros((mb, n), dtype=torch.float64, device=dev).t()
+            done = 0
+            for stop in stops:
+                if stop > done:
+                    X, _, _, _ = rb.block_fgmres(op, None, None, b, X, p=20, rtol=0.0, max_cycles=stop - done, k=160,
+                                                 **kw)
+                    done = stop
+                take = min(mb, ppf - kept)
+                if take <= 0:
+                    break
+                R = rb.colmajor(b - rb.op_apply(op, X))
+                xc.append(rb.unet_scale_inputs(R[:, :take]))
+                fc += [f] * take
+                kept += take
+            rep += 1
     XA = torch.cat([x.t() for x in xab], 0).t()
     FA = torch.tensor(fab, dtype=torch.int32, device=dev)
     XC = torch.cat([x.t() for x in xc], 0).t()
     FC = torch.tensor(fc, dtype=torch.int32, device=dev)
     del xab, xc
     torch.cuda.synchronize()
-    out["pairs"] = {"arnoldi": XA.shape[1], "smooth": XC.shape[1], "s": time.perf_counter() - t0}
+    out["pairs"] = {"arnoldi": XA.shape[1], "solver_residuals": XC.shape[1], "s": time.perf_counter() - t0}
     # ---- training
     params = torch.from_numpy(synth.unet_flat_params(synth.unet_params_levels(widths, 21), widths)).to(dev)
     m1, v1 = torch.zeros_like(params), torch.zeros_like(params)

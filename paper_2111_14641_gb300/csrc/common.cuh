@@ -98,6 +98,49 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int w) {
   return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
 }
 
+// Double-FP32 ("double-float") helpers: a value is an unevaluated sum hi + lo
+// of two floats.
+//
+// df_split: v = hi + lo + d with |d| < 2^-46 |v|, from integer operations on
+// the bits of v (GB300's FP64 pipe, which also converts, is narrow).  hi is v
+// with its 52-bit fraction truncated to 23 bits; lo holds the next 23 bits of
+// the fraction, with the sign of v.  Exponents outside [-80, 127] (zero,
+// subnormals, huge values, inf, NaN) take the FP64 conversion instead.
+__device__ __forceinline__ float2 df_split(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ffu) - 1023;
+  if (ex < -80 || ex > 127) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  }
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const unsigned hi_bits = sign | ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
+  const unsigned r1 = (unsigned)(b >> 6) & 0x7fffffu;  // fraction bits 28..6
+  // r1 as a float (exact: 2^23 + r1 minus 2^23), scaled by 2^(ex - 46)
+  const float lo_mag = (__uint_as_float(0x4B000000u | r1) - 8388608.0f) * __uint_as_float((unsigned)(ex + 81) << 23);
+  return make_float2(__uint_as_float(hi_bits), __uint_as_float(__float_as_uint(lo_mag) | sign));
+}
+
+// TwoSum (Knuth): s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// acc (hi, lo) += k x for a split coefficient k = (k.x, k.y) and a float x:
+// k.x x exactly as a product and its FMA error, k.y x added to the error,
+// the product's leading part added to hi by TwoSum.
+__device__ __forceinline__ void df_fma(float2 k, float x, float& hi, float& lo) {
+  const float p = k.x * x;
+  float e = fmaf(k.x, x, -p);
+  e = fmaf(k.y, x, e);
+  float s, t;
+  df_two_sum(hi, p, s, t);
+  hi = s;
+  lo += t + e;
+}
+
 }  // namespace rbgs
 
 #define RBGS_CUDA_TRY(expr)                  \

@@ -52,6 +52,70 @@ __global__ void stencil5_kernel(int64_t nx, int64_t ny, double cx, double cy, do
   Y[i + col * ldy] = (TO)op_point(nx, ny, cx, cy, ax, ay, fc, ix, iy, c, w, e, s, no);
 }
 
+// The same operator on FP32 columns in double-FP32 arithmetic (the FP32 pipe;
+// GB300's FP64 pipe bounded the FP64 form at a small fraction of the memory
+// rate).  Each result is the FP32 rounding of a sum carried to about 2^-44 of
+// its terms' magnitudes, as the FP64 form's is.  Constant coefficients
+// (fc == null): y = k0 c + kw w + ke e + ks s + kn no with the five split
+// coefficients k (the FP64 values of the FP64 form, split on the host).
+// Face coefficients: y = sum over the four faces of (cx or cy) a_f (c - x_f),
+// each difference exact as a TwoSum pair, each face product cx a_f a
+// double-float.  Grid: x over rows of the grid, y over grid lines, z over
+// columns (no integer division).
+__global__ void __launch_bounds__(256) stencil5_df_kernel(int64_t nx, int64_t ny, float2 k0, float2 kw, float2 ke,
+                                                          float2 ks, float2 kn, float2 cxs, float2 cys,
+                                                          const double* __restrict__ fc, const float* __restrict__ X,
+                                                          int64_t ldx, float* __restrict__ Y, int64_t ldy) {
+  const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t iy = blockIdx.y;
+  if (ix >= nx) return;
+  const int64_t col = blockIdx.z;
+  const float* x = X + col * ldx;
+  const int64_t i = ix + nx * iy;
+  const float c = x[i];
+  const float w = ix > 0 ? x[i - 1] : 0.f;
+  const float e = ix + 1 < nx ? x[i + 1] : 0.f;
+  const float s = iy > 0 ? x[i - nx] : 0.f;
+  const float no = iy + 1 < ny ? x[i + nx] : 0.f;
+  float hi = 0.f, lo = 0.f;
+  if (!fc) {
+    df_fma(k0, c, hi, lo);
+    df_fma(kw, w, hi, lo);
+    df_fma(ke, e, hi, lo);
+    df_fma(ks, s, hi, lo);
+    df_fma(kn, no, hi, lo);
+  } else {
+    const double* fx = fc;
+    const double* fy = fc + (nx + 1) * (ny + 2);
+    const double af[4] = {fx[(ix + 1) + (nx + 1) * (iy + 1)], fx[ix + (nx + 1) * (iy + 1)],
+                          fy[(ix + 1) + (nx + 2) * (iy + 1)], fy[(ix + 1) + (nx + 2) * iy]};
+    const float xf[4] = {e, w, no, s};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float2 h = f < 2 ? cxs : cys;
+      const float2 a = df_split(af[f]);
+      // the face product h a as a double-float (p, q)
+      const float p = h.x * a.x;
+      float q = fmaf(h.x, a.x, -p);
+      q = fmaf(h.x, a.y, q);
+      q = fmaf(h.y, a.x, q);
+      // the difference c - x_f exactly, (d, dl)
+      float d, dl;
+      df_two_sum(c, -xf[f], d, dl);
+      // (p + q)(d + dl): p d exactly with its error, the cross terms into the error
+      const float t = p * d;
+      float te = fmaf(p, d, -t);
+      te = fmaf(p, dl, te);
+      te = fmaf(q, d, te);
+      float sh, sl;
+      df_two_sum(hi, t, sh, sl);
+      hi = sh;
+      lo += sl + te;
+    }
+  }
+  Y[i + col * ldy] = hi + lo;
+}
+
 // Face coefficients of -div(a grad) (layout of RBGS_OP_DIFFUSION): harmonic
 // means of the node values a ((nx+2) x (ny+2)).
 __global__ void diffusion_faces_kernel(int64_t nx, int64_t ny, const double* __restrict__ a,
@@ -249,6 +313,20 @@ rbgs_status stencil_apply_t(const rbgs_op& op, const TI* X, int64_t ldx, int64_t
   if (ncols == 0 || n == 0) return RBGS_OK;
   double cx, cy, ax, ay;
   stencil_coeffs(op, cx, cy, ax, ay);
+  if constexpr (sizeof(TI) == 4 && sizeof(TO) == 4) {
+    if (op.ny <= 65535 && ncols <= 65535) {
+      auto split = [](double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+      };
+      dim3 grid((unsigned)((op.nx + 255) / 256), (unsigned)op.ny, (unsigned)ncols);
+      stencil5_df_kernel<<<grid, 256, 0, st>>>(op.nx, op.ny, split(2.0 * cx + 2.0 * cy), split(-cx - ax),
+                                               split(-cx + ax), split(-cy - ay), split(-cy + ay), split(cx),
+                                               split(cy), op_faces(op), (const float*)X, ldx, (float*)Y, ldy);
+      RBGS_LAUNCH_CHECK();
+      return RBGS_OK;
+    }
+  }
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)ncols);
   stencil5_kernel<TI, TO><<<grid, 256, 0, st>>>(op.nx, op.ny, cx, cy, ax, ay, op_faces(op), X, ldx, Y, ldy);
   RBGS_LAUNCH_CHECK();

@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(256) small_gemm_part(int trans, int64_t M, int
 
 // The same product for FP64 data with double-FP32 ("double-float")
 // arithmetic on the FP32 pipe: each operand is split once, a = a_hi + a_lo
-// with a_hi = fl32(a) and a_lo = fl32(a - a_hi) (48 significant bits), each
+// (df_split: 47 significant bits taken from the FP64 bits by integer
+// operations, since the FP64 pipe that would convert is narrow), each
 // product a_hi b_hi is formed exactly with its FMA error term, the cross
 // terms a_hi b_lo + a_lo b_hi are added into that error, and the running sum
 // is a double-float (s_hi, s_lo) kept by TwoSum (Knuth; Dekker 1971).  The
@@ -141,10 +142,6 @@ __global__ void __launch_bounds__(256) small_gemm_part_df(int trans, int64_t M, 
       rb[q] = (gb < ke && j < N) ? B[gb + (int64_t)j * ldb] : 0.0;
     }
   };
-  auto split2 = [](double v) {
-    const float hi = (float)v;
-    return make_float2(hi, (float)(v - (double)hi));
-  };
   float hi[2][8], lo[2][8];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -158,8 +155,8 @@ __global__ void __launch_bounds__(256) small_gemm_part_df(int trans, int64_t M, 
       int il, ll;
       if (trans) { ll = e % SG_K; il = e / SG_K; }
       else { il = e % SG_T; ll = e / SG_T; }
-      As[ll][il] = split2(ra[q]);
-      Bs[e % SG_K][e / SG_K] = split2(rb[q]);
+      As[ll][il] = df_split(ra[q]);  // integer operations: no FP64 conversions
+      Bs[e % SG_K][e / SG_K] = df_split(rb[q]);
     }
     __syncthreads();
     if (l0 + SG_K < ke) load(l0 + SG_K);
@@ -177,9 +174,8 @@ __global__ void __launch_bounds__(256) small_gemm_part_df(int trans, int64_t M, 
             float e = fmaf(a.x, b.x, -p);
             e = fmaf(a.x, b.y, e);
             e = fmaf(a.y, b.x, e);
-            const float sacc = hi[r][q] + p;
-            const float bp = sacc - hi[r][q];
-            const float err = (hi[r][q] - (sacc - bp)) + (p - bp);
+            float sacc, err;
+            df_two_sum(hi[r][q], p, sacc, err);
             hi[r][q] = sacc;
             lo[r][q] += err + e;
           }
