@@ -118,7 +118,11 @@ typedef struct {
                           instead of the product with the explicit inverse (the remark
                           after Alg. 4), whose error grows with cond(R_ii): needed when a
                           block is numerically rank deficient in the storage precision
-                          (near-duplicate columns); 0 = the explicit inverse (default).
+                          (near-duplicate columns); with FP32 storage the first
+                          Cholesky round of an FP64 sketch space then takes the shift
+                          of shifted Cholesky QR, so that such a block's sketch cannot
+                          break it down;
+                          0 = the explicit inverse (default).
                           RBGS_EINVAL with another interblock                            */
 } rbgs_opts;
 

@@ -104,10 +104,11 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int w) {
 // df_split: v = hi + lo + d with |d| < 2^-46 |v|, from integer operations on
 // the bits of v (GB300's FP64 pipe, which also converts, is narrow).  hi is v
 // with its 52-bit fraction truncated to 23 bits; lo holds the next 23 bits of
-// the fraction, with the sign of v.  Exponents outside [-80, 127] (zero,
-// subnormals, huge values, inf, NaN) take the FP64 conversion instead.
+// the fraction, with the sign of v.  Zero gives (0, 0); other exponents outside
+// [-80, 127] (subnormals, huge values, inf, NaN) take the FP64 conversion.
 __device__ __forceinline__ float2 df_split(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if ((b << 1) == 0ull) return make_float2(0.f, 0.f);  // +-0 (the padding of product tiles)
   const int ex = (int)((b >> 52) & 0x7ffu) - 1023;
   if (ex < -80 || ex > 127) {
     const float hi = (float)v;

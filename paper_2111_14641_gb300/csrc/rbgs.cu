@@ -129,12 +129,14 @@ bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) 
 // kappa_F(R1) = ||R1||_F ||R1^{-1}||_F exceeds 4 mb (decided on the device,
 // flag need2; n2count counts the second rounds).
 // Sp2 is a k x mb scratch for Sp R1^{-1}.
+// shift64 > 0 shifts the first FP64 round too (relative to trace(G)); see
+// alg4_pass.
 template <class TS>
 rbgs_status cholqr2(int64_t k, int mb, const TS* Sp, TS* Sp2, TS** sm, TS* part, int* flag, const int* active,
-                    cudaStream_t st, TS* R, TS* Rinv, int* need2, int* n2count) {
+                    cudaStream_t st, TS* R, TS* Rinv, int* need2, int* n2count, double shift64 = 0.0) {
   TS *gram = sm[0], *R1 = sm[1], *R1inv = sm[2];
   const bool fp64 = sizeof(TS) == 8;
-  const double shift = fp64 ? 0.0 : 1e-6;
+  const double shift = fp64 ? shift64 : 1e-6;
   rbgs_status s;
   s = small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
   if (s) return s;
@@ -154,9 +156,9 @@ rbgs_status cholqr2(int64_t k, int mb, const TS* Sp, TS* Sp2, TS** sm, TS* part,
 // two-pass block only needs an invertible R_ii).
 template <class TS>
 rbgs_status cholqr1(int64_t k, int mb, const TS* Sp, TS** sm, TS* part, int* flag, const int* active,
-                    cudaStream_t st, TS* R, TS* Rinv) {
+                    cudaStream_t st, TS* R, TS* Rinv, double shift64 = 0.0) {
   TS* gram = sm[0];
-  const double shift = sizeof(TS) == 4 ? 1e-6 : 0.0;
+  const double shift = sizeof(TS) == 4 ? 1e-6 : shift64;
   rbgs_status s =
       small_gemm<TS, TS, TS>(1, mb, mb, k, 1.0, Sp, k, Sp, k, 0.0, gram, mb, part, kPartElems, active, st);
   if (s) return s;
@@ -641,8 +643,18 @@ rbgs_status qr_impl(const T* W, int64_t n, int64_t m, int64_t ldw, int mb, rbgs_
       if ((r = make_g(c, Xc, Ieye, Ieye, nullptr, act))) return r;
       if ((r = tall(c, c, src, ldsrc, Qo, act, sraw, false))) return r;
       if ((r = sketch_apply_t<T, TS>(sketch, k, n, seed, Qo, ldq, mb, Sp, k, skscr, sk_bytes, st, act))) return r;
-      if (one_round) r = cholqr1<TS>(k, mb, Sp, sm, partf, brk, act, st, Rd, Rdinv);
-      else r = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, act, st, Rd, Rdinv, need2, n2count);
+      // With the row-wise solve on FP32 storage the blocks are expected to be
+      // numerically rank deficient: the FP64 sketch of Q'_i may then be too
+      // ill-conditioned for an FP64 Cholesky factor (a non-positive pivot).
+      // Its first round takes the shift of shifted Cholesky QR (Fukaya, Kannan,
+      // Nakatsukasa, Yamamoto and Yanagisawa 2020),
+      // 11 (k m_p + m_p (m_p + 1)) u_64 ||S'_i||_F^2; the second round (or the
+      // second pass) removes its effect.  FP64 storage keeps the unshifted
+      // factor, so that its results stay those of the plain method.
+      const double sh64 = (o.trsm && sizeof(T) == 4) ? 11.0 * ((double)k * mb + (double)mb * (mb + 1)) * 0x1p-53
+                                                      : 0.0;
+      if (one_round) r = cholqr1<TS>(k, mb, Sp, sm, partf, brk, act, st, Rd, Rdinv, sh64);
+      else r = cholqr2<TS>(k, mb, Sp, Res, sm, partf, brk, act, st, Rd, Rdinv, need2, n2count, sh64);
       if (r) return r;
       if (o.trsm) {  // Q_i = Q'_i R_ii^{-1} by forward substitution, row by row
         if ((r = trsm_rows<T, TS>(n, mb, Qo, ldq, Rd, act, st))) return r;

@@ -162,3 +162,31 @@ def test_batched_graph_replays_the_batch(rb, prec, interblock, trsm, nstreams):
         for i in range(len(SHAPES)):
             assert torch.equal(Qs[i], Qb[i]) and torch.equal(Rs[i], Rb[i]), (round_, i)
     g.destroy()
+
+
+def test_near_duplicate_blocks_of_32_do_not_break_down(rb):
+    """Problems 3, 12 and 26 of the many-small-problems workload put up to four
+    near-duplicate columns (relative perturbation 1e-7) into one block of 32,
+    so the sketch of the projected block has a condition number near 1e7-1e8
+    and an unshifted FP64 Cholesky factor of its Gram matrix meets a
+    non-positive pivot.  With the row-wise solve (Alg. 4, opts.trsm) the first
+    Cholesky round takes the shifted Cholesky QR shift: every status is OK,
+    W = QR holds at the FP32 level and cond(Q) = O(1)."""
+    specs = synth.batch_specs(32)
+    pick = [3, 12, 26]
+    Ws = [synth.near_duplicate_matrix_torch(specs[i][0], specs[i][1], 11 + i, device="cuda", dtype=torch.float32)
+          for i in pick]
+    mbs = [specs[i][2] for i in pick]
+    ks = [2 * specs[i][1] for i in pick]
+    seeds = [7 + i for i in pick]
+    kw = dict(ls_iters=1, reorth=1, fine=2, interblock=4, trsm=True)
+    Qs, Rs, status, _ = rb.rbgs_qr_batched(Ws, mbs, ks, seeds, "gauss", prec="f16x3", nstreams=2, **kw)
+    assert status == [0, 0, 0]
+    for W, Q, R in zip(Ws, Qs, Rs):
+        Wd, Qd = W.double(), Q.double()
+        fe = float(torch.linalg.norm(Wd - Qd @ R) / torch.linalg.norm(Wd))
+        sv = torch.linalg.svdvals(Qd)
+        assert fe < 1e-6 and float(sv[0] / sv[-1]) < 10.0, (fe, float(sv[0] / sv[-1]))
+    # a single call on the same problem gives the same factors
+    Q1, R1, _ = rb.rbgs_qr(Ws[0], mbs[0], "gauss", ks[0], seeds[0], prec="f16x3", **kw)
+    assert torch.equal(Q1, Qs[0]) and torch.equal(R1, Rs[0])
