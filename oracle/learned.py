@@ -157,7 +157,7 @@ def block_fgmres(apply_A, precond, B, X0, p: int, kind: str, k: int, seed: int, 
     precond=None is M = I (plain block GMRES).
 
     With accept = a (0 < a <= 1) plain block GMRES is the fallback and the
-    true residual the judge: a preconditioned cycle is kept only when it
+    true residual decides: a preconditioned cycle is kept only when it
     brings max_j ||r_j|| / ||b_j|| down to at most a times its value before
     the cycle; otherwise the cycle is run again from the same X with M = I.
 
