@@ -391,9 +391,13 @@ RBGS_API rbgs_status rbgs_block_fom(const rbgs_op* op, const double* B, int64_t 
  * unit columns (step 5); ritz_re, ritz_im and resid_est (host, mb values)
  * hold the Ritz value of each column and the estimate ||H_(p,1:p-1) y|| of
  * its residual (step 3).  (p-1) mb <= RBGS_RITZ_MAX_N.  The small
- * eigenproblem runs on one CTA in FP64 (Hessenberg reduction, Francis
- * double-shift QR, inverse iteration); RBGS_ENOCONV if its QR iteration does
- * not converge within 30 (p-1) mb sweeps; other errors as rbgs_block_gmres.
+ * eigenproblem runs on one CTA (FP32 Hessenberg reduction and Francis
+ * double-shift QR for estimates, then Rayleigh-quotient steps in FP64 on H);
+ * RBGS_ENOCONV if its QR iteration does not converge within 30 (p-1) mb
+ * sweeps.  A breakdown of Alg. 7 after the first iteration (the restart block
+ * spans a numerically invariant subspace, so its Ritz pairs are converged)
+ * ends the iterations and returns the previous iteration's pairs; in the
+ * first iteration it is RBGS_EBREAKDOWN.  Other errors as rbgs_block_gmres.
  * Synchronous.                                                               */
 #define RBGS_RITZ_MAX_N 1024
 RBGS_API rbgs_status rbgs_rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int64_t mb, int64_t p,

@@ -46,17 +46,154 @@ enum : uint32_t {
   kPurposeSparse = 4
 };
 
-// Gaussian pair for column j, row pair rp of Theta (Box-Muller on 53-bit
-// uniforms in (0,1)); z0 serves row 2 rp, z1 row 2 rp + 1.
+// ------------------------------------------------ double-FP32 arithmetic --
+// A double-float is an unevaluated sum x.x + x.y of two floats (Dekker 1971;
+// Knuth's TwoSum).  GB300's FP64 pipe is narrow, so the Gaussian generator
+// below evaluates its logarithm, square root and sine/cosine this way on the
+// FP32 pipe.
+
+__device__ __forceinline__ float2 dfx_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 dfx_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bp = s - a;
+  return make_float2(s, (a - (s - bp)) + (b - bp));
+}
+__device__ __forceinline__ float2 dfx_add(float2 x, float2 y) {
+  const float2 s = dfx_two_sum(x.x, y.x);
+  return dfx_fast_two_sum(s.x, s.y + (x.y + y.y));
+}
+__device__ __forceinline__ float2 dfx_mul(float2 x, float2 y) {
+  const float p = x.x * y.x;
+  float e = fmaf(x.x, y.x, -p);
+  e = fmaf(x.x, y.y, e);
+  e = fmaf(x.y, y.x, e);
+  return dfx_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 dfx_mul_f(float2 x, float f) {
+  const float p = x.x * f;
+  float e = fmaf(x.x, f, -p);
+  e = fmaf(x.y, f, e);
+  return dfx_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 dfx_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 dfx_div(float2 x, float2 y) {  // one correction step
+  const float q1 = __fdiv_rn(x.x, y.x);
+  const float2 r = dfx_add(x, dfx_neg(dfx_mul_f(y, q1)));
+  return dfx_fast_two_sum(q1, __fdiv_rn(r.x, y.x));
+}
+__device__ __forceinline__ float2 dfx_sqrt(float2 x) {  // x >= 0
+  if (!(x.x > 0.f)) return make_float2(0.f, 0.f);
+  const float s = __fsqrt_rn(x.x);
+  const float p = s * s;
+  const float e = fmaf(s, s, -p);
+  return dfx_fast_two_sum(s, __fdiv_rn(((x.x - p) - e) + x.y, 2.f * s));
+}
+// |v| < 2^56 exactly as three 23-bit pieces, summed as a double-float
+__device__ __forceinline__ float2 dfx_from_i64(int64_t v) {
+  const bool neg = v < 0;
+  const uint64_t a = (uint64_t)(neg ? -v : v);
+  auto f23 = [](uint32_t t) { return __uint_as_float(0x4B000000u | t) - 8388608.0f; };  // t < 2^23, exact
+  const float fa = f23((uint32_t)(a >> 46)) * 0x1p46f, fb = f23((uint32_t)(a >> 23) & 0x7fffffu) * 0x1p23f;
+  const float fc = f23((uint32_t)a & 0x7fffffu);
+  const float2 s = dfx_two_sum(fa, fb);
+  const float2 s2 = dfx_two_sum(s.x, fc);
+  const float2 r = dfx_fast_two_sum(s2.x, s.y + s2.y);
+  return neg ? dfx_neg(r) : r;
+}
+// sum_k c_k y^k, the terms k < 5 in double-float, the rest in float
+template <int N>
+__device__ __forceinline__ float2 dfx_poly(float2 y, const float2 (&c)[N]) {
+  float p = c[N - 1].x;
+#pragma unroll
+  for (int k = N - 2; k >= 5; --k) p = fmaf(p, y.x, c[k].x);
+  float2 q = make_float2(p, 0.f);
+#pragma unroll
+  for (int k = 4; k >= 0; --k) q = dfx_add(dfx_mul(q, y), c[k]);
+  return q;
+}
+
+// Gaussian pair for column j, row pair rp of Theta: Box-Muller on the 53-bit
+// uniforms u = (U + 1/2) 2^-53 (U from two Philox words, the sum rounded to
+// FP64 as written), z0 = sqrt(-2 ln u1) cos(2 pi u2) serves row 2 rp and
+// z1 = sqrt(-2 ln u1) sin(2 pi u2) row 2 rp + 1.
+//
+// Evaluated in double-float arithmetic from the exact integers W = u 2^54
+// (about 2^-46 relative to the pair's radius; a CPU model of these steps
+// against 40-digit references gave at most 1.2e-14):
+//   ln u1 = 2 atanh(t) + (e - 54) ln 2 with t = (W1 - 2^e) / (W1 + 2^e),
+//           W1 / 2^e in [sqrt(1/2), sqrt(2)), |t| <= 0.172, the series
+//           atanh(t) = t sum_k t^(2k) / (2k + 1) to k = 10;
+//   2 u2 = q / 2 + r (q an integer, |r| <= 1/4, exact), sin and cos of
+//           theta = pi r by their Taylor series to theta^17 and theta^18,
+//           then rotated by the quarter turns q.
 __device__ __forceinline__ void gauss_pair(uint2 key, int64_t j, uint32_t rp, double& z0, double& z1) {
   const uint4 x = philox10(make_uint4((uint32_t)j, rp, kPurposeGauss, (uint32_t)(j >> 32)), key);
-  const double u1 = ((double)(x.x >> 5) * 67108864.0 + (double)(x.y >> 6) + 0.5) * (1.0 / 9007199254740992.0);
-  const double u2 = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6) + 0.5) * (1.0 / 9007199254740992.0);
-  const double rad = sqrt(-2.0 * log(u1));
-  double s, c;
-  sincospi(2.0 * u2, &s, &c);
-  z0 = rad * c;
-  z1 = rad * s;
+  auto w54 = [](uint32_t hi, uint32_t lo) -> int64_t {  // u 2^54 for U = (hi >> 5) 2^26 + (lo >> 6)
+    const uint64_t U = ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
+    if (U < (1ull << 52)) return (int64_t)(2 * U + 1);  // U + 1/2 is exact in FP64
+    return (int64_t)(2 * (U + (U & 1)));                // rounded to even
+  };
+  const int64_t W1 = w54(x.x, x.y), W2 = w54(x.z, x.w);
+  const float2 kLn2 = {0x1.62e43p-1f, -0x1.05c61p-29f};
+  const float2 kPi = {0x1.921fb6p+1f, -0x1.777a5cp-24f};
+  const float2 kAtanh[11] = {{1.0f, 0.0f},
+                             {0x1.555556p-2f, -0x1.555556p-27f},
+                             {0x1.99999ap-3f, -0x1.99999ap-29f},
+                             {0x1.24924ap-3f, -0x1.b6db6ep-28f},
+                             {0x1.c71c72p-4f, -0x1.c71c72p-31f},
+                             {0x1.745d18p-4f, -0x1.745d18p-29f},
+                             {0x1.3b13b2p-4f, -0x1.89d89ep-29f},
+                             {0x1.111112p-4f, -0x1.dddddep-29f},
+                             {0x1.e1e1e2p-5f, -0x1.e1e1e2p-33f},
+                             {0x1.af286cp-5f, -0x1.af286cp-32f},
+                             {0x1.861862p-5f, -0x1.e79e7ap-31f}};
+  const float2 kSin[9] = {{1.0f, 0.0f},
+                          {-0x1.555556p-3f, 0x1.555556p-28f},
+                          {0x1.111112p-7f, -0x1.dddddep-32f},
+                          {-0x1.a01a02p-13f, 0x1.7f97fap-39f},
+                          {0x1.71de3ap-19f, 0x1.55b1ccp-45f},
+                          {-0x1.ae6456p-26f, -0x1.fd5138p-52f},
+                          {0x1.612462p-33f, -0x1.8af25ep-58f},
+                          {-0x1.ae7f3ep-41f, -0x1.ccee08p-67f},
+                          {0x1.952c78p-49f, -0x1.f9ea56p-74f}};
+  const float2 kCos[10] = {{1.0f, 0.0f},
+                           {-0.5f, 0.0f},
+                           {0x1.555556p-5f, -0x1.555556p-30f},
+                           {-0x1.6c16c2p-10f, 0x1.27d27ep-35f},
+                           {0x1.a01a02p-16f, -0x1.7f97fap-42f},
+                           {-0x1.27e4fcp-22f, 0x1.10ec14p-47f},
+                           {0x1.1eed8ep-29f, 0x1.ff1b12p-54f},
+                           {-0x1.93974ap-37f, -0x1.180f94p-62f},
+                           {0x1.ae7f3ep-45f, 0x1.ccee08p-71f},
+                           {-0x1.682786p-53f, -0x1.dcbeccp-80f}};
+  // ln u1
+  int e = 63 - __clzll((unsigned long long)W1);
+  const uint64_t top = e >= 20 ? ((uint64_t)W1 >> (e - 20)) : ((uint64_t)W1 << (20 - e));
+  if (top > 1482910ull) ++e;  // W1 / 2^e above sqrt(2) (floor(sqrt(2) 2^20) = 1482910)
+  const float2 t = dfx_div(dfx_from_i64(W1 - (1ll << e)), dfx_from_i64(W1 + (1ll << e)));
+  const float2 lm = dfx_mul(t, dfx_poly(dfx_mul(t, t), kAtanh));
+  const float2 lnu = dfx_add(make_float2(2.f * lm.x, 2.f * lm.y), dfx_mul_f(kLn2, (float)(e - 54)));
+  const float2 rad = dfx_sqrt(make_float2(-2.f * lnu.x, -2.f * lnu.y));
+  // sin and cos of pi x, x = 2 u2 = W2 2^-53
+  const int64_t q = (W2 + (1ll << 51)) >> 52;
+  const float2 rr = dfx_from_i64(W2 - (q << 52));
+  const float2 th = dfx_mul(kPi, make_float2(rr.x * 0x1p-53f, rr.y * 0x1p-53f));
+  const float2 y = dfx_mul(th, th);
+  const float2 sn = dfx_mul(th, dfx_poly(y, kSin));
+  const float2 cs = dfx_poly(y, kCos);
+  float2 sv, cv;
+  switch ((int)(q & 3)) {
+    case 0: sv = sn; cv = cs; break;
+    case 1: sv = cs; cv = dfx_neg(sn); break;
+    case 2: sv = dfx_neg(sn); cv = dfx_neg(cs); break;
+    default: sv = dfx_neg(cs); cv = sn; break;
+  }
+  const float2 a = dfx_mul(rad, cv), b = dfx_mul(rad, sv);
+  z0 = (double)a.x + (double)a.y;
+  z1 = (double)b.x + (double)b.y;
 }
 
 // 128 Rademacher sign bits for column j, rows [128 g, 128 g + 128).

@@ -2217,8 +2217,13 @@ rbgs_status rayleigh_ritz(const rbgs_op* op, const double* B0, int64_t ldb, int6
   if (s) return s;
   const int64_t c = N - mb;
   for (int64_t it = 0; it < n_iter; ++it) {
-    // step 1: Alg. 7 from B; H = R(:, mb:)
-    if ((s = arnoldi_run(*op, Bb, n, mb, p, sketch, k, seed, Qb, n, Rm, m, o, nullptr))) return s;
+    // step 1: Alg. 7 from B; H = R(:, mb:).  A breakdown after the first
+    // iteration means the restart block B spans a numerically invariant
+    // subspace (the Krylov space cannot grow): the previous iteration's Ritz
+    // pairs, still in vals, res and B, are converged, and the iterations end.
+    s = arnoldi_run(*op, Bb, n, mb, p, sketch, k, seed, Qb, n, Rm, m, o, nullptr);
+    if (s == RBGS_EBREAKDOWN && it > 0) break;
+    if (s) return s;
     // steps 2-3 on H_(1:p-1,1:p-1) and H_(p,1:p-1)
     RBGS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     if ((s = ritz_eig((int)N, (int)mb, (int)mb, which, Rm + mb * m, m, vals, Y, res, scr, status, st))) return s;

@@ -769,7 +769,7 @@ constexpr int kDenseJ = 32;      // X rows per step
 constexpr int kDenseCols = 64;   // max columns per launch
 constexpr int kDenseThreads = 256;
 
-template <int KIND, class TX, class TC>
+template <int KIND, class TX, class TC, int QN>
 __global__ void __launch_bounds__(kDenseThreads) dense_sketch_part(const TX* __restrict__ X, int64_t ldx, int64_t n,
                                                                    int ncols, int64_t k, uint2 key, double scale,
                                                                    int64_t rows_per_split, TC* __restrict__ part,
@@ -783,6 +783,9 @@ __global__ void __launch_bounds__(kDenseThreads) dense_sketch_part(const TX* __r
   const int64_t j0 = (int64_t)split * rows_per_split;
   const int64_t j1 = min(n, j0 + rows_per_split);
   const int tr = tid & 15, tc = tid >> 4;
+  // QN = ceil(ncols / 16): the column groups of 16 that hold columns of X (a
+  // block of 16 columns needs a quarter of the products of a full tile)
+  static_assert(QN >= 1 && QN <= 4, "column groups");
   TC acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -841,22 +844,22 @@ __global__ void __launch_bounds__(kDenseThreads) dense_sketch_part(const TX* __r
     __syncthreads();
 #pragma unroll 4
     for (int jl = 0; jl < kDenseJ; ++jl) {
-      TC a[4], b[4];
+      TC a[4], b[QN];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = th[tr + 16 * i][jl];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = xs[jl][tc + 16 * q];
+      for (int q = 0; q < QN; ++q) b[q] = xs[jl][tc + 16 * q];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] += a[i] * b[q];
+        for (int q = 0; q < QN; ++q) acc[i][q] += a[i] * b[q];
     }
     __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < QN; ++q) {
       const int64_t r = r0 + tr + 16 * i;
       const int c = tc + 16 * q;
       if (r < k && c < ncols) part[((int64_t)split * ncols + c) * k + r] = acc[i][q];
@@ -1037,16 +1040,24 @@ rbgs_status sketch_apply_t(rbgs_sketch kind, int64_t k, int64_t n, uint64_t seed
     const size_t need = sizeof(TC) * (size_t)nsplit * nc * (size_t)k;
     if (scratch_bytes < need) return RBGS_EINVAL;
     dim3 grid((unsigned)((k + kDenseRows - 1) / kDenseRows), (unsigned)nsplit);
-    if (kind == RBGS_SK_GAUSS)
-      dense_sketch_part<RBGS_SK_GAUSS, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
-                                                                              dscale, rows_per_split, part, active);
-    else if (kind == RBGS_SK_SPARSE)
-      dense_sketch_part<RBGS_SK_SPARSE, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
-                                                                               dscale, rows_per_split, part, active);
-    else
-      dense_sketch_part<RBGS_SK_RADEMACHER, TX, TC><<<grid, kDenseThreads, 0, st>>>(X + c0 * ldx, ldx, n, nc, k, key,
-                                                                                   dscale, rows_per_split, part,
-                                                                                   active);
+    auto launch = [&](auto qn) {
+      constexpr int QN = decltype(qn)::value;
+      if (kind == RBGS_SK_GAUSS)
+        dense_sketch_part<RBGS_SK_GAUSS, TX, TC, QN><<<grid, kDenseThreads, 0, st>>>(
+            X + c0 * ldx, ldx, n, nc, k, key, dscale, rows_per_split, part, active);
+      else if (kind == RBGS_SK_SPARSE)
+        dense_sketch_part<RBGS_SK_SPARSE, TX, TC, QN><<<grid, kDenseThreads, 0, st>>>(
+            X + c0 * ldx, ldx, n, nc, k, key, dscale, rows_per_split, part, active);
+      else
+        dense_sketch_part<RBGS_SK_RADEMACHER, TX, TC, QN><<<grid, kDenseThreads, 0, st>>>(
+            X + c0 * ldx, ldx, n, nc, k, key, dscale, rows_per_split, part, active);
+    };
+    switch ((nc + 15) >> 4) {
+      case 1: launch(std::integral_constant<int, 1>{}); break;
+      case 2: launch(std::integral_constant<int, 2>{}); break;
+      case 3: launch(std::integral_constant<int, 3>{}); break;
+      default: launch(std::integral_constant<int, 4>{}); break;
+    }
     RBGS_LAUNCH_CHECK();
     const int64_t tot = k * nc;
     dense_sketch_reduce<TC, TY><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nsplit, k, nc, Y + c0 * ldy, ldy,
