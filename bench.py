@@ -453,13 +453,21 @@ def run_ours(args, cfg):
             return rb.rbgs_qr_host(W_h, mb, cfg["sketch"], k, cfg["seed_theta"], prec=prec, ls_iters=args.ls_iters,
                                    reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q_h, R=R_h, fine=args.fine)
 
+        def step_host_timed():
+            return rb.rbgs_qr_host(W_h, mb, cfg["sketch"], k, cfg["seed_theta"], prec=prec, ls_iters=args.ls_iters,
+                                   reorth=args.reorth, reorth_tol=args.reorth_tol, Q=Q_h, R=R_h, fine=args.fine,
+                                   timing=True)
+
+        # the plain copy rates of the same pinned buffers, alone and both ways at once
+        rates = copy_rates(W_h, Q_h, W, Q)
         step_host()  # allocates the library's device copies
         torch.cuda.synchronize()
         steps_e2e = max(1, min(args.steps, 5))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tls = []
         a.record()
         for _ in range(steps_e2e):
-            step_host()
+            tls.append(step_host_timed()[2])  # each call's copy / compute timeline from the library's events
         b.record()
         torch.cuda.synchronize()
         ms_e2e = a.elapsed_time(b) / steps_e2e
@@ -468,7 +476,11 @@ def run_ours(args, cfg):
         d2h = Q_h.element_size() * n * m + 8 * m * m
         e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e, "api": "rbgs_qr_host (pinned host buffers)",
-               "max_abs_diff_Q_vs_device_path": diff_q}
+               "max_abs_diff_Q_vs_device_path": diff_q,
+               "timeline_ms": {"W_on_device": [t.host_up_ms for t in tls],
+                               "Q_final_on_device": [t.host_compute_ms for t in tls],
+                               "Q_R_on_host": [t.host_total_ms for t in tls]},
+               "copy_rates_gbs": rates}
         del W_h, Q_h, R_h
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -942,6 +954,41 @@ def unet_forward_gflop(N, widths):
             f += px * 18.0 * (widths[l + 1] + widths[l]) * widths[l]
     f += N * N * 18.0 * widths[0]
     return f / 1e9
+
+
+def copy_rates(W_h, Q_h, W, Q):
+    """GB/s of one plain copy of W up and of Q down between the bench's pinned
+    host buffers and device tensors, alone and both at once on two streams.
+    W and Q hold the same values before and after."""
+    import torch
+
+    nbytes = W_h.element_size() * W_h.numel()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def both():
+        cur = torch.cuda.current_stream()
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            W.copy_(W_h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            Q_h.copy_(Q, non_blocking=True)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    up = timed(lambda: W.copy_(W_h, non_blocking=True))
+    down = timed(lambda: Q_h.copy_(Q, non_blocking=True))
+    bo = timed(both)
+    return {"up": nbytes / up / 1e6, "down": nbytes / down / 1e6, "both_ways_total": 2 * nbytes / bo / 1e6}
 
 
 def _refill(W, cfg, dev, dtype):

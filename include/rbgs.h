@@ -137,6 +137,10 @@ typedef struct {
   int32_t chol_rounds2;  /* block Cholesky QR factorizations that took a second round
                             (always, in the FP32 sketch space; in FP64 only where
                             ||R1||_F ||R1^{-1}||_F > 4 m_p after the first round)       */
+  double host_up_ms;      /* rbgs_qr_host with opts->timing: from the start of the call's
+                             device work to the last column block of W on the device   */
+  double host_compute_ms; /* ... to the last column block of Q final on the device      */
+  double host_total_ms;   /* ... to Q and R back on the host (0 without opts->timing)   */
 } rbgs_stats;
 
 /* Fill *opts with the defaults: FP64, 2 Richardson iterations, reorth 0,
@@ -198,8 +202,10 @@ RBGS_API rbgs_status rbgs_qr_batched(rbgs_problem* probs, int64_t count, rbgs_sk
  * of Q is copied back as soon as it is final, while later blocks compute; R
  * follows at the end.  With page-locked (pinned) host memory the copies
  * overlap the computation; pageable memory gives the same result without the
- * overlap.  Options and errors as rbgs_qr (no certification, no timing; stats
- * receives passes2 and chol_rounds2).  Synchronous.                        */
+ * overlap.  Options and errors as rbgs_qr (no certification; stats receives
+ * passes2 and chol_rounds2, and with opts->timing the copy and compute
+ * timeline host_up_ms, host_compute_ms and host_total_ms instead of the
+ * tall-launch timing).  Synchronous.                                        */
 RBGS_API rbgs_status rbgs_qr_host(const void* W, int64_t n, int64_t m, int64_t ldw, int64_t mb, rbgs_sketch sketch,
                                   int64_t k, uint64_t seed, void* Q, int64_t ldq, double* R, int64_t ldr,
                                   const rbgs_opts* opts, rbgs_stats* stats);

@@ -1283,7 +1283,8 @@ rbgs_status rbgs_qr_host(const void* W, int64_t n, int64_t m, int64_t ldw, int64
       if (*d) cudaFree(*d);
     }
   } evfree{&ev, &dstat};
-  for (auto& e : ev) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // with opts.timing the events keep times: the copy and compute timeline of the call
+  for (auto& e : ev) RBGS_CUDA_TRY(cudaEventCreateWithFlags(&e, o.timing ? cudaEventDefault : cudaEventDisableTiming));
   cudaEvent_t* w_ready = ev.data();
   cudaEvent_t* q_done = ev.data() + p;
   cudaEvent_t start = ev[(size_t)(2 * p)], copied = ev[(size_t)(2 * p + 1)];
@@ -1331,6 +1332,15 @@ rbgs_status rbgs_qr_host(const void* W, int64_t n, int64_t m, int64_t ldw, int64
     stats->delta_tilde = -1.0;
     stats->passes2 = hs[2];
     stats->chol_rounds2 = hs[5];
+    if (o.timing) {
+      float up = 0.f, comp = 0.f, tot = 0.f;
+      RBGS_CUDA_TRY(cudaEventElapsedTime(&up, start, w_ready[p - 1]));
+      RBGS_CUDA_TRY(cudaEventElapsedTime(&comp, start, q_done[p - 1]));
+      RBGS_CUDA_TRY(cudaEventElapsedTime(&tot, start, copied));
+      stats->host_up_ms = up;
+      stats->host_compute_ms = comp;
+      stats->host_total_ms = tot;
+    }
   }
   if (hs[3]) return RBGS_ETIMEOUT;
   if (hs[0]) return RBGS_EBREAKDOWN;

@@ -479,7 +479,7 @@ __global__ void reorth_decide_kernel(int64_t c, int mb, const TS* __restrict__ X
                                      int mode, int* active, int* count, int* blk_flag) {
   __shared__ double red[1024];
   double s = 0.0;
-  const int64_t tot = c * mb;
+  const int64_t tot = mode == 1 ? 0 : c * mb;  // mode 1 (every block) needs no norm
 #pragma unroll 8
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
     const double v = (double)X[(e % c) + (e / c) * ldx];

@@ -96,7 +96,9 @@ def diffusion_op(nx: int, ny: int, coef: torch.Tensor) -> Op:
 class Stats(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("delta_tilde", ctypes.c_double), ("passes2", ctypes.c_int32),
                 ("certified", ctypes.c_int32), ("tall_ms", ctypes.c_double), ("tall_bytes", ctypes.c_double),
-                ("tall_launches", ctypes.c_int32), ("chol_rounds2", ctypes.c_int32)]
+                ("tall_launches", ctypes.c_int32), ("chol_rounds2", ctypes.c_int32),
+                ("host_up_ms", ctypes.c_double), ("host_compute_ms", ctypes.c_double),
+                ("host_total_ms", ctypes.c_double)]
 
 
 @dataclass
@@ -109,6 +111,9 @@ class QRStats:
     tall_bytes: float = 0.0
     tall_launches: int = 0
     chol_rounds2: int = 0
+    host_up_ms: float = 0.0
+    host_compute_ms: float = 0.0
+    host_total_ms: float = 0.0
 
 
 _lib = None
@@ -398,9 +403,11 @@ def cholqr_postprocess(Q: torch.Tensor, R: torch.Tensor, mb: int = 64, prec: str
 def rbgs_qr_host(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None = None, seed: int = 0,
                  prec: str | None = None, ls_iters: int = 2, reorth: int = 0, reorth_tol: float = 1e-8,
                  Q: torch.Tensor | None = None, R: torch.Tensor | None = None, fine: bool = False,
-                 interblock: int = 5, stream=None):
+                 interblock: int = 5, stream=None, timing: bool = False):
     """rbgs_qr on host (CPU) tensors, column-major; pinned memory lets the
-    copies overlap the factorization.  Returns (Q, R, QRStats)."""
+    copies overlap the factorization.  Returns (Q, R, QRStats); with timing
+    the stats carry the call's timeline (host_up_ms, host_compute_ms,
+    host_total_ms)."""
     lib = load()
     if W.is_cuda:
         raise ValueError("W must be a host tensor")
@@ -416,10 +423,12 @@ def rbgs_qr_host(W: torch.Tensor, mb: int, sketch: str = "srht", k: int | None =
     lib.rbgs_opts_default(ctypes.byref(o))
     o.prec, o.ls_iters, o.reorth, o.reorth_tol = PREC[prec], ls_iters, reorth, reorth_tol
     o.fine, o.interblock, o.stream = int(fine), int(interblock), _stream_ptr(stream)
+    o.timing = int(timing)
     st = Stats()
     _check(lib.rbgs_qr_host(W.data_ptr(), n, m, _ld(W, "W"), mb, SKETCH[sketch], k, seed, Q.data_ptr(), _ld(Q, "Q"),
                             R.data_ptr(), _ld(R, "R"), ctypes.byref(o), ctypes.byref(st)), "rbgs_qr_host")
-    return Q, R, QRStats(st.delta, st.delta_tilde, st.passes2, False, 0.0, 0.0, 0, st.chol_rounds2)
+    return Q, R, QRStats(st.delta, st.delta_tilde, st.passes2, False, 0.0, 0.0, 0, st.chol_rounds2, st.host_up_ms,
+                         st.host_compute_ms, st.host_total_ms)
 
 
 def rbgs_qr_batched(Ws: list, mbs, ks, seeds, sketch: str = "gauss", prec: str | None = None, ls_iters: int = 2,

@@ -122,6 +122,28 @@ def test_sketch_matches_oracle(rb, kind, n, c, k, prec):
     assert err.max() <= tol, f"max rel err {err.max():.3e}"
 
 
+@pytest.mark.parametrize("n,k", [(4096, 512), (70001, 64)])
+def test_gaussian_entries_match_oracle(rb, n, k):
+    """Entries of the Gaussian Theta one by one (Box-Muller pairs): with X a
+    set of identity columns, column t of Y = Theta X is column j_t of Theta on
+    both sides exactly (one nonzero term per sum), so this compares the two
+    generators entry by entry.  Bound: 3e-14 of the pair's radius
+    sqrt(z_2r^2 + z_2r+1^2), about 200 ulps of FP64, well above the device's
+    double-float evaluation error (about 2^-46 of the radius) and far below
+    any wrong term of the logarithm or the angle."""
+    rng = np.random.default_rng(n)
+    cols = np.unique(np.concatenate([[0, 1, n - 1], rng.integers(0, n, 253)]))
+    X = np.zeros((n, cols.size))
+    X[cols, np.arange(cols.size)] = 1.0
+    seed = 99 + n
+    Y = host(rb.sketch_apply(dev(X), "gauss", k, seed, prec="fp64"))
+    Yr = oracle.theta_apply("gauss", k, seed, X)
+    rad = np.sqrt(Yr[0::2] ** 2 + Yr[1::2] ** 2)
+    err = np.maximum(np.abs(Y[0::2] - Yr[0::2]), np.abs(Y[1::2] - Yr[1::2])) / rad
+    assert np.isfinite(Y).all()
+    assert err.max() <= 3e-14, f"max error {err.max():.3e} of the pair radius"
+
+
 # --------------------------------------------------------------- tall ops ---
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
