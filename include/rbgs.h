@@ -530,6 +530,17 @@ RBGS_API rbgs_status rbgs_philox(uint64_t seed, const uint32_t* ctr, uint32_t* o
 RBGS_API rbgs_status rbgs_sparse_sign_columns(uint64_t seed, int64_t k, int64_t j0, int64_t count, int64_t* rows,
                                               int32_t* neg);
 
+/* Entries of the Gaussian Theta on the host (the generator the dense sketch
+ * kernels evaluate, exposed so that it can be checked without a device):
+ * out[t] = Theta(r[t], j[t]) for t < count, N(0, 1/k) by the Box-Muller pair
+ * of column j[t] and row pair r[t] / 2 (cosine for even rows, sine for odd
+ * ones), scaled as the kernels scale it.  r, j and out are caller-owned host
+ * arrays of count entries.  RBGS_EINVAL on a null pointer (count > 0),
+ * k < 1, count < 0, r[t] outside [0, k) or j[t] < 0.  Not in the paper,
+ * which uses Rademacher and SRHT sketches (Sec. 2.3).                      */
+RBGS_API rbgs_status rbgs_gaussian_entries(uint64_t seed, int64_t k, const int64_t* r, const int64_t* j, int64_t count,
+                                           double* out);
+
 /* Number of kernels this library has launched in the process so far (all
  * devices, all entry points); a counter for profiling and accounting.     */
 RBGS_API int64_t rbgs_launch_count(void);

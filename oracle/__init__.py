@@ -71,6 +71,8 @@ def _load():
         lib.or_theta_dense.restype = ctypes.c_int
         lib.or_theta_apply.argtypes = [ctypes.c_int, i64, i64, u64, dp, i64, i64, dp, i64]
         lib.or_theta_apply.restype = ctypes.c_int
+        lib.or_theta_gauss_entry.argtypes = [u64, i64, i64, i64]
+        lib.or_theta_gauss_entry.restype = ctypes.c_double
         lib.or_srht_samples.argtypes = [u64, i64, i64, dp]
         lib.or_srht_samples.restype = ctypes.c_int
         lib.or_srht_sign.argtypes = [u64, i64]
@@ -173,6 +175,15 @@ def theta_dense(kind: str, k: int, n: int, seed: int) -> np.ndarray:
     if _load().or_theta_dense(THETA[kind], int(k), int(n), int(seed), _ptr(T)):
         raise ValueError("bad sketch arguments")
     return T
+
+
+def theta_gauss_entries(k: int, seed: int, r, j) -> np.ndarray:
+    """Entries Theta(r[t], j[t]) of the Gaussian Theta, one C call each (for
+    columns beyond what theta_dense can hold)."""
+    lib = _load()
+    r = np.asarray(r, dtype=np.int64).ravel()
+    j = np.asarray(j, dtype=np.int64).ravel()
+    return np.array([lib.or_theta_gauss_entry(int(seed), int(k), int(a), int(b)) for a, b in zip(r, j)])
 
 
 def theta_apply(kind: str, k: int, seed: int, X) -> np.ndarray:

@@ -2,7 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/rbgs.h"
 
@@ -52,50 +54,84 @@ enum : uint32_t {
 // below evaluates its logarithm, square root and sine/cosine this way on the
 // FP32 pipe.
 
-__device__ __forceinline__ float2 dfx_fast_two_sum(float a, float b) {  // |a| >= |b|
+// IEEE round-to-nearest division and square root, count of leading zeros and
+// a bit cast, for the device and for the host copy of the generator
+// (rbgs_gaussian_entries), which must give the same floats.
+__host__ __device__ __forceinline__ float dfx_div_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdiv_rn(a, b);
+#else
+  return a / b;
+#endif
+}
+__host__ __device__ __forceinline__ float dfx_sqrt_rn(float a) {
+#ifdef __CUDA_ARCH__
+  return __fsqrt_rn(a);
+#else
+  return sqrtf(a);
+#endif
+}
+__host__ __device__ __forceinline__ int dfx_clz64(uint64_t v) {  // v != 0
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return __builtin_clzll(v);
+#endif
+}
+__host__ __device__ __forceinline__ float dfx_u2f(uint32_t u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, sizeof f);
+  return f;
+#endif
+}
+
+__host__ __device__ __forceinline__ float2 dfx_fast_two_sum(float a, float b) {  // |a| >= |b|
   const float s = a + b;
   return make_float2(s, b - (s - a));
 }
-__device__ __forceinline__ float2 dfx_two_sum(float a, float b) {
+__host__ __device__ __forceinline__ float2 dfx_two_sum(float a, float b) {
   const float s = a + b;
   const float bp = s - a;
   return make_float2(s, (a - (s - bp)) + (b - bp));
 }
-__device__ __forceinline__ float2 dfx_add(float2 x, float2 y) {
+__host__ __device__ __forceinline__ float2 dfx_add(float2 x, float2 y) {
   const float2 s = dfx_two_sum(x.x, y.x);
   return dfx_fast_two_sum(s.x, s.y + (x.y + y.y));
 }
-__device__ __forceinline__ float2 dfx_mul(float2 x, float2 y) {
+__host__ __device__ __forceinline__ float2 dfx_mul(float2 x, float2 y) {
   const float p = x.x * y.x;
   float e = fmaf(x.x, y.x, -p);
   e = fmaf(x.x, y.y, e);
   e = fmaf(x.y, y.x, e);
   return dfx_fast_two_sum(p, e);
 }
-__device__ __forceinline__ float2 dfx_mul_f(float2 x, float f) {
+__host__ __device__ __forceinline__ float2 dfx_mul_f(float2 x, float f) {
   const float p = x.x * f;
   float e = fmaf(x.x, f, -p);
   e = fmaf(x.y, f, e);
   return dfx_fast_two_sum(p, e);
 }
-__device__ __forceinline__ float2 dfx_neg(float2 x) { return make_float2(-x.x, -x.y); }
-__device__ __forceinline__ float2 dfx_div(float2 x, float2 y) {  // one correction step
-  const float q1 = __fdiv_rn(x.x, y.x);
+__host__ __device__ __forceinline__ float2 dfx_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__host__ __device__ __forceinline__ float2 dfx_div(float2 x, float2 y) {  // one correction step
+  const float q1 = dfx_div_rn(x.x, y.x);
   const float2 r = dfx_add(x, dfx_neg(dfx_mul_f(y, q1)));
-  return dfx_fast_two_sum(q1, __fdiv_rn(r.x, y.x));
+  return dfx_fast_two_sum(q1, dfx_div_rn(r.x, y.x));
 }
-__device__ __forceinline__ float2 dfx_sqrt(float2 x) {  // x >= 0
+__host__ __device__ __forceinline__ float2 dfx_sqrt(float2 x) {  // x >= 0
   if (!(x.x > 0.f)) return make_float2(0.f, 0.f);
-  const float s = __fsqrt_rn(x.x);
+  const float s = dfx_sqrt_rn(x.x);
   const float p = s * s;
   const float e = fmaf(s, s, -p);
-  return dfx_fast_two_sum(s, __fdiv_rn(((x.x - p) - e) + x.y, 2.f * s));
+  return dfx_fast_two_sum(s, dfx_div_rn(((x.x - p) - e) + x.y, 2.f * s));
 }
 // |v| < 2^56 exactly as three 23-bit pieces, summed as a double-float
-__device__ __forceinline__ float2 dfx_from_i64(int64_t v) {
+__host__ __device__ __forceinline__ float2 dfx_from_i64(int64_t v) {
   const bool neg = v < 0;
   const uint64_t a = (uint64_t)(neg ? -v : v);
-  auto f23 = [](uint32_t t) { return __uint_as_float(0x4B000000u | t) - 8388608.0f; };  // t < 2^23, exact
+  auto f23 = [](uint32_t t) { return dfx_u2f(0x4B000000u | t) - 8388608.0f; };  // t < 2^23, exact
   const float fa = f23((uint32_t)(a >> 46)) * 0x1p46f, fb = f23((uint32_t)(a >> 23) & 0x7fffffu) * 0x1p23f;
   const float fc = f23((uint32_t)a & 0x7fffffu);
   const float2 s = dfx_two_sum(fa, fb);
@@ -105,7 +141,7 @@ __device__ __forceinline__ float2 dfx_from_i64(int64_t v) {
 }
 // sum_k c_k y^k, the terms k < 5 in double-float, the rest in float
 template <int N>
-__device__ __forceinline__ float2 dfx_poly(float2 y, const float2 (&c)[N]) {
+__host__ __device__ __forceinline__ float2 dfx_poly(float2 y, const float2 (&c)[N]) {
   float p = c[N - 1].x;
 #pragma unroll
   for (int k = N - 2; k >= 5; --k) p = fmaf(p, y.x, c[k].x);
@@ -129,7 +165,7 @@ __device__ __forceinline__ float2 dfx_poly(float2 y, const float2 (&c)[N]) {
 //   2 u2 = q / 2 + r (q an integer, |r| <= 1/4, exact), sin and cos of
 //           theta = pi r by their Taylor series to theta^17 and theta^18,
 //           then rotated by the quarter turns q.
-__device__ __forceinline__ void gauss_pair(uint2 key, int64_t j, uint32_t rp, double& z0, double& z1) {
+__host__ __device__ __forceinline__ void gauss_pair(uint2 key, int64_t j, uint32_t rp, double& z0, double& z1) {
   const uint4 x = philox10(make_uint4((uint32_t)j, rp, kPurposeGauss, (uint32_t)(j >> 32)), key);
   auto w54 = [](uint32_t hi, uint32_t lo) -> int64_t {  // u 2^54 for U = (hi >> 5) 2^26 + (lo >> 6)
     const uint64_t U = ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
@@ -170,7 +206,7 @@ __device__ __forceinline__ void gauss_pair(uint2 key, int64_t j, uint32_t rp, do
                            {0x1.ae7f3ep-45f, 0x1.ccee08p-71f},
                            {-0x1.682786p-53f, -0x1.dcbeccp-80f}};
   // ln u1
-  int e = 63 - __clzll((unsigned long long)W1);
+  int e = 63 - dfx_clz64((uint64_t)W1);
   const uint64_t top = e >= 20 ? ((uint64_t)W1 >> (e - 20)) : ((uint64_t)W1 << (20 - e));
   if (top > 1482910ull) ++e;  // W1 / 2^e above sqrt(2) (floor(sqrt(2) 2^20) = 1482910)
   const float2 t = dfx_div(dfx_from_i64(W1 - (1ll << e)), dfx_from_i64(W1 + (1ll << e)));

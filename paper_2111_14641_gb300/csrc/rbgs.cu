@@ -1837,6 +1837,21 @@ rbgs_status rbgs_sparse_sign_columns(uint64_t seed, int64_t k, int64_t j0, int64
   return RBGS_OK;
 }
 
+rbgs_status rbgs_gaussian_entries(uint64_t seed, int64_t k, const int64_t* r, const int64_t* j, int64_t count,
+                                  double* out) {
+  if (k < 1 || count < 0 || (count > 0 && (!r || !j || !out))) return RBGS_EINVAL;
+  for (int64_t t = 0; t < count; ++t)
+    if (r[t] < 0 || r[t] >= k || j[t] < 0) return RBGS_EINVAL;
+  const uint2 key = seed_key(seed);
+  const double scale = 1.0 / std::sqrt((double)k);  // as the sketch kernels scale the entries
+  for (int64_t t = 0; t < count; ++t) {
+    double z0, z1;
+    gauss_pair(key, j[t], (uint32_t)(r[t] >> 1), z0, z1);
+    out[t] = ((r[t] & 1) ? z1 : z0) * scale;
+  }
+  return RBGS_OK;
+}
+
 rbgs_status rbgs_release_workspace(void) {
   int dev = 0;
   RBGS_CUDA_TRY(cudaGetDevice(&dev));

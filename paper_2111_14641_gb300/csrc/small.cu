@@ -242,7 +242,12 @@ __device__ __forceinline__ int tri_col(int e) {
 // diagonal of linear index e.
 __device__ __forceinline__ int diag_start(int d, int n) { return d * n - d * (d - 1) / 2; }
 __device__ __forceinline__ int diag_of(int e, int n) {
-  int d = 0;
+  // the root of diag_start(d, n) = e, d = ((2n + 1) - sqrt((2n + 1)^2 - 8 e)) / 2,
+  // then corrected to the exact diagonal
+  const float b = 2.f * (float)n + 1.f;
+  int d = (int)((b - sqrtf(fmaxf(b * b - 8.f * (float)e, 0.f))) * 0.5f);
+  d = max(0, min(d, n - 1));
+  while (d > 0 && diag_start(d, n) > e) --d;
   while (d + 1 < n && diag_start(d + 1, n) <= e) ++d;
   return d;
 }
@@ -264,7 +269,12 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
   __shared__ T pivot_s[2];                     // 1 / sqrt of the current and the next pivot
   __shared__ T shift_s;
   __shared__ int bad_s;
+  __shared__ uint16_t tri_ab[63 * 64 / 2];     // linear index -> a | b << 8 of a trailing triangle
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // 16 x 16 thread grid
+  for (int e = tid; e < (mb - 1) * mb / 2; e += 256) {
+    const int b = tri_col(e);
+    tri_ab[e] = (uint16_t)((e - b * (b + 1) / 2) | (b << 8));
+  }
   for (int l = ty; l < mb; l += 16)
     for (int i = tx; i < mb; i += 16) {
       A[i][l] = (i <= l) ? G[i + l * mb] : (T)0;
@@ -313,8 +323,8 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
     const int nt = mb - 1 - j;  // trailing order
     const int tot = nt * (nt + 1) / 2;
     for (int e = tid; e < tot; e += 256) {
-      const int b = tri_col(e), a = e - b * (b + 1) / 2;  // a <= b < nt
-      const int i = j + 1 + a, l = j + 1 + b;
+      const int ab = tri_ab[e];  // a <= b < nt
+      const int i = j + 1 + (ab & 255), l = j + 1 + (ab >> 8);
       const T v = A[i][l] - A[j][i] * dinv * A[j][l];
       A[i][l] = v;
       if (e == 0) {  // (j + 1, j + 1): the next pivot is final now
@@ -334,8 +344,18 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int mb, const T* __restri
   for (int j = mb - 1; j >= 0; --j) {
     const T fj = xscale[j];
     const int w = mb - j;
+    const float rj = 1.f / (float)max(j, 1);
     for (int e = tid; e < j * w; e += 256) {
-      const int i = e % j, l = j + e / j;
+      // i = e mod j, l = j + e div j; e < 4096, so the float quotient is within one
+      int q = (int)((float)e * rj), i = e - q * j;
+      if (i < 0) {
+        --q;
+        i += j;
+      } else if (i >= j) {
+        ++q;
+        i -= j;
+      }
+      const int l = j + q;
       X[i][l] -= F[i][j] * fj * X[j][l];
     }
     __syncthreads();

@@ -180,13 +180,15 @@ def load(build_if_missing: bool = False):
                                  ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
     lib.rbgs_release_workspace.argtypes = []
     lib.rbgs_sparse_sign_columns.argtypes = [u64, i64, i64, i64, vp, vp]
+    lib.rbgs_gaussian_entries.argtypes = [u64, i64, vp, vp, i64, vp]
     lib.rbgs_version.restype = ctypes.c_char_p
     lib.rbgs_launch_count.restype = ctypes.c_int64
     for name in ("rbgs_qr", "rbgs_sketch_apply", "rbgs_tall_update", "rbgs_tall_update_noalloc", "rbgs_philox",
                  "rbgs_release_workspace", "rbgs_op_apply", "rbgs_block_arnoldi", "rbgs_block_gmres",
                  "rbgs_block_fom", "rbgs_rayleigh_ritz", "rbgs_qr_batched", "rbgs_qr_host",
                  "rbgs_embedding_check", "rbgs_cholqr_postprocess", "rbgs_qr_graph_create",
-                 "rbgs_qr_graph_launch", "rbgs_qr_graph_destroy", "rbgs_sparse_sign_columns"):
+                 "rbgs_qr_graph_launch", "rbgs_qr_graph_destroy", "rbgs_sparse_sign_columns",
+                 "rbgs_gaussian_entries"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -637,6 +639,23 @@ def sparse_sign_columns(seed: int, k: int, j0: int, count: int):
     _check(lib.rbgs_sparse_sign_columns(int(seed), int(k), int(j0), int(count), rows.ctypes.data, neg.ctypes.data),
            "rbgs_sparse_sign_columns")
     return rows, neg
+
+
+def gaussian_entries(seed: int, k: int, r, j):
+    """Entries Theta(r[t], j[t]) of the Gaussian Theta (k rows) as a float64
+    numpy array, from the generator the sketch kernels evaluate, run on the
+    host."""
+    import numpy as np
+
+    lib = load()
+    r = np.ascontiguousarray(r, dtype=np.int64)
+    j = np.ascontiguousarray(j, dtype=np.int64)
+    if r.shape != j.shape:
+        raise ValueError("r and j must have the same shape")
+    out = np.zeros(r.shape, dtype=np.float64)
+    _check(lib.rbgs_gaussian_entries(int(seed), int(k), r.ctypes.data, j.ctypes.data, int(r.size), out.ctypes.data),
+           "rbgs_gaussian_entries")
+    return out
 
 
 def philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
